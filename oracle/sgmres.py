@@ -1,0 +1,174 @@
+"""RHOSVD-Tucker sGMRES (Algorithm 2), MLN-Tucker sGMRES (Algorithm 6), dense sGMRES (Eq. (2.8)).
+
+Test infrastructure only.  Readings of points the paper leaves open:
+  * x_0 = 0, so V_1 = B / ||B||;
+  * breakdown "||W|| ~ 0" means ||W|| <= 1e-14 ||W_0||, W_0 the compressed L(V_k) before
+    the short-recurrence orthogonalization; on breakdown the least-squares problem is still
+    solved with the k columns gathered so far and the solve ends successfully;
+  * the window orthogonalization is classical Gram-Schmidt: every h_j uses the same W;
+  * the sketched least-squares problem is degenerate once k reaches the sketch size s, so
+    at most s - 1 iterations run (status SKETCH_EXHAUSTED if that limit, not N_max, ends it);
+  * RoundSum draws fresh Gaussian matrices on every call, from stream
+    (seed, STREAM_ROUNDSUM, call, mode); the Krylov sketch S_k (or Psi_k) from
+    (seed, STREAM_KRYLOV, 0, mode);
+  * Algorithm 6: Psi_k has r + p columns (Section 3.3); b_s = ||B|| diag(G_Psi(V_1)) so that
+    b_s = S^T vec(B) as in Algorithm 2; after the window's MLN_Sum the sum is recovered
+    (MLN_Recovery) before its norm is taken and V_{i+1} is formed.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+from workloads import (STREAM_KRYLOV, STREAM_ROUNDSUM, Operator, SolverParams, Tucker,
+                       sketch_matrix)
+from .mln import mln_diag, mln_recovery, mln_sketch, mln_sum
+from .operators import apply_op
+from .rhosvd import effective_sketch_size, kron_sketch, roundsum
+from .tensor import inner, norm, scale
+
+CONVERGED, NOT_CONVERGED, BREAKDOWN, SKETCH_EXHAUSTED = 0, 1, 2, 3
+
+
+@dataclass
+class Result:
+    x: Tucker
+    iters: int
+    status: int
+    res_hist: List[float]
+    y: np.ndarray
+    ranks: List[List[int]] = field(default_factory=list)
+    sketch_sizes: List[int] = field(default_factory=list)
+    basis: List[Tucker] = field(default_factory=list)
+
+
+def _ls(mcols: List[np.ndarray], bs: np.ndarray):
+    """y = argmin ||M y - b_s||_2 and ||M y - b_s||_2 (Algorithm 2, sketched residual)."""
+    m = np.stack(mcols, axis=1)
+    y = np.linalg.lstsq(m, bs, rcond=None)[0]
+    return y, float(np.linalg.norm(m @ y - bs))
+
+
+def rhosvd_sgmres(op: Operator, b: Tucker, prm: SolverParams, transpose: bool = False,
+                  bf16_sketch: bool = False, maxit: Optional[int] = None) -> Result:
+    """Algorithm 2.  bf16_sketch rounds RoundSum's Gaussian matrices to bfloat16 values (the
+    mixed-precision form stores them so); the arithmetic stays FP64."""
+    d, n = b.d, b.n
+    s = prm.sketch_s
+    maxit = prm.maxit if maxit is None else maxit
+    call = [0]
+
+    def draw(sr: int):
+        mats = [sketch_matrix(prm.seed, STREAM_ROUNDSUM, call[0], k, n[k], sr, bf16_sketch)
+                for k in range(d)]
+        call[0] += 1
+        return mats
+
+    def rs(terms):
+        sr = (effective_sketch_size(terms, prm.oversample_p, prm.rank_cap, prm.round_tol)
+              if prm.adaptive_rank else prm.rank_cap + prm.oversample_p)
+        out = roundsum(terms, draw(sr), prm.rank_cap, prm.round_tol)
+        sizes.append(sr)
+        return out
+
+    sizes: List[int] = []
+    beta = norm(b)
+    v = [scale(b, 1.0 / beta)]
+    sk = [sketch_matrix(prm.seed, STREAM_KRYLOV, 0, k, n[k], s) for k in range(d)]
+    bs = kron_sketch(b, sk)
+    beta_s = float(np.linalg.norm(bs))
+    mcols: List[np.ndarray] = []
+    hist: List[float] = []
+    ranks: List[List[int]] = []
+    kmax = min(maxit, s - 1)
+    status = SKETCH_EXHAUSTED if kmax < maxit else NOT_CONVERGED
+    y = np.zeros(0)
+    k = 0
+    for k in range(1, kmax + 1):
+        w = rs([(1.0, t) for t in apply_op(op, v[-1], transpose)])
+        w0 = norm(w)
+        mcols.append(kron_sketch(w, sk))
+        window = range(max(1, k - prm.ktrunc + 1), k + 1)
+        hs = [inner(v[j - 1], w) for j in window]
+        w = rs([(1.0, w)] + [(-h, v[j - 1]) for h, j in zip(hs, window)])
+        nw = norm(w)
+        y, res = _ls(mcols, bs)
+        hist.append(res / beta_s)
+        if nw <= 1e-14 * w0:
+            status = BREAKDOWN
+            break
+        v.append(scale(w, 1.0 / nw))
+        ranks.append(v[-1].r)
+        if res / beta_s < prm.eta * prm.tol:
+            status = CONVERGED
+            break
+    x = rs([(float(y[i]), v[i]) for i in range(k)])
+    return Result(x, k, status, hist, y, ranks, sizes, v)
+
+
+def mln_sgmres(op: Operator, b: Tucker, prm: SolverParams, transpose: bool = False,
+               maxit: Optional[int] = None) -> Result:
+    """Algorithm 6 (without the memory-saving truncation), r = rank_cap, r + p sketch columns."""
+    d, n = b.d, b.n
+    r = prm.rank_cap
+    rp = r + prm.oversample_p
+    maxit = prm.maxit if maxit is None else maxit
+    psis = [sketch_matrix(prm.seed, STREAM_KRYLOV, 0, k, n[k], rp) for k in range(d)]
+    beta = norm(b)
+    v = [scale(b, 1.0 / beta)]
+    sks = [mln_sketch(v[0], psis, r)]
+    bs = beta * mln_diag(sks[0][0])
+    beta_s = float(np.linalg.norm(bs))
+    mcols: List[np.ndarray] = []
+    hist: List[float] = []
+    kmax = min(maxit, rp - 1)
+    status = SKETCH_EXHAUSTED if kmax < maxit else NOT_CONVERGED
+    y = np.zeros(0)
+    i = 0
+    for i in range(1, kmax + 1):
+        gw = mln_sum([(1.0, mln_sketch(t, psis, r)) for t in apply_op(op, v[-1], transpose)])
+        mcols.append(mln_diag(gw[0]))
+        w = mln_recovery(gw, psis)
+        w0 = norm(w)
+        window = range(max(1, i - prm.ktrunc + 1), i + 1)
+        hs = [inner(v[j - 1], w) for j in window]
+        gw = mln_sum([(1.0, gw)] + [(-h, sks[j - 1]) for h, j in zip(hs, window)])
+        w = mln_recovery(gw, psis)
+        nw = norm(w)
+        y, res = _ls(mcols, bs)
+        hist.append(res / beta_s)
+        if nw <= 1e-14 * w0:
+            status = BREAKDOWN
+            break
+        v.append(scale(w, 1.0 / nw))
+        sks.append(mln_sketch(v[-1], psis, r))
+        if res / beta_s < prm.eta * prm.tol:
+            status = CONVERGED
+            break
+    x = mln_recovery(mln_sum([(float(y[m]), sks[m]) for m in range(i)]), psis)
+    return Result(x, i, status, hist, y, basis=v)
+
+
+def dense_sgmres(a: np.ndarray, b: np.ndarray, s_mat: np.ndarray, ktrunc: int, iters: int):
+    """Matrix sGMRES (Eq. (2.8)) with the same window orthogonalization, no truncation:
+    v_1 = b/||b||, w = A v_k, M[:, k] = S w, w -= sum_{window} (v_j^T w) v_j, v_{k+1} = w/||w||,
+    y = argmin ||M y - S b||.  Returns x = V y and the sketched residual history."""
+    beta = np.linalg.norm(b)
+    v = [b / beta]
+    bs = s_mat @ b
+    mcols, hist = [], []
+    y = np.zeros(0)
+    for k in range(1, iters + 1):
+        w = a @ v[-1]
+        mcols.append(s_mat @ w)
+        window = range(max(1, k - ktrunc + 1), k + 1)
+        hs = [v[j - 1] @ w for j in window]
+        for h, j in zip(hs, window):
+            w = w - h * v[j - 1]
+        y, res = _ls(mcols, bs)
+        hist.append(res / np.linalg.norm(bs))
+        v.append(w / np.linalg.norm(w))
+    x = sum(y[i] * v[i] for i in range(len(y)))
+    return x, hist

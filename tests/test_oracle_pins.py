@@ -1,0 +1,414 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself:
+published known-answer vectors, closed forms, brute force on small dense problems,
+exact identities stated in the paper and invariants.  CPU only."""
+import os
+from functools import reduce
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import adjoint as A
+from oracle import mln as M
+from oracle import operators as O
+from oracle import residual as RS
+from oracle import rhosvd as R
+from oracle import sgmres as S
+from oracle import tensor as T
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rng(seed=0):
+    return np.random.default_rng(seed)
+
+
+def _rand_tucker(n, r, seed):
+    g = _rng(seed)
+    return W.Tucker(g.standard_normal(tuple(r)), [g.standard_normal((a, b)) for a, b in zip(n, r)])
+
+
+def _vec(x):
+    return x.reshape(-1, order='F')
+
+
+def _dst_basis(n):
+    """Sine eigenvectors of tridiag(-1, 2, -1): V_ij = sqrt(2/(n+1)) sin(i j pi/(n+1)) (Section 3.4)."""
+    i = np.arange(1, n + 1)
+    v = np.sqrt(2.0 / (n + 1)) * np.sin(np.outer(i, i) * np.pi / (n + 1))
+    lam = 2.0 - 2.0 * np.cos(i * np.pi / (n + 1))
+    return v, lam
+
+
+# ------------------------------------------------------------------------------ RNG
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox_kat.txt")) if l.strip() and l[0] != '#']
+    for row in rows:
+        w = [int(x, 16) for x in row]
+        out = W.philox4x32_10([np.array([c]) for c in w[:4]], (w[4], w[5]))
+        assert [int(o[0]) for o in out] == w[6:10]
+
+
+def test_gaussian_stream_distribution():
+    from scipy import stats
+    z = W.gaussian_stream(11, W.stream_id(2, 3, 1), 200001)
+    assert abs(z.mean()) < 0.01 and abs(z.var() - 1.0) < 0.01
+    assert stats.kstest(z, 'norm').pvalue > 1e-3
+    z2 = W.gaussian_stream(11, W.stream_id(2, 3, 2), 200001)
+    assert abs(np.corrcoef(z, z2)[0, 1]) < 0.01
+    # prefix property: element e does not depend on the requested count
+    assert np.array_equal(W.gaussian_stream(11, 5, 7), W.gaussian_stream(11, 5, 1001)[:7])
+
+
+def test_bf16_rounding_against_torch():
+    import torch
+    x = _rng(1).standard_normal(50000).astype(np.float32).astype(np.float64)
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(W.round_to_bf16(x), ref)
+    # ties go to even: 1 + 2^-8 is halfway between 1 and 1 + 2^-7
+    assert W.round_to_bf16(np.array([1 + 2.0 ** -8]))[0] == 1.0
+    assert W.round_to_bf16(np.array([1 + 3 * 2.0 ** -8]))[0] == 1 + 2.0 ** -6
+
+
+# ------------------------------------------------------------------------------ tensor algebra
+def test_unfold_ttm_mttkrp_brute_force():
+    g = _rng(2)
+    x = g.standard_normal((3, 4, 5))
+    # unfold: X_(2)[i2, i1 + 3*i3] = X[i1, i2, i3]
+    u2 = T.unfold(x, 1)
+    for i1 in range(3):
+        for i2 in range(4):
+            for i3 in range(5):
+                assert u2[i2, i1 + 3 * i3] == x[i1, i2, i3]
+    assert np.array_equal(T.fold(u2, 1, x.shape), x)
+    u = g.standard_normal((6, 4))
+    y = T.ttm(x, u, 1)
+    assert np.allclose(y, np.einsum('ajc,bj->abc', x, u))
+    us = [g.standard_normal((3, 7)), g.standard_normal((4, 7)), g.standard_normal((5, 7))]
+    for k in range(3):
+        m = T.mttkrp(x, us, k)
+        ref = np.zeros((x.shape[k], 7))
+        for idx in np.ndindex(*x.shape):
+            for r in range(7):
+                ref[idx[k], r] += x[idx] * np.prod([us[j][idx[j], r] for j in range(3) if j != k])
+        assert np.allclose(m, ref, rtol=1e-13, atol=1e-13)
+    kr = T.khatri_rao([us[0], us[1]])
+    for r in range(7):
+        assert np.allclose(kr[:, r], np.kron(us[0][:, r], us[1][:, r]))
+
+
+def test_tucker_full_inner_norm():
+    x = _rand_tucker([5, 4, 6], [2, 3, 2], 3)
+    y = _rand_tucker([5, 4, 6], [3, 1, 2], 4)
+    fx = T.full(x)
+    vec_ref = reduce(np.kron, [u for u in x.factors][::-1]) @ _vec(x.core)
+    assert np.allclose(_vec(fx), vec_ref)
+    assert np.isclose(T.inner(x, y), np.sum(fx * T.full(y)), rtol=1e-13)
+    assert np.isclose(T.norm(x), np.linalg.norm(fx), rtol=1e-13)
+    q = [np.linalg.qr(u)[0] for u in x.factors]
+    xo = W.Tucker(x.core, q)
+    assert np.isclose(T.norm(xo), np.linalg.norm(x.core), rtol=1e-13)
+    cs = T.concat_sum([(2.0, x), (-0.5, y)])
+    assert np.allclose(T.full(cs), 2.0 * fx - 0.5 * T.full(y))
+
+
+def test_storage_formula_golden():
+    row = [l.split() for l in open(os.path.join(GOLDEN, "storage_deblur.txt")) if l[0] != '#'][0]
+    n, r, dense, tucker = [int(v) for v in row[:3]], [int(v) for v in row[3:6]], int(row[6]), int(row[7])
+    assert int(np.prod(n)) == dense
+    assert T.storage(n, r) == tucker
+
+
+# ------------------------------------------------------------------------------ operators
+def test_band_layout_and_operator_bruteforce():
+    n = 6
+    t = O.mode_dense(W.second_difference(n))
+    assert np.array_equal(t, 2 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1))
+    b = O.mode_dense(W.upwind_backward(n, 3.0))
+    assert np.array_equal(b, 3.0 * (np.eye(n) - np.eye(n, k=-1)))
+    assert np.allclose(O.mode_dense(W.gaussian_blur_band(n + 9)), W.gaussian_blur_dense(n + 9))
+    for wl in [W.convdiff3d(n, 0, None), W.varcoef4d(n, 0, None), W.deblur3d(n, 0, None)]:
+        op = wl.op
+        x = _rand_tucker([n] * op.d, [2] * op.d, 5)
+        lhs = sum(T.full(t) for t in O.apply_op(op, x))
+        rhs = (O.dense_matrix(op) @ _vec(T.full(x))).reshape([n] * op.d, order='F')
+        assert np.allclose(lhs, rhs, rtol=1e-13, atol=1e-12 * np.abs(rhs).max())
+        lhs_t = sum(T.full(t) for t in O.apply_op(op, x, transpose=True))
+        rhs_t = (O.dense_matrix(op).T @ _vec(T.full(x))).reshape([n] * op.d, order='F')
+        assert np.allclose(lhs_t, rhs_t, rtol=1e-13, atol=1e-12 * np.abs(rhs_t).max())
+
+
+def test_poisson_sine_eigentensors():
+    n = 9
+    v, lam = _dst_basis(n)
+    assert np.allclose(O.mode_dense(W.second_difference(n)) @ v, v * lam)
+    op = W.kronecker_sum_operator([W.second_difference(n)], 3)
+    for (i, j, k) in [(0, 0, 0), (2, 5, 8), (4, 1, 3)]:
+        e = W.Tucker(np.ones((1, 1, 1)), [v[:, [i]], v[:, [j]], v[:, [k]]])
+        lx = sum(T.full(t) for t in O.apply_op(op, e))
+        assert np.allclose(lx, (lam[i] + lam[j] + lam[k]) * T.full(e), atol=1e-13)
+
+
+# ------------------------------------------------------------------------------ RoundSum
+def test_st_hosvd_exact_rank_and_bound():
+    g = _rng(6)
+    c = T.multi_ttm(g.standard_normal((2, 3, 2)), [g.standard_normal((7, 2)), g.standard_normal((8, 3)),
+                                                      g.standard_normal((6, 2))])
+    core, ws = R.st_hosvd(c, 1e-13, 10)
+    assert core.shape == (2, 3, 2)
+    assert np.allclose(T.multi_ttm(core, ws), c, atol=1e-12)
+    c2 = g.standard_normal((8, 7, 6))
+    for eps in [0.3, 0.1]:
+        core, ws = R.st_hosvd(c2, eps, 100)
+        err = np.linalg.norm(T.multi_ttm(core, ws) - c2)
+        assert err <= eps * np.linalg.norm(c2) * (1 + 1e-12)
+    core, ws = R.st_hosvd(c2, 0.0, 3)
+    assert core.shape == (3, 3, 3)
+
+
+def test_roundsum_exact_on_low_rank_sums():
+    n = [9, 8, 10]
+    x1 = _rand_tucker(n, [2, 2, 1], 7)
+    x2 = _rand_tucker(n, [1, 2, 2], 8)
+    g = _rng(9)
+    sk = [g.standard_normal((nk, 4 + 5)) for nk in n]
+    out = R.roundsum([(1.5, x1), (-2.0, x2)], sk, 4, 1e-14)
+    ref = 1.5 * T.full(x1) - 2.0 * T.full(x2)
+    assert np.linalg.norm(T.full(out) - ref) <= 1e-13 * np.linalg.norm(ref)
+    # output factors orthonormal, so ||out|| = ||core||
+    for u in out.factors:
+        assert np.allclose(u.T @ u, np.eye(u.shape[1]), atol=1e-13)
+    # idempotent on its own output
+    again = R.roundsum([(1.0, out)], [g.standard_normal((nk, 9)) for nk in n], 4, 1e-14)
+    assert np.linalg.norm(T.full(again) - T.full(out)) <= 1e-13 * np.linalg.norm(ref)
+    # X + (-1) X = 0
+    zero = R.roundsum([(1.0, x1), (-1.0, x1)], sk, 4, 1e-14)
+    assert T.norm(zero) <= 1e-13 * T.norm(x1)
+
+
+def test_roundsum_randomized_bound_vs_hosvd():
+    """Truncating a full-rank sum: the randomized result is within a modest factor of the
+    deterministic truncated HOSVD of the dense sum (Halko-Martinsson-Tropp range finder)."""
+    n, r, p = [12, 12, 12], 4, 5
+    g = _rng(10)
+    terms = []
+    for i in range(3):
+        t = _rand_tucker(n, [4, 4, 4], 20 + i)
+        t.core *= 0.5 ** i
+        terms.append((1.0, t))
+    dense = sum(T.full(t) for _, t in terms)
+    core, ws = R.st_hosvd(dense, 0.0, r)
+    best = np.linalg.norm(T.multi_ttm(core, ws) - dense)
+    errs = []
+    for trial in range(5):
+        sk = [g.standard_normal((12, r + p)) for _ in range(3)]
+        out = R.roundsum(terms, sk, r, 0.0)
+        errs.append(np.linalg.norm(T.full(out) - dense))
+    assert np.median(errs) <= 3.0 * best
+
+
+def test_kron_sketch_explicit():
+    n = [4, 5, 3]
+    x = _rand_tucker(n, [2, 3, 2], 11)
+    g = _rng(12)
+    sk = [g.standard_normal((nk, 7)) for nk in n]
+    explicit = T.khatri_rao([sk[2], sk[1], sk[0]])        # (S_3 (.) S_2 (.) S_1)
+    assert np.allclose(R.kron_sketch(x, sk), explicit.T @ _vec(T.full(x)), rtol=1e-13)
+    y = _rand_tucker(n, [1, 2, 2], 13)
+    lin = R.kron_sketch(T.concat_sum([(2.0, x), (-3.0, y)]), sk)
+    assert np.allclose(lin, 2 * R.kron_sketch(x, sk) - 3 * R.kron_sketch(y, sk))
+
+
+def test_effective_sketch_size():
+    n = [10, 10, 10]
+    x = _rand_tucker(n, [3, 2, 4], 14)
+    assert R.effective_sketch_size([(1.0, x)], 5, 50, 1e-10) == 4 + 5
+    assert R.effective_sketch_size([(1.0, x)], 5, 3, 1e-10) == 3 + 5
+
+
+# ------------------------------------------------------------------------------ MLN
+def test_mln_diag_is_khatri_rao_sketch():
+    n, r, p = [5, 4, 6], 2, 3
+    x = _rand_tucker(n, [2, 3, 2], 15)
+    g = _rng(16)
+    psis = [g.standard_normal((nk, r + p)) for nk in n]
+    gp, _ = M.mln_sketch(x, psis, r)
+    explicit = T.khatri_rao([psis[2], psis[1], psis[0]])
+    assert np.allclose(M.mln_diag(gp), explicit.T @ _vec(T.full(x)), rtol=1e-12)
+    assert np.allclose(gp, T.multi_ttm(T.full(x), [p.T for p in psis]))
+
+
+def test_mln_sketch_factor_is_unfolding_times_omega():
+    n, r, p = [5, 4, 6], 2, 3
+    x = _rand_tucker(n, [2, 3, 2], 17)
+    g = _rng(18)
+    psis = [g.standard_normal((nk, r + p)) for nk in n]
+    _, f = M.mln_sketch(x, psis, r)
+    bars = [ps[:, :r] for ps in psis]
+    for k in range(3):
+        omega = T.khatri_rao([bars[j] for j in reversed(range(3)) if j != k])   # Eq. (3.3)
+        assert np.allclose(f[k], T.unfold(T.full(x), k) @ omega, rtol=1e-12)
+
+
+def test_mln_recovery_exact_for_low_rank():
+    n, r, p = [8, 7, 9], 3, 3
+    x = _rand_tucker(n, [3, 2, 3], 19)
+    g = _rng(20)
+    psis = [g.standard_normal((nk, r + p)) for nk in n]
+    out = M.mln_recovery(M.mln_sketch(x, psis, r), psis)
+    assert np.linalg.norm(T.full(out) - T.full(x)) <= 1e-11 * np.linalg.norm(T.full(x))
+    # Algorithm 4 is linear
+    y = _rand_tucker(n, [1, 2, 1], 21)
+    s = M.mln_sum([(2.0, M.mln_sketch(x, psis, r)), (-1.0, M.mln_sketch(y, psis, r))])
+    ref = M.mln_sketch(T.concat_sum([(2.0, x), (-1.0, y)]), psis, r)
+    assert np.allclose(s[0], ref[0]) and all(np.allclose(a, b) for a, b in zip(s[1], ref[1]))
+
+
+def test_pinv_identity():
+    g = _rng(22)
+    a = g.standard_normal((9, 4))
+    q, rr = np.linalg.qr(a)
+    assert np.allclose(M.pinv_upper(rr) @ q.T, np.linalg.pinv(a))
+    a1 = np.outer(g.standard_normal(9), g.standard_normal(4))     # rank one
+    q, rr = np.linalg.qr(a1)
+    assert np.allclose(M.pinv_upper(rr) @ q.T, np.linalg.pinv(a1), atol=1e-12)
+
+
+# ------------------------------------------------------------------------------ solvers
+def test_dense_sgmres_full_window_is_gmres():
+    g = _rng(23)
+    nn = 30
+    a = np.eye(nn) * 3 + g.standard_normal((nn, nn)) * 0.3
+    b = g.standard_normal(nn)
+    k = 6
+    x, _ = S.dense_sgmres(a, b, np.eye(nn), ktrunc=k, iters=k)
+    kry = np.stack([np.linalg.matrix_power(a, j) @ b for j in range(k)], axis=1)
+    c = np.linalg.lstsq(a @ kry, b, rcond=None)[0]
+    assert np.allclose(x, kry @ c, rtol=1e-9)
+
+
+@pytest.mark.parametrize("variant", ["rhosvd", "mln"])
+def test_untruncated_tucker_sgmres_equals_dense(variant):
+    n = 6
+    wl = W.convdiff3d(n, 1, None)
+    b = W.random_tucker([n] * 3, [1, 2, 1], 24)
+    if variant == "rhosvd":
+        prm = W.SolverParams('rhosvd', n, 40, 5, 14, 1e-15, ktrunc=2, round_tol=1e-15, seed=3)
+        res = S.rhosvd_sgmres(wl.op, b, prm)
+        sk = [W.sketch_matrix(3, W.STREAM_KRYLOV, 0, k, n, 40) for k in range(3)]
+    else:
+        prm = W.SolverParams('mln', n, 0, 20, 14, 1e-15, ktrunc=2, round_tol=1e-15, seed=3)
+        res = S.mln_sgmres(wl.op, b, prm)
+        sk = [W.sketch_matrix(3, W.STREAM_KRYLOV, 0, k, n, n + 20) for k in range(3)]
+    smat = T.khatri_rao([sk[2], sk[1], sk[0]]).T
+    xd, hd = S.dense_sgmres(O.dense_matrix(wl.op), _vec(T.full(b)), smat, 2, res.iters)
+    assert np.allclose(res.res_hist, hd, rtol=1e-9)
+    assert np.linalg.norm(_vec(T.full(res.x)) - xd) <= 1e-10 * np.linalg.norm(xd)
+
+
+def test_poisson_solution_against_sine_closed_form():
+    n = 12
+    v, lam = _dst_basis(n)
+    op = W.kronecker_sum_operator([W.second_difference(n)], 3)
+    b = W.random_tucker([n] * 3, [1, 1, 1], 25)
+    prm = W.SolverParams('rhosvd', 12, 64, 5, 60, 1e-9, ktrunc=2, round_tol=1e-13)
+    res = S.rhosvd_sgmres(op, b, prm)
+    bh = T.multi_ttm(T.full(b), [v.T] * 3)
+    xs = T.multi_ttm(bh / (lam[:, None, None] + lam[None, :, None] + lam[None, None, :]), [v] * 3)
+    tr = RS.true_residual(op, res.x, b)
+    assert np.isclose(tr, RS.dense_residual(op, res.x, b), rtol=1e-6, atol=1e-14)
+    kappa = (3 * lam.max()) / (3 * lam.min())
+    err = np.linalg.norm(T.full(res.x) - xs) / np.linalg.norm(xs)
+    assert err <= kappa * tr * 1.0001
+    assert tr < 1e-7
+
+
+def test_breakdown_on_eigentensor_rhs():
+    n = 8
+    v, lam = _dst_basis(n)
+    op = W.kronecker_sum_operator([W.second_difference(n)], 3)
+    b = W.Tucker(np.full((1, 1, 1), 2.0), [v[:, [1]], v[:, [2]], v[:, [0]]])
+    prm = W.SolverParams('rhosvd', 4, 16, 5, 10, 1e-12)
+    res = S.rhosvd_sgmres(op, b, prm)
+    assert res.status == S.BREAKDOWN and res.iters == 1
+    assert np.allclose(T.full(res.x), T.full(b) / (lam[1] + lam[2] + lam[0]), atol=1e-13)
+
+
+def test_sketched_residual_monotone_and_exhaustion():
+    wl = W.convdiff3d(8, 2, None)
+    prm = W.SolverParams('rhosvd', 4, 10, 5, 40, 1e-14)
+    res = S.rhosvd_sgmres(wl.op, wl.b, prm)
+    h = np.array(res.res_hist)
+    assert np.all(h[1:] <= h[:-1] * (1 + 1e-12))
+    assert res.status == S.SKETCH_EXHAUSTED and res.iters == 9
+
+
+def test_symmetric_window_two_is_lanczos():
+    """Symmetric operator, k_trunc = 2, no truncation: the three-term recurrence keeps the
+    whole basis orthonormal in exact arithmetic (Lanczos)."""
+    n = 6
+    op = W.kronecker_sum_operator([W.second_difference(n)], 3)
+    b = W.random_tucker([n] * 3, [2, 2, 2], 26)
+    prm = W.SolverParams('rhosvd', n, 60, 5, 8, 1e-15, ktrunc=2, round_tol=1e-15)
+    res = S.rhosvd_sgmres(op, b, prm)
+    vs = res.basis[:8]
+    gram = np.array([[T.inner(a, c) for c in vs] for a in vs])
+    assert np.allclose(gram, np.eye(len(vs)), atol=1e-9)
+
+
+def test_true_residual_tucker_form_keeps_relative_accuracy():
+    n = 8
+    v, lam = _dst_basis(n)
+    op = W.kronecker_sum_operator([W.second_difference(n)], 3)
+    b = W.random_tucker([n] * 3, [2, 2, 2], 27)
+    bh = T.multi_ttm(b.core, [v.T @ u for u in b.factors])
+    x = W.Tucker(bh / (lam[:, None, None] + lam[None, :, None] + lam[None, None, :]), [v] * 3)
+    tr = RS.true_residual(op, x, b)
+    assert tr < 1e-14
+    x.core[0, 0, 0] += 1e-6
+    ref = RS.dense_residual(op, x, b)
+    assert np.isclose(RS.true_residual(op, x, b), ref, rtol=1e-8)
+
+
+# ------------------------------------------------------------------------------ adjoint
+def test_dense_gradients_against_finite_differences():
+    n = 4
+    wl = W.deblur3d(n, 3, None, lam=0.3)
+    xt = T.full(W.random_tucker([n] * 3, [2, 2, 2], 28))
+    x, mu, dth = A.dense_gradients(wl.op, wl.b, xt)
+
+    def loss(op):
+        a = O.dense_matrix(op)
+        xx = np.linalg.solve(a, _vec(T.full(wl.b)))
+        return 0.5 * np.sum((xx - _vec(xt)) ** 2)
+
+    for t in range(wl.op.nterms):
+        h = 1e-6
+        op_p = W.Operator(3, wl.op.n, list(wl.op.theta), wl.op.mats)
+        op_m = W.Operator(3, wl.op.n, list(wl.op.theta), wl.op.mats)
+        op_p.theta[t] += h
+        op_m.theta[t] -= h
+        fd = (loss(op_p) - loss(op_m)) / (2 * h)
+        assert np.isclose(dth[t], fd, rtol=1e-6)
+
+
+def test_tucker_adjoint_gradients_match_dense():
+    n = 5
+    wl = W.deblur3d(n, 4, None, lam=0.5)
+    xt = W.random_tucker([n] * 3, [2, 2, 2], 29)
+    prm = W.SolverParams('rhosvd', n, 100, 5, 60, 1e-13, ktrunc=3, round_tol=1e-15)
+    fwd = S.rhosvd_sgmres(wl.op, wl.b, prm)
+    g = T.concat_sum([(1.0, fwd.x), (-1.0, xt)])
+    adj = S.rhosvd_sgmres(wl.op, g, prm, transpose=True)
+    dth = A.theta_gradients(wl.op, fwd.x, adj.x)
+    _, mu_d, dth_d = A.dense_gradients(wl.op, wl.b, T.full(xt))
+    assert np.allclose(dth, dth_d, rtol=1e-7)
+    assert np.allclose(T.full(adj.x), mu_d, atol=1e-9 * np.abs(mu_d).max())
+    # b = [G_b; U_b]: chain rule through the Tucker parameters against the dense mu
+    gcore = A.core_gradient(adj.x, wl.b)
+    assert np.allclose(gcore, T.multi_ttm(mu_d, [u.T for u in wl.b.factors]), atol=1e-9)
+    gf = A.factor_gradients(adj.x, wl.b)
+    for k in range(3):
+        ref = T.unfold(mu_d, k) @ reduce(np.kron, [wl.b.factors[j] for j in reversed(range(3)) if j != k]) \
+            @ T.unfold(wl.b.core, k).T
+        assert np.allclose(gf[k], ref, atol=1e-9 * np.abs(ref).max())
