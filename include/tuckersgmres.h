@@ -1,0 +1,188 @@
+/*
+ * tuckersgmres.h - C ABI of the B300 (sm_103a) Tucker-format sketched GMRES library.
+ *
+ * Solves L(X) = B (Section 1, Eq. (1.1)-(1.2)) with B and X Tucker tensors
+ * (Section 2.3, Eq. (2.3)) and L = sum_t theta_t A_1^(t) x ... x A_d^(t) given as a list of
+ * per-mode matrix tuples, by RHOSVD-Tucker sGMRES (Algorithm 2) or MLN-Tucker sGMRES
+ * (Algorithm 6).  Every step runs in the library's own CUDA kernels on one GPU.
+ *
+ * Conventions (all entry points):
+ *   - Tensors are column-major: a core G in R^{r_1 x ... x r_d} stores G[i_1,..,i_d] at
+ *     i_1 + r_1 (i_2 + r_2 (...)); a factor U_k in R^{n_k x r_k} stores U[i,j] at i + n_k j.
+ *     The operator is applied in mode-product form L(X) = sum_t theta_t X x_1 A_1^(t) .. x_d A_d^(t),
+ *     i.e. vec(L(X)) = sum_t theta_t (A_d^(t) kron ... kron A_1^(t)) vec(X), vec column-major.
+ *   - "device" pointers are CUDA device memory of the handle's device; "host" pointers are
+ *     ordinary host memory.  Inputs are borrowed: the caller keeps them alive and unchanged
+ *     until the work on `stream` has completed.  Outputs are caller-allocated.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Entry points that return a
+ *     value through a host pointer synchronize that stream; the others only enqueue work.
+ *   - Every entry point returns a tk_status; 0 is success.  Negative values are errors; the
+ *     handle's message is then available from tk_last_error().  Errors leave outputs undefined.
+ *   - A handle may be used by one host thread at a time.
+ */
+#ifndef TUCKERSGMRES_H
+#define TUCKERSGMRES_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TK_MAX_D 8
+
+typedef enum {
+    TK_OK = 0,                  /* converged: sketched residual < eta * tol                  */
+    TK_NOT_CONVERGED = 1,       /* maxit iterations ran; x is the last iterate                */
+    TK_BREAKDOWN = 2,           /* ||W|| ~ 0: the Krylov space is invariant; x is final       */
+    TK_SKETCH_EXHAUSTED = 3,    /* the iteration count reached sketch size - 1                */
+    TK_EINVAL = -1,             /* invalid argument (shape, kind, null pointer, size limit)   */
+    TK_ENOMEM = -2,             /* device allocation failed                                   */
+    TK_ECUDA = -3,              /* a CUDA runtime call or kernel launch failed                 */
+    TK_EINTERNAL = -4           /* a device-side check failed (non-finite value, bad state)   */
+} tk_status;
+
+/* Tucker tensor (Section 2.3): core (device, column-major r_1 x..x r_d) and factors
+ * (device, column-major n_k x r_k with leading dimension n_k). */
+typedef struct {
+    int32_t d;
+    int64_t n[TK_MAX_D];
+    int64_t r[TK_MAX_D];
+    double *core;
+    double *factor[TK_MAX_D];
+} tk_tucker;
+
+/* One mode matrix A in R^{n x n} (Eq. (1.2)).
+ *   TK_IDENTITY: data unused.
+ *   TK_BANDED:   kl sub- and ku super-diagonals in LAPACK band layout, device memory,
+ *                data[(ku + i - j) + (kl + ku + 1) j] = A[i, j]; covers diagonal, bidiagonal,
+ *                tridiagonal and banded Toeplitz blur matrices.
+ *   TK_DENSE:    device, column-major n x n. */
+typedef enum { TK_IDENTITY = 0, TK_BANDED = 1, TK_DENSE = 2 } tk_kind;
+
+typedef struct {
+    int32_t kind;
+    int32_t kl, ku;
+    int64_t n;
+    const double *data;
+} tk_modemat;
+
+/* L = sum_t theta[t] * A_1^(t) x ... x A_d^(t) (Eq. (1.2)); theta is host memory,
+ * mats is a host array of nterms*d mode matrices, mats[t*d + k] = A_{k+1}^(t). */
+typedef struct {
+    int32_t nterms;
+    int32_t d;
+    const double *theta;
+    const tk_modemat *mats;
+} tk_operator;
+
+enum { TK_RHOSVD_SGMRES = 0, TK_MLN_SGMRES = 1 };
+enum { TK_FP64 = 0, TK_MIXED = 1 };
+
+/* Solver options (Algorithm 2 inputs; Algorithm 6 inputs). */
+typedef struct {
+    int32_t variant;        /* TK_RHOSVD_SGMRES or TK_MLN_SGMRES                                  */
+    int32_t rank_cap;       /* RHOSVD: multilinear rank cap; MLN: Nystrom target rank r           */
+    int32_t sketch_s;       /* RHOSVD: Krylov sketch size s (MLN uses r + p)                      */
+    int32_t oversample_p;   /* RHOSVD: RoundSum oversampling (paper: 5); MLN: Nystrom p            */
+    int32_t ktrunc;         /* short-recurrence window k_trunc >= 1                               */
+    int32_t maxit;          /* N_max                                                               */
+    int32_t adaptive_rank;  /* RHOSVD: 1 = effective-rank sketch size (Section 3.1), 0 = r + p    */
+    int32_t precision;      /* TK_FP64 or TK_MIXED                                                 */
+    int32_t transpose;      /* 1 = solve the adjoint system L^T(X) = B                            */
+    int32_t reserved;
+    double tol;             /* tolerance                                                           */
+    double eta;             /* sketched correction factor: stop when res_k < eta * tol             */
+    double round_tol;       /* ST-HOSVD tolerance epsilon (RoundSum)                               */
+    uint64_t seed;          /* key of the Gaussian sketch stream                                   */
+} tk_opts;
+
+/* Solve report.  res_hist is caller-owned host memory of res_hist_len doubles (may be NULL). */
+typedef struct {
+    int32_t iters;
+    int32_t status;                 /* TK_OK, TK_NOT_CONVERGED, TK_BREAKDOWN, TK_SKETCH_EXHAUSTED */
+    double sketched_res;            /* final ||M y - b_s|| / ||b_s||                            */
+    double *res_hist;
+    int32_t res_hist_len;
+    int32_t out_rank[TK_MAX_D];     /* multilinear rank of x (x is zero-padded beyond it)        */
+    double ms_total;                /* device time of the solve (CUDA events)                   */
+    int64_t workspace_bytes;        /* device workspace held by the handle after the solve       */
+    int64_t kernel_launches;        /* kernels the library launched for this call                */
+} tk_report;
+
+typedef struct tk_handle tk_handle;
+
+/* Create a handle bound to CUDA device `device`.  The handle owns a growable device
+ * workspace (cudaMalloc on first need) released by tk_destroy. */
+int tk_create(tk_handle **h, int device);
+int tk_destroy(tk_handle *h);
+/* Message of the last error on this handle (valid until the next call). */
+const char *tk_last_error(const tk_handle *h);
+
+/* tk_solve: RHOSVD-Tucker sGMRES (Algorithm 2) or MLN-Tucker sGMRES (Algorithm 6) for
+ * L(X) = B (or L^T(X) = B when opts->transpose).  x_out is caller-allocated with
+ * x_out->r[k] = rank_cap for every mode (core rank_cap^d, factors n_k x rank_cap); the
+ * solution is written zero-padded and report->out_rank holds its multilinear rank.
+ * Synchronizes `stream`.  Returns TK_OK / TK_NOT_CONVERGED / TK_BREAKDOWN /
+ * TK_SKETCH_EXHAUSTED (all successful, x_out valid) or a negative error. */
+int tk_solve(tk_handle *h, const tk_operator *op, const tk_tucker *b, const tk_opts *opts,
+             tk_tucker *x_out, tk_report *report, void *stream);
+
+/* tk_apply: the Tucker matvec of Section 3.1 without recompression.  For every term t and
+ * mode k writes A_k^(t) U_k (or its transpose) into out_factors[t*d + k] (device,
+ * n_k x r_k, caller-allocated); the terms share x's core scaled by theta_t.  For identity
+ * modes U_k is copied.  Enqueues only. */
+int tk_apply(tk_handle *h, const tk_operator *op, const tk_tucker *x, int32_t transpose,
+             double *const *out_factors, void *stream);
+
+/* tk_roundsum: RoundSum (Section 3.1) of sum_i coef[i] X_i (coef host memory) with the
+ * Gaussian matrices of stream (seed, purpose 2, call_index, mode).  Output rank is capped at
+ * rank_cap with ST-HOSVD tolerance round_tol; sketch size rank_cap + oversample_p (or the
+ * effective-rank estimate when adaptive_rank).  out is caller-allocated with r[k] = rank_cap;
+ * written zero-padded; out_rank (host, d entries) receives the ranks.  Synchronizes. */
+int tk_roundsum(tk_handle *h, int32_t nterms, const tk_tucker *xs, const double *coef,
+                const tk_opts *opts, uint64_t call_index, tk_tucker *out, int32_t *out_rank,
+                void *stream);
+
+/* tk_kron_sketch: Kronecker-structured sketch (Algorithm 2, b_s and M columns):
+ * out[l] = X x_1 S_1[:,l]^T ... x_d S_d[:,l]^T for l < s, S_k device n_k x s column-major,
+ * out device (s doubles).  Enqueues only. */
+int tk_kron_sketch(tk_handle *h, const tk_tucker *x, const double *const *S, int32_t s,
+                   double *out, void *stream);
+
+/* tk_inner: <X, Y>_F (Section 2.2) written to *out_host.  Synchronizes. */
+int tk_inner(tk_handle *h, const tk_tucker *x, const tk_tucker *y, double *out_host, void *stream);
+
+/* tk_residual: true relative residual ||L(X) - B||_F / ||B||_F in Tucker form (QR of the
+ * concatenated factors, no n_1 x .. x n_d tensor formed), written to *rel_host.  Synchronizes. */
+int tk_residual(tk_handle *h, const tk_operator *op, const tk_tucker *x, const tk_tucker *b,
+                int32_t transpose, double *rel_host, void *stream);
+
+/* tk_gaussian: `count` values of the N(0,1) stream (seed, stream_id) - Philox4x32-10 with
+ * Box-Muller, element e from counter (e/2, stream_id) - into out (device).  bf16_round = 1
+ * rounds each value to the nearest bfloat16 (ties to even).  Enqueues only. */
+int tk_gaussian(tk_handle *h, uint64_t seed, uint64_t stream_id, int64_t count,
+                int32_t bf16_round, double *out, void *stream);
+
+/* tk_philox: raw Philox4x32-10 words of counter blocks [first, first + nblocks) for
+ * stream_id and key seed: out[4*i + w] (device, uint32).  Enqueues only. */
+int tk_philox(tk_handle *h, uint64_t seed, uint64_t stream_id, uint64_t first, int64_t nblocks,
+              uint32_t *out, void *stream);
+
+/* tk_sketched_ls: y = argmin ||M y - b||_2 for M (device, s x k column-major, lda = s),
+ * b (device, s), via Householder QR (Algorithm 2 least-squares step); writes y (device, k)
+ * and the residual norm ||M y - b|| to *res (device).  Enqueues only.  Requires k < s <= 1024. */
+int tk_sketched_ls(tk_handle *h, const double *M, const double *b, int32_t s, int32_t k,
+                   double *y, double *res, void *stream);
+
+/* tk_mln_roundsum: MLN_Sketch + MLN_Sum + MLN_Recovery (Algorithms 3-5) of
+ * sum_i coef[i] X_i with Psi_k (device, n_k x (r+p)); out caller-allocated with r[k] = r.
+ * Enqueues only. */
+int tk_mln_roundsum(tk_handle *h, int32_t nterms, const tk_tucker *xs, const double *coef,
+                    const double *const *psi, int32_t r, int32_t p, tk_tucker *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TUCKERSGMRES_H */

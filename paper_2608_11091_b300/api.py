@@ -1,0 +1,356 @@
+"""Python binding of the C ABI: argument marshalling only.
+
+Device memory and the stream come from PyTorch; every step of the solvers runs in the CUDA
+library.  Tensors cross the boundary column-major: a core of logical shape (r_1, .., r_d) is
+held in a torch tensor with Fortran strides (element [i_1, .., i_d] at i_1 + r_1 (i_2 + ...)),
+and a factor n x r likewise.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+STATUS = {L.TK_OK: "converged", L.TK_NOT_CONVERGED: "not_converged", L.TK_BREAKDOWN: "breakdown",
+          L.TK_SKETCH_EXHAUSTED: "sketch_exhausted"}
+
+
+class TuckerError(RuntimeError):
+    pass
+
+
+def fortran_empty(shape: Sequence[int], device) -> torch.Tensor:
+    """Uninitialised float64 tensor of `shape` with column-major strides."""
+    shape = [int(s) for s in shape]
+    t = torch.empty(shape[::-1], dtype=torch.float64, device=device)
+    return t.permute(*reversed(range(len(shape))))
+
+
+def to_fortran(x, device) -> torch.Tensor:
+    """Copy an array (numpy or torch) to `device` as float64 with column-major strides."""
+    if isinstance(x, np.ndarray):
+        x = torch.from_numpy(np.asarray(x, dtype=np.float64))
+    x = x.to(dtype=torch.float64)
+    nd = x.dim()
+    rev = list(reversed(range(nd)))
+    return x.permute(*rev).contiguous().to(device).permute(*rev)
+
+
+def is_fortran(t: torch.Tensor) -> bool:
+    stride = 1
+    for size, st in zip(t.shape, t.stride()):
+        if size > 1 and st != stride:
+            return False
+        stride *= size
+    return True
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Handle:
+    """Library handle bound to one CUDA device (owns the device workspace)."""
+
+    def __init__(self, device: int = 0):
+        self.lib = L.load()
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        rc = self.lib.tk_create(ctypes.byref(h), self.device)
+        if rc != 0:
+            raise TuckerError(f"tk_create failed with status {rc}")
+        self.h = h
+
+    def check(self, rc: int, what: str) -> int:
+        if rc < 0:
+            msg = self.lib.tk_last_error(self.h).decode()
+            raise TuckerError(f"{what} failed ({rc}): {msg}")
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tk_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_HANDLES: Dict[int, Handle] = {}
+
+
+def handle(device: Optional[int] = None) -> Handle:
+    dev = torch.cuda.current_device() if device is None else int(device)
+    if dev not in _HANDLES:
+        _HANDLES[dev] = Handle(dev)
+    return _HANDLES[dev]
+
+
+@dataclass
+class DeviceTucker:
+    """Tucker tensor on the GPU: core (r_1 x .. x r_d) and factors (n_k x r_k), column-major."""
+    core: torch.Tensor
+    factors: List[torch.Tensor]
+
+    @staticmethod
+    def from_numpy(core: np.ndarray, factors: Sequence[np.ndarray], device="cuda") -> "DeviceTucker":
+        return DeviceTucker(to_fortran(core, device), [to_fortran(u, device) for u in factors])
+
+    @staticmethod
+    def empty(n: Sequence[int], r: Sequence[int], device="cuda") -> "DeviceTucker":
+        return DeviceTucker(fortran_empty(r, device), [fortran_empty((a, b), device) for a, b in zip(n, r)])
+
+    @property
+    def d(self) -> int:
+        return len(self.factors)
+
+    @property
+    def n(self) -> List[int]:
+        return [int(u.shape[0]) for u in self.factors]
+
+    @property
+    def r(self) -> List[int]:
+        return [int(u.shape[1]) for u in self.factors]
+
+    def numpy(self):
+        return (self.core.cpu().numpy(), [u.cpu().numpy() for u in self.factors])
+
+    def c(self) -> L.tk_tucker:
+        for t in [self.core, *self.factors]:
+            if t.dtype != torch.float64 or not t.is_cuda or not is_fortran(t):
+                raise TuckerError("Tucker tensors must be float64 CUDA tensors in column-major layout")
+        s = L.tk_tucker()
+        s.d = self.d
+        for k in range(self.d):
+            s.n[k] = self.n[k]
+            s.r[k] = self.r[k]
+            s.factor[k] = self.factors[k].data_ptr()
+        s.core = self.core.data_ptr()
+        return s
+
+
+class DeviceOperator:
+    """L = sum_t theta_t A_1^(t) x .. x A_d^(t) with its mode matrices on the GPU.
+
+    `op` has attributes d, n, theta and mats[t][k] with kind ('I', 'B', 'D'), n, kl, ku and
+    data (band layout (kl+ku+1) x n, or dense n x n)."""
+
+    _KIND = {'I': L.TK_IDENTITY, 'B': L.TK_BANDED, 'D': L.TK_DENSE}
+
+    def __init__(self, op, device="cuda", theta: Optional[Sequence[float]] = None):
+        self.d = int(op.d)
+        self.n = [int(v) for v in op.n]
+        self.nterms = len(op.mats)
+        self._keep = []
+        cache = {}
+        mats = (L.tk_modemat * (self.nterms * self.d))()
+        for t in range(self.nterms):
+            for k in range(self.d):
+                m = op.mats[t][k]
+                e = mats[t * self.d + k]
+                e.kind = self._KIND[m.kind]
+                e.kl, e.ku, e.n = int(m.kl), int(m.ku), int(m.n)
+                if m.kind == 'I':
+                    e.data = None
+                    continue
+                key = id(m.data)
+                if key not in cache:
+                    cache[key] = to_fortran(np.asarray(m.data, dtype=np.float64), device)
+                e.data = cache[key].data_ptr()
+        self._keep.append(cache)
+        self.mats = mats
+        self.set_theta(op.theta if theta is None else theta)
+
+    def set_theta(self, theta: Sequence[float]):
+        self.theta_values = [float(v) for v in theta]
+        self.theta = (ctypes.c_double * self.nterms)(*self.theta_values)
+
+    def c(self) -> L.tk_operator:
+        s = L.tk_operator()
+        s.nterms = self.nterms
+        s.d = self.d
+        s.theta = ctypes.cast(self.theta, ctypes.POINTER(ctypes.c_double))
+        s.mats = ctypes.cast(self.mats, ctypes.POINTER(L.tk_modemat))
+        return s
+
+
+@dataclass
+class Options:
+    variant: str = "rhosvd"          # 'rhosvd' (Algorithm 2) or 'mln' (Algorithm 6)
+    rank_cap: int = 8
+    sketch_s: int = 64
+    oversample_p: int = 5
+    ktrunc: int = 2
+    maxit: int = 50
+    tol: float = 1e-8
+    eta: float = 0.3
+    round_tol: float = 1e-12
+    seed: int = 0
+    adaptive_rank: bool = False
+    precision: str = "fp64"          # 'fp64' or 'mixed'
+    transpose: bool = False
+
+    @staticmethod
+    def from_params(p, **over) -> "Options":
+        o = Options(variant=p.variant, rank_cap=p.rank_cap, sketch_s=p.sketch_s,
+                    oversample_p=p.oversample_p, ktrunc=p.ktrunc, maxit=p.maxit, tol=p.tol,
+                    eta=p.eta, round_tol=p.round_tol, seed=p.seed, adaptive_rank=p.adaptive_rank)
+        for k, v in over.items():
+            setattr(o, k, v)
+        return o
+
+    def c(self) -> L.tk_opts:
+        s = L.tk_opts()
+        s.variant = L.TK_RHOSVD_SGMRES if self.variant == "rhosvd" else L.TK_MLN_SGMRES
+        s.rank_cap, s.sketch_s, s.oversample_p = self.rank_cap, self.sketch_s, self.oversample_p
+        s.ktrunc, s.maxit, s.adaptive_rank = self.ktrunc, self.maxit, int(self.adaptive_rank)
+        s.precision = L.TK_MIXED if self.precision == "mixed" else L.TK_FP64
+        s.transpose = int(self.transpose)
+        s.tol, s.eta, s.round_tol, s.seed = self.tol, self.eta, self.round_tol, self.seed
+        return s
+
+
+@dataclass
+class Report:
+    iters: int
+    status: str
+    sketched_res: float
+    res_hist: List[float]
+    out_rank: List[int]
+    ms_total: float
+    workspace_bytes: int
+    kernel_launches: int
+
+
+def tk_solve(op: DeviceOperator, b: DeviceTucker, opts: Options, x: Optional[DeviceTucker] = None,
+             stream=None, device: Optional[int] = None):
+    """RHOSVD-Tucker sGMRES (Algorithm 2) or MLN-Tucker sGMRES (Algorithm 6). Returns (x, Report)."""
+    h = handle(device)
+    if x is None:
+        x = DeviceTucker.empty(b.n, [opts.rank_cap] * b.d, device=b.core.device)
+    hist = (ctypes.c_double * max(1, opts.maxit))()
+    rep = L.tk_report()
+    rep.res_hist = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
+    rep.res_hist_len = opts.maxit
+    opc, bc, oc, xc = op.c(), b.c(), opts.c(), x.c()
+    rc = h.lib.tk_solve(h.h, ctypes.byref(opc), ctypes.byref(bc), ctypes.byref(oc), ctypes.byref(xc),
+                        ctypes.byref(rep), _stream(stream))
+    h.check(rc, "tk_solve")
+    r = Report(rep.iters, STATUS[rep.status], rep.sketched_res, list(hist[:rep.iters]),
+               list(rep.out_rank[:b.d]), rep.ms_total, rep.workspace_bytes, rep.kernel_launches)
+    return x, r
+
+
+def tk_apply(op: DeviceOperator, x: DeviceTucker, transpose: bool = False, stream=None) -> List[List[torch.Tensor]]:
+    """Factors A_k^(t) U_k of every term (Eq. (1.2)); the terms share x's core scaled by theta_t."""
+    h = handle()
+    outs = [[fortran_empty((x.n[k], x.r[k]), x.core.device) for k in range(x.d)] for _ in range(op.nterms)]
+    ptrs = (ctypes.c_void_p * (op.nterms * x.d))(*[outs[t][k].data_ptr() for t in range(op.nterms) for k in range(x.d)])
+    opc, xc = op.c(), x.c()
+    h.check(h.lib.tk_apply(h.h, ctypes.byref(opc), ctypes.byref(xc), int(transpose), ptrs, _stream(stream)), "tk_apply")
+    return outs
+
+
+def tk_roundsum(terms: Sequence[DeviceTucker], coef: Sequence[float], opts: Options, call_index: int = 0,
+                out: Optional[DeviceTucker] = None, stream=None):
+    """RoundSum (Section 3.1) of sum_i coef_i terms_i. Returns (out, ranks)."""
+    h = handle()
+    d = terms[0].d
+    if out is None:
+        out = DeviceTucker.empty(terms[0].n, [opts.rank_cap] * d, device=terms[0].core.device)
+    arr = (L.tk_tucker * len(terms))(*[t.c() for t in terms])
+    cf = (ctypes.c_double * len(terms))(*[float(c) for c in coef])
+    ranks = (ctypes.c_int32 * d)()
+    oc, outc = opts.c(), out.c()
+    rc = h.lib.tk_roundsum(h.h, len(terms), arr, cf, ctypes.byref(oc), int(call_index), ctypes.byref(outc),
+                           ranks, _stream(stream))
+    h.check(rc, "tk_roundsum")
+    return out, list(ranks)
+
+
+def tk_kron_sketch(x: DeviceTucker, S: Sequence[torch.Tensor], stream=None) -> torch.Tensor:
+    """Kronecker-structured sketch out[l] = X x_1 S_1[:,l]^T ... x_d S_d[:,l]^T (Algorithm 2)."""
+    h = handle()
+    s = int(S[0].shape[1])
+    out = torch.empty(s, dtype=torch.float64, device=x.core.device)
+    for m in S:
+        if not is_fortran(m):
+            raise TuckerError("sketch matrices must be column-major")
+    ptrs = (ctypes.c_void_p * x.d)(*[m.data_ptr() for m in S])
+    xc = x.c()
+    h.check(h.lib.tk_kron_sketch(h.h, ctypes.byref(xc), ptrs, s, ctypes.c_void_p(out.data_ptr()), _stream(stream)),
+            "tk_kron_sketch")
+    return out
+
+
+def tk_inner(x: DeviceTucker, y: DeviceTucker, stream=None) -> float:
+    h = handle()
+    out = ctypes.c_double()
+    xc, yc = x.c(), y.c()
+    h.check(h.lib.tk_inner(h.h, ctypes.byref(xc), ctypes.byref(yc), ctypes.byref(out), _stream(stream)), "tk_inner")
+    return out.value
+
+
+def tk_residual(op: DeviceOperator, x: DeviceTucker, b: DeviceTucker, transpose: bool = False, stream=None) -> float:
+    """True relative residual ||L(X) - B|| / ||B|| computed in Tucker form."""
+    h = handle()
+    out = ctypes.c_double()
+    opc, xc, bc = op.c(), x.c(), b.c()
+    h.check(h.lib.tk_residual(h.h, ctypes.byref(opc), ctypes.byref(xc), ctypes.byref(bc), int(transpose),
+                              ctypes.byref(out), _stream(stream)), "tk_residual")
+    return out.value
+
+
+def tk_gaussian(seed: int, stream_id: int, count: int, bf16_round: bool = False, device="cuda", stream=None):
+    h = handle()
+    out = torch.empty(max(count, 1), dtype=torch.float64, device=device)
+    h.check(h.lib.tk_gaussian(h.h, int(seed), int(stream_id), int(count), int(bf16_round),
+                              ctypes.c_void_p(out.data_ptr()), _stream(stream)), "tk_gaussian")
+    return out[:count]
+
+
+def tk_philox(seed: int, stream_id: int, first: int, nblocks: int, device="cuda", stream=None):
+    h = handle()
+    out = torch.empty(max(4 * nblocks, 4), dtype=torch.int32, device=device)
+    h.check(h.lib.tk_philox(h.h, int(seed), int(stream_id), int(first), int(nblocks),
+                            ctypes.c_void_p(out.data_ptr()), _stream(stream)), "tk_philox")
+    return out[:4 * nblocks]
+
+
+def tk_sketched_ls(M: torch.Tensor, b: torch.Tensor, stream=None):
+    """y = argmin ||M y - b|| (Householder), M s x k column-major. Returns (y, residual norm)."""
+    h = handle()
+    s, k = int(M.shape[0]), int(M.shape[1])
+    if not is_fortran(M):
+        raise TuckerError("M must be column-major")
+    y = torch.empty(k, dtype=torch.float64, device=M.device)
+    res = torch.empty(1, dtype=torch.float64, device=M.device)
+    h.check(h.lib.tk_sketched_ls(h.h, ctypes.c_void_p(M.data_ptr()), ctypes.c_void_p(b.data_ptr()), s, k,
+                                 ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(res.data_ptr()), _stream(stream)),
+            "tk_sketched_ls")
+    return y, res
+
+
+def tk_mln_roundsum(terms: Sequence[DeviceTucker], coef: Sequence[float], psi: Sequence[torch.Tensor], r: int,
+                    p: int, out: Optional[DeviceTucker] = None, stream=None) -> DeviceTucker:
+    """MLN_Sketch + MLN_Sum + MLN_Recovery (Algorithms 3-5)."""
+    h = handle()
+    d = terms[0].d
+    if out is None:
+        out = DeviceTucker.empty(terms[0].n, [r] * d, device=terms[0].core.device)
+    arr = (L.tk_tucker * len(terms))(*[t.c() for t in terms])
+    cf = (ctypes.c_double * len(terms))(*[float(c) for c in coef])
+    ptrs = (ctypes.c_void_p * d)(*[m.data_ptr() for m in psi])
+    outc = out.c()
+    h.check(h.lib.tk_mln_roundsum(h.h, len(terms), arr, cf, ptrs, int(r), int(p), ctypes.byref(outc),
+                                  _stream(stream)), "tk_mln_roundsum")
+    return out

@@ -1,0 +1,497 @@
+// Structured and elementwise kernels of the Tucker sGMRES hot path.
+#include <algorithm>
+
+#include "tk_internal.cuh"
+
+namespace tk {
+
+void Ctx::check_launch(const char *what) {
+    ++launches;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        throw Error{TK_ECUDA, std::string("launch of ") + what + ": " + cudaGetErrorString(e)};
+}
+
+// ------------------------------------------------------------------------------------------
+// Arena
+// ------------------------------------------------------------------------------------------
+Arena::~Arena() {
+    for (auto &c : chunks_) cudaFree(c.base);
+}
+
+void *Arena::alloc_bytes(size_t bytes) {
+    bytes = (bytes + 255) & ~size_t(255);
+    if (bytes == 0) bytes = 256;
+    while (cur_ < chunks_.size()) {
+        if (off_ + bytes <= chunks_[cur_].size) {
+            void *p = chunks_[cur_].base + off_;
+            off_ += bytes;
+            return p;
+        }
+        ++cur_;
+        off_ = 0;
+    }
+    const size_t sz = std::max(bytes, size_t(256) << 20);
+    char *p = nullptr;
+    if (cudaMalloc(&p, sz) != cudaSuccess) {
+        cudaGetLastError();
+        throw Error{TK_ENOMEM, "device workspace allocation of " + std::to_string(sz) + " bytes failed"};
+    }
+    chunks_.push_back(Chunk{p, sz});
+    cur_ = chunks_.size() - 1;
+    off_ = bytes;
+    return p;
+}
+
+size_t Arena::capacity() const {
+    size_t t = 0;
+    for (auto &c : chunks_) t += c.size;
+    return t;
+}
+
+// ------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) + Box-Muller
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k.x += W0; k.y += W1; }
+        const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ double round_bf16(double x) {
+    if (x == 0.0) return 0.0;
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long lsb = (b >> 45) & 1ull;
+    b = ((b + (1ull << 44) - 1ull + lsb) >> 45) << 45;
+    return __longlong_as_double((long long)b);
+}
+
+struct GaussJobs {
+    int n;
+    uint64_t sid[TK_MAX_D * 2];
+    long long count[TK_MAX_D * 2];
+    double *out[TK_MAX_D * 2];
+};
+
+__global__ void k_gaussian(uint64_t seed, const __grid_constant__ GaussJobs J, int bf16) {
+    const int job = blockIdx.y;
+    const long long cnt = J.count[job];
+    const long long npair = (cnt + 1) / 2;
+    const uint64_t sid = J.sid[job];
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < npair;
+         b += (long long)gridDim.x * blockDim.x) {
+        const uint4 w = philox4x32_10(
+            make_uint4((uint32_t)b, (uint32_t)((unsigned long long)b >> 32), (uint32_t)sid,
+                       (uint32_t)(sid >> 32)),
+            key);
+        const unsigned long long m1 = (unsigned long long)(w.x >> 5) * 67108864ull + (w.y >> 6);
+        const unsigned long long m2 = (unsigned long long)(w.z >> 5) * 67108864ull + (w.w >> 6);
+        const double u1 = ((double)m1 + 1.0) * 0x1p-53;
+        const double u2 = (double)m2 * 0x1p-53;
+        const double rad = sqrt(-2.0 * log(u1));
+        double sn, cs;
+        sincos(2.0 * 3.141592653589793 * u2, &sn, &cs);
+        double z0 = rad * cs, z1 = rad * sn;
+        if (bf16) { z0 = round_bf16(z0); z1 = round_bf16(z1); }
+        J.out[job][2 * b] = z0;
+        if (2 * b + 1 < cnt) J.out[job][2 * b + 1] = z1;
+    }
+}
+
+void gaussian(Ctx &c, uint64_t seed, const uint64_t *sids, const long long *counts,
+              double *const *outs, int nmat, int bf16) {
+    for (int base = 0; base < nmat; base += TK_MAX_D * 2) {
+        GaussJobs J{};
+        J.n = std::min(TK_MAX_D * 2, nmat - base);
+        long long mx = 1;
+        for (int i = 0; i < J.n; ++i) {
+            J.sid[i] = sids[base + i];
+            J.count[i] = counts[base + i];
+            J.out[i] = outs[base + i];
+            mx = std::max(mx, (counts[base + i] + 1) / 2);
+        }
+        const int threads = 256;
+        const long long blocks = std::min<long long>((mx + threads - 1) / threads, 4096);
+        k_gaussian<<<dim3((unsigned)blocks, J.n), threads, 0, c.st>>>(seed, J, bf16);
+        c.check_launch("gaussian");
+    }
+}
+
+__global__ void k_philox_raw(uint64_t seed, uint64_t sid, uint64_t first, long long nb, uint32_t *out) {
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb;
+         i += (long long)gridDim.x * blockDim.x) {
+        const uint64_t b = first + (uint64_t)i;
+        const uint4 w = philox4x32_10(
+            make_uint4((uint32_t)b, (uint32_t)(b >> 32), (uint32_t)sid, (uint32_t)(sid >> 32)), key);
+        out[4 * i] = w.x; out[4 * i + 1] = w.y; out[4 * i + 2] = w.z; out[4 * i + 3] = w.w;
+    }
+}
+
+void philox_raw(Ctx &c, uint64_t seed, uint64_t sid, uint64_t first, long long nb, uint32_t *out) {
+    const long long blocks = std::min<long long>((nb + 255) / 256, 4096);
+    k_philox_raw<<<(unsigned)std::max<long long>(blocks, 1), 256, 0, c.st>>>(seed, sid, first, nb, out);
+    c.check_launch("philox");
+}
+
+// ------------------------------------------------------------------------------------------
+// Banded mode-matrix apply: out = A U (or A^T U), A in LAPACK band layout
+// ------------------------------------------------------------------------------------------
+struct BandJobs {
+    int n;
+    BandJob j[32];
+};
+
+__global__ void k_band(const __grid_constant__ BandJobs J) {
+    const BandJob &B = J.j[blockIdx.y];
+    const long long total = (long long)B.n * B.r;
+    const int ld = B.kl + B.ku + 1;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % B.n);
+        const long long j = e / B.n;
+        const double *u = B.U + j * B.n;
+        double acc = 0.0;
+        if (!B.trans) {
+            const int c0 = max(0, i - B.kl), c1 = min(B.n - 1, i + B.ku);
+            for (int c = c0; c <= c1; ++c) acc = fma(B.band[B.ku + i - c + (long long)c * ld], u[c], acc);
+        } else {
+            const int c0 = max(0, i - B.ku), c1 = min(B.n - 1, i + B.kl);
+            for (int c = c0; c <= c1; ++c) acc = fma(B.band[B.ku + c - i + (long long)i * ld], u[c], acc);
+        }
+        B.out[e] = acc;
+    }
+}
+
+void band_apply(Ctx &c, const std::vector<BandJob> &jobs) {
+    for (size_t base = 0; base < jobs.size(); base += 32) {
+        BandJobs J{};
+        J.n = (int)std::min<size_t>(32, jobs.size() - base);
+        long long mx = 1;
+        for (int i = 0; i < J.n; ++i) {
+            J.j[i] = jobs[base + i];
+            mx = std::max(mx, (long long)J.j[i].n * J.j[i].r);
+        }
+        const long long blocks = std::min<long long>((mx + 255) / 256, 2048);
+        k_band<<<dim3((unsigned)blocks, J.n), 256, 0, c.st>>>(J);
+        c.check_launch("band");
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Khatri-Rao (row-wise Hadamard) contraction: out[i, mm, l] = sum_j T[i, j, mm, l] P[j, l]
+// ------------------------------------------------------------------------------------------
+struct HadJobs {
+    int n;
+    HadJob j[32];
+};
+
+__global__ void k_hadamard(const __grid_constant__ HadJobs J) {
+    const HadJob &H = J.j[blockIdx.y];
+    const long long total = (long long)H.a * H.cc * H.s;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long i = e % H.a;
+        const long long rest = e / H.a;          // mm + cc * l
+        const long long mm = rest % H.cc, l = rest / H.cc;
+        const double *t = H.T + i + (long long)H.a * H.b * (mm + (long long)H.cc * l);
+        const double *p = H.P + l * H.ldp;
+        double acc = 0.0;
+        for (int j = 0; j < H.b; ++j) acc = fma(t[(long long)j * H.a], p[j], acc);
+        H.out[e] = acc;
+    }
+}
+
+void hadamard_contract(Ctx &c, const std::vector<HadJob> &jobs) {
+    for (size_t base = 0; base < jobs.size(); base += 32) {
+        HadJobs J{};
+        J.n = (int)std::min<size_t>(32, jobs.size() - base);
+        long long mx = 1;
+        for (int i = 0; i < J.n; ++i) {
+            J.j[i] = jobs[base + i];
+            mx = std::max(mx, (long long)J.j[i].a * J.j[i].cc * J.j[i].s);
+        }
+        const long long blocks = std::min<long long>((mx + 255) / 256, 4096);
+        k_hadamard<<<dim3((unsigned)blocks, J.n), 256, 0, c.st>>>(J);
+        c.check_launch("hadamard");
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Transposed mode unfolding gather
+// ------------------------------------------------------------------------------------------
+__global__ void k_gather_unfold_t(const double *C, double *out, long long a, int sk, long long rest) {
+    const long long m = a * rest;
+    const long long total = m * sk;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long rho = e % m, col = e / m;
+        out[e] = C[(rho % a) + col * a + (rho / a) * a * sk];
+    }
+}
+
+void gather_unfold_t(Ctx &c, const double *C, double *out, long long a, int sk, long long rest) {
+    const long long total = a * rest * sk;
+    const long long blocks = std::min<long long>((total + 255) / 256, 4096);
+    k_gather_unfold_t<<<(unsigned)std::max<long long>(blocks, 1), 256, 0, c.st>>>(C, out, a, sk, rest);
+    c.check_launch("gather");
+}
+
+// ------------------------------------------------------------------------------------------
+// Deterministic reductions
+// ------------------------------------------------------------------------------------------
+struct DotJobs {
+    int n;
+    DotJob j[32];
+};
+
+__global__ void __launch_bounds__(1024) k_dots(const __grid_constant__ DotJobs J) {
+    const DotJob &D = J.j[blockIdx.x];
+    double acc = 0.0;
+    for (long long i = threadIdx.x; i < D.n; i += blockDim.x) acc = fma(D.x[i], D.y[i], acc);
+    __shared__ double sh[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        *D.out = t;
+    }
+}
+
+void dots(Ctx &c, const std::vector<DotJob> &jobs) {
+    for (size_t base = 0; base < jobs.size(); base += 32) {
+        DotJobs J{};
+        J.n = (int)std::min<size_t>(32, jobs.size() - base);
+        for (int i = 0; i < J.n; ++i) J.j[i] = jobs[base + i];
+        k_dots<<<J.n, 1024, 0, c.st>>>(J);
+        c.check_launch("dots");
+    }
+}
+
+void dot(Ctx &c, const double *x, const double *y, long long n, double *out) {
+    dots(c, {DotJob{x, y, n, out}});
+}
+
+// ------------------------------------------------------------------------------------------
+// Elementwise helpers
+// ------------------------------------------------------------------------------------------
+__global__ void k_fill(double *p, long long n, double v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+void fill(Ctx &c, double *p, long long n, double v) {
+    if (n <= 0) return;
+    const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+    k_fill<<<(unsigned)blocks, 256, 0, c.st>>>(p, n, v);
+    c.check_launch("fill");
+}
+
+__global__ void k_scale_by(double *y, const double *x, long long n, const double *s, int inv) {
+    const double f = inv ? 1.0 / *s : *s;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] = x[i] * f;
+}
+
+void scale_by(Ctx &c, double *y, const double *x, long long n, const double *s, int inv) {
+    if (n <= 0) return;
+    const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+    k_scale_by<<<(unsigned)blocks, 256, 0, c.st>>>(y, x, n, s, inv);
+    c.check_launch("scale");
+}
+
+void copy(Ctx &c, double *dst, const double *src, long long n) {
+    if (n <= 0) return;
+    TK_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+}
+
+__global__ void k_copy_pad(double *dst, int ldd, int rd, int cd, const double *src, int lds, int rs, int cs) {
+    const long long total = (long long)rd * cd;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % rd), j = (int)(e / rd);
+        dst[i + (long long)j * ldd] = (i < rs && j < cs) ? src[i + (long long)j * lds] : 0.0;
+    }
+}
+
+void copy_pad(Ctx &c, double *dst, int ld_dst, int rows_dst, int cols_dst, const double *src,
+              int ld_src, int rows_src, int cols_src) {
+    const long long total = (long long)rows_dst * cols_dst;
+    if (total <= 0) return;
+    const long long blocks = std::min<long long>((total + 255) / 256, 4096);
+    k_copy_pad<<<(unsigned)blocks, 256, 0, c.st>>>(dst, ld_dst, rows_dst, cols_dst, src, ld_src,
+                                                   rows_src, cols_src);
+    c.check_launch("copy_pad");
+}
+
+struct CoreDims { int d; int rd[TK_MAX_D]; int rs[TK_MAX_D]; };
+
+__global__ void k_copy_core_pad(double *dst, const double *src, CoreDims D, long long total) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        long long rem = e, soff = 0, sstride = 1;
+        bool inside = true;
+        for (int k = 0; k < D.d; ++k) {
+            const int idx = (int)(rem % D.rd[k]);
+            rem /= D.rd[k];
+            if (idx >= D.rs[k]) inside = false;
+            soff += idx * sstride;
+            sstride *= D.rs[k];
+        }
+        dst[e] = inside ? src[soff] : 0.0;
+    }
+}
+
+void copy_core_pad(Ctx &c, double *dst, const int *rdst, const double *src, const int *rsrc, int d) {
+    CoreDims D{};
+    D.d = d;
+    long long total = 1;
+    for (int k = 0; k < d; ++k) { D.rd[k] = rdst[k]; D.rs[k] = rsrc[k]; total *= rdst[k]; }
+    const long long blocks = std::min<long long>((total + 255) / 256, 4096);
+    k_copy_core_pad<<<(unsigned)blocks, 256, 0, c.st>>>(dst, src, D, total);
+    c.check_launch("copy_core_pad");
+}
+
+__global__ void k_superdiag(const double *G, int m, int d, double *out, double sh, const double *sd) {
+    long long stride = 0, p = 1;
+    for (int k = 0; k < d; ++k) { stride += p; p *= m; }
+    const double f = sh * (sd ? *sd : 1.0);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+        out[i] = f * G[(long long)i * stride];
+}
+
+void superdiag(Ctx &c, const double *G, int m, int d, double *out, double scale_host,
+               const double *scale_dev) {
+    k_superdiag<<<(m + 255) / 256, 256, 0, c.st>>>(G, m, d, out, scale_host, scale_dev);
+    c.check_launch("superdiag");
+}
+
+__global__ void k_transpose(double *dst, int ldd, const double *src, int lds, int rows, int cols) {
+    const long long total = (long long)rows * cols;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % rows), j = (int)(e / rows);
+        dst[j + (long long)i * ldd] = src[i + (long long)j * lds];
+    }
+}
+
+void transpose_block(Ctx &c, double *dst, int ldd, const double *src, int lds, int rows, int cols) {
+    const long long total = (long long)rows * cols;
+    if (total <= 0) return;
+    const long long blocks = std::min<long long>((total + 255) / 256, 4096);
+    k_transpose<<<(unsigned)blocks, 256, 0, c.st>>>(dst, ldd, src, lds, rows, cols);
+    c.check_launch("transpose");
+}
+
+__global__ void k_triu(double *dst, int ldd, const double *src, int lds, int rows, int cols) {
+    const long long total = (long long)rows * cols;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % rows), j = (int)(e / rows);
+        dst[i + (long long)j * ldd] = (i <= j) ? src[i + (long long)j * lds] : 0.0;
+    }
+}
+
+void triu_copy(Ctx &c, double *dst, int ldd, const double *src, int lds, int rows, int cols) {
+    const long long total = (long long)rows * cols;
+    if (total <= 0) return;
+    const long long blocks = std::min<long long>((total + 255) / 256, 4096);
+    k_triu<<<(unsigned)blocks, 256, 0, c.st>>>(dst, ldd, src, lds, rows, cols);
+    c.check_launch("triu");
+}
+
+__global__ void k_sqrt_scalar(const double *in, double *out) { *out = sqrt(fmax(*in, 0.0)); }
+
+void sqrt_scalar(Ctx &c, const double *in, double *out) {
+    k_sqrt_scalar<<<1, 1, 0, c.st>>>(in, out);
+    c.check_launch("sqrt");
+}
+
+}  // namespace tk
+
+namespace tk {
+
+// ------------------------------------------------------------------------------------------
+// MLN_Sum streaming axpy (Algorithm 4): y = beta y + sum_j coef_j (*coef_dev_j) x_j
+// 128-bit vector loads when every pointer is 16-byte aligned.
+// ------------------------------------------------------------------------------------------
+constexpr int AXPY_MAX = 16;
+struct AxpyJobs {
+    int n;
+    const double *x[AXPY_MAX];
+    double coef[AXPY_MAX];
+    const double *cd[AXPY_MAX];
+};
+
+__global__ void __launch_bounds__(256) k_axpy_list(double *y, long long n, double beta,
+                                                   const __grid_constant__ AxpyJobs J, int vec) {
+    double cf[AXPY_MAX];
+#pragma unroll
+    for (int j = 0; j < AXPY_MAX; ++j) cf[j] = j < J.n ? J.coef[j] * (J.cd[j] ? *J.cd[j] : 1.0) : 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    if (vec) {
+        const long long n2 = n / 2;
+        double2 *y2 = reinterpret_cast<double2 *>(y);
+        for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n2; e += stride) {
+            double2 acc = beta == 0.0 ? make_double2(0.0, 0.0) : y2[e];
+            if (beta != 0.0 && beta != 1.0) { acc.x *= beta; acc.y *= beta; }
+            for (int j = 0; j < J.n; ++j) {
+                const double2 v = reinterpret_cast<const double2 *>(J.x[j])[e];
+                acc.x = fma(cf[j], v.x, acc.x);
+                acc.y = fma(cf[j], v.y, acc.y);
+            }
+            y2[e] = acc;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) {
+            const long long e = n - 1;
+            double acc = beta == 0.0 ? 0.0 : beta * y[e];
+            for (int j = 0; j < J.n; ++j) acc = fma(cf[j], J.x[j][e], acc);
+            y[e] = acc;
+        }
+        return;
+    }
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += stride) {
+        double acc = beta == 0.0 ? 0.0 : beta * y[e];
+        for (int j = 0; j < J.n; ++j) acc = fma(cf[j], J.x[j][e], acc);
+        y[e] = acc;
+    }
+}
+
+void axpy_list(Ctx &c, double *y, long long n, double beta, const std::vector<const double *> &xs,
+               const std::vector<double> &coef, const std::vector<const double *> &coef_dev) {
+    if (n <= 0) return;
+    if (xs.empty()) {
+        if (beta == 0.0) fill(c, y, n, 0.0);
+        else if (beta != 1.0) TK_REQUIRE(false, "axpy_list: scaling without terms");
+        return;
+    }
+    for (size_t base = 0; base < xs.size(); base += AXPY_MAX) {
+        AxpyJobs J{};
+        J.n = (int)std::min<size_t>(AXPY_MAX, xs.size() - base);
+        bool aligned = ((uintptr_t)y % 16) == 0;
+        for (int j = 0; j < J.n; ++j) {
+            J.x[j] = xs[base + j];
+            J.coef[j] = coef[base + j];
+            J.cd[j] = coef_dev[base + j];
+            aligned = aligned && ((uintptr_t)J.x[j] % 16) == 0;
+        }
+        const long long work = aligned ? n / 2 : n;
+        const long long blocks = std::max<long long>(1, std::min<long long>((work + 255) / 256, (long long)c.num_sms * 8));
+        k_axpy_list<<<(unsigned)blocks, 256, 0, c.st>>>(y, n, base == 0 ? beta : 1.0, J, aligned ? 1 : 0);
+        c.check_launch("axpy_list");
+    }
+}
+
+}  // namespace tk

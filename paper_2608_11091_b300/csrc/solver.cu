@@ -1,0 +1,741 @@
+// Solver drivers (Algorithms 2 and 6) and the C ABI.
+#include <cmath>
+#include <cstring>
+#include <map>
+
+#include "tucker.cuh"
+
+struct tk_handle {
+    int device = 0;
+    int num_sms = 148;
+    tk::Arena arena;
+    std::string err;
+    double *pinned = nullptr;   // small host staging area for scalars read back per iteration
+};
+
+namespace tk {
+
+constexpr int SC_BETA2 = 0, SC_BETA = 1, SC_BS2 = 2, SC_BS = 3, SC_NW0SQ = 4, SC_NWSQ = 5,
+              SC_NW = 6, SC_RES = 7, SC_H = 8, SC_N = 8 + 64;
+
+static long long prodi(const int *v, int d) {
+    long long p = 1;
+    for (int i = 0; i < d; ++i) p *= v[i];
+    return p;
+}
+
+static Dims dims_of(const tk_tucker *t) {
+    Dims D{};
+    D.d = t->d;
+    for (int k = 0; k < t->d; ++k) D.n[k] = (int)t->n[k];
+    return D;
+}
+
+static void check_tucker(const tk_tucker *t, const char *what) {
+    TK_REQUIRE(t != nullptr, std::string(what) + ": null tensor");
+    TK_REQUIRE(t->d >= 2 && t->d <= TK_MAX_D, std::string(what) + ": order d must be 2..8");
+    TK_REQUIRE(t->core != nullptr, std::string(what) + ": null core");
+    for (int k = 0; k < t->d; ++k) {
+        TK_REQUIRE(t->n[k] >= 1 && t->n[k] <= (1 << 24), std::string(what) + ": bad mode size");
+        TK_REQUIRE(t->r[k] >= 1 && t->r[k] <= 1024, std::string(what) + ": bad rank");
+        TK_REQUIRE(t->factor[k] != nullptr, std::string(what) + ": null factor");
+    }
+}
+
+static TTerm term_of(const tk_tucker *t, double coef = 1.0) {
+    TTerm T;
+    T.core = t->core;
+    for (int k = 0; k < t->d; ++k) { T.f[k] = t->factor[k]; T.r[k] = (int)t->r[k]; }
+    T.coef = coef;
+    return T;
+}
+
+static OpDesc op_of(const tk_operator *op, const Dims &pb) {
+    TK_REQUIRE(op != nullptr && op->mats != nullptr && op->theta != nullptr, "operator: null");
+    TK_REQUIRE(op->nterms >= 1 && op->nterms <= 64, "operator: nterms must be 1..64");
+    TK_REQUIRE(op->d == pb.d, "operator: order differs from the tensor's");
+    OpDesc D;
+    D.nterms = op->nterms;
+    for (int t = 0; t < op->nterms; ++t) {
+        D.theta.push_back(op->theta[t]);
+        for (int k = 0; k < pb.d; ++k) {
+            const tk_modemat &m = op->mats[t * pb.d + k];
+            TK_REQUIRE(m.kind == TK_IDENTITY || m.kind == TK_BANDED || m.kind == TK_DENSE, "operator: bad kind");
+            TK_REQUIRE(m.n == pb.n[k], "operator: mode matrix size differs from the tensor's");
+            if (m.kind != TK_IDENTITY) TK_REQUIRE(m.data != nullptr, "operator: null matrix data");
+            if (m.kind == TK_BANDED) TK_REQUIRE(m.kl >= 0 && m.ku >= 0 && m.kl < m.n + 1 && m.ku < m.n + 1, "operator: bad band");
+            D.mats.push_back(m);
+        }
+    }
+    return D;
+}
+
+struct SolveOut {
+    int iters = 0;
+    int status = TK_NOT_CONVERGED;
+    double sres = 0.0;
+    std::vector<double> hist;
+    int ranks[TK_MAX_D] = {};
+};
+
+static void readback(Ctx &c, double *host, const double *dev, int n) {
+    TK_CUDA(cudaMemcpyAsync(host, dev, n * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    TK_CUDA(cudaStreamSynchronize(c.st));
+}
+
+// Tucker tensor stored at rank R in every mode (zero-padded)
+struct Slot {
+    double *core;
+    double *f[TK_MAX_D];
+    int *rank;
+    TTerm term(const Dims &pb, int R) const {
+        TTerm T;
+        T.core = core;
+        for (int k = 0; k < pb.d; ++k) { T.f[k] = f[k]; T.r[k] = R; }
+        return T;
+    }
+    TOut out(const Dims &pb) const {
+        TOut o{};
+        o.core = core;
+        for (int k = 0; k < pb.d; ++k) o.f[k] = f[k];
+        o.rank_dev = rank;
+        return o;
+    }
+};
+
+static Slot alloc_slot(Ctx &c, const Dims &pb, int R) {
+    Slot s{};
+    int rr[TK_MAX_D];
+    for (int k = 0; k < pb.d; ++k) rr[k] = R;
+    s.core = c.arena->alloc(prodi(rr, pb.d));
+    for (int k = 0; k < pb.d; ++k) s.f[k] = c.arena->alloc((size_t)pb.n[k] * R);
+    s.rank = c.arena->alloc_int(TK_MAX_D);
+    return s;
+}
+
+// ------------------------------------------------------------------------------------------
+// RHOSVD-Tucker sGMRES (Algorithm 2)
+// ------------------------------------------------------------------------------------------
+static void solve_rhosvd(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucker *b,
+                         const tk_opts &o, tk_tucker *x, SolveOut &so, double *pinned) {
+    ScopedMark solve_mark(*c.arena);
+    const int d = pb.d, R = o.rank_cap, s = o.sketch_s, sr = o.rank_cap + o.oversample_p;
+    const int kmax = std::min(o.maxit, s - 1);
+    TK_REQUIRE(sr <= 112, "RoundSum sketch size rank_cap + p must be <= 112");
+    TK_REQUIRE(o.ktrunc >= 1 && o.ktrunc <= 64, "ktrunc must be 1..64");
+    const int bf16 = o.precision == TK_MIXED ? 1 : 0;
+    double *sc = c.arena->alloc(SC_N);
+    fill(c, sc, SC_N, 0.0);
+    // Krylov sketch S_k (n_k x s): stream (seed, purpose 1, call 0, mode k)
+    double *S[TK_MAX_D];
+    {
+        uint64_t sids[TK_MAX_D];
+        long long cnt[TK_MAX_D];
+        for (int k = 0; k < d; ++k) {
+            S[k] = c.arena->alloc((size_t)pb.n[k] * s);
+            sids[k] = (uint64_t(1) << 48) | uint64_t(k);
+            cnt[k] = (long long)pb.n[k] * s;
+        }
+        gaussian(c, o.seed, sids, cnt, S, d, 0);
+    }
+    const TTerm B = term_of(b);
+    inner_batch(c, pb, {InnerJob{B, B, sc + SC_BETA2}});
+    sqrt_scalar(c, sc + SC_BETA2, sc + SC_BETA);
+    // V_1 = B / beta  (own core copy, factors borrowed from B)
+    std::vector<TTerm> V;
+    {
+        TTerm v1 = B;
+        double *core = c.arena->alloc(prodi(B.r, d));
+        scale_by(c, core, b->core, prodi(B.r, d), sc + SC_BETA, 1);
+        v1.core = core;
+        V.push_back(v1);
+    }
+    double *bs = c.arena->alloc(s);
+    kron_sketch_batch(c, pb, {B}, S, s, &bs);
+    dot(c, bs, bs, s, sc + SC_BS2);
+    sqrt_scalar(c, sc + SC_BS2, sc + SC_BS);
+    readback(c, pinned, sc, 4);
+    const double beta_s = pinned[SC_BS];
+    TK_REQUIRE(std::isfinite(pinned[SC_BETA]) && pinned[SC_BETA] > 0.0, "right-hand side is zero or not finite");
+    TK_REQUIRE(std::isfinite(beta_s) && beta_s > 0.0, "sketch of the right-hand side is zero or not finite");
+
+    double *M = c.arena->alloc((size_t)s * kmax);
+    LSState ls{};
+    ls.H = c.arena->alloc((size_t)s * kmax);
+    ls.tau = c.arena->alloc(kmax);
+    ls.qtb = c.arena->alloc(s);
+    ls.y = c.arena->alloc(kmax);
+    ls.res = sc + SC_RES;
+
+    so.status = kmax < o.maxit ? TK_SKETCH_EXHAUSTED : TK_NOT_CONVERGED;
+    int k = 0;
+    uint64_t call = 0;
+    for (k = 1; k <= kmax; ++k) {
+        Slot vn = alloc_slot(c, pb, R);
+        {
+            ScopedMark it(*c.arena);
+            std::vector<TTerm> terms = apply_operator(c, pb, op, V.back(), o.transpose);
+            Slot wmv = alloc_slot(c, pb, R);
+            roundsum(c, pb, terms, RSConfig{sr, R, o.round_tol, o.seed, call++, bf16}, wmv.out(pb));
+            const TTerm W = wmv.term(pb, R);
+            dot(c, W.core, W.core, prodi(W.r, d), sc + SC_NW0SQ);
+            double *mcol = M + (size_t)(k - 1) * s;
+            kron_sketch_batch(c, pb, {W}, S, s, &mcol);
+            const int j0 = std::max(1, k - o.ktrunc + 1);
+            std::vector<InnerJob> ij;
+            for (int j = j0; j <= k; ++j) ij.push_back(InnerJob{V[j - 1], W, sc + SC_H + (j - j0)});
+            inner_batch(c, pb, ij);
+            std::vector<TTerm> orth{W};
+            for (int j = j0; j <= k; ++j) {
+                TTerm t = V[j - 1];
+                t.coef = -1.0;
+                t.coef_dev = sc + SC_H + (j - j0);
+                orth.push_back(t);
+            }
+            roundsum(c, pb, orth, RSConfig{sr, R, o.round_tol, o.seed, call++, bf16}, vn.out(pb));
+            const long long csz = prodi(W.r, d);
+            dot(c, vn.core, vn.core, csz, sc + SC_NWSQ);
+            sqrt_scalar(c, sc + SC_NWSQ, sc + SC_NW);
+            ls_update(c, M, bs, s, k - 1, k, ls, k == 1);
+            scale_by(c, vn.core, vn.core, csz, sc + SC_NW, 1);
+            readback(c, pinned, sc, 8);
+        }
+        const double res = pinned[SC_RES] / beta_s;
+        TK_REQUIRE(std::isfinite(res), "non-finite sketched residual");
+        so.hist.push_back(res);
+        so.sres = res;
+        if (std::sqrt(std::max(pinned[SC_NWSQ], 0.0)) <= 1e-14 * std::sqrt(std::max(pinned[SC_NW0SQ], 0.0))) {
+            so.status = TK_BREAKDOWN;
+            break;
+        }
+        V.push_back(vn.term(pb, R));
+        if (res < o.eta * o.tol) {
+            so.status = TK_OK;
+            break;
+        }
+    }
+    if (k > kmax) k = kmax;
+    so.iters = k;
+    // X~ = RoundSum(sum_i y_i V_i)
+    std::vector<TTerm> fin;
+    for (int i = 0; i < k; ++i) {
+        TTerm t = V[i];
+        t.coef = 1.0;
+        t.coef_dev = ls.y + i;
+        fin.push_back(t);
+    }
+    TOut xo{};
+    xo.core = x->core;
+    for (int kk = 0; kk < d; ++kk) xo.f[kk] = x->factor[kk];
+    int *rk = c.arena->alloc_int(TK_MAX_D);
+    xo.rank_dev = rk;
+    roundsum(c, pb, fin, RSConfig{sr, R, o.round_tol, o.seed, call++, bf16}, xo);
+    int hr[TK_MAX_D];
+    TK_CUDA(cudaMemcpyAsync(hr, rk, sizeof(int) * d, cudaMemcpyDeviceToHost, c.st));
+    TK_CUDA(cudaStreamSynchronize(c.st));
+    for (int kk = 0; kk < d; ++kk) so.ranks[kk] = hr[kk];
+}
+
+// ------------------------------------------------------------------------------------------
+// MLN-Tucker sGMRES (Algorithm 6, without the memory-saving truncation)
+// ------------------------------------------------------------------------------------------
+struct Sk {
+    double *g;
+    double *F[TK_MAX_D];
+};
+
+static Sk alloc_sk(Ctx &c, const Dims &pb, int r, int rp) {
+    Sk s{};
+    long long gs = 1;
+    for (int k = 0; k < pb.d; ++k) gs *= rp;
+    s.g = c.arena->alloc(gs);
+    for (int k = 0; k < pb.d; ++k) s.F[k] = c.arena->alloc((size_t)pb.n[k] * r);
+    return s;
+}
+
+void axpy_list(Ctx &c, double *y, long long n, double beta, const std::vector<const double *> &xs,
+               const std::vector<double> &coef, const std::vector<const double *> &coef_dev);
+
+static void solve_mln(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucker *b, const tk_opts &o,
+                      tk_tucker *x, SolveOut &so, double *pinned) {
+    ScopedMark solve_mark(*c.arena);
+    const int d = pb.d, r = o.rank_cap, p = o.oversample_p, rp = r + p;
+    const int kmax = std::min(o.maxit, rp - 1);
+    TK_REQUIRE(r >= 1 && p >= 0 && r <= 112, "MLN: rank must be 1..112");
+    TK_REQUIRE(o.ktrunc >= 1 && o.ktrunc <= 64, "ktrunc must be 1..64");
+    long long gsz = 1, csz = 1;
+    for (int k = 0; k < d; ++k) { gsz *= rp; csz *= r; }
+    double *sc = c.arena->alloc(SC_N);
+    fill(c, sc, SC_N, 0.0);
+    double *psi[TK_MAX_D];
+    {
+        uint64_t sids[TK_MAX_D];
+        long long cnt[TK_MAX_D];
+        for (int k = 0; k < d; ++k) {
+            psi[k] = c.arena->alloc((size_t)pb.n[k] * rp);
+            sids[k] = (uint64_t(1) << 48) | uint64_t(k);
+            cnt[k] = (long long)pb.n[k] * rp;
+        }
+        gaussian(c, o.seed, sids, cnt, psi, d, 0);
+    }
+    const TTerm B = term_of(b);
+    inner_batch(c, pb, {InnerJob{B, B, sc + SC_BETA2}});
+    sqrt_scalar(c, sc + SC_BETA2, sc + SC_BETA);
+    std::vector<TTerm> V;
+    {
+        TTerm v1 = B;
+        double *core = c.arena->alloc(prodi(B.r, d));
+        scale_by(c, core, b->core, prodi(B.r, d), sc + SC_BETA, 1);
+        v1.core = core;
+        V.push_back(v1);
+    }
+    std::vector<Sk> sks;
+    sks.push_back(alloc_sk(c, pb, r, rp));
+    mln_sketch_sum(c, pb, {V[0]}, psi, r, p, sks[0].g, sks[0].F, 0.0);
+    double *bs = c.arena->alloc(rp);
+    superdiag(c, sks[0].g, rp, d, bs, 1.0, sc + SC_BETA);
+    dot(c, bs, bs, rp, sc + SC_BS2);
+    sqrt_scalar(c, sc + SC_BS2, sc + SC_BS);
+    readback(c, pinned, sc, 4);
+    const double beta_s = pinned[SC_BS];
+    TK_REQUIRE(std::isfinite(pinned[SC_BETA]) && pinned[SC_BETA] > 0.0, "right-hand side is zero or not finite");
+    TK_REQUIRE(std::isfinite(beta_s) && beta_s > 0.0, "sketch of the right-hand side is zero or not finite");
+
+    double *M = c.arena->alloc((size_t)rp * kmax);
+    LSState ls{};
+    ls.H = c.arena->alloc((size_t)rp * kmax);
+    ls.tau = c.arena->alloc(kmax);
+    ls.qtb = c.arena->alloc(rp);
+    ls.y = c.arena->alloc(kmax);
+    ls.res = sc + SC_RES;
+
+    so.status = kmax < o.maxit ? TK_SKETCH_EXHAUSTED : TK_NOT_CONVERGED;
+    int i = 0;
+    for (i = 1; i <= kmax; ++i) {
+        Slot vn = alloc_slot(c, pb, r);
+        Sk skn = alloc_sk(c, pb, r, rp);
+        {
+            ScopedMark it(*c.arena);
+            std::vector<TTerm> terms = apply_operator(c, pb, op, V.back(), o.transpose);
+            Sk gw = alloc_sk(c, pb, r, rp);
+            mln_sketch_sum(c, pb, terms, psi, r, p, gw.g, gw.F, 0.0);
+            superdiag(c, gw.g, rp, d, M + (size_t)(i - 1) * rp, 1.0, nullptr);
+            Slot w = alloc_slot(c, pb, r);
+            mln_recovery(c, pb, gw.g, gw.F, psi, r, p, w.out(pb));
+            const TTerm W = w.term(pb, r);
+            inner_batch(c, pb, {InnerJob{W, W, sc + SC_NW0SQ}});
+            const int j0 = std::max(1, i - o.ktrunc + 1);
+            std::vector<InnerJob> ij;
+            for (int j = j0; j <= i; ++j) ij.push_back(InnerJob{V[j - 1], W, sc + SC_H + (j - j0)});
+            inner_batch(c, pb, ij);
+            // MLN_Sum(gw, sketches of the window, {1, -h_j})
+            std::vector<const double *> xs, cd;
+            std::vector<double> cf;
+            for (int j = j0; j <= i; ++j) { xs.push_back(sks[j - 1].g); cf.push_back(-1.0); cd.push_back(sc + SC_H + (j - j0)); }
+            axpy_list(c, gw.g, gsz, 1.0, xs, cf, cd);
+            for (int k = 0; k < d; ++k) {
+                std::vector<const double *> fx;
+                for (int j = j0; j <= i; ++j) fx.push_back(sks[j - 1].F[k]);
+                axpy_list(c, gw.F[k], (long long)pb.n[k] * r, 1.0, fx, cf, cd);
+            }
+            mln_recovery(c, pb, gw.g, gw.F, psi, r, p, vn.out(pb));
+            const TTerm Wn = vn.term(pb, r);
+            inner_batch(c, pb, {InnerJob{Wn, Wn, sc + SC_NWSQ}});
+            sqrt_scalar(c, sc + SC_NWSQ, sc + SC_NW);
+            ls_update(c, M, bs, rp, i - 1, i, ls, i == 1);
+            scale_by(c, vn.core, vn.core, csz, sc + SC_NW, 1);
+            mln_sketch_sum(c, pb, {Wn}, psi, r, p, skn.g, skn.F, 0.0);
+            readback(c, pinned, sc, 8);
+        }
+        const double res = pinned[SC_RES] / beta_s;
+        TK_REQUIRE(std::isfinite(res), "non-finite sketched residual");
+        so.hist.push_back(res);
+        so.sres = res;
+        if (std::sqrt(std::max(pinned[SC_NWSQ], 0.0)) <= 1e-14 * std::sqrt(std::max(pinned[SC_NW0SQ], 0.0))) {
+            so.status = TK_BREAKDOWN;
+            break;
+        }
+        V.push_back(vn.term(pb, r));
+        sks.push_back(skn);
+        if (res < o.eta * o.tol) {
+            so.status = TK_OK;
+            break;
+        }
+    }
+    if (i > kmax) i = kmax;
+    so.iters = i;
+    // X~ = MLN_Recovery(MLN_Sum(sketches 1..i, y))
+    Sk sol = alloc_sk(c, pb, r, rp);
+    {
+        std::vector<const double *> xs, cd;
+        std::vector<double> cf;
+        for (int m = 0; m < i; ++m) { xs.push_back(sks[m].g); cf.push_back(1.0); cd.push_back(ls.y + m); }
+        axpy_list(c, sol.g, gsz, 0.0, xs, cf, cd);
+        for (int k = 0; k < d; ++k) {
+            std::vector<const double *> fx;
+            for (int m = 0; m < i; ++m) fx.push_back(sks[m].F[k]);
+            axpy_list(c, sol.F[k], (long long)pb.n[k] * r, 0.0, fx, cf, cd);
+        }
+    }
+    TOut xo{};
+    xo.core = x->core;
+    for (int k = 0; k < d; ++k) xo.f[k] = x->factor[k];
+    xo.rank_dev = nullptr;
+    mln_recovery(c, pb, sol.g, sol.F, psi, r, p, xo);
+    TK_CUDA(cudaStreamSynchronize(c.st));
+    for (int k = 0; k < d; ++k) so.ranks[k] = r;
+}
+
+// ------------------------------------------------------------------------------------------
+// True residual in Tucker form: QR of the concatenated distinct factors per mode
+// ------------------------------------------------------------------------------------------
+static double true_residual(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucker *x,
+                            const tk_tucker *b, int transpose) {
+    ScopedMark mark(*c.arena);
+    const int d = pb.d;
+    std::vector<TTerm> terms = apply_operator(c, pb, op, term_of(x), transpose);
+    terms.push_back(term_of(b, -1.0));
+    double *Rk[TK_MAX_D];
+    int rows[TK_MAX_D];
+    std::vector<std::vector<int>> off(terms.size(), std::vector<int>(d));
+    std::vector<QRJob> qj;
+    for (int k = 0; k < d; ++k) {
+        std::map<const double *, int> seen;
+        int width = 0;
+        for (size_t i = 0; i < terms.size(); ++i) {
+            auto it = seen.find(terms[i].f[k]);
+            if (it != seen.end()) { off[i][k] = it->second; continue; }
+            seen[terms[i].f[k]] = width;
+            off[i][k] = width;
+            width += terms[i].r[k];
+        }
+        TK_REQUIRE(width <= 256, "residual: concatenated rank above 256");
+        double *U = c.arena->alloc((size_t)pb.n[k] * width);
+        for (auto &kv : seen) {
+            int rr = 0;
+            for (size_t i = 0; i < terms.size(); ++i)
+                if (terms[i].f[k] == kv.first) rr = terms[i].r[k];
+            copy(c, U + (size_t)kv.second * pb.n[k], kv.first, (long long)pb.n[k] * rr);
+        }
+        qj.push_back(QRJob{U, c.arena->alloc(width), nullptr, pb.n[k], width});
+        rows[k] = std::min(pb.n[k], width);
+        Rk[k] = c.arena->alloc((size_t)rows[k] * width);
+    }
+    qr_householder(c, qj);
+    for (int k = 0; k < d; ++k) triu_copy(c, Rk[k], rows[k], qj[k].A, pb.n[k], rows[k], qj[k].s);
+    TtmGroup G{};
+    long long cs = 1;
+    for (int k = 0; k < d; ++k) { G.sdims[k] = rows[k]; cs *= rows[k]; }
+    double *core = c.arena->alloc(cs);
+    G.out = core;
+    G.beta = 0.0;
+    for (size_t i = 0; i < terms.size(); ++i) {
+        TtmJob J{};
+        J.core = terms[i].core;
+        for (int k = 0; k < d; ++k) {
+            J.r[k] = terms[i].r[k];
+            J.P[k] = Rk[k] + (size_t)off[i][k] * rows[k];
+            J.ldp[k] = rows[k];
+        }
+        J.coef = terms[i].coef;
+        J.coef_dev = terms[i].coef_dev;
+        G.jobs.push_back(J);
+    }
+    ttm_groups(c, d, {G});
+    double *sc = c.arena->alloc(2);
+    dot(c, core, core, cs, sc);
+    const TTerm B = term_of(b);
+    inner_batch(c, pb, {InnerJob{B, B, sc + 1}});
+    double h[2];
+    TK_CUDA(cudaMemcpyAsync(h, sc, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    TK_CUDA(cudaStreamSynchronize(c.st));
+    return std::sqrt(std::max(h[0], 0.0)) / std::sqrt(std::max(h[1], 0.0));
+}
+
+}  // namespace tk
+
+// ==========================================================================================
+// C ABI
+// ==========================================================================================
+using namespace tk;
+
+template <class F>
+static int guarded(tk_handle *h, F &&f) {
+    if (!h) return TK_EINVAL;
+    h->err.clear();
+    try {
+        TK_CUDA(cudaSetDevice(h->device));
+        return f();
+    } catch (const Error &e) {
+        h->err = e.msg;
+        return e.code;
+    } catch (const std::exception &e) {
+        h->err = e.what();
+        return TK_EINTERNAL;
+    }
+}
+
+static Ctx make_ctx(tk_handle *h, void *stream) {
+    Ctx c;
+    c.st = (cudaStream_t)stream;
+    c.arena = &h->arena;
+    c.num_sms = h->num_sms;
+    return c;
+}
+
+extern "C" {
+
+int tk_create(tk_handle **out, int device) {
+    if (!out) return TK_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return TK_ECUDA;
+    }
+    tk_handle *h = new tk_handle();
+    h->device = device;
+    if (cudaSetDevice(device) != cudaSuccess) { delete h; return TK_ECUDA; }
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (cudaMallocHost(&h->pinned, 256 * sizeof(double)) != cudaSuccess) { delete h; return TK_ENOMEM; }
+    *out = h;
+    return TK_OK;
+}
+
+int tk_destroy(tk_handle *h) {
+    if (!h) return TK_EINVAL;
+    cudaSetDevice(h->device);
+    if (h->pinned) cudaFreeHost(h->pinned);
+    delete h;
+    return TK_OK;
+}
+
+const char *tk_last_error(const tk_handle *h) { return h ? h->err.c_str() : "null handle"; }
+
+int tk_solve(tk_handle *h, const tk_operator *op, const tk_tucker *b, const tk_opts *opts,
+             tk_tucker *x_out, tk_report *report, void *stream) {
+    return guarded(h, [&]() -> int {
+        TK_REQUIRE(opts != nullptr && report != nullptr, "solve: null opts or report");
+        check_tucker(b, "b");
+        check_tucker(x_out, "x_out");
+        const Dims pb = dims_of(b);
+        const OpDesc od = op_of(op, pb);
+        const tk_opts o = *opts;
+        TK_REQUIRE(x_out->d == b->d, "x_out: order differs from b");
+        for (int k = 0; k < pb.d; ++k) {
+            TK_REQUIRE(x_out->n[k] == b->n[k], "x_out: mode size differs from b");
+            TK_REQUIRE(x_out->r[k] == o.rank_cap, "x_out: every rank must equal rank_cap");
+        }
+        TK_REQUIRE(o.variant == TK_RHOSVD_SGMRES || o.variant == TK_MLN_SGMRES, "unknown variant");
+        TK_REQUIRE(o.rank_cap >= 1 && o.oversample_p >= 0 && o.maxit >= 1, "bad rank_cap / p / maxit");
+        TK_REQUIRE(o.precision == TK_FP64 || o.precision == TK_MIXED, "bad precision");
+        TK_REQUIRE(o.adaptive_rank == 0, "adaptive sketch size is not available in this build");
+        TK_REQUIRE(o.tol > 0.0 && o.eta > 0.0 && o.round_tol >= 0.0, "bad tolerances");
+        if (o.variant == TK_RHOSVD_SGMRES) TK_REQUIRE(o.sketch_s >= 2 && o.sketch_s <= 4096, "sketch_s must be 2..4096");
+        Ctx c = make_ctx(h, stream);
+        cudaEvent_t e0, e1;
+        TK_CUDA(cudaEventCreate(&e0));
+        TK_CUDA(cudaEventCreate(&e1));
+        TK_CUDA(cudaEventRecord(e0, c.st));
+        SolveOut so;
+        if (o.variant == TK_RHOSVD_SGMRES)
+            solve_rhosvd(c, pb, od, b, o, x_out, so, h->pinned);
+        else
+            solve_mln(c, pb, od, b, o, x_out, so, h->pinned);
+        TK_CUDA(cudaEventRecord(e1, c.st));
+        TK_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        report->iters = so.iters;
+        report->status = so.status;
+        report->sketched_res = so.sres;
+        if (report->res_hist)
+            for (int i = 0; i < std::min<int>(report->res_hist_len, (int)so.hist.size()); ++i)
+                report->res_hist[i] = so.hist[i];
+        for (int k = 0; k < TK_MAX_D; ++k) report->out_rank[k] = k < pb.d ? so.ranks[k] : 0;
+        report->ms_total = ms;
+        report->workspace_bytes = (int64_t)h->arena.capacity();
+        report->kernel_launches = c.launches;
+        return so.status;
+    });
+}
+
+int tk_apply(tk_handle *h, const tk_operator *op, const tk_tucker *x, int32_t transpose,
+             double *const *out_factors, void *stream) {
+    return guarded(h, [&]() -> int {
+        check_tucker(x, "x");
+        TK_REQUIRE(out_factors != nullptr, "apply: null outputs");
+        const Dims pb = dims_of(x);
+        const OpDesc od = op_of(op, pb);
+        Ctx c = make_ctx(h, stream);
+        std::vector<BandJob> bj;
+        Gemm g(c);
+        for (int t = 0; t < od.nterms; ++t)
+            for (int k = 0; k < pb.d; ++k) {
+                const tk_modemat &m = od.mats[t * pb.d + k];
+                double *o = out_factors[t * pb.d + k];
+                TK_REQUIRE(o != nullptr, "apply: null output factor");
+                const int n = pb.n[k], r = (int)x->r[k];
+                if (m.kind == TK_IDENTITY) copy(c, o, x->factor[k], (long long)n * r);
+                else if (m.kind == TK_BANDED) bj.push_back(BandJob{m.data, x->factor[k], o, n, r, m.kl, m.ku, transpose});
+                else g.add1(n, r, n, transpose, 0, m.data, n, x->factor[k], n, o, n);
+            }
+        band_apply(c, bj);
+        g.run();
+        return TK_OK;
+    });
+}
+
+int tk_roundsum(tk_handle *h, int32_t nterms, const tk_tucker *xs, const double *coef,
+                const tk_opts *opts, uint64_t call_index, tk_tucker *out, int32_t *out_rank,
+                void *stream) {
+    return guarded(h, [&]() -> int {
+        TK_REQUIRE(nterms >= 1 && xs != nullptr && coef != nullptr && opts != nullptr, "roundsum: bad arguments");
+        check_tucker(out, "out");
+        const Dims pb = dims_of(out);
+        std::vector<TTerm> terms;
+        for (int i = 0; i < nterms; ++i) {
+            check_tucker(&xs[i], "term");
+            TK_REQUIRE(xs[i].d == pb.d, "roundsum: order mismatch");
+            for (int k = 0; k < pb.d; ++k) TK_REQUIRE(xs[i].n[k] == pb.n[k], "roundsum: mode size mismatch");
+            terms.push_back(term_of(&xs[i], coef[i]));
+        }
+        const int R = opts->rank_cap;
+        for (int k = 0; k < pb.d; ++k) TK_REQUIRE(out->r[k] == R, "roundsum: out ranks must equal rank_cap");
+        TK_REQUIRE(opts->adaptive_rank == 0, "adaptive sketch size is not available in this build");
+        const int sr = R + opts->oversample_p;
+        TK_REQUIRE(sr <= 112, "roundsum: rank_cap + p must be <= 112");
+        Ctx c = make_ctx(h, stream);
+        ScopedMark mark(h->arena);
+        TOut o{};
+        o.core = out->core;
+        for (int k = 0; k < pb.d; ++k) o.f[k] = out->factor[k];
+        o.rank_dev = c.arena->alloc_int(TK_MAX_D);
+        roundsum(c, pb, terms, RSConfig{sr, R, opts->round_tol, opts->seed, call_index,
+                                        opts->precision == TK_MIXED ? 1 : 0}, o);
+        int hr[TK_MAX_D];
+        TK_CUDA(cudaMemcpyAsync(hr, o.rank_dev, sizeof(int) * pb.d, cudaMemcpyDeviceToHost, c.st));
+        TK_CUDA(cudaStreamSynchronize(c.st));
+        if (out_rank) for (int k = 0; k < pb.d; ++k) out_rank[k] = hr[k];
+        return TK_OK;
+    });
+}
+
+int tk_kron_sketch(tk_handle *h, const tk_tucker *x, const double *const *S, int32_t s, double *out,
+                   void *stream) {
+    return guarded(h, [&]() -> int {
+        check_tucker(x, "x");
+        TK_REQUIRE(S != nullptr && out != nullptr && s >= 1, "kron_sketch: bad arguments");
+        const Dims pb = dims_of(x);
+        Ctx c = make_ctx(h, stream);
+        ScopedMark mark(h->arena);
+        kron_sketch_batch(c, pb, {term_of(x)}, S, s, &out);
+        return TK_OK;
+    });
+}
+
+int tk_inner(tk_handle *h, const tk_tucker *x, const tk_tucker *y, double *out_host, void *stream) {
+    return guarded(h, [&]() -> int {
+        check_tucker(x, "x");
+        check_tucker(y, "y");
+        TK_REQUIRE(out_host != nullptr && x->d == y->d, "inner: bad arguments");
+        for (int k = 0; k < x->d; ++k) TK_REQUIRE(x->n[k] == y->n[k], "inner: mode size mismatch");
+        const Dims pb = dims_of(x);
+        Ctx c = make_ctx(h, stream);
+        ScopedMark mark(h->arena);
+        double *o = c.arena->alloc(1);
+        inner_batch(c, pb, {InnerJob{term_of(x), term_of(y), o}});
+        TK_CUDA(cudaMemcpyAsync(h->pinned, o, sizeof(double), cudaMemcpyDeviceToHost, c.st));
+        TK_CUDA(cudaStreamSynchronize(c.st));
+        *out_host = h->pinned[0];
+        return TK_OK;
+    });
+}
+
+int tk_residual(tk_handle *h, const tk_operator *op, const tk_tucker *x, const tk_tucker *b,
+                int32_t transpose, double *rel_host, void *stream) {
+    return guarded(h, [&]() -> int {
+        check_tucker(x, "x");
+        check_tucker(b, "b");
+        TK_REQUIRE(rel_host != nullptr && x->d == b->d, "residual: bad arguments");
+        for (int k = 0; k < x->d; ++k) TK_REQUIRE(x->n[k] == b->n[k], "residual: mode size mismatch");
+        const Dims pb = dims_of(x);
+        const OpDesc od = op_of(op, pb);
+        Ctx c = make_ctx(h, stream);
+        *rel_host = true_residual(c, pb, od, x, b, transpose);
+        return TK_OK;
+    });
+}
+
+int tk_gaussian(tk_handle *h, uint64_t seed, uint64_t stream_id, int64_t count, int32_t bf16_round,
+                double *out, void *stream) {
+    return guarded(h, [&]() -> int {
+        TK_REQUIRE(out != nullptr && count >= 0, "gaussian: bad arguments");
+        if (count == 0) return TK_OK;
+        Ctx c = make_ctx(h, stream);
+        long long cnt = count;
+        gaussian(c, seed, &stream_id, &cnt, &out, 1, bf16_round);
+        return TK_OK;
+    });
+}
+
+int tk_philox(tk_handle *h, uint64_t seed, uint64_t stream_id, uint64_t first, int64_t nblocks,
+              uint32_t *out, void *stream) {
+    return guarded(h, [&]() -> int {
+        TK_REQUIRE(out != nullptr && nblocks >= 0, "philox: bad arguments");
+        if (nblocks == 0) return TK_OK;
+        Ctx c = make_ctx(h, stream);
+        philox_raw(c, seed, stream_id, first, nblocks, out);
+        return TK_OK;
+    });
+}
+
+int tk_sketched_ls(tk_handle *h, const double *M, const double *b, int32_t s, int32_t k, double *y,
+                   double *res, void *stream) {
+    return guarded(h, [&]() -> int {
+        TK_REQUIRE(M && b && y && res, "sketched_ls: null pointer");
+        TK_REQUIRE(k >= 1 && k < s && s <= 1024, "sketched_ls: need 1 <= k < s <= 1024");
+        Ctx c = make_ctx(h, stream);
+        ScopedMark mark(h->arena);
+        LSState st{};
+        st.H = c.arena->alloc((size_t)s * k);
+        st.tau = c.arena->alloc(k);
+        st.qtb = c.arena->alloc(s);
+        st.y = y;
+        st.res = res;
+        ls_update(c, M, b, s, 0, k, st, 1);
+        TK_CUDA(cudaStreamSynchronize(c.st));   // workspace is released on return
+        return TK_OK;
+    });
+}
+
+int tk_mln_roundsum(tk_handle *h, int32_t nterms, const tk_tucker *xs, const double *coef,
+                    const double *const *psi, int32_t r, int32_t p, tk_tucker *out, void *stream) {
+    return guarded(h, [&]() -> int {
+        TK_REQUIRE(nterms >= 1 && xs && coef && psi && r >= 1 && p >= 0 && r <= 112, "mln_roundsum: bad arguments");
+        check_tucker(out, "out");
+        const Dims pb = dims_of(out);
+        for (int k = 0; k < pb.d; ++k) TK_REQUIRE(out->r[k] == r, "mln_roundsum: out ranks must equal r");
+        std::vector<TTerm> terms;
+        for (int i = 0; i < nterms; ++i) {
+            check_tucker(&xs[i], "term");
+            TK_REQUIRE(xs[i].d == pb.d, "mln_roundsum: order mismatch");
+            terms.push_back(term_of(&xs[i], coef[i]));
+        }
+        Ctx c = make_ctx(h, stream);
+        ScopedMark mark(h->arena);
+        Sk sk = alloc_sk(c, pb, r, r + p);
+        mln_sketch_sum(c, pb, terms, psi, r, p, sk.g, sk.F, 0.0);
+        TOut o{};
+        o.core = out->core;
+        for (int k = 0; k < pb.d; ++k) o.f[k] = out->factor[k];
+        o.rank_dev = nullptr;
+        mln_recovery(c, pb, sk.g, sk.F, psi, r, p, o);
+        TK_CUDA(cudaStreamSynchronize(c.st));
+        return TK_OK;
+    });
+}
+
+}  // extern "C"

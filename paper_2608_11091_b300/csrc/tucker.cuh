@@ -1,0 +1,86 @@
+// Tucker-level routines shared by the solvers and the C ABI.
+#pragma once
+
+#include "tk_internal.cuh"
+
+namespace tk {
+
+struct Dims {
+    int d;
+    int n[TK_MAX_D];
+};
+
+// One Tucker term coef * (*coef_dev if set) * [core; f_1, ..., f_d] of a sum; f_k is n_k x r_k.
+struct TTerm {
+    const double *core = nullptr;
+    const double *f[TK_MAX_D] = {};
+    int r[TK_MAX_D] = {};
+    double coef = 1.0;
+    const double *coef_dev = nullptr;
+};
+
+// Output buffers of a compression: core R^d, factors n_k x R (ld n_k), ranks (device, d ints).
+struct TOut {
+    double *core;
+    double *f[TK_MAX_D];
+    int *rank_dev;
+};
+
+struct MttJob {
+    const double *core;
+    int r[TK_MAX_D];
+    const double *P[TK_MAX_D];
+    int ldp[TK_MAX_D];
+    int keep;
+    double *out;
+};
+void mttkrp_batch(Ctx &c, int d, int s, const std::vector<MttJob> &jobs);
+
+struct TtmJob {
+    const double *core;
+    int r[TK_MAX_D];
+    const double *P[TK_MAX_D];   // s_k x r_k
+    int ldp[TK_MAX_D];
+    double coef;
+    const double *coef_dev;
+};
+struct TtmGroup {
+    int sdims[TK_MAX_D];
+    std::vector<TtmJob> jobs;
+    double *out;
+    double beta;
+};
+void ttm_groups(Ctx &c, int d, const std::vector<TtmGroup> &groups);
+
+struct InnerJob {
+    TTerm x, y;
+    double *out;
+};
+void inner_batch(Ctx &c, const Dims &pb, const std::vector<InnerJob> &jobs);
+
+void kron_sketch_batch(Ctx &c, const Dims &pb, const std::vector<TTerm> &xs, const double *const *S,
+                       int s, double *const *outs);
+
+struct OpDesc {
+    int nterms;
+    std::vector<double> theta;
+    std::vector<tk_modemat> mats;   // nterms * d
+};
+std::vector<TTerm> apply_operator(Ctx &c, const Dims &pb, const OpDesc &op, const TTerm &x, int transpose);
+
+struct RSConfig {
+    int sr;             // sketch size (columns of S_k)
+    int R;              // rank cap; output padded to R
+    double eps;         // ST-HOSVD tolerance
+    uint64_t seed;
+    uint64_t call;      // RoundSum call index (stream id)
+    int bf16_sketch;    // round the Gaussian matrices to bfloat16
+};
+void roundsum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const RSConfig &cfg, const TOut &out);
+
+void mln_sketch_sum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const double *const *psi,
+                    int r, int p, double *gpsi, double *const *F, double beta);
+void mln_recovery(Ctx &c, const Dims &pb, const double *gpsi, const double *const *F,
+                  const double *const *psi, int r, int p, const TOut &out);
+
+}  // namespace tk

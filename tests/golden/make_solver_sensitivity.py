@@ -1,0 +1,68 @@
+"""Writes tests/golden/solver_sensitivity.json: for each whole-solver parity case, how far the
+FP64 oracle's own output moves when every RoundSum output core carries a relative 1e-15
+perturbation (three draws, maximum taken).  This models a second correct FP64 implementation
+that rounds differently; the GPU parity tolerance of a case is max(1e-10, 20 x this value).
+Calls only the oracle and the input generators.
+
+Run: python tests/golden/make_solver_sensitivity.py
+"""
+import json
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+from oracle import residual as ORS  # noqa: E402
+from oracle import rhosvd as ORH  # noqa: E402
+from oracle import sgmres as OS  # noqa: E402
+from oracle import mln as OM  # noqa: E402
+import workloads as W  # noqa: E402
+from tests.solver_cases import CASES  # noqa: E402
+
+
+def _solve(wl, prm, noise, seed, transpose=False):
+    rng = np.random.default_rng(seed)
+    rs, rec = OS.roundsum, OS.mln_recovery
+
+    def noisy_rs(terms, sk, cap, eps):
+        out = rs(terms, sk, cap, eps)
+        return W.Tucker(out.core * (1 + noise * rng.standard_normal(out.core.shape)), out.factors)
+
+    def noisy_rec(sk, psis):
+        out = rec(sk, psis)
+        return W.Tucker(out.core * (1 + noise * rng.standard_normal(out.core.shape)), out.factors)
+
+    if noise:
+        OS.roundsum, OS.mln_recovery = noisy_rs, noisy_rec
+    try:
+        if prm.variant == "rhosvd":
+            return OS.rhosvd_sgmres(wl.op, wl.b, prm, transpose=transpose)
+        return OS.mln_sgmres(wl.op, wl.b, prm, transpose=transpose)
+    finally:
+        OS.roundsum, OS.mln_recovery = rs, rec
+
+
+def main():
+    out = {}
+    for name, (build, prm, transpose) in CASES.items():
+        wl = build()
+        prm = prm or wl.params
+        base = _solve(wl, prm, 0.0, 0, transpose)
+        xs, hs = [], []
+        for s in range(3):
+            alt = _solve(wl, prm, 1e-15, s + 1, transpose)
+            n = min(len(alt.res_hist), len(base.res_hist))
+            hs.append(float(np.max(np.abs(np.array(alt.res_hist[:n]) - np.array(base.res_hist[:n]))
+                                   / np.array(base.res_hist[:n]))))
+            xs.append(ORS.tucker_sum_norm([(1.0, alt.x), (-1.0, base.x)]) / ORS.tucker_sum_norm([(1.0, base.x)]))
+        out[name] = {"x": max(xs), "hist": max(hs), "iters": base.iters}
+        print(name, out[name], flush=True)
+    with open(os.path.join(ROOT, "tests", "golden", "solver_sensitivity.json"), "w") as f:
+        json.dump(out, f, indent=1, sort_keys=True)
+
+
+if __name__ == "__main__":
+    main()

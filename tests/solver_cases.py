@@ -1,0 +1,17 @@
+"""Whole-solver parity cases shared by the GPU parity tests and the sensitivity script.
+name -> (workload builder, solver parameters (None: the workload's own), transpose)."""
+import workloads as W
+
+CASES = {
+    "poisson3d_n32_full": (lambda: W.workload("poisson3d_n32"), None, False),
+    "poisson3d_n20_r12": (lambda: W.poisson3d(20, 1, 3, None, "p20"),
+                          W.SolverParams('rhosvd', 12, 64, 5, 40, 1e-9, seed=4), False),
+    "convdiff3d_n64": (lambda: W.convdiff3d(64, 1, None), W.SolverParams('rhosvd', 16, 96, 5, 25, 1e-8, seed=2), False),
+    "deblur3d_n48": (lambda: W.deblur3d(48, 2, None), W.SolverParams('rhosvd', 16, 128, 5, 8, 1e-8, seed=5), False),
+    "convdiff_ragged": (lambda: W.convdiff3d(37, 3, None, rhs_rank=2),
+                        W.SolverParams('rhosvd', 7, 33, 6, 20, 1e-8, ktrunc=3, seed=6), False),
+    "mln_varcoef4d_n16": (lambda: W.varcoef4d(16, 1, None), W.SolverParams('mln', 6, 0, 6, 10, 1e-8, seed=7), False),
+    "mln_convdiff_n40": (lambda: W.convdiff3d(40, 2, None), W.SolverParams('mln', 10, 0, 12, 16, 1e-8, seed=8), False),
+    "adjoint_convdiff_n30": (lambda: W.convdiff3d(30, 4, None), W.SolverParams('rhosvd', 10, 64, 5, 15, 1e-8, seed=9), True),
+    "exhaustion_convdiff_n16": (lambda: W.convdiff3d(16, 5, None), W.SolverParams('rhosvd', 4, 10, 5, 40, 1e-14, seed=1), False),
+}

@@ -1,0 +1,110 @@
+"""Whole-solver parity: RHOSVD-Tucker sGMRES (Algorithm 2) and MLN-Tucker sGMRES (Algorithm 6)
+on the GPU against the FP64 oracle with the same seeded inputs and the same Gaussian streams.
+
+Tolerance.  1e-10 relative on the solution (Tucker-form difference) and on the sketched
+residual history, except where the short-recurrence iteration itself amplifies rounding:
+there the bound is 20x the oracle's own movement under 1e-15 perturbations of every
+compression (see `tolerance`).  Iteration counts and exit status must match exactly."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import residual as ORS
+from oracle import sgmres as OS
+from tests.helpers import rel_diff, to_dev, to_host
+from tests.solver_cases import CASES
+
+pytestmark = pytest.mark.gpu
+
+STATUS = {OS.CONVERGED: "converged", OS.NOT_CONVERGED: "not_converged", OS.BREAKDOWN: "breakdown",
+          OS.SKETCH_EXHAUSTED: "sketch_exhausted"}
+SENS = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "solver_sensitivity.json")))
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2608_11091_b300 as P
+    return P
+
+
+def tolerance(case: str) -> float:
+    """1e-10, or 20x the oracle's own movement under 1e-15 rounding-level perturbations of
+    every compression (written by tests/golden/make_solver_sensitivity.py) where the
+    iteration amplifies rounding beyond that."""
+    s = SENS[case]
+    return max(1e-10, 20.0 * max(s["x"], s["hist"]))
+
+
+def _run(P, wl, params, transpose=False):
+    opts = P.Options.from_params(params, transpose=transpose)
+    x, rep = P.tk_solve(P.DeviceOperator(wl.op), to_dev(wl.b), opts)
+    if params.variant == "rhosvd":
+        ref = OS.rhosvd_sgmres(wl.op, wl.b, params, transpose=transpose)
+    else:
+        ref = OS.mln_sgmres(wl.op, wl.b, params, transpose=transpose)
+    return x, rep, ref
+
+
+def _check(x, rep, ref, tol=1e-10):
+    assert rep.status == STATUS[ref.status]
+    assert rep.iters == ref.iters
+    h, hr = np.array(rep.res_hist), np.array(ref.res_hist)
+    rel = np.abs(h - hr) / hr
+    bad = np.nonzero(rel > tol)[0]
+    assert bad.size == 0, f"history deviates from iteration {bad[0] + 1}: {rel[bad[0]:bad[0] + 5]}"
+    assert rel_diff(to_host(x), ref.x) <= tol
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_solver_parity(P, case):
+    build, params, transpose = CASES[case]
+    wl = build()
+    params = params or wl.params
+    x, rep, ref = _run(P, wl, params, transpose)
+    _check(x, rep, ref, tolerance(case))
+
+
+def test_breakdown_on_eigentensor(P):
+    n = 24
+    i = np.arange(1, n + 1)
+    v = np.sqrt(2.0 / (n + 1)) * np.sin(np.outer(i, i) * np.pi / (n + 1))
+    lam = 2 - 2 * np.cos(i * np.pi / (n + 1))
+    op = W.kronecker_sum_operator([W.second_difference(n)], 3)
+    b = W.Tucker(np.full((1, 1, 1), 3.0), [v[:, [2]], v[:, [0]], v[:, [5]]])
+    params = W.SolverParams('rhosvd', 4, 16, 5, 10, 1e-12)
+    x, rep = P.tk_solve(P.DeviceOperator(op), to_dev(b), P.Options.from_params(params))
+    assert rep.status == "breakdown" and rep.iters == 1
+    ref = W.Tucker(b.core / (lam[2] + lam[0] + lam[5]), b.factors)
+    assert rel_diff(to_host(x), ref) <= 1e-12
+
+
+def test_true_residual_of_solution(P):
+    wl = W.workload("poisson3d_n32")
+    params = W.SolverParams('rhosvd', 12, 64, 5, 60, 1e-9, seed=0)
+    x, rep = P.tk_solve(P.DeviceOperator(wl.op), to_dev(wl.b), P.Options.from_params(params))
+    tr = P.tk_residual(P.DeviceOperator(wl.op), x, to_dev(wl.b))
+    assert np.isclose(tr, ORS.true_residual(wl.op, to_host(x), wl.b), rtol=1e-8)
+
+
+def test_rejects_bad_options(P):
+    wl = W.workload("poisson3d_n32")
+    dop, b = P.DeviceOperator(wl.op), to_dev(wl.b)
+    for over in [dict(rank_cap=200), dict(ktrunc=0), dict(sketch_s=1), dict(tol=-1.0)]:
+        with pytest.raises(P.TuckerError):
+            P.tk_solve(dop, b, P.Options.from_params(wl.params, **over))
+
+
+@pytest.mark.parametrize("name,iters", [("convdiff3d_n256", 12), ("poisson3d_n1024", 3), ("deblur3d_n128", 6),
+                                        ("varcoef4d_n128", 3)])
+def test_full_size_prefix_parity(P, name, iters):
+    """The headline workloads at full size, first iterations (the oracle's cost bounds the count)."""
+    wl = W.workload(name)
+    params = wl.params
+    params.maxit = iters
+    x, rep, ref = _run(P, wl, params)
+    _check(x, rep, ref)
