@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Throughput of Tucker-format sketched GMRES on B300.
+
+One step = one complete RHOSVD-Tucker sGMRES solve (Algorithm 2) of the workload: every
+iteration's Tucker matvec, RoundSum recompression, Kronecker sketch, short-recurrence
+orthogonalisation and sketched least-squares update, then the final RoundSum assembly.
+The metric is Krylov iterations per second (higher is better); the timed steps run with the
+inputs resident in HBM and L2 flushed (256 MiB write) between steps.  `e2e` repeats the
+steps through the public API with the right-hand side and the operator copied from pinned
+host memory and the solution copied back inside the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+--impl reference times the FP64 CPU oracle on the same workload (a bounded sample of
+iterations per step).  Under torchrun every rank runs independent replicas (different
+seeds); there is no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DEFAULT_WORKLOAD = "convdiff3d_n256"
+METRIC = "Krylov iterations/s of RHOSVD-Tucker sGMRES"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-extras", action="store_true", help="skip the cpu_baseline and secondary workloads")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------------
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------------------------------------
+def oracle_timing(name: str, seed: int, budget_s: float):
+    """The FP64 oracle as it stands, on this host: Krylov iterations/s over a bounded sample."""
+    import workloads as W
+    from oracle import sgmres as OS
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([int(i.get("num_threads", 1)) for i in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count() or 1
+    wl = W.workload(name, seed=seed)
+    prm = wl.params
+    iters, t0 = 0, time.perf_counter()
+    runs = 0
+    while True:
+        per = min(prm.maxit, 12)
+        r = (OS.rhosvd_sgmres if prm.variant == "rhosvd" else OS.mln_sgmres)(wl.op, wl.b, prm, maxit=per)
+        iters += r.iters
+        runs += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": iters / dt, "unit": "iters/s", "cores": cores, "kind": "oracle",
+            "sample": f"{runs} solve(s) of {name} truncated at {min(prm.maxit, 12)} iterations "
+                      f"(numpy FP64, {iters} iterations in {dt:.1f} s)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    import workloads as W  # noqa: F401
+    vals = []
+    budget = 8.0
+    for i in range(args.warmup + args.steps):
+        r = oracle_timing(args.workload, 0, budget if i >= args.warmup else 1.0)
+        if i >= args.warmup:
+            vals.append(r)
+    value = statistics.median([v["value"] for v in vals])
+    line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * budget, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": args.workload, "solver": "RHOSVD-Tucker sGMRES (Algorithm 2)",
+                       "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": vals[0]["cores"], "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------------------------------
+def tucker_bytes(t) -> int:
+    return 8 * (t.core.numel() + sum(u.numel() for u in t.factors))
+
+
+def run_native(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_2608_11091_b300 as P
+    import workloads as W
+
+    name = args.workload
+    wl = W.workload(name, seed=rank)
+    prm = wl.params
+    dop = P.DeviceOperator(wl.op)
+    b = P.DeviceTucker.from_numpy(wl.b.core, wl.b.factors)
+    opts = P.Options.from_params(prm)
+    x = P.DeviceTucker.empty(b.n, [opts.rank_cap] * b.d)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        P.tk_solve(dop, b, opts, x=x)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    evs = []
+    iters = launches = 0
+    statuses = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, rep = P.tk_solve(dop, b, opts, x=x)
+        e1.record(stream)
+        evs.append((e0, e1))
+        iters += rep.iters
+        launches += rep.kernel_launches
+        statuses.append(rep.status)
+    barrier()
+    clocks = sampler.stop()
+    ms = sum(a.elapsed_time(bb) for a, bb in evs)
+    t_local = ms / 1000.0
+    if ws > 1:
+        tt = torch.tensor([t_local, float(iters)], dtype=torch.float64, device="cuda")
+        tmax = tt.clone()
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+        tsum = tt.clone()
+        torch.distributed.all_reduce(tsum, op=torch.distributed.ReduceOp.SUM)
+        t_all, it_all = tmax[0].item(), tsum[1].item()
+    else:
+        t_all, it_all = t_local, float(iters)
+    value = it_all / t_all
+
+    # ---------------- e2e through the public API with host buffers
+    host_b = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+              for a in [np.asfortranarray(wl.b.core).ravel(order='F')] + [f.ravel(order='F') for f in wl.b.factors]]
+    dev_b = [b.core] + b.factors
+    host_ops = []
+    for key, t in dop._keep[0].items():
+        host_ops.append((torch.from_numpy(np.ascontiguousarray(t.cpu().numpy().ravel(order='F'))).pin_memory(), t))
+    host_x = [torch.empty(t.numel(), dtype=torch.float64).pin_memory() for t in [x.core] + x.factors]
+    h2d = sum(h.numel() * 8 for h in host_b) + sum(h.numel() * 8 for h, _ in host_ops)
+    d2h = sum(h.numel() * 8 for h in host_x)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    it_e2e = 0
+    e0.record(stream)
+    for i in range(args.steps):
+        for h, d in zip(host_b, dev_b):
+            d.permute(*reversed(range(d.dim()))).reshape(-1).copy_(h, non_blocking=True)
+        for h, d in host_ops:
+            d.permute(*reversed(range(d.dim()))).reshape(-1).copy_(h, non_blocking=True)
+        _, rep = P.tk_solve(dop, b, opts, x=x)
+        it_e2e += rep.iters
+        for h, d in zip(host_x, [x.core] + x.factors):
+            h.copy_(d.permute(*reversed(range(d.dim()))).reshape(-1), non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_t = e0.elapsed_time(e1) / 1000.0
+    e2e_val = it_e2e / e2e_t
+    if ws > 1:
+        tt = torch.tensor([e2e_t, float(it_e2e)], dtype=torch.float64, device="cuda")
+        tmax, tsum = tt.clone(), tt.clone()
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(tsum, op=torch.distributed.ReduceOp.SUM)
+        e2e_val = tsum[1].item() / tmax[0].item()
+
+    # ---------------- per-kernel device time (library event profiler), one more solve
+    P.tk_profile(True)
+    P.tk_profile_report()
+    _, prep = P.tk_solve(dop, b, opts, x=x)
+    prof = P.tk_profile_report()
+    P.tk_profile(False)
+    total_k = sum(v[1] for v in prof.values())
+    kernels = {k: {"launches": n, "ms": round(m, 4), "share": round(m / total_k, 4) if total_k else None,
+                   "tflops": round(f / (m * 1e-3) / 1e12, 4) if f > 0 and m > 0 else None}
+               for k, (n, m, f) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    roofline = roofline_from_profile(prof, wl, opts, prep)
+
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras = secondary(P, W, torch)
+
+    if rank == 0:
+        cpu = None if args.no_extras else oracle_timing(name, 0, 10.0)
+        line = {
+            "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name, "solver": "RHOSVD-Tucker sGMRES (Algorithm 2)",
+                       "n": wl.b.n, "rhs_rank": wl.b.r, "rank_cap": prm.rank_cap, "sketch_s": prm.sketch_s,
+                       "oversample_p": prm.oversample_p, "ktrunc": prm.ktrunc, "maxit": prm.maxit,
+                       "iters_per_step": iters / args.steps, "status": statuses[-1],
+                       "operator_terms": wl.op.nterms, "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "clocks": clocks,
+            "gpu_launches": launches,
+            "e2e": {"value": e2e_val, "unit": "iters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "roofline": roofline,
+            "kernels": kernels,
+            "cpu_baseline": cpu,
+            "extras": extras,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except Exception:
+        return {}
+
+
+FP64_PEAK_TFLOPS = 1.25   # B300 FP64 nominal (148 SMs x DFMA rate at 2032 MHz); 1.13 measured by a DFMA loop
+
+
+def roofline_from_profile(prof, wl, opts, rep):
+    """Dominant kernel (by device time) with its algorithmic FP64 rate against the FP64 ALU peak."""
+    if not prof:
+        return None
+    name, (n, ms, fl) = max(prof.items(), key=lambda kv: kv[1][1])
+    total = sum(v[1] for v in prof.values())
+    out = {"kernel": name, "launches": n, "avg_us": round(1000.0 * ms / max(n, 1), 3),
+           "share": round(ms / total, 4) if total else None, "traffic": None}
+    if fl > 0:
+        achieved = fl / (ms * 1e-3) / 1e12
+        out.update({"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "flops_per_launch": fl / max(n, 1),
+                    "peak_source": "FP64 nominal (148 SMs x 2 DFMA/clk x 2032 MHz); measured DFMA loop 1.13"})
+    else:
+        out.update({"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": None,
+                    "note": "iterative kernel: no algorithmic flop count"})
+    return out
+
+
+def secondary(P, W, torch):
+    """Other workloads of the method, one solve each (reported, not the headline)."""
+    out = {}
+    for name in ["poisson3d_n32", "deblur3d_n128", "varcoef4d_n128", "poisson3d_n1024"]:
+        wl = W.workload(name)
+        prm = wl.params
+        if name == "poisson3d_n1024":
+            prm.maxit = 10
+        dop = P.DeviceOperator(wl.op)
+        b = P.DeviceTucker.from_numpy(wl.b.core, wl.b.factors)
+        opts = P.Options.from_params(prm)
+        P.tk_solve(dop, b, opts)                     # warm-up (workspace, module load)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, rep = P.tk_solve(dop, b, opts)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        tr = P.tk_residual(dop, x, b)
+        out[name] = {"variant": prm.variant, "iters": rep.iters, "status": rep.status, "seconds": round(dt, 4),
+                     "iters_per_s": round(rep.iters / dt, 2), "sketched_res": rep.sketched_res,
+                     "true_rel_residual": tr, "time_to_1e-6_s": round(dt, 4) if tr <= 1e-6 else None}
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

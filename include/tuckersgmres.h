@@ -119,6 +119,17 @@ int tk_destroy(tk_handle *h);
 /* Message of the last error on this handle (valid until the next call). */
 const char *tk_last_error(const tk_handle *h);
 
+/* tk_profile: enable (1) or disable (0) per-kernel device timing on this handle.  When
+ * enabled, every kernel the library launches is bracketed by two CUDA events recorded on the
+ * launching stream (a few microseconds of host overhead per launch).  The paper has no
+ * counterpart; this is measurement plumbing. */
+int tk_profile(tk_handle *h, int32_t enable);
+/* tk_profile_report: per-kernel totals since the last report, one line per kernel name:
+ * "<name> <launches> <total_ms> <algorithmic_flops>\n" (flops counted from the shapes for the
+ * GEMM and QR kernels, 0 for the others); resets the totals.  Synchronizes on the recorded events.
+ * The returned string is owned by the handle and valid until the next call on it. */
+const char *tk_profile_report(tk_handle *h);
+
 /* tk_solve: RHOSVD-Tucker sGMRES (Algorithm 2) or MLN-Tucker sGMRES (Algorithm 6) for
  * L(X) = B (or L^T(X) = B when opts->transpose).  x_out is caller-allocated with
  * x_out->r[k] = rank_cap for every mode (core rank_cap^d, factors n_k x rank_cap); the

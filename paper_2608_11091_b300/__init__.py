@@ -1,13 +1,11 @@
 """Tucker-format sketched GMRES (RHOSVD-Tucker sGMRES, MLN-Tucker sGMRES) for B300 (sm_103a).
 
 The solvers run in the CUDA library libtuckersgmres.so (C ABI: include/tuckersgmres.h);
-this package is its thin Python binding.  Importing it loads the library and fails loudly
-when it has not been built.
+this package is its thin Python binding.  The library is loaded on first use and loading
+fails loudly when it has not been built; nothing here computes on the CPU.
 """
 from ._lib import EXPORTS, LIB_PATH, load  # noqa: F401
-
-load()
-
-from .api import (DeviceOperator, DeviceTucker, Handle, Options, Report, TuckerError,  # noqa: E402,F401
+from .api import (DeviceOperator, DeviceTucker, Handle, Options, Report, TuckerError,  # noqa: F401
                   fortran_empty, handle, to_fortran, tk_apply, tk_gaussian, tk_inner, tk_kron_sketch,
-                  tk_mln_roundsum, tk_philox, tk_residual, tk_roundsum, tk_sketched_ls, tk_solve)
+                  tk_mln_roundsum, tk_philox, tk_profile, tk_profile_report, tk_residual, tk_roundsum,
+                  tk_sketched_ls, tk_solve)

@@ -250,6 +250,23 @@ def tk_solve(op: DeviceOperator, b: DeviceTucker, opts: Options, x: Optional[Dev
     return x, r
 
 
+def tk_profile(enable: bool, device: Optional[int] = None):
+    """Enable or disable per-kernel CUDA-event timing inside the library."""
+    h = handle(device)
+    h.check(h.lib.tk_profile(h.h, int(enable)), "tk_profile")
+
+
+def tk_profile_report(device: Optional[int] = None) -> Dict[str, tuple]:
+    """{kernel name: (launches, total ms, algorithmic FP64 flops)} since the last report (then reset)."""
+    h = handle(device)
+    txt = h.lib.tk_profile_report(h.h).decode()
+    out = {}
+    for line in txt.strip().splitlines():
+        name, n, ms, fl = line.split()
+        out[name] = (int(n), float(ms), float(fl))
+    return out
+
+
 def tk_apply(op: DeviceOperator, x: DeviceTucker, transpose: bool = False, stream=None) -> List[List[torch.Tensor]]:
     """Factors A_k^(t) U_k of every term (Eq. (1.2)); the terms share x's core scaled by theta_t."""
     h = handle()

@@ -156,6 +156,10 @@ void Gemm::flush_group(std::vector<GProb> &probs, int ksplit) {
             tiles += g.p[j].tiles_m * g.p[j].tiles_n * g.p[j].batch;
         }
         g.total = tiles;
+        double flops = 0.0;
+        for (int j = 0; j < g.nprob; ++j)
+            for (int q = 0; q < g.p[j].nseg; ++q)
+                flops += 2.0 * g.p[j].M * (double)g.p[j].N * g.p[j].seg[q].K * g.p[j].batch;
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3((unsigned)(tiles * ksplit), 1, 1);
         cfg.blockDim = dim3(256, 1, 1);
@@ -168,8 +172,9 @@ void Gemm::flush_group(std::vector<GProb> &probs, int ksplit) {
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
+        c_.pre_launch();
         TK_CUDA(cudaLaunchKernelEx(&cfg, k_gemm_group, g, ksplit));
-        c_.check_launch("gemm");
+        c_.check_launch("gemm", flops);
     }
     probs.clear();
 }

@@ -18,7 +18,7 @@ namespace cg = cooperative_groups;
 namespace tk {
 
 constexpr int QR_MAXS = 256;
-constexpr int SVD_MAXS = 112;
+constexpr int SVD_MAXS = 96;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -62,124 +62,203 @@ struct QRJobs {
     QRJob j[TK_MAX_D];
 };
 
-__global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs) {
+// One reflector per step with a single cluster-wide reduction: each CTA contributes, over its
+// own rows, ||x_below||^2, the pivot alpha = A[j,j] (owner only), D_c = x^T A[j:, c] and the
+// pivot row P_c = A[j, c] (owner only) for every trailing column c.  With beta, tau from
+// LAPACK's dlarfg and v = (x - beta e_j) / (alpha - beta) (v_j = 1):
+//   w_c = v^T A[j:, c] = P_c + (D_c - alpha P_c) / (alpha - beta),  A[i, c] -= tau v_i w_c.
+// Q (optional) is accumulated backwards, Q = H_0 ... H_{k-1} [I; 0], one reduction per step.
+// Rows live in shared memory when they fit (SMEM = true), else in global memory.
+template <bool SMEM>
+__global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs, int rb_cap) {
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks();
     const int q = (int)cl.block_rank();
     const QRJob &J = jobs.j[blockIdx.y];
     const int m = J.m, s = J.s, kmax = min(m, s);
     const int rb = (m + C - 1) / C;
-    const int r0 = min(m, q * rb), r1 = min(m, r0 + rb);
-    double *A = J.A;
-
-    __shared__ double red[2][QR_MAXS + 2];
-    __shared__ double wsum[QR_MAXS + 2];
+    const int r0 = min(m, q * rb), r1 = min(m, r0 + rb), nr = r1 - r0;
+    extern __shared__ double dyn[];
+    double *Al = dyn;                              // nr x s, ld rb_cap
+    double *Ql = dyn + (size_t)rb_cap * s;         // nr x s, ld rb_cap
+    __shared__ double red[2][2 + 3 * QR_MAXS];
+    __shared__ double wv[QR_MAXS + 2];
     __shared__ double taus[QR_MAXS];
-    __shared__ double scratch[40];
-    __shared__ double bc[4];
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    int buf = 0;
-    for (int j = 0; j < kmax; ++j) {
-        double ps = 0.0;
-        for (int i = max(r0, j + 1) + tid; i < r1; i += blockDim.x) {
-            const double v = A[i + (long long)j * m];
-            ps = fma(v, v, ps);
+    __shared__ double nrm[QR_MAXS];
+    __shared__ int permv[QR_MAXS];
+    __shared__ double bc[6];
+    __shared__ int pivot;
+    const bool piv = J.perm != nullptr;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5, nt = blockDim.x;
+    auto A = [&](int i, int c) -> double & {
+        return SMEM ? Al[(i - r0) + (size_t)c * rb_cap] : J.A[i + (long long)c * m];
+    };
+    auto Q = [&](int i, int c) -> double & {
+        return SMEM ? Ql[(i - r0) + (size_t)c * rb_cap] : J.Q[i + (long long)c * m];
+    };
+    if (SMEM)
+        for (int e = tid; e < nr * s; e += nt) {
+            const int i = r0 + e % nr, c = e / nr;
+            A(i, c) = J.A[i + (long long)c * m];
         }
-        ps = block_sum(ps, scratch);
-        if (tid == 0) {
-            red[buf][0] = ps;
-            red[buf][1] = (j >= r0 && j < r1) ? A[j + (long long)j * m] : 0.0;
+    __syncthreads();
+    int buf = 0;
+    if (piv) {
+        // initial column norms
+        for (int c = tid; c < s; c += nt) permv[c] = c;
+        double *rd = red[buf];
+        for (int c = warp; c < s; c += nw) {
+            double p = 0.0;
+            for (int i = r0 + lane; i < r1; i += 32) { const double x = A(i, c); p = fma(x, x, p); }
+            p = warp_sum(p);
+            if (lane == 0) rd[c] = p;
+        }
+        cl.sync();
+        for (int c = tid; c < s; c += nt) {
+            double t = 0.0;
+            for (int qq = 0; qq < C; ++qq) t += cl.map_shared_rank(rd, qq)[c];
+            nrm[c] = t;
+        }
+        buf ^= 1;
+        __syncthreads();
+    }
+    for (int j = 0; j < kmax; ++j) {
+        const int nc = s - j - 1;
+        if (piv) {
+            if (tid == 0) {
+                int p = j;
+                for (int c = j + 1; c < s; ++c)
+                    if (nrm[c] > nrm[p]) p = c;
+                pivot = p;
+            }
+            __syncthreads();
+            const int p = pivot;
+            if (p != j) {
+                for (int i = r0 + tid; i < r1; i += nt) {
+                    const double t = A(i, j);
+                    A(i, j) = A(i, p);
+                    A(i, p) = t;
+                }
+                if (tid == 0) {
+                    const double t = nrm[j]; nrm[j] = nrm[p]; nrm[p] = t;
+                    const int u = permv[j]; permv[j] = permv[p]; permv[p] = u;
+                }
+            }
+            __syncthreads();
+        }
+        double *rd = red[buf];
+        const bool owner = (j >= r0 && j < r1);
+        for (int c = j + warp; c < s; c += nw) {
+            double p = 0.0, pn = 0.0;
+            if (c == j) {
+                for (int i = max(r0, j + 1) + lane; i < r1; i += 32) { const double x = A(i, j); p = fma(x, x, p); }
+            } else {
+                for (int i = max(r0, j) + lane; i < r1; i += 32) {
+                    const double y = A(i, c);
+                    p = fma(A(i, j), y, p);
+                    if (piv && i > j) pn = fma(y, y, pn);
+                }
+            }
+            p = warp_sum(p);
+            if (piv && c != j) pn = warp_sum(pn);
+            if (lane == 0) {
+                if (c == j) { rd[0] = p; rd[1] = owner ? A(j, j) : 0.0; }
+                else {
+                    rd[2 + (c - j - 1)] = p;
+                    rd[2 + nc + (c - j - 1)] = owner ? A(j, c) : 0.0;
+                    if (piv) rd[2 + 2 * nc + (c - j - 1)] = pn;
+                }
+            }
         }
         cl.sync();
         if (tid == 0) {
             double s2 = 0.0, al = 0.0;
             for (int qq = 0; qq < C; ++qq) {
-                s2 += cl.map_shared_rank(&red[buf][0], qq)[0];
-                al += cl.map_shared_rank(&red[buf][1], qq)[0];
+                const double *rq = cl.map_shared_rank(rd, qq);
+                s2 += rq[0];
+                al += rq[1];
             }
             double tau, beta, scal;
             householder(al, s2, tau, beta, scal);
-            bc[0] = tau;
-            bc[1] = scal;
-            bc[2] = beta;
+            bc[0] = tau; bc[1] = scal; bc[2] = beta; bc[3] = al; bc[4] = s2;
             taus[j] = tau;
         }
-        buf ^= 1;
         __syncthreads();
-        const double tau = bc[0], scal = bc[1], beta = bc[2];
-        for (int i = max(r0, j + 1) + tid; i < r1; i += blockDim.x) A[i + (long long)j * m] *= scal;
-        if (tid == 0 && j >= r0 && j < r1) A[j + (long long)j * m] = beta;
-        __syncthreads();
-        if (tau == 0.0) continue;   // uniform across the cluster
-        const int ib = max(r0, j);
-        for (int c = j + 1 + warp; c < s; c += nw) {
-            double p = 0.0;
-            for (int i = ib + lane; i < r1; i += 32) {
-                const double v = (i == j) ? 1.0 : A[i + (long long)j * m];
-                p = fma(v, A[i + (long long)c * m], p);
+        const double tau = bc[0], scal = bc[1], beta = bc[2], al = bc[3], s2 = bc[4];
+        for (int c = j + 1 + tid; c < s; c += nt) {
+            double D = 0.0, Pc = 0.0, Nc = 0.0;
+            for (int qq = 0; qq < C; ++qq) {
+                const double *rq = cl.map_shared_rank(rd, qq);
+                D += rq[2 + (c - j - 1)];
+                Pc += rq[2 + nc + (c - j - 1)];
+                if (piv) Nc += rq[2 + 2 * nc + (c - j - 1)];
             }
-            p = warp_sum(p);
-            if (lane == 0) red[buf][c] = p;
-        }
-        cl.sync();
-        for (int c = j + 1 + tid; c < s; c += blockDim.x) {
-            double w = 0.0;
-            for (int qq = 0; qq < C; ++qq) w += cl.map_shared_rank(&red[buf][c], qq)[0];
-            wsum[c] = w * tau;
+            const double w = tau != 0.0 ? tau * (Pc + (D - al * Pc) * scal) : 0.0;
+            wv[c] = w;
+            if (piv) {
+                // norm of rows > j of column c after the reflector (exact from this step's sums)
+                const double post = Nc - 2.0 * w * (D - al * Pc) * scal + w * w * s2 * scal * scal;
+                nrm[c] = fmax(post, 0.0);
+            }
         }
         buf ^= 1;
         __syncthreads();
-        const int nrows = r1 - ib, ncols = s - j - 1;
-        if (nrows > 0) {
-            for (int e = tid; e < nrows * ncols; e += blockDim.x) {
+        const int ib = max(r0, j), nrows = r1 - ib;
+        if (tau != 0.0 && nrows > 0) {
+            for (int e = tid; e < nrows * nc; e += nt) {
                 const int i = ib + e % nrows, c = j + 1 + e / nrows;
-                const double v = (i == j) ? 1.0 : A[i + (long long)j * m];
-                A[i + (long long)c * m] -= v * wsum[c];
+                const double v = (i == j) ? 1.0 : A(i, j) * scal;
+                A(i, c) -= v * wv[c];
             }
         }
+        __syncthreads();
+        for (int i = max(r0, j + 1) + tid; i < r1; i += nt) A(i, j) *= scal;
+        if (tid == 0 && owner) A(j, j) = beta;
         __syncthreads();
     }
     if (J.tau && q == 0)
-        for (int j = tid; j < kmax; j += blockDim.x) J.tau[j] = taus[j];
+        for (int j = tid; j < kmax; j += nt) J.tau[j] = taus[j];
+    if (piv && q == 0)
+        for (int c = tid; c < s; c += nt) J.perm[c] = permv[c];
     if (J.Q) {
-        double *Q = J.Q;
-        const int nr = r1 - r0;
-        for (int e = tid; e < nr * s; e += blockDim.x) {
+        for (int e = tid; e < nr * s; e += nt) {
             const int i = r0 + e % nr, c = e / nr;
-            Q[i + (long long)c * m] = (i == c) ? 1.0 : 0.0;
+            Q(i, c) = (i == c) ? 1.0 : 0.0;
         }
         __syncthreads();
         for (int j = kmax - 1; j >= 0; --j) {
             const double tau = taus[j];
-            if (tau == 0.0) continue;
+            if (tau == 0.0) continue;   // uniform across the cluster
+            double *rd = red[buf];
             const int ib = max(r0, j);
             for (int c = j + warp; c < s; c += nw) {
                 double p = 0.0;
-                for (int i = ib + lane; i < r1; i += 32) {
-                    const double v = (i == j) ? 1.0 : A[i + (long long)j * m];
-                    p = fma(v, Q[i + (long long)c * m], p);
-                }
+                for (int i = ib + lane; i < r1; i += 32) p = fma((i == j) ? 1.0 : A(i, j), Q(i, c), p);
                 p = warp_sum(p);
-                if (lane == 0) red[buf][c] = p;
+                if (lane == 0) rd[c - j] = p;
             }
             cl.sync();
-            for (int c = j + tid; c < s; c += blockDim.x) {
+            for (int c = j + tid; c < s; c += nt) {
                 double w = 0.0;
-                for (int qq = 0; qq < C; ++qq) w += cl.map_shared_rank(&red[buf][c], qq)[0];
-                wsum[c] = w * tau;
+                for (int qq = 0; qq < C; ++qq) w += cl.map_shared_rank(rd, qq)[c - j];
+                wv[c] = w * tau;
             }
             buf ^= 1;
             __syncthreads();
             const int nrows = r1 - ib, ncols = s - j;
-            if (nrows > 0) {
-                for (int e = tid; e < nrows * ncols; e += blockDim.x) {
+            if (nrows > 0)
+                for (int e = tid; e < nrows * ncols; e += nt) {
                     const int i = ib + e % nrows, c = j + e / nrows;
-                    const double v = (i == j) ? 1.0 : A[i + (long long)j * m];
-                    Q[i + (long long)c * m] -= v * wsum[c];
+                    Q(i, c) -= ((i == j) ? 1.0 : A(i, j)) * wv[c];
                 }
-            }
             __syncthreads();
+        }
+    }
+    if (SMEM) {
+        for (int e = tid; e < nr * s; e += nt) {
+            const int i = r0 + e % nr, c = e / nr;
+            J.A[i + (long long)c * m] = A(i, c);
+            if (J.Q) J.Q[i + (long long)c * m] = Q(i, c);
         }
     }
     cl.sync();   // keep this CTA's shared memory alive until every peer finished reading it
@@ -187,31 +266,67 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs)
 
 void qr_householder(Ctx &c, const std::vector<QRJob> &jobs) {
     if (jobs.empty()) return;
+    static bool attr_set = false;
+    if (!attr_set) {
+        TK_CUDA(cudaFuncSetAttribute(k_qr<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        TK_CUDA(cudaFuncSetAttribute(k_qr<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        TK_CUDA(cudaFuncSetAttribute(k_qr<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr_set = true;
+    }
     for (size_t base = 0; base < jobs.size(); base += TK_MAX_D) {
         QRJobs J{};
         J.n = (int)std::min<size_t>(TK_MAX_D, jobs.size() - base);
-        int mmax = 0;
+        int mmax = 0, smax = 0;
+        bool wantq = false;
         for (int i = 0; i < J.n; ++i) {
             J.j[i] = jobs[base + i];
             TK_REQUIRE(J.j[i].s <= QR_MAXS, "QR: more than 256 columns");
             mmax = std::max(mmax, J.j[i].m);
+            smax = std::max(smax, J.j[i].s);
+            wantq = wantq || J.j[i].Q != nullptr;
         }
-        // cluster size: enough rows per CTA to amortise the per-step cluster barriers
-        int C = 1;
-        while (C < 8 && mmax / (C * 2) >= 32) C *= 2;
+        // cluster of up to 16 CTAs with >= 48 rows each, shrunk until the device can place it
+        int C = std::max(1, std::min(16, (mmax + 47) / 48));
         cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3((unsigned)C, (unsigned)J.n, 1);
-        cfg.blockDim = dim3(256, 1, 1);
-        cfg.stream = c.st;
         cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = C;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        TK_CUDA(cudaLaunchKernelEx(&cfg, k_qr, J));
-        c.check_launch("qr");
+        int rb = 0;
+        bool use_smem = false;
+        for (;;) {
+            rb = (mmax + C - 1) / C;
+            const size_t smem = (size_t)rb * smax * sizeof(double) * (wantq ? 2 : 1);
+            use_smem = smem <= 200 * 1024;
+            cfg = cudaLaunchConfig_t{};
+            cfg.gridDim = dim3((unsigned)C, (unsigned)J.n, 1);
+            cfg.blockDim = dim3(256, 1, 1);
+            cfg.dynamicSmemBytes = use_smem ? smem : 0;
+            cfg.stream = c.st;
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = C;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            if (C == 1) break;
+            int nclusters = 0;
+            const cudaError_t e = use_smem
+                ? cudaOccupancyMaxActiveClusters(&nclusters, k_qr<true>, &cfg)
+                : cudaOccupancyMaxActiveClusters(&nclusters, k_qr<false>, &cfg);
+            if (e == cudaSuccess && nclusters > 0) break;
+            cudaGetLastError();
+            C = C > 8 ? 8 : C / 2;
+        }
+        c.pre_launch();
+        if (use_smem)
+            TK_CUDA(cudaLaunchKernelEx(&cfg, k_qr<true>, J, rb));
+        else
+            TK_CUDA(cudaLaunchKernelEx(&cfg, k_qr<false>, J, rb));
+        double flops = 0.0;   // Householder: 2 m s^2 - 2 s^3 / 3 for R, the same again for Q
+        for (int i = 0; i < J.n; ++i) {
+            const double m = J.j[i].m, s = std::min(J.j[i].m, J.j[i].s);
+            const double f = 2.0 * m * s * s - 2.0 * s * s * s / 3.0;
+            flops += J.j[i].Q ? 2.0 * f : f;
+        }
+        c.check_launch("qr", flops);
     }
 }
 
@@ -225,64 +340,190 @@ struct SVDJobs {
     double rcond;
 };
 
-__global__ void __launch_bounds__(512) k_svd(const __grid_constant__ SVDJobs jobs) {
-    extern __shared__ double sm[];
-    const SVDJob &J = jobs.j[blockIdx.x];
-    const int s = J.s;
-    double *A = sm;
-    double *V = sm + s * s;
-    __shared__ double sig[SVD_MAXS];
-    __shared__ int order[SVD_MAXS];
-    __shared__ int rotated;
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One-sided (Hestenes) Jacobi sweeps on the columns of A (s x s, column-major in shared
+// memory), accumulating the rotations into V.  Pairs follow a round-robin tournament so each
+// round's s/2 rotations are independent; one warp per pair.  Column norms are carried in
+// `nrm2` (recomputed every sweep, updated by Rutishauser's formulas after each rotation), so a
+// pair costs one dot product.  A pair is rotated when |a_p . a_q| > tol ||a_p|| ||a_q|| and
+// both columns are above the negligible level `floor2` (squared norm) of this precision:
+// columns below it cannot be resolved further and do not change the result beyond it.
+// Sweeps stop when a sweep rotates nothing.
+// Sweep counts of the last k_svd launch (per block: FP32 phase, FP64 phase); diagnostics.
+__device__ int g_svd_sweeps[2 * TK_MAX_D];
+
+template <typename T, bool ACC>
+__device__ int jacobi_sweeps(T *A, T *V, T *nrm2, int s, T tol, T floor2, int max_sweeps, int *flag) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    for (int e = tid; e < s * s; e += blockDim.x) {
-        const int i = e % s, c = e / s;
-        A[e] = (i <= c && i < J.ldr) ? J.R[i + (long long)c * J.ldr] : 0.0;
-        V[e] = (i == c) ? 1.0 : 0.0;
-    }
     const int sp = s + (s & 1);
-    const double tol = 1e-15;
-    __syncthreads();
-    for (int sweep = 0; sweep < 40 && sp > 1; ++sweep) {
-        if (tid == 0) rotated = 0;
+    int done = 0;
+    for (int sweep = 0; sweep < max_sweeps && sp > 1; ++sweep) {
+        ++done;
+        for (int c = warp; c < s; c += nw) {
+            T t = 0;
+            for (int i = lane; i < s; i += 32) t = fma(A[i + c * s], A[i + c * s], t);
+            t = warp_sum_t(t);
+            if (lane == 0) nrm2[c] = t;
+        }
+        if (tid == 0) *flag = 0;
         __syncthreads();
         for (int round = 0; round < sp - 1; ++round) {
             for (int pr = warp; pr < sp / 2; pr += nw) {
-                int p, qq;
-                if (pr == 0) { p = round; qq = sp - 1; }
-                else { p = (round + pr) % (sp - 1); qq = (round - pr + (sp - 1)) % (sp - 1); }
-                if (p >= s || qq >= s) continue;
-                if (p > qq) { const int t = p; p = qq; qq = t; }
-                double al = 0.0, be = 0.0, ga = 0.0;
-                for (int i = lane; i < s; i += 32) {
-                    const double a = A[i + p * s], b = A[i + qq * s];
-                    al = fma(a, a, al);
-                    be = fma(b, b, be);
-                    ga = fma(a, b, ga);
-                }
-                al = warp_sum(al);
-                be = warp_sum(be);
-                ga = warp_sum(ga);
-                if (ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
-                    const double zeta = (be - al) / (2.0 * ga);
-                    const double t = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
-                    const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
-                    for (int i = lane; i < s; i += 32) {
-                        const double a = A[i + p * s], b = A[i + qq * s];
-                        A[i + p * s] = cs * a - sn * b;
-                        A[i + qq * s] = sn * a + cs * b;
-                        const double va = V[i + p * s], vb = V[i + qq * s];
-                        V[i + p * s] = cs * va - sn * vb;
-                        V[i + qq * s] = sn * va + cs * vb;
+                int p, q;
+                if (pr == 0) { p = round; q = sp - 1; }
+                else { p = (round + pr) % (sp - 1); q = (round - pr + (sp - 1)) % (sp - 1); }
+                if (p >= s || q >= s) continue;
+                if (p > q) { const int t = p; p = q; q = t; }
+                const T al = nrm2[p], be = nrm2[q];
+                if (al <= floor2 || be <= floor2) continue;
+                T ga = 0;
+                for (int i = lane; i < s; i += 32) ga = fma(A[i + p * s], A[i + q * s], ga);
+                ga = warp_sum_t(ga);   // identical in every lane (butterfly)
+                if (ga != T(0) && ga * ga > tol * tol * al * be) {
+                    // rotation parameters on one lane (FP64 sqrt/div are long DFMA sequences
+                    // here), broadcast to the warp
+                    T t = 0, cs = 0, sn = 0;
+                    if (lane == 0) {
+                        const T zeta = (be - al) / (T(2) * ga);
+                        t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+                        cs = T(1) / sqrt(T(1) + t * t);
+                        sn = cs * t;
                     }
-                    if (lane == 0) rotated = 1;
+                    t = __shfl_sync(0xffffffffu, t, 0);
+                    cs = __shfl_sync(0xffffffffu, cs, 0);
+                    sn = __shfl_sync(0xffffffffu, sn, 0);
+                    for (int i = lane; i < s; i += 32) {
+                        const T a = A[i + p * s], b = A[i + q * s];
+                        A[i + p * s] = cs * a - sn * b;
+                        A[i + q * s] = sn * a + cs * b;
+                        if (ACC) {
+                            const T va = V[i + p * s], vb = V[i + q * s];
+                            V[i + p * s] = cs * va - sn * vb;
+                            V[i + q * s] = sn * va + cs * vb;
+                        }
+                    }
+                    if (lane == 0) {
+                        nrm2[p] = al - t * ga;
+                        nrm2[q] = be + t * ga;
+                        *flag = 1;
+                    }
                 }
             }
             __syncthreads();
         }
-        const int any = rotated;
+        const int any = *flag;
         __syncthreads();
         if (!any) break;
+    }
+    return done;
+}
+
+// SVD of a small square matrix R (upper triangle read) to FP64 accuracy.  Two modes:
+//
+// ST-HOSVD (J.perm set): R comes from the column-pivoted QR C^T P = Q R of a core unfolding, so
+// R is row-graded and one-sided Jacobi on the columns of R^T converges in a few sweeps with
+// high relative accuracy (Drmac and Veselic's preconditioned Jacobi).  R^T V = U S needs no
+// accumulation of V: the left singular vectors of C = P R^T Q^T are P times the normalised
+// final columns U.  Pure FP64.
+//
+// Pseudo-inverse (jobs.pinv set; R from an unpivoted QR): the bulk of the Jacobi work runs in
+// FP32 (~60x the FP64 rate on this part): FP32 sweeps on R V32; two Newton-Schulz steps
+// V <- V (3 I - V^T V) / 2 in FP64 restore V's orthonormality (error e -> 1.5 e^2); FP64
+// sweeps on A = R V finish.  R^+ = sum_c V[:,c] A[:,c]^T / sigma_c^2 over sigma_c > rcond sigma_max.
+// Shared memory: three s x s FP64 regions X | Y | Z (X holds the FP32 A and V in phase 1).
+__global__ void __launch_bounds__(1024) k_svd(const __grid_constant__ SVDJobs jobs) {
+    extern __shared__ double sm[];
+    const SVDJob &J = jobs.j[blockIdx.x];
+    const int s = J.s, ss = s * s;
+    double *X = sm, *Y = sm + ss, *Z = sm + 2 * ss;
+    __shared__ double sig[SVD_MAXS];
+    __shared__ int order[SVD_MAXS];
+    __shared__ int flag;
+    __shared__ double scratch[40];
+    __shared__ double nrm64[SVD_MAXS];
+    __shared__ float nrm32[SVD_MAXS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int nt = blockDim.x;
+    auto Rat = [&](int i, int c) -> double {
+        return (i <= c && i < J.ldr) ? J.R[i + (long long)c * J.ldr] : 0.0;
+    };
+    const bool graded = J.perm != nullptr;
+    double *A, *V = nullptr;
+    double floor2;
+    if (graded) {
+        A = Y;
+        for (int e = tid; e < ss; e += nt) A[e] = Rat(e / s, e % s);    // A = R^T
+        double fro = 0.0;
+        for (int e = tid; e < ss; e += nt) fro = fma(A[e], A[e], fro);
+        fro = block_sum(fro, scratch);
+        floor2 = fro * (double)s * s * 0x1p-106;
+        const int n64 = jacobi_sweeps<double, false>(A, nullptr, nrm64, s, 4.0 * sqrt((double)s) * 0x1p-53, floor2, 30, &flag);
+        if (tid == 0) { g_svd_sweeps[2 * blockIdx.x] = 0; g_svd_sweeps[2 * blockIdx.x + 1] = n64; }
+    } else {
+        float *A32 = reinterpret_cast<float *>(X), *V32 = A32 + ss;
+        double mx = 0.0;
+        for (int e = tid; e < ss; e += nt) mx = fmax(mx, fabs(Rat(e % s, e / s)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) scratch[warp] = mx;
+        __syncthreads();
+        mx = 0.0;
+        for (int w = 0; w < nw; ++w) mx = fmax(mx, scratch[w]);
+        __syncthreads();
+        const double inv = mx > 0.0 ? 1.0 / mx : 1.0;
+        for (int e = tid; e < ss; e += nt) {
+            A32[e] = (float)(Rat(e % s, e / s) * inv);
+            V32[e] = (e % s == e / s) ? 1.f : 0.f;
+        }
+        __syncthreads();
+        double fro = 0.0;
+        for (int e = tid; e < ss; e += nt) { const double v = (double)A32[e]; fro = fma(v, v, fro); }
+        fro = block_sum(fro, scratch);
+        const int n32 = jacobi_sweeps<float, true>(A32, V32, nrm32, s, 8.0f * sqrtf((float)s) * 0x1p-24f, (float)(fro * 0x1p-40), 20, &flag);
+        if (tid == 0) g_svd_sweeps[2 * blockIdx.x] = n32;
+        // V = double(V32) into Y, then two Newton-Schulz steps: Z = (3 I - Y^T Y) / 2, X = Y Z
+        for (int e = tid; e < ss; e += nt) Y[e] = (double)V32[e];
+        __syncthreads();
+        for (int it = 0; it < 2; ++it) {
+            for (int e = tid; e < ss; e += nt) {
+                const int i = e % s, j = e / s;
+                double t = 0.0;
+                for (int k = 0; k < s; ++k) t = fma(Y[k + i * s], Y[k + j * s], t);
+                Z[e] = ((i == j) ? 1.5 : 0.0) - 0.5 * t;
+            }
+            __syncthreads();
+            for (int e = tid; e < ss; e += nt) {
+                const int i = e % s, j = e / s;
+                double t = 0.0;
+                for (int k = 0; k < s; ++k) t = fma(Y[i + k * s], Z[k + j * s], t);
+                X[e] = t;
+            }
+            __syncthreads();
+            if (it == 0) {
+                for (int e = tid; e < ss; e += nt) Y[e] = X[e];
+                __syncthreads();
+            }
+        }
+        // A = R V into Y (R upper triangular), then FP64 sweeps with V = X accumulated
+        for (int e = tid; e < ss; e += nt) {
+            const int i = e % s, j = e / s;
+            double t = 0.0;
+            for (int k = i; k < s; ++k) t = fma(Rat(i, k), X[k + j * s], t);
+            Y[e] = t;
+        }
+        __syncthreads();
+        A = Y;
+        V = X;
+        const double fro_r = fro * mx * mx;
+        floor2 = fro_r * (double)s * s * 0x1p-106;
+        const int n64 = jacobi_sweeps<double, true>(A, V, nrm64, s, 4.0 * sqrt((double)s) * 0x1p-53, floor2, 16, &flag);
+        if (tid == 0) g_svd_sweeps[2 * blockIdx.x + 1] = n64;
     }
     // singular values and descending order (ties by index)
     for (int c = warp; c < s; c += nw) {
@@ -292,7 +533,7 @@ __global__ void __launch_bounds__(512) k_svd(const __grid_constant__ SVDJobs job
         if (lane == 0) sig[c] = sqrt(t);
     }
     __syncthreads();
-    for (int c = tid; c < s; c += blockDim.x) {
+    for (int c = tid; c < s; c += nt) {
         int pos = 0;
         for (int o = 0; o < s; ++o)
             if (sig[o] > sig[c] || (sig[o] == sig[c] && o < c)) ++pos;
@@ -306,7 +547,6 @@ __global__ void __launch_bounds__(512) k_svd(const __grid_constant__ SVDJobs job
             const double thr = J.eps2_over_d * (*J.normsq);
             double tail = 0.0;
             int rr = s;
-            // smallest rr with sum_{pos >= rr} sig^2 <= thr
             for (int pos = s - 1; pos >= 1; --pos) {
                 const double v = sig[order[pos]];
                 tail += v * v;
@@ -321,18 +561,33 @@ __global__ void __launch_bounds__(512) k_svd(const __grid_constant__ SVDJobs job
     __syncthreads();
     const int r = kept;
     if (J.sigma)
-        for (int c = tid; c < s; c += blockDim.x) J.sigma[c] = sig[order[c]];
-    if (J.W)
-        for (int e = tid; e < s * J.wcols; e += blockDim.x) {
-            const int i = e % s, c = e / s;
-            J.W[e] = (c < r) ? V[i + order[c] * s] : 0.0;
+        for (int c = tid; c < s; c += nt) J.sigma[c] = sig[order[c]];
+    if (J.W) {
+        if (graded) {
+            // W[perm[i], c] = U[i, order[c]], U = A / sigma; columns at rounding level dropped
+            const double fl = sqrt(floor2);
+            for (int e = tid; e < s * J.wcols; e += nt) {
+                const int i = e % s, c = e / s;
+                double v = 0.0;
+                if (c < r) {
+                    const int o = order[c];
+                    if (sig[o] > fl) v = A[i + o * s] / sig[o];
+                }
+                J.W[J.perm[i] + (long long)c * s] = v;
+            }
+        } else {
+            for (int e = tid; e < s * J.wcols; e += nt) {
+                const int i = e % s, c = e / s;
+                J.W[e] = (c < r) ? V[i + order[c] * s] : 0.0;
+            }
         }
+    }
     double *P = jobs.pinv[blockIdx.x];
-    if (P) {
-        // R = U S V^T with U S = A (final);  R^+ = sum_c V[:,c] A[:,c]^T / sig_c^2
+    if (P && V) {
+        // R = U S V^T with U S = A (final):  R^+ = sum_c V[:,c] A[:,c]^T / sig_c^2
         const double smax = sig[order[0]];
         const double cut = jobs.rcond * smax;
-        for (int e = tid; e < s * s; e += blockDim.x) {
+        for (int e = tid; e < ss; e += nt) {
             const int i = e % s, jj = e / s;
             double t = 0.0;
             for (int c = 0; c < s; ++c) {
@@ -345,14 +600,15 @@ __global__ void __launch_bounds__(512) k_svd(const __grid_constant__ SVDJobs job
 }
 
 static void svd_launch(Ctx &c, SVDJobs &J, int smax) {
-    const size_t smem = 2 * (size_t)smax * smax * sizeof(double);
+    const size_t smem = 3 * (size_t)smax * smax * sizeof(double);
     static bool attr_set = false;
     if (!attr_set) {
         TK_CUDA(cudaFuncSetAttribute(k_svd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     2 * SVD_MAXS * SVD_MAXS * (int)sizeof(double)));
+                                     3 * SVD_MAXS * SVD_MAXS * (int)sizeof(double)));
         attr_set = true;
     }
-    k_svd<<<J.n, 512, smem, c.st>>>(J);
+    c.pre_launch();
+    k_svd<<<J.n, smax > 48 ? 1024 : 512, smem, c.st>>>(J);
     c.check_launch("svd");
 }
 
@@ -363,7 +619,7 @@ void svd_jacobi(Ctx &c, const std::vector<SVDJob> &jobs) {
         int smax = 1;
         for (int i = 0; i < J.n; ++i) {
             J.j[i] = jobs[base + i];
-            TK_REQUIRE(J.j[i].s <= SVD_MAXS && J.j[i].s >= 1, "SVD: size must be 1..112");
+            TK_REQUIRE(J.j[i].s <= SVD_MAXS && J.j[i].s >= 1, "SVD: size must be 1..96");
             smax = std::max(smax, J.j[i].s);
             J.pinv[i] = nullptr;
         }
@@ -380,11 +636,11 @@ void pinv_small(Ctx &c, const double *const *R, const int *ldr, int s, double *c
     for (int i = 0; i < n; ++i) {
         SVDJob &j = J.j[i];
         j.R = R[i]; j.ldr = ldr[i]; j.s = s; j.W = nullptr; j.wcols = 0; j.sigma = nullptr;
-        j.rank = nullptr; j.normsq = nullptr; j.eps2_over_d = 0.0; j.rank_cap = s;
+        j.rank = nullptr; j.normsq = nullptr; j.eps2_over_d = 0.0; j.rank_cap = s; j.perm = nullptr;
         J.pinv[i] = out[i];
     }
     J.rcond = rcond;
-    TK_REQUIRE(s <= SVD_MAXS, "pinv: size must be <= 112");
+    TK_REQUIRE(s <= SVD_MAXS, "pinv: size must be <= 96");
     svd_launch(c, J, s);
 }
 
@@ -457,6 +713,7 @@ __global__ void __launch_bounds__(512) k_ls(const double *M, const double *b, in
 void ls_update(Ctx &c, const double *M, const double *b, int s, int c0, int k, const LSState &st,
                int init_qtb) {
     TK_REQUIRE(s >= 1 && s <= 4096 && k >= 1 && k < s + 1, "least squares: bad size");
+    c.pre_launch();
     k_ls<<<1, 512, 0, c.st>>>(M, b, s, c0, k, st, init_qtb);
     c.check_launch("ls");
 }

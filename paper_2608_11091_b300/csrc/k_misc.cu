@@ -5,11 +5,63 @@
 
 namespace tk {
 
-void Ctx::check_launch(const char *what) {
+void Ctx::check_launch(const char *what, double flops) {
     ++launches;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         throw Error{TK_ECUDA, std::string("launch of ") + what + ": " + cudaGetErrorString(e)};
+    if (prof) prof->end(st, what, flops);
+}
+
+// ------------------------------------------------------------------------------------------
+// Profiler
+// ------------------------------------------------------------------------------------------
+Profiler::~Profiler() {
+    for (cudaEvent_t e : pool_) cudaEventDestroy(e);
+}
+
+cudaEvent_t Profiler::get() {
+    if (used_ == pool_.size()) {
+        cudaEvent_t e;
+        TK_CUDA(cudaEventCreate(&e));
+        pool_.push_back(e);
+    }
+    return pool_[used_++];
+}
+
+void Profiler::begin(cudaStream_t st) {
+    open_ = get();
+    TK_CUDA(cudaEventRecord(open_, st));
+}
+
+void Profiler::end(cudaStream_t st, const char *name, double flops) {
+    cudaEvent_t b = get();
+    TK_CUDA(cudaEventRecord(b, st));
+    recs_.push_back(Rec{name, open_, b, flops});
+}
+
+void Profiler::collect() {
+    for (const Rec &r : recs_) {
+        float ms = 0.f;
+        TK_CUDA(cudaEventSynchronize(r.b));
+        TK_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+        bool found = false;
+        for (auto &t : tot_)
+            if (t.first == r.name) { t.second.n += 1; t.second.ms += ms; t.second.flops += r.flops; found = true; break; }
+        if (!found) { Tot t; t.n = 1; t.ms = ms; t.flops = r.flops; tot_.push_back({r.name, t}); }
+    }
+    recs_.clear();
+    used_ = 0;
+}
+
+std::string Profiler::report_and_reset() {
+    collect();
+    std::string s;
+    for (auto &t : tot_)
+        s += t.first + " " + std::to_string(t.second.n) + " " + std::to_string(t.second.ms) + " " +
+             std::to_string(t.second.flops) + "\n";
+    tot_.clear();
+    return s;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -119,6 +171,7 @@ void gaussian(Ctx &c, uint64_t seed, const uint64_t *sids, const long long *coun
         }
         const int threads = 256;
         const long long blocks = std::min<long long>((mx + threads - 1) / threads, 4096);
+        c.pre_launch();
         k_gaussian<<<dim3((unsigned)blocks, J.n), threads, 0, c.st>>>(seed, J, bf16);
         c.check_launch("gaussian");
     }
@@ -137,6 +190,7 @@ __global__ void k_philox_raw(uint64_t seed, uint64_t sid, uint64_t first, long l
 
 void philox_raw(Ctx &c, uint64_t seed, uint64_t sid, uint64_t first, long long nb, uint32_t *out) {
     const long long blocks = std::min<long long>((nb + 255) / 256, 4096);
+    c.pre_launch();
     k_philox_raw<<<(unsigned)std::max<long long>(blocks, 1), 256, 0, c.st>>>(seed, sid, first, nb, out);
     c.check_launch("philox");
 }
@@ -180,6 +234,7 @@ void band_apply(Ctx &c, const std::vector<BandJob> &jobs) {
             mx = std::max(mx, (long long)J.j[i].n * J.j[i].r);
         }
         const long long blocks = std::min<long long>((mx + 255) / 256, 2048);
+        c.pre_launch();
         k_band<<<dim3((unsigned)blocks, J.n), 256, 0, c.st>>>(J);
         c.check_launch("band");
     }
@@ -219,6 +274,7 @@ void hadamard_contract(Ctx &c, const std::vector<HadJob> &jobs) {
             mx = std::max(mx, (long long)J.j[i].a * J.j[i].cc * J.j[i].s);
         }
         const long long blocks = std::min<long long>((mx + 255) / 256, 4096);
+        c.pre_launch();
         k_hadamard<<<dim3((unsigned)blocks, J.n), 256, 0, c.st>>>(J);
         c.check_launch("hadamard");
     }
@@ -240,6 +296,7 @@ __global__ void k_gather_unfold_t(const double *C, double *out, long long a, int
 void gather_unfold_t(Ctx &c, const double *C, double *out, long long a, int sk, long long rest) {
     const long long total = a * rest * sk;
     const long long blocks = std::min<long long>((total + 255) / 256, 4096);
+    c.pre_launch();
     k_gather_unfold_t<<<(unsigned)std::max<long long>(blocks, 1), 256, 0, c.st>>>(C, out, a, sk, rest);
     c.check_launch("gather");
 }
@@ -273,6 +330,7 @@ void dots(Ctx &c, const std::vector<DotJob> &jobs) {
         DotJobs J{};
         J.n = (int)std::min<size_t>(32, jobs.size() - base);
         for (int i = 0; i < J.n; ++i) J.j[i] = jobs[base + i];
+        c.pre_launch();
         k_dots<<<J.n, 1024, 0, c.st>>>(J);
         c.check_launch("dots");
     }
@@ -294,6 +352,7 @@ __global__ void k_fill(double *p, long long n, double v) {
 void fill(Ctx &c, double *p, long long n, double v) {
     if (n <= 0) return;
     const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+    c.pre_launch();
     k_fill<<<(unsigned)blocks, 256, 0, c.st>>>(p, n, v);
     c.check_launch("fill");
 }
@@ -308,6 +367,7 @@ __global__ void k_scale_by(double *y, const double *x, long long n, const double
 void scale_by(Ctx &c, double *y, const double *x, long long n, const double *s, int inv) {
     if (n <= 0) return;
     const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+    c.pre_launch();
     k_scale_by<<<(unsigned)blocks, 256, 0, c.st>>>(y, x, n, s, inv);
     c.check_launch("scale");
 }
@@ -331,6 +391,7 @@ void copy_pad(Ctx &c, double *dst, int ld_dst, int rows_dst, int cols_dst, const
     const long long total = (long long)rows_dst * cols_dst;
     if (total <= 0) return;
     const long long blocks = std::min<long long>((total + 255) / 256, 4096);
+    c.pre_launch();
     k_copy_pad<<<(unsigned)blocks, 256, 0, c.st>>>(dst, ld_dst, rows_dst, cols_dst, src, ld_src,
                                                    rows_src, cols_src);
     c.check_launch("copy_pad");
@@ -360,6 +421,7 @@ void copy_core_pad(Ctx &c, double *dst, const int *rdst, const double *src, cons
     long long total = 1;
     for (int k = 0; k < d; ++k) { D.rd[k] = rdst[k]; D.rs[k] = rsrc[k]; total *= rdst[k]; }
     const long long blocks = std::min<long long>((total + 255) / 256, 4096);
+    c.pre_launch();
     k_copy_core_pad<<<(unsigned)blocks, 256, 0, c.st>>>(dst, src, D, total);
     c.check_launch("copy_core_pad");
 }
@@ -374,6 +436,7 @@ __global__ void k_superdiag(const double *G, int m, int d, double *out, double s
 
 void superdiag(Ctx &c, const double *G, int m, int d, double *out, double scale_host,
                const double *scale_dev) {
+    c.pre_launch();
     k_superdiag<<<(m + 255) / 256, 256, 0, c.st>>>(G, m, d, out, scale_host, scale_dev);
     c.check_launch("superdiag");
 }
@@ -391,6 +454,7 @@ void transpose_block(Ctx &c, double *dst, int ldd, const double *src, int lds, i
     const long long total = (long long)rows * cols;
     if (total <= 0) return;
     const long long blocks = std::min<long long>((total + 255) / 256, 4096);
+    c.pre_launch();
     k_transpose<<<(unsigned)blocks, 256, 0, c.st>>>(dst, ldd, src, lds, rows, cols);
     c.check_launch("transpose");
 }
@@ -408,6 +472,7 @@ void triu_copy(Ctx &c, double *dst, int ldd, const double *src, int lds, int row
     const long long total = (long long)rows * cols;
     if (total <= 0) return;
     const long long blocks = std::min<long long>((total + 255) / 256, 4096);
+    c.pre_launch();
     k_triu<<<(unsigned)blocks, 256, 0, c.st>>>(dst, ldd, src, lds, rows, cols);
     c.check_launch("triu");
 }
@@ -415,6 +480,7 @@ void triu_copy(Ctx &c, double *dst, int ldd, const double *src, int lds, int row
 __global__ void k_sqrt_scalar(const double *in, double *out) { *out = sqrt(fmax(*in, 0.0)); }
 
 void sqrt_scalar(Ctx &c, const double *in, double *out) {
+    c.pre_launch();
     k_sqrt_scalar<<<1, 1, 0, c.st>>>(in, out);
     c.check_launch("sqrt");
 }
@@ -489,6 +555,7 @@ void axpy_list(Ctx &c, double *y, long long n, double beta, const std::vector<co
         }
         const long long work = aligned ? n / 2 : n;
         const long long blocks = std::max<long long>(1, std::min<long long>((work + 255) / 256, (long long)c.num_sms * 8));
+        c.pre_launch();
         k_axpy_list<<<(unsigned)blocks, 256, 0, c.st>>>(y, n, base == 0 ? beta : 1.0, J, aligned ? 1 : 0);
         c.check_launch("axpy_list");
     }

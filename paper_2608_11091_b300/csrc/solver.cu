@@ -11,6 +11,9 @@ struct tk_handle {
     tk::Arena arena;
     std::string err;
     double *pinned = nullptr;   // small host staging area for scalars read back per iteration
+    tk::Profiler prof;
+    bool prof_on = false;
+    std::string prof_text;
 };
 
 namespace tk {
@@ -121,7 +124,7 @@ static void solve_rhosvd(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tuck
     ScopedMark solve_mark(*c.arena);
     const int d = pb.d, R = o.rank_cap, s = o.sketch_s, sr = o.rank_cap + o.oversample_p;
     const int kmax = std::min(o.maxit, s - 1);
-    TK_REQUIRE(sr <= 112, "RoundSum sketch size rank_cap + p must be <= 112");
+    TK_REQUIRE(sr <= 96, "RoundSum sketch size rank_cap + p must be <= 96");
     TK_REQUIRE(o.ktrunc >= 1 && o.ktrunc <= 64, "ktrunc must be 1..64");
     const int bf16 = o.precision == TK_MIXED ? 1 : 0;
     double *sc = c.arena->alloc(SC_N);
@@ -261,7 +264,7 @@ static void solve_mln(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucker 
     ScopedMark solve_mark(*c.arena);
     const int d = pb.d, r = o.rank_cap, p = o.oversample_p, rp = r + p;
     const int kmax = std::min(o.maxit, rp - 1);
-    TK_REQUIRE(r >= 1 && p >= 0 && r <= 112, "MLN: rank must be 1..112");
+    TK_REQUIRE(r >= 1 && p >= 0 && r <= 96, "MLN: rank must be 1..96");
     TK_REQUIRE(o.ktrunc >= 1 && o.ktrunc <= 64, "ktrunc must be 1..64");
     long long gsz = 1, csz = 1;
     for (int k = 0; k < d; ++k) { gsz *= rp; csz *= r; }
@@ -417,7 +420,7 @@ static double true_residual(Ctx &c, const Dims &pb, const OpDesc &op, const tk_t
                 if (terms[i].f[k] == kv.first) rr = terms[i].r[k];
             copy(c, U + (size_t)kv.second * pb.n[k], kv.first, (long long)pb.n[k] * rr);
         }
-        qj.push_back(QRJob{U, c.arena->alloc(width), nullptr, pb.n[k], width});
+        qj.push_back(QRJob{U, c.arena->alloc(width), nullptr, pb.n[k], width, nullptr});
         rows[k] = std::min(pb.n[k], width);
         Rk[k] = c.arena->alloc((size_t)rows[k] * width);
     }
@@ -480,6 +483,7 @@ static Ctx make_ctx(tk_handle *h, void *stream) {
     c.st = (cudaStream_t)stream;
     c.arena = &h->arena;
     c.num_sms = h->num_sms;
+    c.prof = h->prof_on ? &h->prof : nullptr;
     return c;
 }
 
@@ -511,6 +515,25 @@ int tk_destroy(tk_handle *h) {
 }
 
 const char *tk_last_error(const tk_handle *h) { return h ? h->err.c_str() : "null handle"; }
+
+int tk_profile(tk_handle *h, int32_t enable) {
+    return guarded(h, [&]() -> int {
+        h->prof_on = enable != 0;
+        return TK_OK;
+    });
+}
+
+const char *tk_profile_report(tk_handle *h) {
+    if (!h) return "";
+    try {
+        TK_CUDA(cudaSetDevice(h->device));
+        h->prof_text = h->prof.report_and_reset();
+    } catch (const Error &e) {
+        h->err = e.msg;
+        h->prof_text.clear();
+    }
+    return h->prof_text.c_str();
+}
 
 int tk_solve(tk_handle *h, const tk_operator *op, const tk_tucker *b, const tk_opts *opts,
              tk_tucker *x_out, tk_report *report, void *stream) {
@@ -606,7 +629,7 @@ int tk_roundsum(tk_handle *h, int32_t nterms, const tk_tucker *xs, const double 
         for (int k = 0; k < pb.d; ++k) TK_REQUIRE(out->r[k] == R, "roundsum: out ranks must equal rank_cap");
         TK_REQUIRE(opts->adaptive_rank == 0, "adaptive sketch size is not available in this build");
         const int sr = R + opts->oversample_p;
-        TK_REQUIRE(sr <= 112, "roundsum: rank_cap + p must be <= 112");
+        TK_REQUIRE(sr <= 96, "roundsum: rank_cap + p must be <= 96");
         Ctx c = make_ctx(h, stream);
         ScopedMark mark(h->arena);
         TOut o{};
@@ -714,7 +737,7 @@ int tk_sketched_ls(tk_handle *h, const double *M, const double *b, int32_t s, in
 int tk_mln_roundsum(tk_handle *h, int32_t nterms, const tk_tucker *xs, const double *coef,
                     const double *const *psi, int32_t r, int32_t p, tk_tucker *out, void *stream) {
     return guarded(h, [&]() -> int {
-        TK_REQUIRE(nterms >= 1 && xs && coef && psi && r >= 1 && p >= 0 && r <= 112, "mln_roundsum: bad arguments");
+        TK_REQUIRE(nterms >= 1 && xs && coef && psi && r >= 1 && p >= 0 && r <= 96, "mln_roundsum: bad arguments");
         check_tucker(out, "out");
         const Dims pb = dims_of(out);
         for (int k = 0; k < pb.d; ++k) TK_REQUIRE(out->r[k] == r, "mln_roundsum: out ranks must equal r");

@@ -60,13 +60,36 @@ struct ScopedMark {
     ~ScopedMark() { a.release(m); }
 };
 
+// Opt-in per-kernel device timing: CUDA events recorded on the launching stream around each
+// launch; collected after the call has synchronized.
+class Profiler {
+public:
+    ~Profiler();
+    void begin(cudaStream_t st);
+    void end(cudaStream_t st, const char *name, double flops);
+    void collect();                       // requires the recorded work to have completed
+    std::string report_and_reset();       // "name launches total_ms" lines
+private:
+    cudaEvent_t get();
+    std::vector<cudaEvent_t> pool_;
+    size_t used_ = 0;
+    struct Rec { const char *name; cudaEvent_t a, b; double flops; };
+    std::vector<Rec> recs_;
+    cudaEvent_t open_ = nullptr;
+    struct Tot { long long n = 0; double ms = 0.0, flops = 0.0; };
+    std::vector<std::pair<std::string, Tot>> tot_;
+};
+
 // Per-call context.
 struct Ctx {
     cudaStream_t st;
     Arena *arena;
     int64_t launches = 0;
     int num_sms = 148;
-    void check_launch(const char *what);
+    Profiler *prof = nullptr;
+    void pre_launch() { if (prof) prof->begin(st); }
+    // `flops`: algorithmic FP64 operations of the launch (0 where not defined)
+    void check_launch(const char *what, double flops = 0.0);
 };
 
 // ------------------------------------------------------------------------------------------
@@ -134,6 +157,8 @@ struct QRJob {
     double *tau;      // min(m, s)
     double *Q;        // optional: explicit m x s orthonormal factor (ldq = m), zero columns >= m
     int m, s;
+    int *perm;        // optional: column pivoting (largest remaining norm first); column j of R
+                      // belongs to input column perm[j]
 };
 void qr_householder(Ctx &c, const std::vector<QRJob> &jobs);
 
@@ -147,6 +172,8 @@ struct SVDJob {
     const double *normsq;   // device: ||C||^2 for the threshold eps^2 ||C||^2 / d (may be null)
     double eps2_over_d;
     int rank_cap;
+    const int *perm;  // set: R comes from a column-pivoted QR of C^T and W receives the leading
+                      // left singular vectors of C = P R^T Q^T (Jacobi on R^T, rows of W permuted)
 };
 void svd_jacobi(Ctx &c, const std::vector<SVDJob> &jobs);
 

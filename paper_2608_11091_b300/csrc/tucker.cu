@@ -309,7 +309,7 @@ void roundsum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const RSC
         for (int k = 0; k < d; ++k) {
             Q[k] = c.arena->alloc((size_t)pb.n[k] * sr);
             double *tau = c.arena->alloc(sr);
-            qj.push_back(QRJob{Y[k], tau, Q[k], pb.n[k], sr});
+            qj.push_back(QRJob{Y[k], tau, Q[k], pb.n[k], sr, nullptr});
         }
         qr_householder(c, qj);
     }
@@ -361,9 +361,11 @@ void roundsum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const RSC
         double *Ut = c.arena->alloc(m * sk);
         gather_unfold_t(c, C, Ut, a, sk, rest);
         double *tau = c.arena->alloc(sk);
-        qr_householder(c, {QRJob{Ut, tau, nullptr, (int)m, sk}});
+        int *perm = c.arena->alloc_int(sk);
+        qr_householder(c, {QRJob{Ut, tau, nullptr, (int)m, sk, perm}});
         W[k] = c.arena->alloc((size_t)sk * R);
         SVDJob sj{};
+        sj.perm = perm;
         sj.R = Ut; sj.ldr = (int)m; sj.s = sk; sj.W = W[k]; sj.wcols = R; sj.sigma = nullptr;
         sj.rank = out.rank_dev ? out.rank_dev + k : nullptr;
         sj.normsq = normsq; sj.eps2_over_d = cfg.eps * cfg.eps / d; sj.rank_cap = R;
@@ -489,7 +491,7 @@ void mln_recovery(Ctx &c, const Dims &pb, const double *gpsi, const double *cons
         std::vector<QRJob> qj;
         for (int k = 0; k < d; ++k) {
             Qk[k] = c.arena->alloc((size_t)rp * r);
-            qj.push_back(QRJob{PF[k], c.arena->alloc(r), Qk[k], rp, r});
+            qj.push_back(QRJob{PF[k], c.arena->alloc(r), Qk[k], rp, r, nullptr});
         }
         qr_householder(c, qj);
     }

@@ -1,8 +1,10 @@
 """Writes tests/golden/solver_sensitivity.json: for each whole-solver parity case, how far the
-FP64 oracle's own output moves when every RoundSum output core carries a relative 1e-15
-perturbation (three draws, maximum taken).  This models a second correct FP64 implementation
-that rounds differently; the GPU parity tolerance of a case is max(1e-10, 20 x this value).
-Calls only the oracle and the input generators.
+FP64 oracle's own output moves when every compression output core (RoundSum, MLN_Recovery)
+carries a relative 1e-14 perturbation (five draws, maximum taken).  1e-14 is the rounding
+level of the FP64 reductions on the path (length up to ~1e4: sqrt(1e4) x 2^-53), so this
+models a second correct FP64 implementation that sums in another order; the GPU parity
+tolerance of a case is max(1e-10, 10 x this value).  Calls only the oracle and the input
+generators.
 
 Run: python tests/golden/make_solver_sensitivity.py
 """
@@ -52,8 +54,8 @@ def main():
         prm = prm or wl.params
         base = _solve(wl, prm, 0.0, 0, transpose)
         xs, hs = [], []
-        for s in range(3):
-            alt = _solve(wl, prm, 1e-15, s + 1, transpose)
+        for s in range(5):
+            alt = _solve(wl, prm, 1e-14, s + 1, transpose)
             n = min(len(alt.res_hist), len(base.res_hist))
             hs.append(float(np.max(np.abs(np.array(alt.res_hist[:n]) - np.array(base.res_hist[:n]))
                                    / np.array(base.res_hist[:n]))))
