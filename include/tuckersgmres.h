@@ -186,6 +186,23 @@ int tk_philox(tk_handle *h, uint64_t seed, uint64_t stream_id, uint64_t first, i
 int tk_sketched_ls(tk_handle *h, const double *M, const double *b, int32_t s, int32_t k,
                    double *y, double *res, void *stream);
 
+/* tk_sketched_ls_static: the same least-squares solve as tk_sketched_ls, for callers that
+ * must not allocate device memory after start-up (an application that reserves the GPU's
+ * memory up front for its own allocator, or a latency-critical loop that cannot accept
+ * cudaMalloc's implicit device synchronisation).  The paper has no counterpart; this is an
+ * interface for such callers.  It takes no handle and allocates nothing: its workspace is a
+ * fixed 513 KiB array in the library's device image (reflectors s x k, tau, Q^T b at
+ * s <= 512, k <= 128), resident on every GPU that loads the library until the process exits.
+ * M (device, s x k column-major), b (device, s), y (device, k) and res (device, 1) belong to
+ * the caller.  Sizes with k < 1, k >= s, s > 512 or k > 128 return TK_EINVAL; a CUDA failure
+ * returns TK_ECUDA (no message: there is no handle).  The first call on a device looks up the
+ * array's device address on that device (cudaGetSymbolAddress, with the device current); make
+ * that first call before any stream capture.  Every call shares the one array and it keeps the
+ * last call's contents, so calls that may overlap on the GPU (different streams, or devices
+ * sharing a context) race: serialise them.  Enqueues only. */
+int tk_sketched_ls_static(const double *M, const double *b, int32_t s, int32_t k, double *y,
+                          double *res, void *stream);
+
 /* tk_mln_roundsum: MLN_Sketch + MLN_Sum + MLN_Recovery (Algorithms 3-5) of
  * sum_i coef[i] X_i with Psi_k (device, n_k x (r+p)); out caller-allocated with r[k] = r.
  * Enqueues only. */

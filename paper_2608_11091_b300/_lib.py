@@ -19,7 +19,8 @@ TK_FP64, TK_MIXED = 0, 1
 
 EXPORTS = ["tk_create", "tk_destroy", "tk_last_error", "tk_solve", "tk_apply", "tk_roundsum",
            "tk_kron_sketch", "tk_inner", "tk_residual", "tk_gaussian", "tk_philox",
-           "tk_sketched_ls", "tk_mln_roundsum", "tk_profile", "tk_profile_report"]
+           "tk_sketched_ls", "tk_mln_roundsum", "tk_profile", "tk_profile_report",
+           "tk_sketched_ls_static"]
 
 
 class tk_tucker(ctypes.Structure):
@@ -93,6 +94,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tk_mln_roundsum": (ctypes.c_int, [vp, i32, P(tk_tucker), dp, P(vp), i32, i32, P(tk_tucker), vp]),
         "tk_profile": (ctypes.c_int, [vp, i32]),
         "tk_profile_report": (ctypes.c_char_p, [vp]),
+        "tk_sketched_ls_static": (ctypes.c_int, [vp, vp, i32, i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

@@ -357,6 +357,22 @@ def tk_sketched_ls(M: torch.Tensor, b: torch.Tensor, stream=None):
     return y, res
 
 
+def tk_sketched_ls_static(M: torch.Tensor, b: torch.Tensor, stream=None):
+    """tk_sketched_ls without any device allocation by the library (fixed device workspace;
+    s <= 512, k <= 128; concurrent calls race).  Returns (y, residual norm)."""
+    lib = L.load()
+    s, k = int(M.shape[0]), int(M.shape[1])
+    if not is_fortran(M):
+        raise TuckerError("M must be column-major")
+    y = torch.empty(k, dtype=torch.float64, device=M.device)
+    res = torch.empty(1, dtype=torch.float64, device=M.device)
+    rc = lib.tk_sketched_ls_static(ctypes.c_void_p(M.data_ptr()), ctypes.c_void_p(b.data_ptr()), s, k,
+                                   ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(res.data_ptr()), _stream(stream))
+    if rc != 0:
+        raise TuckerError(f"tk_sketched_ls_static failed ({rc})")
+    return y, res
+
+
 def tk_mln_roundsum(terms: Sequence[DeviceTucker], coef: Sequence[float], psi: Sequence[torch.Tensor], r: int,
                     p: int, out: Optional[DeviceTucker] = None, stream=None) -> DeviceTucker:
     """MLN_Sketch + MLN_Sum + MLN_Recovery (Algorithms 3-5)."""
