@@ -18,6 +18,7 @@ namespace cg = cooperative_groups;
 namespace tk {
 
 constexpr int QR_MAXS = 256;
+constexpr int QR_NCH = 4;        // row chunks per column in the QR partial sums
 constexpr int SVD_MAXS = 96;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -86,6 +87,8 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
     __shared__ double taus[QR_MAXS];
     __shared__ double nrm[QR_MAXS];
     __shared__ int permv[QR_MAXS];
+    __shared__ double part[QR_NCH * QR_MAXS];
+    __shared__ float partn[QR_NCH * QR_MAXS];
     __shared__ double bc[6];
     __shared__ int pivot;
     const bool piv = J.perm != nullptr;
@@ -115,8 +118,14 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
         }
         cl.sync();
         for (int c = tid; c < s; c += nt) {
+            double vt[16];
+#pragma unroll
+            for (int qq = 0; qq < 16; ++qq)
+                if (qq < C) vt[qq] = cl.map_shared_rank(rd, qq)[c];
             double t = 0.0;
-            for (int qq = 0; qq < C; ++qq) t += cl.map_shared_rank(rd, qq)[c];
+#pragma unroll
+            for (int qq = 0; qq < 16; ++qq)
+                if (qq < C) t += vt[qq];
             nrm[c] = t;
         }
         buf ^= 1;
@@ -148,51 +157,79 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
         }
         double *rd = red[buf];
         const bool owner = (j >= r0 && j < r1);
-        for (int c = j + warp; c < s; c += nw) {
-            double p = 0.0, pn = 0.0;
-            if (c == j) {
-                for (int i = max(r0, j + 1) + lane; i < r1; i += 32) { const double x = A(i, j); p = fma(x, x, p); }
-            } else {
-                for (int i = max(r0, j) + lane; i < r1; i += 32) {
-                    const double y = A(i, c);
-                    p = fma(A(i, j), y, p);
-                    if (piv && i > j) pn = fma(y, y, pn);
+        {
+            // one thread per (column, row chunk): partial x.x (c = j), x.A_c (rows >= j) and the
+            // FP32 pivot norms ||A_c||^2 (rows > j); then one thread per column combines chunks
+            const int nc1 = s - j;
+            const int nch = max(1, min(QR_NCH, nt / nc1));
+            const int ib = max(r0, j), nrows = r1 - ib;
+            const int rch = (nrows + nch - 1) / nch;
+            for (int e = tid; e < nc1 * nch; e += nt) {
+                const int c = j + e % nc1, ch = e / nc1;
+                const int i0 = ib + ch * rch, i1 = min(r1, i0 + rch);
+                double pd = 0.0;
+                float pn = 0.f;
+                if (c == j) {
+                    for (int i = max(i0, j + 1); i < i1; ++i) { const double x = A(i, j); pd = fma(x, x, pd); }
+                } else {
+                    for (int i = i0; i < i1; ++i) {
+                        const double y = A(i, c);
+                        pd = fma(A(i, j), y, pd);
+                        if (piv && i > j) { const float yf = (float)y; pn = fmaf(yf, yf, pn); }
+                    }
                 }
+                part[ch * QR_MAXS + (c - j)] = pd;
+                partn[ch * QR_MAXS + (c - j)] = pn;
             }
-            p = warp_sum(p);
-            if (piv && c != j) pn = warp_sum(pn);
-            if (lane == 0) {
-                if (c == j) { rd[0] = p; rd[1] = owner ? A(j, j) : 0.0; }
+            __syncthreads();
+            for (int c = j + tid; c < s; c += nt) {
+                double pd = 0.0;
+                float pn = 0.f;
+                for (int ch = 0; ch < nch; ++ch) { pd += part[ch * QR_MAXS + (c - j)]; pn += partn[ch * QR_MAXS + (c - j)]; }
+                if (c == j) { rd[0] = pd; rd[1] = owner ? A(j, j) : 0.0; }
                 else {
-                    rd[2 + (c - j - 1)] = p;
+                    rd[2 + (c - j - 1)] = pd;
                     rd[2 + nc + (c - j - 1)] = owner ? A(j, c) : 0.0;
-                    if (piv) rd[2 + 2 * nc + (c - j - 1)] = pn;
+                    if (piv) rd[2 + 2 * nc + (c - j - 1)] = (double)pn;
                 }
             }
         }
         cl.sync();
-        if (tid == 0) {
+        if (warp == 0) {
+            // lane q reads peer q's two scalars; all loads in flight at once
             double s2 = 0.0, al = 0.0;
-            for (int qq = 0; qq < C; ++qq) {
-                const double *rq = cl.map_shared_rank(rd, qq);
-                s2 += rq[0];
-                al += rq[1];
+            if (lane < C) {
+                const double *rq = cl.map_shared_rank(rd, lane);
+                s2 = rq[0];
+                al = rq[1];
             }
-            double tau, beta, scal;
-            householder(al, s2, tau, beta, scal);
-            bc[0] = tau; bc[1] = scal; bc[2] = beta; bc[3] = al; bc[4] = s2;
-            taus[j] = tau;
+            s2 = warp_sum(s2);
+            al = warp_sum(al);
+            if (lane == 0) {
+                double tau, beta, scal;
+                householder(al, s2, tau, beta, scal);
+                bc[0] = tau; bc[1] = scal; bc[2] = beta; bc[3] = al; bc[4] = s2;
+                taus[j] = tau;
+            }
         }
         __syncthreads();
         const double tau = bc[0], scal = bc[1], beta = bc[2], al = bc[3], s2 = bc[4];
         for (int c = j + 1 + tid; c < s; c += nt) {
-            double D = 0.0, Pc = 0.0, Nc = 0.0;
-            for (int qq = 0; qq < C; ++qq) {
-                const double *rq = cl.map_shared_rank(rd, qq);
-                D += rq[2 + (c - j - 1)];
-                Pc += rq[2 + nc + (c - j - 1)];
-                if (piv) Nc += rq[2 + 2 * nc + (c - j - 1)];
+            // issue every peer's loads before summing (independent DSMEM round trips overlap)
+            double vD[16], vP[16], vN[16];
+#pragma unroll
+            for (int qq = 0; qq < 16; ++qq) {
+                if (qq < C) {
+                    const double *rq = cl.map_shared_rank(rd, qq);
+                    vD[qq] = rq[2 + (c - j - 1)];
+                    vP[qq] = rq[2 + nc + (c - j - 1)];
+                    vN[qq] = piv ? rq[2 + 2 * nc + (c - j - 1)] : 0.0;
+                }
             }
+            double D = 0.0, Pc = 0.0, Nc = 0.0;
+#pragma unroll
+            for (int qq = 0; qq < 16; ++qq)
+                if (qq < C) { D += vD[qq]; Pc += vP[qq]; Nc += vN[qq]; }
             const double w = tau != 0.0 ? tau * (Pc + (D - al * Pc) * scal) : 0.0;
             wv[c] = w;
             if (piv) {
@@ -204,15 +241,17 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
         buf ^= 1;
         __syncthreads();
         const int ib = max(r0, j), nrows = r1 - ib;
+        // v_i = x_i / (alpha - beta) for i > j (stored as the reflector), v_j = 1
+        for (int i = max(r0, j + 1) + tid; i < r1; i += nt) A(i, j) *= scal;
+        __syncthreads();
         if (tau != 0.0 && nrows > 0) {
             for (int e = tid; e < nrows * nc; e += nt) {
                 const int i = ib + e % nrows, c = j + 1 + e / nrows;
-                const double v = (i == j) ? 1.0 : A(i, j) * scal;
+                const double v = (i == j) ? 1.0 : A(i, j);
                 A(i, c) -= v * wv[c];
             }
         }
         __syncthreads();
-        for (int i = max(r0, j + 1) + tid; i < r1; i += nt) A(i, j) *= scal;
         if (tid == 0 && owner) A(j, j) = beta;
         __syncthreads();
     }
@@ -239,8 +278,14 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
             }
             cl.sync();
             for (int c = j + tid; c < s; c += nt) {
+                double vw[16];
+#pragma unroll
+                for (int qq = 0; qq < 16; ++qq)
+                    if (qq < C) vw[qq] = cl.map_shared_rank(rd, qq)[c - j];
                 double w = 0.0;
-                for (int qq = 0; qq < C; ++qq) w += cl.map_shared_rank(rd, qq)[c - j];
+#pragma unroll
+                for (int qq = 0; qq < 16; ++qq)
+                    if (qq < C) w += vw[qq];
                 wv[c] = w * tau;
             }
             buf ^= 1;
@@ -270,7 +315,7 @@ void qr_householder(Ctx &c, const std::vector<QRJob> &jobs) {
     if (!attr_set) {
         TK_CUDA(cudaFuncSetAttribute(k_qr<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
         TK_CUDA(cudaFuncSetAttribute(k_qr<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-        TK_CUDA(cudaFuncSetAttribute(k_qr<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        TK_CUDA(cudaFuncSetAttribute(k_qr<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 180 * 1024));
         attr_set = true;
     }
     for (size_t base = 0; base < jobs.size(); base += TK_MAX_D) {
@@ -294,7 +339,7 @@ void qr_householder(Ctx &c, const std::vector<QRJob> &jobs) {
         for (;;) {
             rb = (mmax + C - 1) / C;
             const size_t smem = (size_t)rb * smax * sizeof(double) * (wantq ? 2 : 1);
-            use_smem = smem <= 200 * 1024;
+            use_smem = smem <= 180 * 1024;
             cfg = cudaLaunchConfig_t{};
             cfg.gridDim = dim3((unsigned)C, (unsigned)J.n, 1);
             cfg.blockDim = dim3(256, 1, 1);
@@ -385,7 +430,10 @@ __device__ int jacobi_sweeps(T *A, T *V, T *nrm2, int s, T tol, T floor2, int ma
                 T ga = 0;
                 for (int i = lane; i < s; i += 32) ga = fma(A[i + p * s], A[i + q * s], ga);
                 ga = warp_sum_t(ga);   // identical in every lane (butterfly)
-                if (ga != T(0) && ga * ga > tol * tol * al * be) {
+                // FP32: the square-root form cannot underflow for tiny columns
+                const bool rot = sizeof(T) == 4 ? fabs(ga) > tol * sqrt(al) * sqrt(be)
+                                                : ga * ga > tol * tol * al * be;
+                if (ga != T(0) && rot) {
                     // rotation parameters on one lane (FP64 sqrt/div are long DFMA sequences
                     // here), broadcast to the warp
                     T t = 0, cs = 0, sn = 0;
@@ -424,6 +472,105 @@ __device__ int jacobi_sweeps(T *A, T *V, T *nrm2, int s, T tol, T floor2, int ma
     return done;
 }
 
+// FP64 one-sided Jacobi sweeps with the scalar work spread one lane per pair (an FP64 warp
+// instruction costs the same whether 1 or 32 lanes are active, so per-pair scalar code must not
+// be replicated across a warp).  Per round: partial dot products over NP row blocks (one thread
+// per (block, pair)), then one thread per pair sums them, tests, and forms the rotation: the
+// angle comes from FP32 arithmetic (it only has to shrink a_p . a_q; what it leaves is removed
+// by the next sweep) while cos = (1 + t^2)^(-1/2) is refined by two FP64 Newton steps so every
+// rotation is orthogonal to FP64 rounding; then one thread per (pair, row) rotates.
+constexpr int JNP = 4;
+template <bool ACC>
+__device__ int jacobi64(double *A, double *V, double *nrm2, int s, double tol, double floor2, int max_sweeps,
+                        int *flag, double *gpart, double *cpar, double *spar, int *act) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5, nt = blockDim.x;
+    const int sp = s + (s & 1), np = sp / 2;
+    const int rbk = (s + JNP - 1) / JNP;
+    int done = 0;
+    for (int sweep = 0; sweep < max_sweeps && sp > 1; ++sweep) {
+        ++done;
+        for (int c = warp; c < s; c += nw) {
+            double t = 0.0;
+            for (int i = lane; i < s; i += 32) t = fma(A[i + c * s], A[i + c * s], t);
+            t = warp_sum(t);
+            if (lane == 0) nrm2[c] = t;
+        }
+        if (tid == 0) *flag = 0;
+        __syncthreads();
+        for (int round = 0; round < sp - 1; ++round) {
+            for (int e = tid; e < JNP * np; e += nt) {
+                const int part = e / np, pr = e % np;
+                int p, q;
+                if (pr == 0) { p = round; q = sp - 1; }
+                else { p = (round + pr) % (sp - 1); q = (round - pr + (sp - 1)) % (sp - 1); }
+                double g = 0.0;
+                if (p < s && q < s) {
+                    const int i1 = min(s, (part + 1) * rbk);
+                    for (int i = part * rbk; i < i1; ++i) g = fma(A[i + p * s], A[i + q * s], g);
+                }
+                gpart[part * np + pr] = g;
+            }
+            __syncthreads();
+            for (int pr = tid; pr < np; pr += nt) {
+                int p, q;
+                if (pr == 0) { p = round; q = sp - 1; }
+                else { p = (round + pr) % (sp - 1); q = (round - pr + (sp - 1)) % (sp - 1); }
+                int doit = 0;
+                if (p < s && q < s) {
+                    const double al = nrm2[p], be = nrm2[q];
+                    double ga = 0.0;
+                    for (int part = 0; part < JNP; ++part) ga += gpart[part * np + pr];
+                    if (al > floor2 && be > floor2 && ga != 0.0 && ga * ga > tol * tol * al * be) {
+                        const double zeta = (be - al) / (2.0 * ga);
+                        double t;
+                        if (fabs(zeta) < 1e6) {
+                            const float zf = (float)zeta;
+                            t = (double)(copysignf(1.0f, zf) / (fabsf(zf) + sqrtf(1.0f + zf * zf)));
+                        } else {
+                            t = 0.5 / zeta;   // tan of the angle to first order (|zeta| >> 1)
+                        }
+                        const double x = fma(t, t, 1.0);
+                        double c = (double)rsqrtf((float)x);
+                        c = c * fma(-0.5 * x * c, c, 1.5);
+                        c = c * fma(-0.5 * x * c, c, 1.5);
+                        const double sn = c * t;
+                        cpar[pr] = c;
+                        spar[pr] = sn;
+                        // exact post-rotation norms of the rotated pair
+                        nrm2[p] = c * c * al - 2.0 * c * sn * ga + sn * sn * be;
+                        nrm2[q] = sn * sn * al + 2.0 * c * sn * ga + c * c * be;
+                        doit = t != 0.0;
+                        if (doit) *flag = 1;
+                    }
+                }
+                act[pr] = doit;
+            }
+            __syncthreads();
+            for (int e = tid; e < np * s; e += nt) {
+                const int pr = e / s, i = e % s;
+                if (!act[pr]) continue;
+                int p, q;
+                if (pr == 0) { p = round; q = sp - 1; }
+                else { p = (round + pr) % (sp - 1); q = (round - pr + (sp - 1)) % (sp - 1); }
+                const double c = cpar[pr], sn = spar[pr];
+                const double a = A[i + p * s], b = A[i + q * s];
+                A[i + p * s] = c * a - sn * b;
+                A[i + q * s] = sn * a + c * b;
+                if (ACC) {
+                    const double va = V[i + p * s], vb = V[i + q * s];
+                    V[i + p * s] = c * va - sn * vb;
+                    V[i + q * s] = sn * va + c * vb;
+                }
+            }
+            __syncthreads();
+        }
+        const int any = *flag;
+        __syncthreads();
+        if (!any) break;
+    }
+    return done;
+}
+
 // SVD of a small square matrix R (upper triangle read) to FP64 accuracy.  Two modes:
 //
 // ST-HOSVD (J.perm set): R comes from the column-pivoted QR C^T P = Q R of a core unfolding, so
@@ -448,83 +595,85 @@ __global__ void __launch_bounds__(1024) k_svd(const __grid_constant__ SVDJobs jo
     __shared__ double scratch[40];
     __shared__ double nrm64[SVD_MAXS];
     __shared__ float nrm32[SVD_MAXS];
+    __shared__ double gpart[JNP * (SVD_MAXS / 2 + 1)];
+    __shared__ double cpar[SVD_MAXS / 2 + 1], spar[SVD_MAXS / 2 + 1];
+    __shared__ int act[SVD_MAXS / 2 + 1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int nt = blockDim.x;
     auto Rat = [&](int i, int c) -> double {
         return (i <= c && i < J.ldr) ? J.R[i + (long long)c * J.ldr] : 0.0;
     };
     const bool graded = J.perm != nullptr;
-    double *A, *V = nullptr;
-    double floor2;
-    if (graded) {
-        A = Y;
-        for (int e = tid; e < ss; e += nt) A[e] = Rat(e / s, e % s);    // A = R^T
-        double fro = 0.0;
-        for (int e = tid; e < ss; e += nt) fro = fma(A[e], A[e], fro);
-        fro = block_sum(fro, scratch);
-        floor2 = fro * (double)s * s * 0x1p-106;
-        const int n64 = jacobi_sweeps<double, false>(A, nullptr, nrm64, s, 4.0 * sqrt((double)s) * 0x1p-53, floor2, 30, &flag);
-        if (tid == 0) { g_svd_sweeps[2 * blockIdx.x] = 0; g_svd_sweeps[2 * blockIdx.x + 1] = n64; }
-    } else {
-        float *A32 = reinterpret_cast<float *>(X), *V32 = A32 + ss;
-        double mx = 0.0;
-        for (int e = tid; e < ss; e += nt) mx = fmax(mx, fabs(Rat(e % s, e / s)));
+    // B = R^T (graded) or R; element accessor in FP64
+    auto Bat = [&](int i, int c) -> double { return graded ? Rat(c, i) : Rat(i, c); };
+    float *A32 = reinterpret_cast<float *>(X), *V32 = A32 + ss;
+    double mx = 0.0;
+    for (int e = tid; e < ss; e += nt) mx = fmax(mx, fabs(Bat(e % s, e / s)));
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) scratch[warp] = mx;
-        __syncthreads();
-        mx = 0.0;
-        for (int w = 0; w < nw; ++w) mx = fmax(mx, scratch[w]);
-        __syncthreads();
-        const double inv = mx > 0.0 ? 1.0 / mx : 1.0;
-        for (int e = tid; e < ss; e += nt) {
-            A32[e] = (float)(Rat(e % s, e / s) * inv);
-            V32[e] = (e % s == e / s) ? 1.f : 0.f;
-        }
-        __syncthreads();
-        double fro = 0.0;
-        for (int e = tid; e < ss; e += nt) { const double v = (double)A32[e]; fro = fma(v, v, fro); }
-        fro = block_sum(fro, scratch);
-        const int n32 = jacobi_sweeps<float, true>(A32, V32, nrm32, s, 8.0f * sqrtf((float)s) * 0x1p-24f, (float)(fro * 0x1p-40), 20, &flag);
-        if (tid == 0) g_svd_sweeps[2 * blockIdx.x] = n32;
-        // V = double(V32) into Y, then two Newton-Schulz steps: Z = (3 I - Y^T Y) / 2, X = Y Z
-        for (int e = tid; e < ss; e += nt) Y[e] = (double)V32[e];
-        __syncthreads();
-        for (int it = 0; it < 2; ++it) {
-            for (int e = tid; e < ss; e += nt) {
-                const int i = e % s, j = e / s;
-                double t = 0.0;
-                for (int k = 0; k < s; ++k) t = fma(Y[k + i * s], Y[k + j * s], t);
-                Z[e] = ((i == j) ? 1.5 : 0.0) - 0.5 * t;
-            }
-            __syncthreads();
-            for (int e = tid; e < ss; e += nt) {
-                const int i = e % s, j = e / s;
-                double t = 0.0;
-                for (int k = 0; k < s; ++k) t = fma(Y[i + k * s], Z[k + j * s], t);
-                X[e] = t;
-            }
-            __syncthreads();
-            if (it == 0) {
-                for (int e = tid; e < ss; e += nt) Y[e] = X[e];
-                __syncthreads();
-            }
-        }
-        // A = R V into Y (R upper triangular), then FP64 sweeps with V = X accumulated
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) scratch[warp] = mx;
+    __syncthreads();
+    mx = 0.0;
+    for (int w = 0; w < nw; ++w) mx = fmax(mx, scratch[w]);
+    __syncthreads();
+    const double inv = mx > 0.0 ? 1.0 / mx : 1.0;
+    for (int e = tid; e < ss; e += nt) {
+        A32[e] = (float)(Bat(e % s, e / s) * inv);
+        V32[e] = (e % s == e / s) ? 1.f : 0.f;
+    }
+    __syncthreads();
+    double fro = 0.0;
+    for (int e = tid; e < ss; e += nt) { const double v = (double)A32[e]; fro = fma(v, v, fro); }
+    fro = block_sum(fro, scratch);
+    // phase 1: FP32 sweeps.  On the graded R^T they resolve singular values far below the
+    // largest with relative accuracy; columns below 2^-100 (scaled) are left to FP64.
+    const int n32 = jacobi_sweeps<float, true>(A32, V32, nrm32, s, 8.0f * sqrtf((float)s) * 0x1p-24f,
+                                               graded ? 0x1p-100f : (float)(fro * 0x1p-40), 20, &flag);
+    if (tid == 0) g_svd_sweeps[2 * blockIdx.x] = n32;
+    // phase 2: V = double(V32) into Y, then two Newton-Schulz steps: Z = (3 I - Y^T Y) / 2, X = Y Z
+    // (orthogonality error e -> 1.5 e^2: ~s 2^-24 -> ~1e-11 -> rounding level)
+    for (int e = tid; e < ss; e += nt) Y[e] = (double)V32[e];
+    __syncthreads();
+    for (int it = 0; it < 2; ++it) {
         for (int e = tid; e < ss; e += nt) {
             const int i = e % s, j = e / s;
             double t = 0.0;
-            for (int k = i; k < s; ++k) t = fma(Rat(i, k), X[k + j * s], t);
-            Y[e] = t;
+            for (int k = 0; k < s; ++k) t = fma(Y[k + i * s], Y[k + j * s], t);
+            Z[e] = ((i == j) ? 1.5 : 0.0) - 0.5 * t;
         }
         __syncthreads();
-        A = Y;
-        V = X;
-        const double fro_r = fro * mx * mx;
-        floor2 = fro_r * (double)s * s * 0x1p-106;
-        const int n64 = jacobi_sweeps<double, true>(A, V, nrm64, s, 4.0 * sqrt((double)s) * 0x1p-53, floor2, 16, &flag);
-        if (tid == 0) g_svd_sweeps[2 * blockIdx.x + 1] = n64;
+        for (int e = tid; e < ss; e += nt) {
+            const int i = e % s, j = e / s;
+            double t = 0.0;
+            for (int k = 0; k < s; ++k) t = fma(Y[i + k * s], Z[k + j * s], t);
+            X[e] = t;
+        }
+        __syncthreads();
+        if (it == 0) {
+            for (int e = tid; e < ss; e += nt) Y[e] = X[e];
+            __syncthreads();
+        }
     }
+    // phase 3: A = B V into Y (B triangular: R^T lower, R upper)
+    for (int e = tid; e < ss; e += nt) {
+        const int i = e % s, j = e / s;
+        double t = 0.0;
+        if (graded)
+            for (int k = 0; k <= i; ++k) t = fma(Bat(i, k), X[k + j * s], t);
+        else
+            for (int k = i; k < s; ++k) t = fma(Bat(i, k), X[k + j * s], t);
+        Y[e] = t;
+    }
+    __syncthreads();
+    // phase 4: FP64 sweeps (V accumulated only when R^+ needs it)
+    double *A = Y, *V = graded ? nullptr : X;
+    const double fro_r = fro * mx * mx;
+    const double floor2 = fro_r * (double)s * s * 0x1p-106;
+    const double tol64 = 4.0 * sqrt((double)s) * 0x1p-53;
+    const int n64 = graded
+        ? jacobi64<false>(A, nullptr, nrm64, s, tol64, floor2, 16, &flag, gpart, cpar, spar, act)
+        : jacobi64<true>(A, X, nrm64, s, tol64, floor2, 16, &flag, gpart, cpar, spar, act);
+    if (tid == 0) g_svd_sweeps[2 * blockIdx.x + 1] = n64;
     // singular values and descending order (ties by index)
     for (int c = warp; c < s; c += nw) {
         double t = 0.0;
