@@ -169,6 +169,24 @@ int tk_inner(tk_handle *h, const tk_tucker *x, const tk_tucker *y, double *out_h
 int tk_residual(tk_handle *h, const tk_operator *op, const tk_tucker *x, const tk_tucker *b,
                 int32_t transpose, double *rel_host, void *stream);
 
+/* tk_sum_norm: ||sum_i coef[i] X_i||_F (coef host memory) written to *out_host, in Tucker form:
+ * QR of the concatenated distinct factors of each mode, then the norm of the small projected
+ * core, so differences of nearly equal tensors keep their relative accuracy.  The
+ * concatenated rank per mode must be <= 256.  Synchronizes. */
+int tk_sum_norm(tk_handle *h, int32_t nterms, const tk_tucker *xs, const double *coef, double *out_host,
+                void *stream);
+
+/* tk_adjoint_grads: gradients of a loss l(x) through the solve x = L^{-1}(b), given the adjoint
+ * solution mu of L^T(mu) = dl/dx (tk_solve with opts->transpose = 1).  The paper has no
+ * counterpart; these are the adjoint contractions of the differentiable form:
+ *   dtheta_host[t] = dl/dtheta_t = -<mu, A_1^(t) x ... x A_d^(t) applied to x>   (host, nterms)
+ *   dcore_b        = dl/dG_b  = mu x_1 U_b1^T ... x_d U_bd^T        (device, r_b1 x .. x r_bd)
+ *   dfactor_b[k]   = dl/dU_bk = mu_(k) (kron_{j != k} U_bj) G_b(k)^T  (device, n_k x r_bk)
+ * for b = [G_b; U_b1, ..., U_bd].  Any output pointer may be NULL to skip it.  Synchronizes. */
+int tk_adjoint_grads(tk_handle *h, const tk_operator *op, const tk_tucker *mu, const tk_tucker *x,
+                     const tk_tucker *b, double *dtheta_host, double *dcore_b, double *const *dfactor_b,
+                     void *stream);
+
 /* tk_gaussian: `count` values of the N(0,1) stream (seed, stream_id) - Philox4x32-10 with
  * Box-Muller, element e from counter (e/2, stream_id) - into out (device).  bf16_round = 1
  * rounds each value to the nearest bfloat16 (ties to even).  Enqueues only. */

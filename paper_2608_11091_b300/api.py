@@ -327,6 +327,29 @@ def tk_residual(op: DeviceOperator, x: DeviceTucker, b: DeviceTucker, transpose:
     return out.value
 
 
+def tk_sum_norm(terms: Sequence[DeviceTucker], coef: Sequence[float], stream=None) -> float:
+    """||sum_i coef_i terms_i||_F computed in Tucker form (QR of concatenated factors)."""
+    h = handle()
+    arr = (L.tk_tucker * len(terms))(*[t.c() for t in terms])
+    cf = (ctypes.c_double * len(terms))(*[float(c) for c in coef])
+    out = ctypes.c_double()
+    h.check(h.lib.tk_sum_norm(h.h, len(terms), arr, cf, ctypes.byref(out), _stream(stream)), "tk_sum_norm")
+    return out.value
+
+
+def tk_adjoint_grads(op: DeviceOperator, mu: DeviceTucker, x: DeviceTucker, b: DeviceTucker, stream=None):
+    """(dl/dtheta (list), dl/dG_b, [dl/dU_bk]) from the adjoint solution mu and forward solution x."""
+    h = handle()
+    dth = (ctypes.c_double * op.nterms)()
+    dcore = fortran_empty(b.r, b.core.device)
+    dfac = [fortran_empty((b.n[k], b.r[k]), b.core.device) for k in range(b.d)]
+    ptrs = (ctypes.c_void_p * b.d)(*[t.data_ptr() for t in dfac])
+    opc, muc, xc, bc = op.c(), mu.c(), x.c(), b.c()
+    h.check(h.lib.tk_adjoint_grads(h.h, ctypes.byref(opc), ctypes.byref(muc), ctypes.byref(xc), ctypes.byref(bc),
+                                   dth, ctypes.c_void_p(dcore.data_ptr()), ptrs, _stream(stream)), "tk_adjoint_grads")
+    return list(dth), dcore, dfac
+
+
 def tk_gaussian(seed: int, stream_id: int, count: int, bf16_round: bool = False, device="cuda", stream=None):
     h = handle()
     out = torch.empty(max(count, 1), dtype=torch.float64, device=device)

@@ -477,6 +477,22 @@ void triu_copy(Ctx &c, double *dst, int ldd, const double *src, int lds, int row
     c.check_launch("triu");
 }
 
+__global__ void k_set_identity(double *p, int n) {
+    const long long total = (long long)n * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x)
+        p[e] = (e % n == e / n) ? 1.0 : 0.0;
+}
+
+void set_identity(Ctx &c, double *p, int n) {
+    const long long total = (long long)n * n;
+    if (total <= 0) return;
+    const long long blocks = std::min<long long>((total + 255) / 256, 1024);
+    c.pre_launch();
+    k_set_identity<<<(unsigned)blocks, 256, 0, c.st>>>(p, n);
+    c.check_launch("identity");
+}
+
 __global__ void k_sqrt_scalar(const double *in, double *out) { *out = sqrt(fmax(*in, 0.0)); }
 
 void sqrt_scalar(Ctx &c, const double *in, double *out) {

@@ -66,7 +66,7 @@ static OpDesc op_of(const tk_operator *op, const Dims &pb) {
             TK_REQUIRE(m.kind == TK_IDENTITY || m.kind == TK_BANDED || m.kind == TK_DENSE, "operator: bad kind");
             TK_REQUIRE(m.n == pb.n[k], "operator: mode matrix size differs from the tensor's");
             if (m.kind != TK_IDENTITY) TK_REQUIRE(m.data != nullptr, "operator: null matrix data");
-            if (m.kind == TK_BANDED) TK_REQUIRE(m.kl >= 0 && m.ku >= 0 && m.kl < m.n + 1 && m.ku < m.n + 1, "operator: bad band");
+            if (m.kind == TK_BANDED) TK_REQUIRE(m.kl >= 0 && m.ku >= 0 && m.kl + m.ku < 65536, "operator: bad band");
             D.mats.push_back(m);
         }
     }
@@ -390,14 +390,12 @@ static void solve_mln(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucker 
 }
 
 // ------------------------------------------------------------------------------------------
-// True residual in Tucker form: QR of the concatenated distinct factors per mode
+// ||sum_i c_i X_i|| in Tucker form: QR of the concatenated distinct factors per mode, then the
+// norm of the small dense core sum_i c_i G_i x_k R_k[:, block_i] (no cancellation between terms)
 // ------------------------------------------------------------------------------------------
-static double true_residual(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucker *x,
-                            const tk_tucker *b, int transpose) {
+static double sum_norm(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms) {
     ScopedMark mark(*c.arena);
     const int d = pb.d;
-    std::vector<TTerm> terms = apply_operator(c, pb, op, term_of(x), transpose);
-    terms.push_back(term_of(b, -1.0));
     double *Rk[TK_MAX_D];
     int rows[TK_MAX_D];
     std::vector<std::vector<int>> off(terms.size(), std::vector<int>(d));
@@ -412,7 +410,7 @@ static double true_residual(Ctx &c, const Dims &pb, const OpDesc &op, const tk_t
             off[i][k] = width;
             width += terms[i].r[k];
         }
-        TK_REQUIRE(width <= 256, "residual: concatenated rank above 256");
+        TK_REQUIRE(width <= 256, "sum norm: concatenated rank above 256");
         double *U = c.arena->alloc((size_t)pb.n[k] * width);
         for (auto &kv : seen) {
             int rr = 0;
@@ -445,14 +443,118 @@ static double true_residual(Ctx &c, const Dims &pb, const OpDesc &op, const tk_t
         G.jobs.push_back(J);
     }
     ttm_groups(c, d, {G});
-    double *sc = c.arena->alloc(2);
+    double *sc = c.arena->alloc(1);
     dot(c, core, core, cs, sc);
-    const TTerm B = term_of(b);
-    inner_batch(c, pb, {InnerJob{B, B, sc + 1}});
-    double h[2];
-    TK_CUDA(cudaMemcpyAsync(h, sc, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    double h;
+    TK_CUDA(cudaMemcpyAsync(&h, sc, sizeof(double), cudaMemcpyDeviceToHost, c.st));
     TK_CUDA(cudaStreamSynchronize(c.st));
-    return std::sqrt(std::max(h[0], 0.0)) / std::sqrt(std::max(h[1], 0.0));
+    return std::sqrt(std::max(h, 0.0));
+}
+
+// True relative residual ||L(X) - B|| / ||B|| (output contract of Algorithms 2 and 6)
+static double true_residual(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucker *x,
+                            const tk_tucker *b, int transpose) {
+    ScopedMark mark(*c.arena);
+    std::vector<TTerm> terms = apply_operator(c, pb, op, term_of(x), transpose);
+    terms.push_back(term_of(b, -1.0));
+    const double num = sum_norm(c, pb, terms);
+    const double den = sum_norm(c, pb, {term_of(b)});
+    return num / den;
+}
+
+// ------------------------------------------------------------------------------------------
+// Adjoint contractions.  With mu the adjoint solution (L^T mu = dl/dx) and x the forward
+// solution:  dl/dtheta_t = -<mu, L_t(x)>,  dl/dG_b = mu x_k U_bk^T = G_mu x_k (U_bk^T U_mu,k),
+// dl/dU_bk = U_mu,k [G_mu x_{j != k} (U_bj^T U_mu,j)]_(k) G_b(k)^T.
+// ------------------------------------------------------------------------------------------
+static void adjoint_grads(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucker *mu, const tk_tucker *x,
+                          const tk_tucker *b, double *dtheta_host, double *dcore, double *const *dfac) {
+    ScopedMark mark(*c.arena);
+    const int d = pb.d;
+    const TTerm M = term_of(mu), X = term_of(x), Bt = term_of(b);
+    double *dth = c.arena->alloc(op.nterms);
+    if (dtheta_host) {
+        OpDesc unit = op;
+        for (auto &t : unit.theta) t = 1.0;
+        std::vector<TTerm> lx = apply_operator(c, pb, unit, X, 0);
+        std::vector<InnerJob> ij;
+        for (int t = 0; t < op.nterms; ++t) ij.push_back(InnerJob{M, lx[t], dth + t});
+        inner_batch(c, pb, ij);
+    }
+    // P_k = U_bk^T U_mu,k  (r_b x r_mu)
+    double *P[TK_MAX_D];
+    {
+        Gemm g(c);
+        for (int k = 0; k < d; ++k) {
+            P[k] = c.arena->alloc((size_t)Bt.r[k] * M.r[k]);
+            g.add1(Bt.r[k], M.r[k], pb.n[k], 1, 0, Bt.f[k], pb.n[k], M.f[k], pb.n[k], P[k], Bt.r[k]);
+        }
+        g.run();
+    }
+    if (dcore) {
+        TtmGroup G{};
+        for (int k = 0; k < d; ++k) G.sdims[k] = Bt.r[k];
+        G.out = dcore;
+        G.beta = 0.0;
+        TtmJob J{};
+        J.core = M.core;
+        for (int k = 0; k < d; ++k) { J.r[k] = M.r[k]; J.P[k] = P[k]; J.ldp[k] = Bt.r[k]; }
+        J.coef = 1.0;
+        G.jobs.push_back(J);
+        ttm_groups(c, d, {G});
+    }
+    if (dfac) {
+        // H_k = G_mu x_{j != k} P_j  (identity in mode k), then dU_bk = U_mu,k H_k(k) G_b(k)^T
+        std::vector<TtmGroup> groups(d);
+        std::vector<double *> Hk(d);
+        std::vector<double *> eye(d);
+        for (int k = 0; k < d; ++k) {
+            eye[k] = c.arena->alloc((size_t)M.r[k] * M.r[k]);
+            set_identity(c, eye[k], M.r[k]);
+        }
+        for (int k = 0; k < d; ++k) {
+            TtmGroup &G = groups[k];
+            long long sz = 1;
+            for (int j = 0; j < d; ++j) { G.sdims[j] = j == k ? M.r[j] : Bt.r[j]; sz *= G.sdims[j]; }
+            Hk[k] = c.arena->alloc(sz);
+            G.out = Hk[k];
+            G.beta = 0.0;
+            TtmJob J{};
+            J.core = M.core;
+            for (int j = 0; j < d; ++j) {
+                J.r[j] = M.r[j];
+                J.P[j] = j == k ? eye[k] : P[j];
+                J.ldp[j] = j == k ? M.r[j] : Bt.r[j];
+            }
+            J.coef = 1.0;
+            G.jobs.push_back(J);
+        }
+        ttm_groups(c, d, groups);
+        // T_k (r_mu,k x r_b,k) = H_k(k) G_b(k)^T : contraction over all modes but k
+        for (int k = 0; k < d; ++k) {
+            const long long a = [&]() { long long p = 1; for (int j = 0; j < k; ++j) p *= Bt.r[j]; return p; }();
+            const long long rest = [&]() { long long p = 1; for (int j = k + 1; j < d; ++j) p *= Bt.r[j]; return p; }();
+            double *Ht = c.arena->alloc((size_t)M.r[k] * a * rest);
+            double *Gt = c.arena->alloc((size_t)Bt.r[k] * a * rest);
+            // unfoldings as (a*rest) x r transposes
+            gather_unfold_t(c, Hk[k], Ht, a, M.r[k], rest);
+            gather_unfold_t(c, Bt.core, Gt, a, Bt.r[k], rest);
+            double *T = c.arena->alloc((size_t)M.r[k] * Bt.r[k]);
+            Gemm g(c);
+            g.add1(M.r[k], Bt.r[k], (int)(a * rest), 1, 0, Ht, (int)(a * rest), Gt, (int)(a * rest), T, M.r[k]);
+            g.run();
+            Gemm g2(c);
+            g2.add1(pb.n[k], Bt.r[k], M.r[k], 0, 0, M.f[k], pb.n[k], T, M.r[k], dfac[k], pb.n[k]);
+            g2.run();
+        }
+    }
+    if (dtheta_host) {
+        TK_CUDA(cudaMemcpyAsync(dtheta_host, dth, sizeof(double) * op.nterms, cudaMemcpyDeviceToHost, c.st));
+        TK_CUDA(cudaStreamSynchronize(c.st));
+        for (int t = 0; t < op.nterms; ++t) dtheta_host[t] = -dtheta_host[t];
+    } else {
+        TK_CUDA(cudaStreamSynchronize(c.st));
+    }
 }
 
 }  // namespace tk
@@ -688,6 +790,43 @@ int tk_residual(tk_handle *h, const tk_operator *op, const tk_tucker *x, const t
         const OpDesc od = op_of(op, pb);
         Ctx c = make_ctx(h, stream);
         *rel_host = true_residual(c, pb, od, x, b, transpose);
+        return TK_OK;
+    });
+}
+
+int tk_sum_norm(tk_handle *h, int32_t nterms, const tk_tucker *xs, const double *coef, double *out_host,
+                void *stream) {
+    return guarded(h, [&]() -> int {
+        TK_REQUIRE(nterms >= 1 && xs && coef && out_host, "sum_norm: bad arguments");
+        check_tucker(&xs[0], "term");
+        const Dims pb = dims_of(&xs[0]);
+        std::vector<TTerm> terms;
+        for (int i = 0; i < nterms; ++i) {
+            check_tucker(&xs[i], "term");
+            TK_REQUIRE(xs[i].d == pb.d, "sum_norm: order mismatch");
+            for (int k = 0; k < pb.d; ++k) TK_REQUIRE(xs[i].n[k] == pb.n[k], "sum_norm: mode size mismatch");
+            terms.push_back(term_of(&xs[i], coef[i]));
+        }
+        Ctx c = make_ctx(h, stream);
+        *out_host = sum_norm(c, pb, terms);
+        return TK_OK;
+    });
+}
+
+int tk_adjoint_grads(tk_handle *h, const tk_operator *op, const tk_tucker *mu, const tk_tucker *x,
+                     const tk_tucker *b, double *dtheta_host, double *dcore_b, double *const *dfactor_b,
+                     void *stream) {
+    return guarded(h, [&]() -> int {
+        check_tucker(mu, "mu");
+        check_tucker(x, "x");
+        check_tucker(b, "b");
+        const Dims pb = dims_of(mu);
+        for (int k = 0; k < pb.d; ++k)
+            TK_REQUIRE(x->n[k] == pb.n[k] && b->n[k] == pb.n[k], "adjoint_grads: mode size mismatch");
+        TK_REQUIRE(x->d == pb.d && b->d == pb.d, "adjoint_grads: order mismatch");
+        const OpDesc od = op_of(op, pb);
+        Ctx c = make_ctx(h, stream);
+        adjoint_grads(c, pb, od, mu, x, b, dtheta_host, dcore_b, dfactor_b);
         return TK_OK;
     });
 }

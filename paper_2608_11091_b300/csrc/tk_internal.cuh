@@ -234,6 +234,8 @@ void superdiag(Ctx &c, const double *G, int m, int d, double *out, double scale_
                const double *scale_dev);
 // scalar helpers for the solver control flow
 void sqrt_scalar(Ctx &c, const double *in, double *out);
+// p = I (n x n)
+void set_identity(Ctx &c, double *p, int n);
 // dst (cols x rows, ld ldd) = src(rows x cols, ld lds)^T
 void transpose_block(Ctx &c, double *dst, int ldd, const double *src, int lds, int rows, int cols);
 // upper triangle (rows x cols) of src into dst, zeros below the diagonal
