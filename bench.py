@@ -327,27 +327,61 @@ def roofline_from_profile(prof, wl, opts, rep):
     return out
 
 
+def _timed_solve(P, torch, dop, b, opts):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x, rep = P.tk_solve(dop, b, opts)
+    torch.cuda.synchronize()
+    return x, rep, time.perf_counter() - t0
+
+
 def secondary(P, W, torch):
-    """Other workloads of the method, one solve each (reported, not the headline)."""
+    """Other workloads of the method, FP64 and mixed form, one solve each after a warm-up
+    (reported, not the headline), and the cost of a gradient (forward + adjoint solve)."""
     out = {}
-    for name in ["poisson3d_n32", "deblur3d_n128", "varcoef4d_n128", "poisson3d_n1024"]:
+    for name in ["convdiff3d_n256", "poisson3d_n32", "deblur3d_n128", "varcoef4d_n128", "poisson3d_n1024"]:
         wl = W.workload(name)
         prm = wl.params
         if name == "poisson3d_n1024":
             prm.maxit = 10
         dop = P.DeviceOperator(wl.op)
         b = P.DeviceTucker.from_numpy(wl.b.core, wl.b.factors)
-        opts = P.Options.from_params(prm)
-        P.tk_solve(dop, b, opts)                     # warm-up (workspace, module load)
+        entry = {"variant": prm.variant}
+        forms = ["fp64", "mixed"] if prm.variant == "rhosvd" else ["fp64"]
+        for form in forms:
+            opts = P.Options.from_params(prm, precision=form)
+            P.tk_solve(dop, b, opts)                     # warm-up (workspace, module load)
+            x, rep, dt = _timed_solve(P, torch, dop, b, opts)
+            tr = P.tk_residual(dop, x, b)
+            entry[form] = {"iters": rep.iters, "status": rep.status, "seconds": round(dt, 4),
+                           "iters_per_s": round(rep.iters / dt, 2), "sketched_res": rep.sketched_res,
+                           "true_rel_residual": tr, "time_to_1e-6_s": round(dt, 4) if tr <= 1e-6 else None}
+        out[name] = entry
+    # gradient of 0.5||x - x_ref||^2 w.r.t. theta and b: forward solve + adjoint solve + contractions
+    wl = W.workload("deblur3d_n128")
+    prm = wl.params
+    prm.maxit = 30
+    dop = P.DeviceOperator(wl.op)
+    xr = P.DeviceTucker.from_numpy(wl.x_true.core, wl.x_true.factors)
+    grads = {}
+    for form in ["fp64", "mixed"]:
+        opts = P.Options.from_params(prm, precision=form)
+        theta = torch.tensor(wl.op.theta, dtype=torch.float64, requires_grad=True)
+        core = P.to_fortran(wl.b.core, "cuda").requires_grad_(True)
+        facs = [P.to_fortran(u, "cuda").requires_grad_(True) for u in wl.b.factors]
+        loss = P.autograd.tucker_solve_mse(dop, theta, core, facs, xr, opts)   # warm-up
+        loss.backward()
+        theta.grad = None
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        x, rep = P.tk_solve(dop, b, opts)
+        loss = P.autograd.tucker_solve_mse(dop, theta, core, facs, xr, opts)
+        t1 = time.perf_counter()
+        loss.backward()
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        tr = P.tk_residual(dop, x, b)
-        out[name] = {"variant": prm.variant, "iters": rep.iters, "status": rep.status, "seconds": round(dt, 4),
-                     "iters_per_s": round(rep.iters / dt, 2), "sketched_res": rep.sketched_res,
-                     "true_rel_residual": tr, "time_to_1e-6_s": round(dt, 4) if tr <= 1e-6 else None}
+        t2 = time.perf_counter()
+        grads[form] = {"forward_s": round(t1 - t0, 4), "backward_s": round(t2 - t1, 4),
+                       "loss": loss.item(), "dloss_dtheta": theta.grad.tolist()}
+    out["gradient_deblur3d_n128_30it"] = grads
     return out
 
 

@@ -669,6 +669,8 @@ int tk_solve(tk_handle *h, const tk_operator *op, const tk_tucker *b, const tk_o
             solve_mln(c, pb, od, b, o, x_out, so, h->pinned);
         TK_CUDA(cudaEventRecord(e1, c.st));
         TK_CUDA(cudaEventSynchronize(e1));
+        if (o.precision == TK_MIXED && tc_error_flag(true) != 0)
+            throw Error{TK_EINTERNAL, "a tensor-core GEMM timed out waiting for its MMAs"};
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         cudaEventDestroy(e0);

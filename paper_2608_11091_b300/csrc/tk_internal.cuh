@@ -150,6 +150,21 @@ private:
 };
 
 // ------------------------------------------------------------------------------------------
+// Tensor-core GEMM of the mixed-precision form: C = beta C + coef op(A) op(B), FP64 operands
+// split into na (nb) BF16 pieces, FP32 accumulation in tensor memory (k_gemm_tc.cu).
+// ------------------------------------------------------------------------------------------
+struct TcProb {
+    const double *A, *B;
+    double *C;
+    int M, N, K, lda, ldb, ldc, ta, tb, na, nb;
+    double coef, beta;
+    int tiles_m, tiles_n, tile_begin;
+};
+void gemm_tc(Ctx &c, const std::vector<TcProb> &probs);
+// 1 if a tensor-core GEMM gave up waiting for its MMAs since the last reset
+int tc_error_flag(bool reset);
+
+// ------------------------------------------------------------------------------------------
 // Small dense linear algebra (FP64)
 // ------------------------------------------------------------------------------------------
 struct QRJob {

@@ -21,28 +21,38 @@ static long long prod(const int *v, int a, int b) {
 //   keep <  0:  out (s)          with out[l] = sum_a G[a] prod_j P_j[a_j, l]
 // One GEMM contracts an outer mode, then row-wise Hadamard contractions remove the rest.
 // ------------------------------------------------------------------------------------------
-void mttkrp_batch(Ctx &c, int d, int s, const std::vector<MttJob> &jobs) {
+void mttkrp_batch(Ctx &c, int d, int s, const std::vector<MttJob> &jobs, bool tensor_cores) {
     struct St { std::vector<int> dims, modes; const double *T; };
     std::vector<St> st(jobs.size());
     Gemm g(c);
+    std::vector<TcProb> tc;
     for (size_t i = 0; i < jobs.size(); ++i) {
         const MttJob &J = jobs[i];
         const int nleft = (J.keep >= 0) ? d - 2 : d - 1;   // contractions after the GEMM
         if (J.keep != d - 1) {
             const long long rest = prod(J.r, 0, d - 1);
             double *T = nleft == 0 ? J.out : c.arena->alloc(rest * s);
-            g.add1((int)rest, s, J.r[d - 1], 0, 0, J.core, (int)rest, J.P[d - 1], J.ldp[d - 1], T, (int)rest);
+            if (tensor_cores)
+                tc.push_back(TcProb{J.core, J.P[d - 1], T, (int)rest, s, J.r[d - 1], (int)rest, J.ldp[d - 1], (int)rest,
+                                    0, 0, 3, 3, 1.0, 0.0, 0, 0, 0});
+            else
+                g.add1((int)rest, s, J.r[d - 1], 0, 0, J.core, (int)rest, J.P[d - 1], J.ldp[d - 1], T, (int)rest);
             for (int k = 0; k < d - 1; ++k) { st[i].dims.push_back(J.r[k]); st[i].modes.push_back(k); }
             st[i].T = T;
         } else {
             const long long rest = prod(J.r, 1, d);
             double *T = nleft == 0 ? J.out : c.arena->alloc(rest * s);
-            g.add1((int)rest, s, J.r[0], 1, 0, J.core, J.r[0], J.P[0], J.ldp[0], T, (int)rest);
+            if (tensor_cores)
+                tc.push_back(TcProb{J.core, J.P[0], T, (int)rest, s, J.r[0], J.r[0], J.ldp[0], (int)rest,
+                                    1, 0, 3, 3, 1.0, 0.0, 0, 0, 0});
+            else
+                g.add1((int)rest, s, J.r[0], 1, 0, J.core, J.r[0], J.P[0], J.ldp[0], T, (int)rest);
             for (int k = 1; k < d; ++k) { st[i].dims.push_back(J.r[k]); st[i].modes.push_back(k); }
             st[i].T = T;
         }
     }
     g.run();
+    gemm_tc(c, tc);
     for (;;) {
         std::vector<HadJob> hj;
         for (size_t i = 0; i < jobs.size(); ++i) {
@@ -258,20 +268,28 @@ void roundsum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const RSC
         gaussian(c, cfg.seed, sids, cnt, S, d, cfg.bf16_sketch);
     }
     // 2. factor sketches M_j^(i) = U_j^(i)T S_j, shared between terms with the same factor
+    // (mixed form: on tensor cores, U in three BF16 pieces, S exact in BF16)
+    const bool mixed = cfg.bf16_sketch != 0;
     std::vector<std::vector<const double *>> M(N, std::vector<const double *>(d));
     {
         Gemm g(c);
+        std::vector<TcProb> tc;
         std::map<const double *, double *> made[TK_MAX_D];
         for (int i = 0; i < N; ++i)
             for (int j = 0; j < d; ++j) {
                 auto it = made[j].find(terms[i].f[j]);
                 if (it != made[j].end()) { M[i][j] = it->second; continue; }
                 double *m = c.arena->alloc((size_t)terms[i].r[j] * sr);
-                g.add1(terms[i].r[j], sr, pb.n[j], 1, 0, terms[i].f[j], pb.n[j], S[j], pb.n[j], m, terms[i].r[j]);
+                if (mixed)
+                    tc.push_back(TcProb{terms[i].f[j], S[j], m, terms[i].r[j], sr, pb.n[j], pb.n[j], pb.n[j],
+                                        terms[i].r[j], 1, 0, 3, 1, 1.0, 0.0, 0, 0, 0});
+                else
+                    g.add1(terms[i].r[j], sr, pb.n[j], 1, 0, terms[i].f[j], pb.n[j], S[j], pb.n[j], m, terms[i].r[j]);
                 made[j][terms[i].f[j]] = m;
                 M[i][j] = m;
             }
         g.run();
+        gemm_tc(c, tc);
     }
     // 3. Z_k^(i) = G_(k)^(i) (KR_{j != k} M_j^(i))   (r_k x sr)
     std::vector<std::vector<double *>> Z(N, std::vector<double *>(d));
@@ -287,7 +305,7 @@ void roundsum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const RSC
                 J.out = Z[i][k];
                 mj.push_back(J);
             }
-        mttkrp_batch(c, d, sr, mj);
+        mttkrp_batch(c, d, sr, mj, mixed);
     }
     // 4. Y_k = sum_i c_i U_k^(i) Z_k^(i)   (n_k x sr)
     double *Y[TK_MAX_D], *Q[TK_MAX_D];

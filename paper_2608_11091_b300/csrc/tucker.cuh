@@ -34,7 +34,8 @@ struct MttJob {
     int keep;
     double *out;
 };
-void mttkrp_batch(Ctx &c, int d, int s, const std::vector<MttJob> &jobs);
+// tensor_cores: the leading GEMM runs on tcgen05 (mixed-precision form), the rest in FP64
+void mttkrp_batch(Ctx &c, int d, int s, const std::vector<MttJob> &jobs, bool tensor_cores = false);
 
 struct TtmJob {
     const double *core;

@@ -6,7 +6,8 @@ models a second correct FP64 implementation that sums in another order; the GPU 
 tolerance of a case is max(1e-10, 10 x this value).  Calls only the oracle and the input
 generators.
 
-Run: python tests/golden/make_solver_sensitivity.py
+Run: python tests/golden/make_solver_sensitivity.py [--mixed]
+(--mixed writes tests/golden/mixed_sensitivity.json for the mixed-precision cases instead.)
 """
 import json
 import os
@@ -22,10 +23,10 @@ from oracle import rhosvd as ORH  # noqa: E402
 from oracle import sgmres as OS  # noqa: E402
 from oracle import mln as OM  # noqa: E402
 import workloads as W  # noqa: E402
-from tests.solver_cases import CASES  # noqa: E402
+from tests.solver_cases import CASES, MIXED_CASES  # noqa: E402
 
 
-def _solve(wl, prm, noise, seed, transpose=False):
+def _solve(wl, prm, noise, seed, transpose=False, bf16=False):
     rng = np.random.default_rng(seed)
     rs, rec = OS.roundsum, OS.mln_recovery
 
@@ -41,10 +42,33 @@ def _solve(wl, prm, noise, seed, transpose=False):
         OS.roundsum, OS.mln_recovery = noisy_rs, noisy_rec
     try:
         if prm.variant == "rhosvd":
-            return OS.rhosvd_sgmres(wl.op, wl.b, prm, transpose=transpose)
+            return OS.rhosvd_sgmres(wl.op, wl.b, prm, transpose=transpose, bf16_sketch=bf16)
         return OS.mln_sgmres(wl.op, wl.b, prm, transpose=transpose)
     finally:
         OS.roundsum, OS.mln_recovery = rs, rec
+
+
+def _movement(wl, prm, noise, transpose=False, bf16=False):
+    base = _solve(wl, prm, 0.0, 0, transpose, bf16)
+    xs, hs = [], []
+    for s in range(5):
+        alt = _solve(wl, prm, noise, s + 1, transpose, bf16)
+        n = min(len(alt.res_hist), len(base.res_hist))
+        hs.append(float(np.max(np.abs(np.array(alt.res_hist[:n]) - np.array(base.res_hist[:n]))
+                               / np.array(base.res_hist[:n]))))
+        xs.append(ORS.tucker_sum_norm([(1.0, alt.x), (-1.0, base.x)]) / ORS.tucker_sum_norm([(1.0, base.x)]))
+    return {"x": max(xs), "hist": max(hs), "iters": base.iters}
+
+
+def main_mixed():
+    """Mixed form: BF16-rounded sketches, 1e-7 perturbations (the FP32-level accuracy of the
+    tensor-core range finder) -> tests/golden/mixed_sensitivity.json."""
+    out = {}
+    for name, (build, prm) in MIXED_CASES.items():
+        out[name] = _movement(build(), prm, 1e-7, bf16=True)
+        print(name, out[name], flush=True)
+    with open(os.path.join(ROOT, "tests", "golden", "mixed_sensitivity.json"), "w") as f:
+        json.dump(out, f, indent=1, sort_keys=True)
 
 
 def main():
@@ -67,4 +91,7 @@ def main():
 
 
 if __name__ == "__main__":
-    main()
+    if "--mixed" in sys.argv:
+        main_mixed()
+    else:
+        main()

@@ -15,3 +15,12 @@ CASES = {
     "adjoint_convdiff_n30": (lambda: W.convdiff3d(30, 4, None), W.SolverParams('rhosvd', 10, 64, 5, 15, 1e-8, seed=9), True),
     "exhaustion_convdiff_n16": (lambda: W.convdiff3d(16, 5, None), W.SolverParams('rhosvd', 4, 10, 5, 40, 1e-14, seed=1), False),
 }
+
+
+# Mixed-precision parity cases: (builder, parameters); RoundSum sketches rounded to BF16.
+MIXED_CASES = {
+    "poisson3d_n20_r12": (lambda: W.poisson3d(20, 1, 3, None, "p20"), W.SolverParams('rhosvd', 12, 64, 5, 25, 1e-9, seed=4)),
+    "convdiff3d_n48": (lambda: W.convdiff3d(48, 1, None), W.SolverParams('rhosvd', 12, 96, 5, 15, 1e-8, seed=2)),
+    "deblur3d_n40": (lambda: W.deblur3d(40, 2, None), W.SolverParams('rhosvd', 12, 128, 5, 8, 1e-8, seed=5)),
+    "convdiff3d_n256_prefix": (lambda: W.workload("convdiff3d_n256"), W.SolverParams('rhosvd', 32, 128, 5, 10, 1e-6, seed=0)),
+}
