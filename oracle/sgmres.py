@@ -52,9 +52,14 @@ def _ls(mcols: List[np.ndarray], bs: np.ndarray):
 
 
 def rhosvd_sgmres(op: Operator, b: Tucker, prm: SolverParams, transpose: bool = False,
-                  bf16_sketch: bool = False, maxit: Optional[int] = None) -> Result:
+                  bf16_sketch: bool = False, maxit: Optional[int] = None,
+                  precond: Optional[Operator] = None) -> Result:
     """Algorithm 2.  bf16_sketch rounds RoundSum's Gaussian matrices to bfloat16 values (the
-    mixed-precision form stores them so); the arithmetic stays FP64."""
+    mixed-precision form stores them so); the arithmetic stays FP64.
+
+    precond: a separable operator M applied with truncation, Z_k = RoundSum(M(V_k)), in the
+    flexible form of Section 3.4: the Krylov columns sketch RoundSum(L(Z_k)) and the solution is
+    RoundSum(sum_i y_i Z_i)."""
     d, n = b.d, b.n
     s = prm.sketch_s
     maxit = prm.maxit if maxit is None else maxit
@@ -86,8 +91,13 @@ def rhosvd_sgmres(op: Operator, b: Tucker, prm: SolverParams, transpose: bool = 
     status = SKETCH_EXHAUSTED if kmax < maxit else NOT_CONVERGED
     y = np.zeros(0)
     k = 0
+    zs: List[Tucker] = []
     for k in range(1, kmax + 1):
-        w = rs([(1.0, t) for t in apply_op(op, v[-1], transpose)])
+        if precond is not None:
+            zs.append(rs([(1.0, t) for t in apply_op(precond, v[-1], transpose)]))
+            w = rs([(1.0, t) for t in apply_op(op, zs[-1], transpose)])
+        else:
+            w = rs([(1.0, t) for t in apply_op(op, v[-1], transpose)])
         w0 = norm(w)
         mcols.append(kron_sketch(w, sk))
         window = range(max(1, k - prm.ktrunc + 1), k + 1)
@@ -104,7 +114,8 @@ def rhosvd_sgmres(op: Operator, b: Tucker, prm: SolverParams, transpose: bool = 
         if res / beta_s < prm.eta * prm.tol:
             status = CONVERGED
             break
-    x = rs([(float(y[i]), v[i]) for i in range(k)])
+    basis = zs if precond is not None else v
+    x = rs([(float(y[i]), basis[i]) for i in range(k)])
     return Result(x, k, status, hist, y, ranks, sizes, v)
 
 

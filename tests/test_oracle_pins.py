@@ -412,3 +412,60 @@ def test_tucker_adjoint_gradients_match_dense():
         ref = T.unfold(mu_d, k) @ reduce(np.kron, [wl.b.factors[j] for j in reversed(range(3)) if j != k]) \
             @ T.unfold(wl.b.core, k).T
         assert np.allclose(gf[k], ref, atol=1e-9 * np.abs(ref).max())
+
+
+# ------------------------------------------------------------------------------ preconditioner
+def test_expsum_mode_matrices_are_matrix_exponentials():
+    from scipy.linalg import expm
+    from oracle import precond as OP
+    n, q = 12, 4
+    m = OP.expsum_preconditioner(n, 3, q)
+    c, t = OP.expsum_weights(q)
+    tn = O.mode_dense(W.second_difference(n))
+    for h in [0, 3, 2 * q]:
+        assert np.allclose(m.mats[h][0].data, expm(-t[h] * tn), atol=1e-12)
+        assert np.isclose(m.theta[h], c[h])
+
+
+def test_expsum_approximates_inverse_laplacian_spectrum():
+    """sum_h c_h exp(-t_h lambda) ~ 1/lambda over the 3D Poisson spectrum; the error falls
+    quickly with q (sinc quadrature of 1/lambda = int exp(-t lambda) dt)."""
+    from oracle import precond as OP
+    n = 32
+    _, lam = OP.sine_eigenpairs(n)
+    L = (lam[:, None, None] + lam[None, :, None] + lam[None, None, :]).ravel()
+    errs = []
+    for q in [4, 8, 16]:
+        c, t = OP.expsum_weights(q)
+        approx = (c[None, :] * np.exp(-np.outer(L, t))).sum(axis=1)
+        errs.append(np.max(np.abs(approx * L - 1.0)))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[1] < 1e-2 and errs[2] < 1e-3
+
+
+def test_flexible_sgmres_with_exact_inverse_converges_at_once():
+    """Flexible sGMRES with M = L^{-1} exactly (dense inverse as one mode-matrix term of a d = 3
+    Kronecker-product operator is not separable; use the 1D-separable operator
+    L = T (x) T (x) T whose inverse is T^{-1} (x) T^{-1} (x) T^{-1})."""
+    n = 6
+    t = O.mode_dense(W.second_difference(n))
+    op = W.Operator(3, [n] * 3, [1.0], [[W.ModeMat('D', n, 0, 0, t)] * 3])
+    inv = W.Operator(3, [n] * 3, [1.0], [[W.ModeMat('D', n, 0, 0, np.linalg.inv(t))] * 3])
+    b = W.random_tucker([n] * 3, [2, 1, 2], 40)
+    prm = W.SolverParams('rhosvd', n, 40, 5, 5, 1e-12, round_tol=1e-15)
+    res = S.rhosvd_sgmres(op, b, prm, precond=inv)
+    assert res.iters <= 2 and res.res_hist[0] < 1e-12
+    xs = T.full(b)
+    for k in range(3):
+        xs = T.ttm(xs, np.linalg.inv(t), k)
+    assert np.linalg.norm(T.full(res.x) - xs) <= 1e-11 * np.linalg.norm(xs)
+
+
+def test_preconditioned_poisson_reaches_1e6_quickly():
+    from oracle import precond as OP
+    n = 32
+    wl = W.workload("poisson3d_n32")
+    prm = W.SolverParams('rhosvd', 12, 64, 5, 20, 1e-6, seed=0)
+    res = S.rhosvd_sgmres(wl.op, wl.b, prm, precond=OP.expsum_preconditioner(n, 3, 8))
+    assert res.status == S.CONVERGED and res.iters <= 12
+    assert RS.true_residual(wl.op, res.x, wl.b) < 1e-5
