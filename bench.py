@@ -52,6 +52,21 @@ def dist_info():
     return ws, rank, local
 
 
+def aggregate_over_ranks(t_local: float, units_local: float, device) -> tuple:
+    """Whole-job figures of independent replicas: (max over ranks of the timed seconds, sum over
+    ranks of the units processed).  One process per rank; `device` is where the reduction tensor
+    lives ("cuda" under NCCL, "cpu" under gloo).  A single process returns its own figures."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(t_local), float(units_local)
+    tmax = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    usum = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(usum, op=dist.ReduceOp.SUM)
+    return tmax.item(), usum.item()
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -211,15 +226,7 @@ def run_native(args):
     clocks = sampler.stop()
     ms = sum(a.elapsed_time(bb) for a, bb in evs)
     t_local = ms / 1000.0
-    if ws > 1:
-        tt = torch.tensor([t_local, float(iters)], dtype=torch.float64, device="cuda")
-        tmax = tt.clone()
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-        tsum = tt.clone()
-        torch.distributed.all_reduce(tsum, op=torch.distributed.ReduceOp.SUM)
-        t_all, it_all = tmax[0].item(), tsum[1].item()
-    else:
-        t_all, it_all = t_local, float(iters)
+    t_all, it_all = aggregate_over_ranks(t_local, iters, "cuda")
     value = it_all / t_all
 
     # ---------------- e2e through the public API with host buffers
@@ -248,13 +255,8 @@ def run_native(args):
     e1.record(stream)
     barrier()
     e2e_t = e0.elapsed_time(e1) / 1000.0
-    e2e_val = it_e2e / e2e_t
-    if ws > 1:
-        tt = torch.tensor([e2e_t, float(it_e2e)], dtype=torch.float64, device="cuda")
-        tmax, tsum = tt.clone(), tt.clone()
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(tsum, op=torch.distributed.ReduceOp.SUM)
-        e2e_val = tsum[1].item() / tmax[0].item()
+    e2e_tmax, e2e_iters = aggregate_over_ranks(e2e_t, it_e2e, "cuda")
+    e2e_val = e2e_iters / e2e_tmax
 
     # ---------------- per-kernel device time (library event profiler), one more solve
     P.tk_profile(True)
@@ -357,6 +359,34 @@ def secondary(P, W, torch):
                            "iters_per_s": round(rep.iters / dt, 2), "sketched_res": rep.sketched_res,
                            "true_rel_residual": tr, "time_to_1e-6_s": round(dt, 4) if tr <= 1e-6 else None}
         out[name] = entry
+    # the paper's preconditioned Poisson setting: exponential-sum preconditioner (Section 3.4),
+    # flexible iteration, rank-1 point-source right-hand side, n = 1000
+    wl = W.workload("poisson3d_point_n1000")
+    q = wl.extra["precond_q"]
+    dop = P.DeviceOperator(wl.op)
+    b = P.DeviceTucker.from_numpy(wl.b.core, wl.b.factors)
+    P.tk_expsum_laplacian(wl.b.n[0], 3, q)              # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pc = P.tk_expsum_laplacian(wl.b.n[0], 3, q)
+    torch.cuda.synchronize()
+    entry = {"precond_terms": 2 * q + 1, "precond_build_s": round(time.perf_counter() - t0, 4),
+             "tol": wl.params.tol}
+    for form in ["fp64", "mixed"]:
+        opts = P.Options.from_params(wl.params, precision=form)
+        P.tk_solve_precond(dop, pc, b, opts)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, rep = P.tk_solve_precond(dop, pc, b, opts)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        entry[form] = {"iters": rep.iters, "status": rep.status, "seconds": round(dt, 4),
+                       "true_rel_residual": P.tk_residual(dop, x, b), "ranks": rep.out_rank}
+    opts = P.Options.from_params(wl.params)
+    x, rep, dt = _timed_solve(P, torch, dop, b, opts)
+    entry["unpreconditioned"] = {"iters": rep.iters, "status": rep.status, "seconds": round(dt, 4),
+                                 "true_rel_residual": P.tk_residual(dop, x, b)}
+    out["poisson3d_point_n1000_expsum_q8"] = entry
     # gradient of 0.5||x - x_ref||^2 w.r.t. theta and b: forward solve + adjoint solve + contractions
     wl = W.workload("deblur3d_n128")
     prm = wl.params

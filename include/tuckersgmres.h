@@ -139,6 +139,23 @@ const char *tk_profile_report(tk_handle *h);
 int tk_solve(tk_handle *h, const tk_operator *op, const tk_tucker *b, const tk_opts *opts,
              tk_tucker *x_out, tk_report *report, void *stream);
 
+/* tk_solve_precond: RHOSVD-Tucker sGMRES with flexible preconditioning (Section 3.4): each
+ * iteration forms Z_k = RoundSum(M(V_k)) with the separable operator `precond` (same layout as
+ * `op`), sketches RoundSum(L(Z_k)), and the solution is RoundSum(sum_i y_i Z_i).  Otherwise as
+ * tk_solve; TK_EINVAL for the MLN variant or a NULL precond. */
+int tk_solve_precond(tk_handle *h, const tk_operator *op, const tk_operator *precond, const tk_tucker *b,
+                     const tk_opts *opts, tk_tucker *x_out, tk_report *report, void *stream);
+
+/* tk_expsum_laplacian: the exponential-sum approximation of the inverse Laplacian
+ * (Section 3.4): Delta_d^{-1} ~ sum_{h=-q}^{q} c_h E_h x ... x E_h with E_h = exp(-t_h T_n),
+ * T_n = tridiag(-1, 2, -1), t_h = exp(h eta), c_h = eta t_h, eta = pi / sqrt(q) (the printed
+ * exp(+t_h Delta_1) read with the minus sign that makes the sum approximate the inverse).
+ * E_h is formed on the GPU through the sine eigenpairs of T_n: V exp(-t_h Lambda) V^T.
+ * mats: 2q+1 caller-allocated device n x n column-major outputs, mats[h+q] = E_h;
+ * coef_host: 2q+1 doubles, coef_host[h+q] = c_h.  Build a tk_operator from them with
+ * TK_DENSE mode matrices (the same E_h in every mode).  Synchronizes. */
+int tk_expsum_laplacian(tk_handle *h, int64_t n, int32_t q, double *const *mats, double *coef_host, void *stream);
+
 /* tk_apply: the Tucker matvec of Section 3.1 without recompression.  For every term t and
  * mode k writes A_k^(t) U_k (or its transpose) into out_factors[t*d + k] (device,
  * n_k x r_k, caller-allocated); the terms share x's core scaled by theta_t.  For identity

@@ -20,7 +20,8 @@ TK_FP64, TK_MIXED = 0, 1
 EXPORTS = ["tk_create", "tk_destroy", "tk_last_error", "tk_solve", "tk_apply", "tk_roundsum",
            "tk_kron_sketch", "tk_inner", "tk_residual", "tk_gaussian", "tk_philox",
            "tk_sketched_ls", "tk_mln_roundsum", "tk_profile", "tk_profile_report",
-           "tk_sketched_ls_static", "tk_sum_norm", "tk_adjoint_grads"]
+           "tk_sketched_ls_static", "tk_sum_norm", "tk_adjoint_grads", "tk_solve_precond",
+           "tk_expsum_laplacian"]
 
 
 class tk_tucker(ctypes.Structure):
@@ -97,6 +98,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tk_sketched_ls_static": (ctypes.c_int, [vp, vp, i32, i32, vp, vp, vp]),
         "tk_sum_norm": (ctypes.c_int, [vp, i32, P(tk_tucker), dp, dp, vp]),
         "tk_adjoint_grads": (ctypes.c_int, [vp, P(tk_operator), P(tk_tucker), P(tk_tucker), P(tk_tucker), dp, vp, P(vp), vp]),
+        "tk_solve_precond": (ctypes.c_int, [vp, P(tk_operator), P(tk_operator), P(tk_tucker), P(tk_opts), P(tk_tucker),
+                                            P(tk_report), vp]),
+        "tk_expsum_laplacian": (ctypes.c_int, [vp, i64, i32, P(vp), dp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

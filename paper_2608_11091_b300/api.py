@@ -170,6 +170,31 @@ class DeviceOperator:
         self.mats = mats
         self.set_theta(op.theta if theta is None else theta)
 
+    @classmethod
+    def from_device(cls, d: int, n: Sequence[int], theta: Sequence[float], mats) -> "DeviceOperator":
+        """Operator from mode matrices already on the GPU: mats[t][k] = (kind, tensor, kl, ku) with
+        kind 'I' (tensor None), 'B' (band layout (kl+ku+1) x n) or 'D' (dense n x n), float64 and
+        column-major.  The tensors are referenced, not copied."""
+        self = cls.__new__(cls)
+        self.d, self.n, self.nterms = int(d), [int(v) for v in n], len(mats)
+        mm = (L.tk_modemat * (self.nterms * self.d))()
+        keep = []
+        for t in range(self.nterms):
+            for k in range(self.d):
+                kind, data, kl, ku = mats[t][k]
+                e = mm[t * self.d + k]
+                e.kind, e.kl, e.ku, e.n = cls._KIND[kind], int(kl), int(ku), self.n[k]
+                if kind == 'I':
+                    e.data = None
+                    continue
+                if data.dtype != torch.float64 or not data.is_cuda or not is_fortran(data):
+                    raise TuckerError("mode matrices must be float64 CUDA tensors in column-major layout")
+                e.data = data.data_ptr()
+                keep.append(data)
+        self._keep, self.mats = [keep], mm
+        self.set_theta(theta)
+        return self
+
     def set_theta(self, theta: Sequence[float]):
         self.theta_values = [float(v) for v in theta]
         self.theta = (ctypes.c_double * self.nterms)(*self.theta_values)
@@ -248,6 +273,38 @@ def tk_solve(op: DeviceOperator, b: DeviceTucker, opts: Options, x: Optional[Dev
     r = Report(rep.iters, STATUS[rep.status], rep.sketched_res, list(hist[:rep.iters]),
                list(rep.out_rank[:b.d]), rep.ms_total, rep.workspace_bytes, rep.kernel_launches)
     return x, r
+
+
+def tk_solve_precond(op: DeviceOperator, precond: DeviceOperator, b: DeviceTucker, opts: Options,
+                     x: Optional[DeviceTucker] = None, stream=None, device: Optional[int] = None):
+    """RHOSVD-Tucker sGMRES with flexible preconditioning by the separable operator `precond`
+    (Section 3.4). Returns (x, Report)."""
+    h = handle(device)
+    if x is None:
+        x = DeviceTucker.empty(b.n, [opts.rank_cap] * b.d, device=b.core.device)
+    hist = (ctypes.c_double * max(1, opts.maxit))()
+    rep = L.tk_report()
+    rep.res_hist = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
+    rep.res_hist_len = opts.maxit
+    opc, pc, bc, oc, xc = op.c(), precond.c(), b.c(), opts.c(), x.c()
+    rc = h.lib.tk_solve_precond(h.h, ctypes.byref(opc), ctypes.byref(pc), ctypes.byref(bc), ctypes.byref(oc),
+                                ctypes.byref(xc), ctypes.byref(rep), _stream(stream))
+    h.check(rc, "tk_solve_precond")
+    r = Report(rep.iters, STATUS[rep.status], rep.sketched_res, list(hist[:rep.iters]),
+               list(rep.out_rank[:b.d]), rep.ms_total, rep.workspace_bytes, rep.kernel_launches)
+    return x, r
+
+
+def tk_expsum_laplacian(n: int, d: int, q: int, device="cuda", stream=None) -> DeviceOperator:
+    """Exponential-sum approximation of the inverse of the d-dimensional Laplacian
+    T_n (+) .. (+) T_n, T_n = tridiag(-1, 2, -1): 2q+1 separable terms c_h E_h x .. x E_h with
+    E_h = exp(-t_h T_n) formed on the GPU (Section 3.4)."""
+    h = handle()
+    mats = [fortran_empty((n, n), device) for _ in range(2 * q + 1)]
+    ptrs = (ctypes.c_void_p * (2 * q + 1))(*[m.data_ptr() for m in mats])
+    coef = (ctypes.c_double * (2 * q + 1))()
+    h.check(h.lib.tk_expsum_laplacian(h.h, int(n), int(q), ptrs, coef, _stream(stream)), "tk_expsum_laplacian")
+    return DeviceOperator.from_device(d, [n] * d, list(coef), [[('D', m, 0, 0)] * d for m in mats])
 
 
 def tk_profile(enable: bool, device: Optional[int] = None):

@@ -477,6 +477,30 @@ void triu_copy(Ctx &c, double *dst, int ldd, const double *src, int lds, int row
     c.check_launch("triu");
 }
 
+// Sine eigenvectors of tridiag(-1, 2, -1) (the DST-I basis, Section 3.4), column-major:
+// V[i, j] = sqrt(2/(n+1)) sin((i+1)(j+1) pi / (n+1)); optionally scaled per column by
+// exp(-t lambda_j), lambda_j = 2 - 2 cos((j+1) pi / (n+1)).
+__global__ void k_sine_basis(double *V, int n, double t) {
+    const long long total = (long long)n * n;
+    const double sc = sqrt(2.0 / (n + 1));
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long i = e % n, j = e / n;
+        const long long prod = ((i + 1) * (j + 1)) % (2 * (n + 1));   // sin is 2(n+1)-periodic here
+        double v = sc * sinpi((double)prod / (n + 1));
+        if (t != 0.0) v *= exp(-t * (2.0 - 2.0 * cospi((double)(j + 1) / (n + 1))));
+        V[e] = v;
+    }
+}
+
+void sine_basis(Ctx &c, double *V, int n, double t) {
+    const long long total = (long long)n * n;
+    const long long blocks = std::min<long long>((total + 255) / 256, 4096);
+    c.pre_launch();
+    k_sine_basis<<<(unsigned)blocks, 256, 0, c.st>>>(V, n, t);
+    c.check_launch("sine_basis");
+}
+
 __global__ void k_set_identity(double *p, int n) {
     const long long total = (long long)n * n;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;

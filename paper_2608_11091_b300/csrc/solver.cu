@@ -120,7 +120,8 @@ static Slot alloc_slot(Ctx &c, const Dims &pb, int R) {
 // RHOSVD-Tucker sGMRES (Algorithm 2)
 // ------------------------------------------------------------------------------------------
 static void solve_rhosvd(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucker *b,
-                         const tk_opts &o, tk_tucker *x, SolveOut &so, double *pinned) {
+                         const tk_opts &o, tk_tucker *x, SolveOut &so, double *pinned,
+                         const OpDesc *precond = nullptr) {
     ScopedMark solve_mark(*c.arena);
     const int d = pb.d, R = o.rank_cap, s = o.sketch_s, sr = o.rank_cap + o.oversample_p;
     const int kmax = std::min(o.maxit, s - 1);
@@ -173,11 +174,19 @@ static void solve_rhosvd(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tuck
     so.status = kmax < o.maxit ? TK_SKETCH_EXHAUSTED : TK_NOT_CONVERGED;
     int k = 0;
     uint64_t call = 0;
+    std::vector<TTerm> Z;   // flexible preconditioning (Section 3.4): Z_k = RoundSum(M(V_k))
     for (k = 1; k <= kmax; ++k) {
         Slot vn = alloc_slot(c, pb, R);
+        if (precond) {
+            Slot zs = alloc_slot(c, pb, R);
+            ScopedMark it(*c.arena);
+            std::vector<TTerm> mterms = apply_operator(c, pb, *precond, V.back(), o.transpose);
+            roundsum(c, pb, mterms, RSConfig{sr, R, o.round_tol, o.seed, call++, bf16}, zs.out(pb));
+            Z.push_back(zs.term(pb, R));
+        }
         {
             ScopedMark it(*c.arena);
-            std::vector<TTerm> terms = apply_operator(c, pb, op, V.back(), o.transpose);
+            std::vector<TTerm> terms = apply_operator(c, pb, op, precond ? Z.back() : V.back(), o.transpose);
             Slot wmv = alloc_slot(c, pb, R);
             roundsum(c, pb, terms, RSConfig{sr, R, o.round_tol, o.seed, call++, bf16}, wmv.out(pb));
             const TTerm W = wmv.term(pb, R);
@@ -219,10 +228,10 @@ static void solve_rhosvd(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tuck
     }
     if (k > kmax) k = kmax;
     so.iters = k;
-    // X~ = RoundSum(sum_i y_i V_i)
+    // X~ = RoundSum(sum_i y_i V_i)  (flexible form: sum_i y_i Z_i)
     std::vector<TTerm> fin;
     for (int i = 0; i < k; ++i) {
-        TTerm t = V[i];
+        TTerm t = precond ? Z[i] : V[i];
         t.coef = 1.0;
         t.coef_dev = ls.y + i;
         fin.push_back(t);
@@ -637,8 +646,8 @@ const char *tk_profile_report(tk_handle *h) {
     return h->prof_text.c_str();
 }
 
-int tk_solve(tk_handle *h, const tk_operator *op, const tk_tucker *b, const tk_opts *opts,
-             tk_tucker *x_out, tk_report *report, void *stream) {
+static int solve_entry(tk_handle *h, const tk_operator *op, const tk_operator *pc, const tk_tucker *b,
+                       const tk_opts *opts, tk_tucker *x_out, tk_report *report, void *stream) {
     return guarded(h, [&]() -> int {
         TK_REQUIRE(opts != nullptr && report != nullptr, "solve: null opts or report");
         check_tucker(b, "b");
@@ -663,8 +672,13 @@ int tk_solve(tk_handle *h, const tk_operator *op, const tk_tucker *b, const tk_o
         TK_CUDA(cudaEventCreate(&e1));
         TK_CUDA(cudaEventRecord(e0, c.st));
         SolveOut so;
+        OpDesc pd;
+        if (pc) {
+            TK_REQUIRE(o.variant == TK_RHOSVD_SGMRES, "preconditioning is available for RHOSVD-Tucker sGMRES");
+            pd = op_of(pc, pb);
+        }
         if (o.variant == TK_RHOSVD_SGMRES)
-            solve_rhosvd(c, pb, od, b, o, x_out, so, h->pinned);
+            solve_rhosvd(c, pb, od, b, o, x_out, so, h->pinned, pc ? &pd : nullptr);
         else
             solve_mln(c, pb, od, b, o, x_out, so, h->pinned);
         TK_CUDA(cudaEventRecord(e1, c.st));
@@ -686,6 +700,41 @@ int tk_solve(tk_handle *h, const tk_operator *op, const tk_tucker *b, const tk_o
         report->workspace_bytes = (int64_t)h->arena.capacity();
         report->kernel_launches = c.launches;
         return so.status;
+    });
+}
+
+int tk_solve(tk_handle *h, const tk_operator *op, const tk_tucker *b, const tk_opts *opts,
+             tk_tucker *x_out, tk_report *report, void *stream) {
+    return solve_entry(h, op, nullptr, b, opts, x_out, report, stream);
+}
+
+int tk_solve_precond(tk_handle *h, const tk_operator *op, const tk_operator *precond, const tk_tucker *b,
+                     const tk_opts *opts, tk_tucker *x_out, tk_report *report, void *stream) {
+    if (!precond) return TK_EINVAL;
+    return solve_entry(h, op, precond, b, opts, x_out, report, stream);
+}
+
+int tk_expsum_laplacian(tk_handle *h, int64_t n, int32_t q, double *const *mats, double *coef_host, void *stream) {
+    return guarded(h, [&]() -> int {
+        TK_REQUIRE(n >= 1 && n <= 16384 && q >= 1 && q <= 64 && mats && coef_host, "expsum: bad arguments");
+        Ctx c = make_ctx(h, stream);
+        ScopedMark mark(h->arena);
+        const int nn = (int)n;
+        double *V = c.arena->alloc((size_t)nn * nn);
+        double *B = c.arena->alloc((size_t)nn * nn);
+        sine_basis(c, V, nn, 0.0);
+        const double eta = M_PI / std::sqrt((double)q);
+        for (int hh = -q; hh <= q; ++hh) {
+            const double t = std::exp(hh * eta);
+            coef_host[hh + q] = eta * t;
+            TK_REQUIRE(mats[hh + q] != nullptr, "expsum: null output matrix");
+            sine_basis(c, B, nn, t);                      // V diag(exp(-t lambda))
+            Gemm g(c);
+            g.add1(nn, nn, nn, 0, 1, B, nn, V, nn, mats[hh + q], nn);   // (V D) V^T
+            g.run();
+        }
+        TK_CUDA(cudaStreamSynchronize(c.st));
+        return TK_OK;
     });
 }
 

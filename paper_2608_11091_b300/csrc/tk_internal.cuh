@@ -249,6 +249,8 @@ void superdiag(Ctx &c, const double *G, int m, int d, double *out, double scale_
                const double *scale_dev);
 // scalar helpers for the solver control flow
 void sqrt_scalar(Ctx &c, const double *in, double *out);
+// V (n x n) = sine eigenvectors of tridiag(-1,2,-1), columns scaled by exp(-t lambda_j) if t != 0
+void sine_basis(Ctx &c, double *V, int n, double t);
 // p = I (n x n)
 void set_identity(Ctx &c, double *p, int n);
 // dst (cols x rows, ld ldd) = src(rows x cols, ld lds)^T

@@ -24,3 +24,13 @@ MIXED_CASES = {
     "deblur3d_n40": (lambda: W.deblur3d(40, 2, None), W.SolverParams('rhosvd', 12, 128, 5, 8, 1e-8, seed=5)),
     "convdiff3d_n256_prefix": (lambda: W.workload("convdiff3d_n256"), W.SolverParams('rhosvd', 32, 128, 5, 10, 1e-6, seed=0)),
 }
+
+
+# Preconditioned (flexible) parity cases: (builder, parameters, q of the exponential sum).
+PRECOND_CASES = {
+    "poisson3d_n32_q8": (lambda: W.workload("poisson3d_n32"), W.SolverParams('rhosvd', 12, 64, 5, 20, 3e-7, seed=3), 8),
+    "poisson3d_n32_q8_r16": (lambda: W.workload("poisson3d_n32"), W.SolverParams('rhosvd', 16, 64, 5, 20, 2e-8, seed=3), 8),
+    "point_n203_q4": (lambda: W.poisson3d_point(203, None, 4, "p203"),
+                      W.SolverParams('rhosvd', 17, 40, 9, 12, 1e-6, eta=0.4, ktrunc=2, seed=11), 4),
+    "poisson3d_point_n1000": (lambda: W.workload("poisson3d_point_n1000"), None, 8),
+}

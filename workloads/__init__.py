@@ -280,6 +280,21 @@ def poisson3d(n: int, rhs_rank: int, seed: int, params: SolverParams, name: str)
     return Workload(name, op, b, params)
 
 
+def point_source_rhs(n: int, d: int = 3) -> Tucker:
+    """Rank-1 right-hand side (ones / sqrt(n)) (x) e_1 (x) .. (x) e_1 of the Poisson and
+    convection-diffusion experiments (Section 4)."""
+    ones = np.ones((n, 1)) / np.sqrt(n)
+    fac = [ones] + [np.eye(n, 1) for _ in range(d - 1)]
+    return Tucker(np.ones((1,) * d), fac)
+
+
+def poisson3d_point(n: int, params: SolverParams, q: int, name: str) -> Workload:
+    """3-D Poisson (T_n per mode) with the rank-1 point-source right-hand side, solved with the
+    exponential-sum preconditioner of q (2q+1 terms)."""
+    op = kronecker_sum_operator([second_difference(n)], 3)
+    return Workload(name, op, point_source_rhs(n), params, extra={"precond_q": q})
+
+
 def convdiff3d(n: int, seed: int, params: SolverParams, weight: float = 10.0,
                rhs_rank: int = 4) -> Workload:
     """Six terms: per mode (1/h^2) T_n and weight * (1/h) B_n, h = 1/(n+1)."""
@@ -335,6 +350,9 @@ def workload(name: str, seed: int = 0) -> Workload:
     if name == "poisson3d_n1024":
         p = SolverParams('rhosvd', 64, 256, 5, 100, 1e-6, seed=seed)
         return poisson3d(1024, 8, seed, p, name)
+    if name == "poisson3d_point_n1000":
+        p = SolverParams('rhosvd', 40, 64, 40, 20, 1e-7, eta=0.4, ktrunc=1, seed=seed)
+        return poisson3d_point(1000, p, 8, name)
     raise KeyError(name)
 
 
