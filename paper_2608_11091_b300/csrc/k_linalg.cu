@@ -385,6 +385,9 @@ struct SVDJobs {
     double rcond;
 };
 
+// Sweep counts of the last k_svd launch (per block: FP32 phase, FP64 phase); diagnostics.
+__device__ int g_svd_sweeps[2 * TK_MAX_D];
+
 template <typename T>
 __device__ __forceinline__ T warp_sum_t(T v) {
 #pragma unroll
@@ -392,166 +395,312 @@ __device__ __forceinline__ T warp_sum_t(T v) {
     return v;
 }
 
-// One-sided (Hestenes) Jacobi sweeps on the columns of A (s x s, column-major in shared
-// memory), accumulating the rotations into V.  Pairs follow a round-robin tournament so each
-// round's s/2 rotations are independent; one warp per pair.  Column norms are carried in
-// `nrm2` (recomputed every sweep, updated by Rutishauser's formulas after each rotation), so a
-// pair costs one dot product.  A pair is rotated when |a_p . a_q| > tol ||a_p|| ||a_q|| and
-// both columns are above the negligible level `floor2` (squared norm) of this precision:
-// columns below it cannot be resolved further and do not change the result beyond it.
-// Sweeps stop when a sweep rotates nothing.
-// Sweep counts of the last k_svd launch (per block: FP32 phase, FP64 phase); diagnostics.
-__device__ int g_svd_sweeps[2 * TK_MAX_D];
+// Block-wide reductions with a single combining warp.  On this part an FP64 warp instruction
+// occupies the SMSP's FP64 pipe for ~64 cycles however many lanes are active, so partials are
+// combined once by warp 0, never re-added by every thread.  `scratch` holds >= 33 elements.
+__device__ float block_sum_f(float v, float *scratch) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum_t(v);
+    if (lane == 0) scratch[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        float t = lane < nw ? scratch[lane] : 0.f;
+        t = warp_sum_t(t);
+        if (lane == 0) scratch[32] = t;
+    }
+    __syncthreads();
+    const float r = scratch[32];
+    __syncthreads();
+    return r;
+}
 
-template <typename T, bool ACC>
-__device__ int jacobi_sweeps(T *A, T *V, T *nrm2, int s, T tol, T floor2, int max_sweeps, int *flag) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    const int sp = s + (s & 1);
-    int done = 0;
-    for (int sweep = 0; sweep < max_sweeps && sp > 1; ++sweep) {
-        ++done;
-        for (int c = warp; c < s; c += nw) {
-            T t = 0;
-            for (int i = lane; i < s; i += 32) t = fma(A[i + c * s], A[i + c * s], t);
-            t = warp_sum_t(t);
-            if (lane == 0) nrm2[c] = t;
+__device__ int block_max_i(int v, int *scratch) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) scratch[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        int t = lane < nw ? scratch[lane] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t = max(t, __shfl_xor_sync(0xffffffffu, t, o));
+        if (lane == 0) scratch[32] = t;
+    }
+    __syncthreads();
+    const int r = scratch[32];
+    __syncthreads();
+    return r;
+}
+
+// Round-robin tournament: in round `round` of a sweep over sp (even) columns, pair `pr` joins
+// columns p < q; every column appears in exactly one pair per round.
+__device__ __forceinline__ void rr_pair(int round, int pr, int sp, int &p, int &q) {
+    if (pr == 0) { p = round; q = sp - 1; }
+    else {
+        // (round + pr) mod (sp - 1) and (round - pr) mod (sp - 1), both arguments in
+        // (-(sp - 1), 2 (sp - 1)): one conditional correction each, no integer division
+        p = round + pr;
+        if (p >= sp - 1) p -= sp - 1;
+        q = round - pr;
+        if (q < 0) q += sp - 1;
+    }
+    if (p > q) { const int t = p; p = q; q = t; }
+}
+
+// FP32 one-sided (Hestenes) Jacobi on the columns of A (s x s, column-major, shared memory),
+// rotations accumulated into V.  One warp per pair with the rows across lanes; the butterfly
+// reduction leaves a_p . a_q in every lane, so every lane forms the rotation itself (fast
+// FP32 intrinsics: the FP32 phase only has to bring the columns close to orthogonal, the
+// FP64 phase finishes).  A pair is rotated when |a_p . a_q| > tol ||a_p|| ||a_q|| and both
+// squared norms exceed `floor2`.  Convergence is checked after every sweep on the full Gram
+// matrix A^T A (one dot product per thread), which replaces a final rotation-free sweep.
+// Column squared norms are kept in `nrm2` (Rutishauser's updates inside a sweep, exact from
+// the Gram check between sweeps).  Returns the number of sweeps.
+__device__ int jacobi32(float *A, float *V, float *nrm2, int s, float tol, float floor2, int max_sweeps,
+                        int *flag) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5, nt = blockDim.x;
+    const int sp = s + (s & 1), np = sp / 2;
+    int sweeps = 0;
+    for (;;) {
+        // Gram check: squared norms first, then every pair p < q
+        for (int c = tid; c < s; c += nt) {
+            float t = 0.f;
+            for (int i = 0; i < s; ++i) t = fmaf(A[i + c * s], A[i + c * s], t);
+            nrm2[c] = t;
         }
         if (tid == 0) *flag = 0;
         __syncthreads();
+        for (int e = tid; e < s * s; e += nt) {
+            const int p = e % s, q = e / s;
+            if (p >= q) continue;
+            const float al = nrm2[p], be = nrm2[q];
+            if (al <= floor2 || be <= floor2) continue;
+            float g = 0.f;
+            for (int i = 0; i < s; ++i) g = fmaf(A[i + p * s], A[i + q * s], g);
+            // 4x the rotation tolerance: the check's dot product is summed in another order
+            // than the sweep's, and a pair between the two must not keep the loop alive
+            if (fabsf(g) > 4.f * tol * __fsqrt_rn(al) * __fsqrt_rn(be)) *flag = 1;
+        }
+        __syncthreads();
+        const int more = *flag;
+        __syncthreads();
+        if (!more || sweeps >= max_sweeps || sp < 2) break;
+        ++sweeps;
         for (int round = 0; round < sp - 1; ++round) {
-            for (int pr = warp; pr < sp / 2; pr += nw) {
+            for (int pr = warp; pr < np; pr += nw) {
                 int p, q;
-                if (pr == 0) { p = round; q = sp - 1; }
-                else { p = (round + pr) % (sp - 1); q = (round - pr + (sp - 1)) % (sp - 1); }
-                if (p >= s || q >= s) continue;
-                if (p > q) { const int t = p; p = q; q = t; }
-                const T al = nrm2[p], be = nrm2[q];
+                rr_pair(round, pr, sp, p, q);
+                if (q >= s) continue;
+                const float al = nrm2[p], be = nrm2[q];
                 if (al <= floor2 || be <= floor2) continue;
-                T ga = 0;
-                for (int i = lane; i < s; i += 32) ga = fma(A[i + p * s], A[i + q * s], ga);
-                ga = warp_sum_t(ga);   // identical in every lane (butterfly)
-                // FP32: the square-root form cannot underflow for tiny columns
-                const bool rot = sizeof(T) == 4 ? fabs(ga) > tol * sqrt(al) * sqrt(be)
-                                                : ga * ga > tol * tol * al * be;
-                if (ga != T(0) && rot) {
-                    // rotation parameters on one lane (FP64 sqrt/div are long DFMA sequences
-                    // here), broadcast to the warp
-                    T t = 0, cs = 0, sn = 0;
-                    if (lane == 0) {
-                        const T zeta = (be - al) / (T(2) * ga);
-                        t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-                        cs = T(1) / sqrt(T(1) + t * t);
-                        sn = cs * t;
-                    }
-                    t = __shfl_sync(0xffffffffu, t, 0);
-                    cs = __shfl_sync(0xffffffffu, cs, 0);
-                    sn = __shfl_sync(0xffffffffu, sn, 0);
-                    for (int i = lane; i < s; i += 32) {
-                        const T a = A[i + p * s], b = A[i + q * s];
-                        A[i + p * s] = cs * a - sn * b;
-                        A[i + q * s] = sn * a + cs * b;
-                        if (ACC) {
-                            const T va = V[i + p * s], vb = V[i + q * s];
-                            V[i + p * s] = cs * va - sn * vb;
-                            V[i + q * s] = sn * va + cs * vb;
-                        }
-                    }
-                    if (lane == 0) {
-                        nrm2[p] = al - t * ga;
-                        nrm2[q] = be + t * ga;
-                        *flag = 1;
-                    }
+                float ga = 0.f;
+                for (int i = lane; i < s; i += 32) ga = fmaf(A[i + p * s], A[i + q * s], ga);
+                ga = warp_sum_t(ga);
+                if (!(fabsf(ga) > tol * __fsqrt_rn(al) * __fsqrt_rn(be))) continue;
+                const float zeta = __fdividef(be - al, 2.f * ga);
+                const float az = fabsf(zeta);
+                const float t = az < 1e18f ? copysignf(1.f, zeta) / (az + __fsqrt_rn(fmaf(zeta, zeta, 1.f)))
+                                           : 0.5f / zeta;
+                const float cs = rsqrtf(fmaf(t, t, 1.f)), sn = cs * t;
+                for (int i = lane; i < s; i += 32) {
+                    const float a = A[i + p * s], b = A[i + q * s];
+                    A[i + p * s] = cs * a - sn * b;
+                    A[i + q * s] = sn * a + cs * b;
+                    const float va = V[i + p * s], vb = V[i + q * s];
+                    V[i + p * s] = cs * va - sn * vb;
+                    V[i + q * s] = sn * va + cs * vb;
+                }
+                if (lane == 0) {
+                    nrm2[p] = fmaxf(al - t * ga, 0.f);
+                    nrm2[q] = be + t * ga;
                 }
             }
             __syncthreads();
         }
-        const int any = *flag;
-        __syncthreads();
-        if (!any) break;
     }
-    return done;
+    return sweeps;
 }
 
-// FP64 one-sided Jacobi sweeps with the scalar work spread one lane per pair (an FP64 warp
-// instruction costs the same whether 1 or 32 lanes are active, so per-pair scalar code must not
-// be replicated across a warp).  Per round: partial dot products over NP row blocks (one thread
-// per (block, pair)), then one thread per pair sums them, tests, and forms the rotation: the
-// angle comes from FP32 arithmetic (it only has to shrink a_p . a_q; what it leaves is removed
-// by the next sweep) while cos = (1 + t^2)^(-1/2) is refined by two FP64 Newton steps so every
-// rotation is orthogonal to FP64 rounding; then one thread per (pair, row) rotates.
+// FP64 phase of the one-sided Jacobi SVD.  Every FP64 warp instruction occupies an SMSP's FP64
+// pipe for ~64 cycles on this part whatever the active lanes, so the work is organised by
+// FP64 instruction count.  Each step starts with a Gram check: H = A^T A (one FP64 dot per
+// thread, packed upper triangle in `gram`), diagonal into `nrm2`; a pair (p, q) still needs
+// work when H_pq^2 > (4 tol)^2 H_pp H_qq with both squared norms above `floor2`.  Then:
+//
+//  * correction step (graded mode, when every such pair is well separated,
+//    |H_pq| <= 1e-3 |H_qq - H_pp|): all rotations at once, A <- A (I + T + T^2 / 2) with the
+//    skew first-order angles T_pq = H_pq / (H_qq - H_pp) (pairs below tolerance: 0).  The
+//    off-diagonal left is second order in the angles (quadratic convergence) and
+//    I + T + T^2 / 2 is orthogonal to third order; T^2 is formed in FP32 (its entries are
+//    squares of the angles).  One FP64 GEMM instead of s - 1 sequential rounds.
+//  * otherwise a full sweep of round-robin rotations: (1) partial dot products over JNP row
+//    blocks, warp = row block, lane = pair; (2) one thread per pair, spread over four warps
+//    (one per SMSP), sums the parts, tests, and forms the rotation: angle from FP32 arithmetic,
+//    cos = (1 + t^2)^(-1/2) refined by two FP64 Newton steps so that the rotation is
+//    orthogonal to FP64 rounding; (3) one thread per (pair, row) rotates.
+//
+// The loop ends at the first Gram check with no pair left (or after max_steps steps).
+// Scratch for the correction step (graded mode only): `tmat` s x s FP64, `tf` 2 s^2 floats
+// (may alias `gram`, which is dead once T is formed).
 constexpr int JNP = 4;
+constexpr int SVD_REGS = 9;   // outputs per thread held in registers by an in-place GEMM (s^2 / threads)
 template <bool ACC>
-__device__ int jacobi64(double *A, double *V, double *nrm2, int s, double tol, double floor2, int max_sweeps,
-                        int *flag, double *gpart, double *cpar, double *spar, int *act) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5, nt = blockDim.x;
+__device__ int jacobi64(double *A, double *V, double *nrm2, int s, double tol, double floor2, int max_steps,
+                        int *flag, double *gpart, double *cpar, double *spar, int *act, double *gram,
+                        double *tmat, float *tf, int *nsweeps) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
     const int sp = s + (s & 1), np = sp / 2;
+    const int wpp = (np + 31) / 32;             // warps per row block in sweep step (1)
     const int rbk = (s + JNP - 1) / JNP;
-    int done = 0;
-    for (int sweep = 0; sweep < max_sweeps && sp > 1; ++sweep) {
-        ++done;
-        for (int c = warp; c < s; c += nw) {
-            double t = 0.0;
-            for (int i = lane; i < s; i += 32) t = fma(A[i + c * s], A[i + c * s], t);
-            t = warp_sum(t);
-            if (lane == 0) nrm2[c] = t;
+    const int nps = s * (s + 1) / 2;
+    const double chk2 = 16.0 * tol * tol;
+    __shared__ int sep_bad;
+    int steps = 0, sweeps = 0;
+    auto unpack = [](int e, int &p, int &q) {
+        q = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
+        while (q * (q + 1) / 2 > e) --q;
+        while ((q + 1) * (q + 2) / 2 <= e) ++q;
+        p = e - q * (q + 1) / 2;
+    };
+    for (;;) {
+        // Gram check
+        for (int e = tid; e < nps; e += nt) {
+            int p, q;
+            unpack(e, p, q);
+            double g = 0.0;
+            for (int i = 0; i < s; ++i) g = fma(A[i + p * s], A[i + q * s], g);
+            gram[e] = g;
+            if (p == q) nrm2[p] = g;
         }
-        if (tid == 0) *flag = 0;
+        if (tid == 0) { *flag = 0; sep_bad = 0; }
         __syncthreads();
+        for (int e = tid; e < nps; e += nt) {
+            int p, q;
+            unpack(e, p, q);
+            if (p == q) continue;
+            const double al = nrm2[p], be = nrm2[q], g = gram[e];
+            if (al > floor2 && be > floor2 && g * g > chk2 * al * be) {
+                *flag = 1;
+                if (!(fabs(g) <= 1e-3 * fabs(be - al))) sep_bad = 1;
+            }
+        }
+        __syncthreads();
+        const int more = *flag, simultaneous = (tmat != nullptr) && !sep_bad;
+        __syncthreads();
+        if (!more || steps >= max_steps || sp < 2) break;
+        ++steps;
+        if (simultaneous) {
+            // T (skew) into tmat, and an FP32 copy into tf[0 .. s^2)
+            for (int e = tid; e < s * s; e += nt) {
+                const int p = e % s, q = e / s;
+                double t = 0.0;
+                if (p != q) {
+                    const int lo = min(p, q), hi = max(p, q);
+                    const double al = nrm2[lo], be = nrm2[hi], g = gram[lo + hi * (hi + 1) / 2];
+                    if (al > floor2 && be > floor2 && g * g > chk2 * al * be) {
+                        const double tl = g / (be - al);      // T[lo, hi]
+                        t = (p == lo) ? tl : -tl;
+                    }
+                }
+                tmat[e] = t;
+            }
+            __syncthreads();
+            for (int e = tid; e < s * s; e += nt) tf[e] = (float)tmat[e];
+            __syncthreads();
+            // D = T + T^2 / 2 (T^2 in FP32 into tf[s^2 ..)), then in place into tmat
+            float *t2 = tf + s * s;
+            for (int e = tid; e < s * s; e += nt) {
+                const int i = e % s, j = e / s;
+                float acc = 0.f;
+                for (int k = 0; k < s; ++k) acc = fmaf(tf[i + k * s], tf[k + j * s], acc);
+                t2[e] = acc;
+            }
+            __syncthreads();
+            for (int e = tid; e < s * s; e += nt) tmat[e] += 0.5 * (double)t2[e];
+            __syncthreads();
+            // A <- A + A D, outputs held in registers until every thread has read A
+            double r[SVD_REGS];
+#pragma unroll
+            for (int k = 0; k < SVD_REGS; ++k) {
+                const int e = tid + k * nt;
+                if (e < s * s) {
+                    const int i = e % s, j = e / s;
+                    double acc = A[e];
+                    for (int kk = 0; kk < s; ++kk) acc = fma(A[i + kk * s], tmat[kk + j * s], acc);
+                    r[k] = acc;
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < SVD_REGS; ++k) {
+                const int e = tid + k * nt;
+                if (e < s * s) A[e] = r[k];
+            }
+            __syncthreads();
+            continue;
+        }
+        ++sweeps;
         for (int round = 0; round < sp - 1; ++round) {
-            for (int e = tid; e < JNP * np; e += nt) {
-                const int part = e / np, pr = e % np;
+            // (1) partial dots: warp = (part, pair block), lane = pair
+            for (int w = warp; w < JNP * wpp; w += nt >> 5) {
+                const int part = w / wpp, pr = (w % wpp) * 32 + lane;
+                if (pr >= np) continue;
                 int p, q;
-                if (pr == 0) { p = round; q = sp - 1; }
-                else { p = (round + pr) % (sp - 1); q = (round - pr + (sp - 1)) % (sp - 1); }
+                rr_pair(round, pr, sp, p, q);
                 double g = 0.0;
-                if (p < s && q < s) {
+                if (q < s) {
                     const int i1 = min(s, (part + 1) * rbk);
                     for (int i = part * rbk; i < i1; ++i) g = fma(A[i + p * s], A[i + q * s], g);
                 }
                 gpart[part * np + pr] = g;
             }
             __syncthreads();
-            for (int pr = tid; pr < np; pr += nt) {
-                int p, q;
-                if (pr == 0) { p = round; q = sp - 1; }
-                else { p = (round + pr) % (sp - 1); q = (round - pr + (sp - 1)) % (sp - 1); }
-                int doit = 0;
-                if (p < s && q < s) {
-                    const double al = nrm2[p], be = nrm2[q];
-                    double ga = 0.0;
-                    for (int part = 0; part < JNP; ++part) ga += gpart[part * np + pr];
-                    if (al > floor2 && be > floor2 && ga != 0.0 && ga * ga > tol * tol * al * be) {
-                        const double zeta = (be - al) / (2.0 * ga);
-                        double t;
-                        if (fabs(zeta) < 1e6) {
-                            const float zf = (float)zeta;
-                            t = (double)(copysignf(1.0f, zf) / (fabsf(zf) + sqrtf(1.0f + zf * zf)));
-                        } else {
-                            t = 0.5 / zeta;   // tan of the angle to first order (|zeta| >> 1)
+            // (2) rotation per pair: pair pr on warp pr % 4, lane pr / 4
+            if (warp < 4) {
+                for (int pr = lane * 4 + warp; pr < np; pr += 128) {
+                    int p, q;
+                    rr_pair(round, pr, sp, p, q);
+                    int doit = 0;
+                    if (q < s) {
+                        const double al = nrm2[p], be = nrm2[q];
+                        double ga = gpart[pr];
+#pragma unroll
+                        for (int part = 1; part < JNP; ++part) ga += gpart[part * np + pr];
+                        if (al > floor2 && be > floor2 && ga * ga > tol * tol * al * be) {
+                            // zeta = (be - al) / (2 ga) in FP32 after a power-of-two scaling
+                            // that brings 2 ga to [1, 2) (no FP64 divide)
+                            const double g2 = 2.0 * ga;
+                            const int eg = (__double2hiint(g2) >> 20) & 0x7ff;
+                            const double sc = __hiloint2double((2046 - eg) << 20, 0);
+                            const float zf = __fdividef((float)((be - al) * sc), (float)(g2 * sc));
+                            const float az = fabsf(zf);
+                            const float tf32 = az < 1e18f ? copysignf(1.f, zf) / (az + __fsqrt_rn(fmaf(zf, zf, 1.f)))
+                                                          : 0.5f / zf;
+                            const double t = (double)tf32;
+                            const double x = fma(t, t, 1.0), hx = -0.5 * x;
+                            double c = (double)rsqrtf((float)x);
+                            c = c * fma(hx * c, c, 1.5);
+                            c = c * fma(hx * c, c, 1.5);
+                            const double sn = c * t, tg = t * ga;
+                            cpar[pr] = c;
+                            spar[pr] = sn;
+                            // Rutishauser's updates (approximate for the FP32 angle; the next
+                            // Gram check recomputes the norms exactly)
+                            nrm2[p] = fmax(al - tg, 0.0);
+                            nrm2[q] = be + tg;
+                            doit = tf32 != 0.f;
                         }
-                        const double x = fma(t, t, 1.0);
-                        double c = (double)rsqrtf((float)x);
-                        c = c * fma(-0.5 * x * c, c, 1.5);
-                        c = c * fma(-0.5 * x * c, c, 1.5);
-                        const double sn = c * t;
-                        cpar[pr] = c;
-                        spar[pr] = sn;
-                        // exact post-rotation norms of the rotated pair
-                        nrm2[p] = c * c * al - 2.0 * c * sn * ga + sn * sn * be;
-                        nrm2[q] = sn * sn * al + 2.0 * c * sn * ga + c * c * be;
-                        doit = t != 0.0;
-                        if (doit) *flag = 1;
                     }
+                    act[pr] = doit;
                 }
-                act[pr] = doit;
             }
             __syncthreads();
+            // (3) rotations
             for (int e = tid; e < np * s; e += nt) {
-                const int pr = e / s, i = e % s;
+                const int pr = e / s, i = e - pr * s;
                 if (!act[pr]) continue;
                 int p, q;
-                if (pr == 0) { p = round; q = sp - 1; }
-                else { p = (round + pr) % (sp - 1); q = (round - pr + (sp - 1)) % (sp - 1); }
+                rr_pair(round, pr, sp, p, q);
                 const double c = cpar[pr], sn = spar[pr];
                 const double a = A[i + p * s], b = A[i + q * s];
                 A[i + p * s] = c * a - sn * b;
@@ -564,95 +713,110 @@ __device__ int jacobi64(double *A, double *V, double *nrm2, int s, double tol, d
             }
             __syncthreads();
         }
-        const int any = *flag;
-        __syncthreads();
-        if (!any) break;
     }
-    return done;
+    if (nsweeps) *nsweeps = sweeps;
+    return steps;
 }
 
 // SVD of a small square matrix R (upper triangle read) to FP64 accuracy.  Two modes:
 //
-// ST-HOSVD (J.perm set): R comes from the column-pivoted QR C^T P = Q R of a core unfolding, so
-// R is row-graded and one-sided Jacobi on the columns of R^T converges in a few sweeps with
-// high relative accuracy (Drmac and Veselic's preconditioned Jacobi).  R^T V = U S needs no
-// accumulation of V: the left singular vectors of C = P R^T Q^T are P times the normalised
-// final columns U.  Pure FP64.
+// ST-HOSVD (J.perm set): R comes from the column-pivoted QR C^T P = Q R of a core unfolding;
+// one-sided Jacobi runs on the columns of R^T (row-graded R: high relative accuracy and few
+// sweeps, after Drmac and Veselic).  R^T V = U S needs no V: the left singular vectors of
+// C = P R^T Q^T are P times the normalised final columns U.
 //
-// Pseudo-inverse (jobs.pinv set; R from an unpivoted QR): the bulk of the Jacobi work runs in
-// FP32 (~60x the FP64 rate on this part): FP32 sweeps on R V32; two Newton-Schulz steps
-// V <- V (3 I - V^T V) / 2 in FP64 restore V's orthonormality (error e -> 1.5 e^2); FP64
-// sweeps on A = R V finish.  R^+ = sum_c V[:,c] A[:,c]^T / sigma_c^2 over sigma_c > rcond sigma_max.
-// Shared memory: three s x s FP64 regions X | Y | Z (X holds the FP32 A and V in phase 1).
+// Pseudo-inverse (jobs.pinv set; R from an unpivoted QR): Jacobi on R with V accumulated;
+// R^+ = sum_c V[:,c] A[:,c]^T / sigma_c^2 over sigma_c > rcond sigma_max.
+//
+// Both: the bulk of the Jacobi work runs in FP32 (~60x the FP64 rate on this part) on B
+// scaled by a power of two; two Newton-Schulz steps V <- V (3 I - V^T V) / 2 in FP64 restore
+// the orthonormality of the FP32 V (error e -> 1.5 e^2); FP64 sweeps on A = B V finish.
+// Shared memory: three s x s FP64 regions X | Y | Z (X holds the FP32 A and V in phase 1,
+// Z the packed Gram matrix in phase 4).
 __global__ void __launch_bounds__(1024) k_svd(const __grid_constant__ SVDJobs jobs) {
     extern __shared__ double sm[];
     const SVDJob &J = jobs.j[blockIdx.x];
     const int s = J.s, ss = s * s;
     double *X = sm, *Y = sm + ss, *Z = sm + 2 * ss;
     __shared__ double sig[SVD_MAXS];
+    __shared__ double rsig[SVD_MAXS];
+    __shared__ long long skey[SVD_MAXS];
     __shared__ int order[SVD_MAXS];
     __shared__ int flag;
-    __shared__ double scratch[40];
+    __shared__ float fscr[40];
+    __shared__ int iscr[40];
     __shared__ double nrm64[SVD_MAXS];
     __shared__ float nrm32[SVD_MAXS];
     __shared__ double gpart[JNP * (SVD_MAXS / 2 + 1)];
     __shared__ double cpar[SVD_MAXS / 2 + 1], spar[SVD_MAXS / 2 + 1];
     __shared__ int act[SVD_MAXS / 2 + 1];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    const int nt = blockDim.x;
+    __shared__ int kept;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
     auto Rat = [&](int i, int c) -> double {
         return (i <= c && i < J.ldr) ? J.R[i + (long long)c * J.ldr] : 0.0;
     };
     const bool graded = J.perm != nullptr;
-    // B = R^T (graded) or R; element accessor in FP64
+    // B = R^T (graded) or R
     auto Bat = [&](int i, int c) -> double { return graded ? Rat(c, i) : Rat(i, c); };
     float *A32 = reinterpret_cast<float *>(X), *V32 = A32 + ss;
-    double mx = 0.0;
-    for (int e = tid; e < ss; e += nt) mx = fmax(mx, fabs(Bat(e % s, e / s)));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) scratch[warp] = mx;
-    __syncthreads();
-    mx = 0.0;
-    for (int w = 0; w < nw; ++w) mx = fmax(mx, scratch[w]);
-    __syncthreads();
-    const double inv = mx > 0.0 ? 1.0 / mx : 1.0;
+    // power-of-two scale from the largest biased exponent (integer work only)
+    int emax = 0;
+    for (int e = tid; e < ss; e += nt) emax = max(emax, (__double2hiint(Bat(e % s, e / s)) >> 20) & 0x7ff);
+    emax = min(block_max_i(emax, iscr), 2044);
+    const double inv = __hiloint2double((2045 - emax) << 20, 0);       // 2^(1022 - emax)
+    const double mx = __hiloint2double((emax + 1) << 20, 0);           // 2^(emax - 1022)
     for (int e = tid; e < ss; e += nt) {
         A32[e] = (float)(Bat(e % s, e / s) * inv);
         V32[e] = (e % s == e / s) ? 1.f : 0.f;
     }
+    float frop = 0.f;
+    for (int e = tid; e < ss; e += nt) frop = fmaf(A32[e], A32[e], frop);
     __syncthreads();
-    double fro = 0.0;
-    for (int e = tid; e < ss; e += nt) { const double v = (double)A32[e]; fro = fma(v, v, fro); }
-    fro = block_sum(fro, scratch);
+    const float fro = block_sum_f(frop, fscr);
     // phase 1: FP32 sweeps.  On the graded R^T they resolve singular values far below the
     // largest with relative accuracy; columns below 2^-100 (scaled) are left to FP64.
-    const int n32 = jacobi_sweeps<float, true>(A32, V32, nrm32, s, 8.0f * sqrtf((float)s) * 0x1p-24f,
-                                               graded ? 0x1p-100f : (float)(fro * 0x1p-40), 20, &flag);
+    const int n32 = jacobi32(A32, V32, nrm32, s, 8.0f * sqrtf((float)s) * 0x1p-24f,
+                             graded ? 0x1p-100f : fro * 0x1p-40f, 20, &flag);
     if (tid == 0) g_svd_sweeps[2 * blockIdx.x] = n32;
-    // phase 2: V = double(V32) into Y, then two Newton-Schulz steps: Z = (3 I - Y^T Y) / 2, X = Y Z
-    // (orthogonality error e -> 1.5 e^2: ~s 2^-24 -> ~1e-11 -> rounding level)
+    // phase 2: V = double(V32) into Y, orthonormalised by one step of the polar iteration with
+    // its second-order term: V = Y (I + E)^(-1/2) ~ Y (I - E / 2 + 3 E^2 / 8), E = Y^T Y - I
+    // (|E| ~ s 2^-24, so the E^3 term is below FP64 rounding; E^2 in FP32).  E (symmetric)
+    // into Z, FP32 copies of E and E^2 into X, Z <- I - E / 2 + 3 E^2 / 8, X = Y Z.
     for (int e = tid; e < ss; e += nt) Y[e] = (double)V32[e];
     __syncthreads();
-    for (int it = 0; it < 2; ++it) {
+    {
+        float *ef = reinterpret_cast<float *>(X), *e2f = ef + ss;
         for (int e = tid; e < ss; e += nt) {
             const int i = e % s, j = e / s;
+            if (i > j) continue;
             double t = 0.0;
             for (int k = 0; k < s; ++k) t = fma(Y[k + i * s], Y[k + j * s], t);
-            Z[e] = ((i == j) ? 1.5 : 0.0) - 0.5 * t;
+            const double ev = t - ((i == j) ? 1.0 : 0.0);
+            Z[i + j * s] = ev;
+            Z[j + i * s] = ev;
+            ef[i + j * s] = (float)ev;
+            ef[j + i * s] = (float)ev;
+        }
+        __syncthreads();
+        for (int e = tid; e < ss; e += nt) {
+            const int i = e % s, j = e / s;
+            float acc = 0.f;
+            for (int k = 0; k < s; ++k) acc = fmaf(ef[i + k * s], ef[k + j * s], acc);
+            e2f[e] = acc;
+        }
+        __syncthreads();
+        for (int e = tid; e < ss; e += nt) {
+            const int i = e % s, j = e / s;
+            Z[e] = ((i == j) ? 1.0 : 0.0) - 0.5 * Z[e] + 0.375 * (double)e2f[e];
         }
         __syncthreads();
         for (int e = tid; e < ss; e += nt) {
             const int i = e % s, j = e / s;
             double t = 0.0;
             for (int k = 0; k < s; ++k) t = fma(Y[i + k * s], Z[k + j * s], t);
-            X[e] = t;
+            X[e] = t;   // X's FP32 contents were last read before the previous barrier
         }
         __syncthreads();
-        if (it == 0) {
-            for (int e = tid; e < ss; e += nt) Y[e] = X[e];
-            __syncthreads();
-        }
     }
     // phase 3: A = B V into Y (B triangular: R^T lower, R upper)
     for (int e = tid; e < ss; e += nt) {
@@ -667,45 +831,76 @@ __global__ void __launch_bounds__(1024) k_svd(const __grid_constant__ SVDJobs jo
     __syncthreads();
     // phase 4: FP64 sweeps (V accumulated only when R^+ needs it)
     double *A = Y, *V = graded ? nullptr : X;
-    const double fro_r = fro * mx * mx;
+    const double fro_r = (double)fro * mx * mx;
     const double floor2 = fro_r * (double)s * s * 0x1p-106;
     const double tol64 = 4.0 * sqrt((double)s) * 0x1p-53;
+    // graded mode: X (V no longer needed) holds T, the FP32 scratch aliases the Gram region Z
+    int nsw = 0;
     const int n64 = graded
-        ? jacobi64<false>(A, nullptr, nrm64, s, tol64, floor2, 16, &flag, gpart, cpar, spar, act)
-        : jacobi64<true>(A, X, nrm64, s, tol64, floor2, 16, &flag, gpart, cpar, spar, act);
-    if (tid == 0) g_svd_sweeps[2 * blockIdx.x + 1] = n64;
-    // singular values and descending order (ties by index)
-    for (int c = warp; c < s; c += nw) {
-        double t = 0.0;
-        for (int i = lane; i < s; i += 32) t = fma(A[i + c * s], A[i + c * s], t);
-        t = warp_sum(t);
-        if (lane == 0) sig[c] = sqrt(t);
+        ? jacobi64<false>(A, nullptr, nrm64, s, tol64, floor2, 16, &flag, gpart, cpar, spar, act, Z, X,
+                          reinterpret_cast<float *>(Z), &nsw)
+        : jacobi64<true>(A, X, nrm64, s, tol64, floor2, 16, &flag, gpart, cpar, spar, act, Z, nullptr,
+                         nullptr, &nsw);
+    if (tid == 0) g_svd_sweeps[2 * blockIdx.x + 1] = n64 * 100 + nsw;
+    // singular values from the final Gram check's diagonal; descending order by the integer
+    // image of the (non-negative) doubles, ties by index
+    for (int c = tid; c < s; c += nt) {
+        const double v = sqrt(nrm64[c]);
+        sig[c] = v;
+        skey[c] = __double_as_longlong(v);
+        rsig[c] = v > 0.0 ? 1.0 / v : 0.0;
     }
     __syncthreads();
     for (int c = tid; c < s; c += nt) {
         int pos = 0;
+        const long long kc = skey[c];
         for (int o = 0; o < s; ++o)
-            if (sig[o] > sig[c] || (sig[o] == sig[c] && o < c)) ++pos;
+            if (skey[o] > kc || (skey[o] == kc && o < c)) ++pos;
         order[pos] = c;
     }
     __syncthreads();
-    __shared__ int kept;
-    if (tid == 0) {
+    // kept rank: smallest r with sum_{pos >= r} sigma_pos^2 <= eps^2 ||C||^2 / d (suffix sums
+    // by one warp, SVD_MAXS <= 96 = 3 x 32 positions)
+    if (warp == 0) {
         int r = min(s, J.rank_cap);
         if (J.normsq) {
             const double thr = J.eps2_over_d * (*J.normsq);
-            double tail = 0.0;
-            int rr = s;
-            for (int pos = s - 1; pos >= 1; --pos) {
-                const double v = sig[order[pos]];
-                tail += v * v;
-                if (tail <= thr) rr = pos; else break;
+            double e2[3], suf[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int pos = k * 32 + lane;
+                e2[k] = pos < s ? nrm64[order[pos]] : 0.0;
             }
-            r = min(rr, J.rank_cap);
+            // suffix sums: within each 32-block by shuffles, then block carries
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                double v = e2[k];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const double u = __shfl_down_sync(0xffffffffu, v, o);
+                    if (lane + o < 32) v += u;
+                }
+                suf[k] = v;
+            }
+            const double c2 = __shfl_sync(0xffffffffu, suf[2], 0);
+            const double c1 = __shfl_sync(0xffffffffu, suf[1], 0) + c2;
+            suf[1] += c2;
+            suf[0] += c1;
+            // candidate r = pos (pos >= 1) when tail[pos] <= thr; smallest such pos
+            int best = s;
+#pragma unroll
+            for (int k = 2; k >= 0; --k) {
+                const int pos = k * 32 + lane;
+                const unsigned m = __ballot_sync(0xffffffffu, pos >= 1 && pos < s && suf[k] <= thr);
+                if (m) best = k * 32 + __ffs(m) - 1;
+            }
+            r = min(best, J.rank_cap);
         }
         r = max(r, 1);
-        kept = r;
-        if (J.rank) *J.rank = r;
+        if (lane == 0) {
+            kept = r;
+            if (J.rank) *J.rank = r;
+        }
     }
     __syncthreads();
     const int r = kept;
@@ -720,7 +915,7 @@ __global__ void __launch_bounds__(1024) k_svd(const __grid_constant__ SVDJobs jo
                 double v = 0.0;
                 if (c < r) {
                     const int o = order[c];
-                    if (sig[o] > fl) v = A[i + o * s] / sig[o];
+                    if (sig[o] > fl) v = A[i + o * s] * rsig[o];
                 }
                 J.W[J.perm[i] + (long long)c * s] = v;
             }
@@ -734,14 +929,13 @@ __global__ void __launch_bounds__(1024) k_svd(const __grid_constant__ SVDJobs jo
     double *P = jobs.pinv[blockIdx.x];
     if (P && V) {
         // R = U S V^T with U S = A (final):  R^+ = sum_c V[:,c] A[:,c]^T / sig_c^2
-        const double smax = sig[order[0]];
-        const double cut = jobs.rcond * smax;
+        const double cut = jobs.rcond * sig[order[0]];
         for (int e = tid; e < ss; e += nt) {
             const int i = e % s, jj = e / s;
             double t = 0.0;
             for (int c = 0; c < s; ++c) {
                 const double sc = sig[c];
-                if (sc > cut && sc > 0.0) t += V[i + c * s] * A[jj + c * s] / (sc * sc);
+                if (sc > cut && sc > 0.0) t += V[i + c * s] * A[jj + c * s] * (rsig[c] * rsig[c]);
             }
             P[i + (long long)jj * s] = t;
         }
@@ -757,7 +951,9 @@ static void svd_launch(Ctx &c, SVDJobs &J, int smax) {
         attr_set = true;
     }
     c.pre_launch();
-    k_svd<<<J.n, smax > 48 ? 1024 : 512, smem, c.st>>>(J);
+    // 1024 threads: the FP32 sweeps run one warp per pair, and s <= 64 gives at most 32 pairs
+    // per round (512 threads would serialise pairs on a warp and double each round's latency)
+    k_svd<<<J.n, 1024, smem, c.st>>>(J);
     // algorithmic work: Golub and Van Loan's count for the singular values and one set of
     // singular vectors of an s x s matrix, 12 s^3
     double flops = 0.0;
