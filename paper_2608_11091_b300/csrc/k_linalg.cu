@@ -18,7 +18,7 @@ namespace cg = cooperative_groups;
 namespace tk {
 
 constexpr int QR_MAXS = 256;
-constexpr int QR_NCH = 4;        // row chunks per column in the QR partial sums
+constexpr int QR_NCH = 8;        // row chunks per column in the QR partial sums
 constexpr int SVD_MAXS = 96;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -63,13 +63,23 @@ struct QRJobs {
     QRJob j[TK_MAX_D];
 };
 
-// One reflector per step with a single cluster-wide reduction: each CTA contributes, over its
-// own rows, ||x_below||^2, the pivot alpha = A[j,j] (owner only), D_c = x^T A[j:, c] and the
-// pivot row P_c = A[j, c] (owner only) for every trailing column c.  With beta, tau from
-// LAPACK's dlarfg and v = (x - beta e_j) / (alpha - beta) (v_j = 1):
-//   w_c = v^T A[j:, c] = P_c + (D_c - alpha P_c) / (alpha - beta),  A[i, c] -= tau v_i w_c.
-// Q (optional) is accumulated backwards, Q = H_0 ... H_{k-1} [I; 0], one reduction per step.
-// Rows live in shared memory when they fit (SMEM = true), else in global memory.
+// One reflector per step, one cluster-wide exchange per step.  With x = A[j:, j], alpha = x_0,
+// sigma2 = ||x_1:||^2, nrm = (alpha^2 + sigma2)^(1/2), beta = -sign(alpha) nrm, the reflector
+// is H = I - tau v v^T with the unnormalised v = x - beta e_0 (v_0 = alpha - beta, the rest
+// of x kept in place below the diagonal) and tau = 1 / (nrm (nrm + |alpha|)): one reciprocal.
+// For every trailing column c, v^T A[j:, c] = D_c - beta P_c with D_c = x^T A[j:, c] and
+// P_c = A[j, c], so a step needs, from every CTA over its own rows, the partial sigma2 and
+// D_c, and from the CTA owning row j its row (alpha, P_c): exchanged through distributed
+// shared memory after one cluster barrier.  On this part an FP64 warp instruction holds an
+// SMSP's FP64 pipe for ~64 cycles whatever the active lanes, so the scalar work is kept off
+// the FP64 pipe where it can be: pivoting (largest remaining norm first) uses FP32 norms,
+// scaled once by the largest initial column norm and downdated by the new row of R each step
+// (a pivot only has to grade R, it does not enter the result); the argmax is one warp of
+// FP32 shuffles; peer sums use four threads per column.
+// Q (optional) is accumulated backwards, Q = H_0 ... H_{k-1} [I; 0], one exchange per step.
+// Rows live in shared memory when they fit (SMEM = true), else in global memory.  The
+// exchange buffers alternate by a running exchange count, so a buffer is rewritten only after
+// every peer has passed the next cluster barrier.
 template <bool SMEM>
 __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs, int rb_cap) {
     cg::cluster_group cl = cg::this_cluster();
@@ -82,17 +92,16 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
     extern __shared__ double dyn[];
     double *Al = dyn;                              // nr x s, ld rb_cap
     double *Ql = dyn + (size_t)rb_cap * s;         // nr x s, ld rb_cap
-    __shared__ double red[2][2 + 3 * QR_MAXS];
-    __shared__ double wv[QR_MAXS + 2];
-    __shared__ double taus[QR_MAXS];
-    __shared__ double nrm[QR_MAXS];
-    __shared__ int permv[QR_MAXS];
+    __shared__ double red[2][2 * QR_MAXS];         // [0, nc1): partial sums, [nc1, 2 nc1): owner's row
     __shared__ double part[QR_NCH * QR_MAXS];
-    __shared__ float partn[QR_NCH * QR_MAXS];
-    __shared__ double bc[6];
+    __shared__ double wv[QR_MAXS];
+    __shared__ double taus[QR_MAXS], vjs[QR_MAXS];
+    __shared__ float nrmf[QR_MAXS];
+    __shared__ int permv[QR_MAXS];
+    __shared__ double bc[4];
     __shared__ int pivot;
     const bool piv = J.perm != nullptr;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5, nt = blockDim.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
     auto A = [&](int i, int c) -> double & {
         return SMEM ? Al[(i - r0) + (size_t)c * rb_cap] : J.A[i + (long long)c * m];
     };
@@ -105,42 +114,99 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
             A(i, c) = J.A[i + (long long)c * m];
         }
     __syncthreads();
-    int buf = 0;
+    int xch = 0;   // exchanges so far (selects the buffer)
+    // partial sums over this CTA's rows [ib, r1) for columns j0 .. j0 + ncols - 1: one thread per
+    // (column, row chunk) calls chunk(c, i0, i1) (a plain FMA loop), chunks combined per column
+    // into out[]
+    auto column_sums = [&](int j0, int ncols, int ib, auto chunk, double *out) {
+        const int nrows = max(0, r1 - ib);
+        const int nch = max(1, min(QR_NCH, nt / max(ncols, 1)));
+        const int rch = (nrows + nch - 1) / nch;
+        for (int e = tid; e < ncols * nch; e += nt) {
+            const int cc = e % ncols, ch = e / ncols;
+            const int i0 = ib + ch * rch, i1 = min(r1, i0 + rch);
+            part[ch * QR_MAXS + cc] = chunk(j0 + cc, i0, i1);
+        }
+        __syncthreads();
+        for (int cc = tid; cc < ncols; cc += nt) {
+            double t = part[cc];
+            for (int ch = 1; ch < nch; ++ch) t += part[ch * QR_MAXS + cc];
+            out[cc] = t;
+        }
+    };
+    // rows across threads, trailing columns in groups: thread (row lane il, group g) updates
+    // rows ib + il, ib + il + RT, ... in columns cbeg + g, cbeg + g + ng, ... (no division)
+    auto row_layout = [&](int nrows, int &RT, int &ng, int &il, int &g) {
+        RT = nrows <= 64 ? 64 : (nrows <= 128 ? 128 : 256);
+        ng = nt / RT;
+        il = tid % RT;
+        g = tid / RT;
+    };
+    // sum over the cluster of rd[lo .. hi) of every peer into dst[lo .. hi): four threads per
+    // entry, each over a quarter of the peers, combined by two shuffles within the group
+    auto peer_sums = [&](const double *rd, int lo, int hi, int t0, int nthr, double *dst) {
+        const int n4 = (hi - lo) * 4;
+        for (int e = tid - t0; e >= 0 && e < ((n4 + 31) & ~31); e += nthr) {
+            const int cc = lo + e / 4, g = e & 3;
+            double d = 0.0;
+            if (e < n4)
+                for (int qq = g; qq < C; qq += 4) d += cl.map_shared_rank(rd, qq)[cc];
+            d += __shfl_xor_sync(0xffffffffu, d, 1);
+            d += __shfl_xor_sync(0xffffffffu, d, 2);
+            if (e < n4 && g == 0) dst[cc] = d;
+        }
+    };
+    double sc2 = 1.0, scr = 1.0;   // pivot-norm scaling (1 / largest initial squared norm)
     if (piv) {
-        // initial column norms
         for (int c = tid; c < s; c += nt) permv[c] = c;
-        double *rd = red[buf];
-        for (int c = warp; c < s; c += nw) {
-            double p = 0.0;
-            for (int i = r0 + lane; i < r1; i += 32) { const double x = A(i, c); p = fma(x, x, p); }
-            p = warp_sum(p);
-            if (lane == 0) rd[c] = p;
-        }
+        double *rd = red[xch & 1];
+        column_sums(0, s, r0, [&](int c, int i0, int i1) {
+            double pd = 0.0;
+            for (int i = i0; i < i1; ++i) { const double x = A(i, c); pd = fma(x, x, pd); }
+            return pd;
+        }, rd);
         cl.sync();
-        for (int c = tid; c < s; c += nt) {
-            double vt[16];
-#pragma unroll
-            for (int qq = 0; qq < 16; ++qq)
-                if (qq < C) vt[qq] = cl.map_shared_rank(rd, qq)[c];
-            double t = 0.0;
-#pragma unroll
-            for (int qq = 0; qq < 16; ++qq)
-                if (qq < C) t += vt[qq];
-            nrm[c] = t;
+        ++xch;
+        peer_sums(rd, 0, s, 0, nt, wv);
+        __syncthreads();
+        if (tid == 0) {
+            double mxn = 0.0;
+            for (int c = 0; c < s; ++c) mxn = fmax(mxn, wv[c]);
+            bc[0] = mxn > 0.0 ? 1.0 / mxn : 1.0;
         }
-        buf ^= 1;
+        __syncthreads();
+        sc2 = bc[0];
+        scr = sqrt(sc2);
+        for (int c = tid; c < s; c += nt) nrmf[c] = (float)(wv[c] * sc2);
         __syncthreads();
     }
+    // warp 0: column of largest FP32 norm among j0 .. s-1 (ties: lowest index) into `pivot`
+    auto argmax_pivot = [&](int j0) {
+        float bv = -1.f;
+        int bi = j0;
+        for (int c = j0 + lane; c < s; c += 32) {
+            const float v = nrmf[c];
+            if (v > bv) { bv = v; bi = c; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+        }
+        if (lane == 0) pivot = bi;
+    };
     for (int j = 0; j < kmax; ++j) {
-        const int nc = s - j - 1;
+        const int nc1 = s - j;              // columns j .. s-1
+        const int own = j / rb;              // CTA holding row j
+        const bool owner = (q == own);
         if (piv) {
-            if (tid == 0) {
-                int p = j;
-                for (int c = j + 1; c < s; ++c)
-                    if (nrm[c] > nrm[p]) p = c;
-                pivot = p;
+            // pivot for column j: chosen by warp 0 during the previous step's update (step 0:
+            // here), from nrmf, which every CTA holds identically
+            if (j == 0) {
+                if (warp == 0) argmax_pivot(0);
+                __syncthreads();
             }
-            __syncthreads();
             const int p = pivot;
             if (p != j) {
                 for (int i = r0 + tid; i < r1; i += nt) {
@@ -149,110 +215,74 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
                     A(i, p) = t;
                 }
                 if (tid == 0) {
-                    const double t = nrm[j]; nrm[j] = nrm[p]; nrm[p] = t;
+                    const float t = nrmf[j]; nrmf[j] = nrmf[p]; nrmf[p] = t;
                     const int u = permv[j]; permv[j] = permv[p]; permv[p] = u;
                 }
             }
             __syncthreads();
         }
-        double *rd = red[buf];
-        const bool owner = (j >= r0 && j < r1);
-        {
-            // one thread per (column, row chunk): partial x.x (c = j), x.A_c (rows >= j) and the
-            // FP32 pivot norms ||A_c||^2 (rows > j); then one thread per column combines chunks
-            const int nc1 = s - j;
-            const int nch = max(1, min(QR_NCH, nt / nc1));
-            const int ib = max(r0, j), nrows = r1 - ib;
-            const int rch = (nrows + nch - 1) / nch;
-            for (int e = tid; e < nc1 * nch; e += nt) {
-                const int c = j + e % nc1, ch = e / nc1;
-                const int i0 = ib + ch * rch, i1 = min(r1, i0 + rch);
-                double pd = 0.0;
-                float pn = 0.f;
-                if (c == j) {
-                    for (int i = max(i0, j + 1); i < i1; ++i) { const double x = A(i, j); pd = fma(x, x, pd); }
-                } else {
-                    for (int i = i0; i < i1; ++i) {
-                        const double y = A(i, c);
-                        pd = fma(A(i, j), y, pd);
-                        if (piv && i > j) { const float yf = (float)y; pn = fmaf(yf, yf, pn); }
-                    }
-                }
-                part[ch * QR_MAXS + (c - j)] = pd;
-                partn[ch * QR_MAXS + (c - j)] = pn;
+        double *rd = red[xch & 1];
+        // rd[0] = sigma2 part (rows > j), rd[cc] = D_{j+cc} part (rows >= j); owner: its row j
+        const int ib = max(r0, j);
+        column_sums(j, nc1, ib, [&](int c, int i0, int i1) {
+            double pd = 0.0;
+            if (c == j) {
+                for (int i = max(i0, j + 1); i < i1; ++i) { const double x = A(i, j); pd = fma(x, x, pd); }
+            } else {
+                for (int i = i0; i < i1; ++i) pd = fma(A(i, j), A(i, c), pd);
             }
-            __syncthreads();
-            for (int c = j + tid; c < s; c += nt) {
-                double pd = 0.0;
-                float pn = 0.f;
-                for (int ch = 0; ch < nch; ++ch) { pd += part[ch * QR_MAXS + (c - j)]; pn += partn[ch * QR_MAXS + (c - j)]; }
-                if (c == j) { rd[0] = pd; rd[1] = owner ? A(j, j) : 0.0; }
-                else {
-                    rd[2 + (c - j - 1)] = pd;
-                    rd[2 + nc + (c - j - 1)] = owner ? A(j, c) : 0.0;
-                    if (piv) rd[2 + 2 * nc + (c - j - 1)] = (double)pn;
-                }
-            }
-        }
+            return pd;
+        }, rd);
+        if (owner)
+            for (int cc = tid; cc < nc1; cc += nt) rd[nc1 + cc] = A(j, j + cc);
         cl.sync();
+        ++xch;
+        const double *ro = cl.map_shared_rank(rd, own);
         if (warp == 0) {
-            // lane q reads peer q's two scalars; all loads in flight at once
-            double s2 = 0.0, al = 0.0;
-            if (lane < C) {
-                const double *rq = cl.map_shared_rank(rd, lane);
-                s2 = rq[0];
-                al = rq[1];
-            }
-            s2 = warp_sum(s2);
-            al = warp_sum(al);
+            // sigma2 over the peers (lane = peer, C <= 16), alpha from the owner, the scalars
+            double s2 = lane < C ? cl.map_shared_rank(rd, lane)[0] : 0.0;
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
             if (lane == 0) {
-                double tau, beta, scal;
-                householder(al, s2, tau, beta, scal);
-                bc[0] = tau; bc[1] = scal; bc[2] = beta; bc[3] = al; bc[4] = s2;
-                taus[j] = tau;
-            }
-        }
-        __syncthreads();
-        const double tau = bc[0], scal = bc[1], beta = bc[2], al = bc[3], s2 = bc[4];
-        for (int c = j + 1 + tid; c < s; c += nt) {
-            // issue every peer's loads before summing (independent DSMEM round trips overlap)
-            double vD[16], vP[16], vN[16];
-#pragma unroll
-            for (int qq = 0; qq < 16; ++qq) {
-                if (qq < C) {
-                    const double *rq = cl.map_shared_rank(rd, qq);
-                    vD[qq] = rq[2 + (c - j - 1)];
-                    vP[qq] = rq[2 + nc + (c - j - 1)];
-                    vN[qq] = piv ? rq[2 + 2 * nc + (c - j - 1)] : 0.0;
+                const double al = ro[nc1];
+                double tau = 0.0, beta = al, vj = 0.0;
+                if (s2 > 0.0) {
+                    const double nrm = sqrt(fma(al, al, s2));
+                    beta = al >= 0.0 ? -nrm : nrm;
+                    tau = 1.0 / (nrm * (nrm + fabs(al)));
+                    vj = al - beta;
                 }
+                bc[0] = tau; bc[1] = beta; bc[2] = vj;
+                taus[j] = tau;
+                vjs[j] = vj;
             }
-            double D = 0.0, Pc = 0.0, Nc = 0.0;
-#pragma unroll
-            for (int qq = 0; qq < 16; ++qq)
-                if (qq < C) { D += vD[qq]; Pc += vP[qq]; Nc += vN[qq]; }
-            const double w = tau != 0.0 ? tau * (Pc + (D - al * Pc) * scal) : 0.0;
-            wv[c] = w;
+        } else {
+            peer_sums(rd, 1, nc1, 32, nt - 32, wv);
+        }
+        __syncthreads();
+        const double tau = bc[0], beta = bc[1], vj = bc[2];
+        // w_c = tau (D_c - beta P_c); pivot norms lose the new row of R, R_jc = P_c - v_j w_c
+        for (int cc = 1 + tid; cc < nc1; cc += nt) {
+            const double Pc = ro[nc1 + cc];
+            const double w = tau * fma(-beta, Pc, wv[cc]);
+            wv[cc] = w;
             if (piv) {
-                // norm of rows > j of column c after the reflector (exact from this step's sums)
-                const double post = Nc - 2.0 * w * (D - al * Pc) * scal + w * w * s2 * scal * scal;
-                nrm[c] = fmax(post, 0.0);
+                const float rf = (float)(fma(-vj, w, Pc) * scr);
+                nrmf[j + cc] = fmaxf(nrmf[j + cc] - rf * rf, 0.f);
             }
         }
-        buf ^= 1;
+        if (owner && tid == 0) A(j, j) = beta;
         __syncthreads();
-        const int ib = max(r0, j), nrows = r1 - ib;
-        // v_i = x_i / (alpha - beta) for i > j (stored as the reflector), v_j = 1
-        for (int i = max(r0, j + 1) + tid; i < r1; i += nt) A(i, j) *= scal;
-        __syncthreads();
-        if (tau != 0.0 && nrows > 0) {
-            for (int e = tid; e < nrows * nc; e += nt) {
-                const int i = ib + e % nrows, c = j + 1 + e / nrows;
-                const double v = (i == j) ? 1.0 : A(i, j);
-                A(i, c) -= v * wv[c];
+        const int nrows = max(0, r1 - ib), nc = nc1 - 1;
+        if (piv && warp == 0 && j + 1 < kmax) argmax_pivot(j + 1);   // nrmf is final for step j + 1
+        if (tau != 0.0 && nrows > 0 && nc > 0) {
+            int RT, ng, il, g;
+            row_layout(nrows, RT, ng, il, g);
+            for (int i = ib + il; i < r1; i += RT) {
+                const double v = (i == j) ? vj : A(i, j);
+                for (int cc = 1 + g; cc < nc1; cc += ng) A(i, j + cc) = fma(-v, wv[cc], A(i, j + cc));
             }
         }
-        __syncthreads();
-        if (tid == 0 && owner) A(j, j) = beta;
         __syncthreads();
     }
     if (J.tau && q == 0)
@@ -268,34 +298,31 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
         for (int j = kmax - 1; j >= 0; --j) {
             const double tau = taus[j];
             if (tau == 0.0) continue;   // uniform across the cluster
-            double *rd = red[buf];
-            const int ib = max(r0, j);
-            for (int c = j + warp; c < s; c += nw) {
-                double p = 0.0;
-                for (int i = ib + lane; i < r1; i += 32) p = fma((i == j) ? 1.0 : A(i, j), Q(i, c), p);
-                p = warp_sum(p);
-                if (lane == 0) rd[c - j] = p;
-            }
+            const double vj = vjs[j];
+            double *rd = red[xch & 1];
+            const int ib = max(r0, j), ncq = s - j;
+            column_sums(j, ncq, ib, [&](int c, int i0, int i1) {
+                double pd = 0.0;
+                int i = i0;
+                if (i == j && i < i1) { pd = vj * Q(j, c); ++i; }
+                for (; i < i1; ++i) pd = fma(A(i, j), Q(i, c), pd);
+                return pd;
+            }, rd);
             cl.sync();
-            for (int c = j + tid; c < s; c += nt) {
-                double vw[16];
-#pragma unroll
-                for (int qq = 0; qq < 16; ++qq)
-                    if (qq < C) vw[qq] = cl.map_shared_rank(rd, qq)[c - j];
-                double w = 0.0;
-#pragma unroll
-                for (int qq = 0; qq < 16; ++qq)
-                    if (qq < C) w += vw[qq];
-                wv[c] = w * tau;
-            }
-            buf ^= 1;
+            ++xch;
+            peer_sums(rd, 0, ncq, 0, nt, wv);
             __syncthreads();
-            const int nrows = r1 - ib, ncols = s - j;
-            if (nrows > 0)
-                for (int e = tid; e < nrows * ncols; e += nt) {
-                    const int i = ib + e % nrows, c = j + e / nrows;
-                    Q(i, c) -= ((i == j) ? 1.0 : A(i, j)) * wv[c];
+            const int nrows = r1 - ib;
+            for (int cc = tid; cc < ncq; cc += nt) wv[cc] *= tau;
+            __syncthreads();
+            if (nrows > 0) {
+                int RT, ng, il, g;
+                row_layout(nrows, RT, ng, il, g);
+                for (int i = ib + il; i < r1; i += RT) {
+                    const double v = (i == j) ? vj : A(i, j);
+                    for (int cc = g; cc < ncq; cc += ng) Q(i, j + cc) = fma(-v, wv[cc], Q(i, j + cc));
                 }
+            }
             __syncthreads();
         }
     }
