@@ -65,9 +65,11 @@ struct QRJobs {
 
 // One reflector per step, one cluster-wide exchange per step.  With x = A[j:, j], alpha = x_0,
 // sigma2 = ||x_1:||^2, nrm = (alpha^2 + sigma2)^(1/2), beta = -sign(alpha) nrm, the reflector
-// is H = I - tau v v^T with the unnormalised v = x - beta e_0 (v_0 = alpha - beta, the rest
-// of x kept in place below the diagonal) and tau = 1 / (nrm (nrm + |alpha|)): one reciprocal.
-// For every trailing column c, v^T A[j:, c] = D_c - beta P_c with D_c = x^T A[j:, c] and
+// is LAPACK's H = I - tau v v^T, v = (x - beta e_0) / (alpha - beta) (v_0 = 1), tau =
+// (beta - alpha) / beta in [1, 2].  (The unnormalised v = x - beta e_0 would need
+// tau = 1 / (nrm (nrm + |alpha|)), which overflows once the columns left after an exact
+// low-rank block are rounding noise and each step shrinks them further.)  For every trailing
+// column c, v^T A[j:, c] = P_c + (D_c - alpha P_c) / (alpha - beta) with D_c = x^T A[j:, c] and
 // P_c = A[j, c], so a step needs, from every CTA over its own rows, the partial sigma2 and
 // D_c, and from the CTA owning row j its row (alpha, P_c): exchanged through distributed
 // shared memory after one cluster barrier.  On this part an FP64 warp instruction holds an
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
     __shared__ double red[2][2 * QR_MAXS];         // [0, nc1): partial sums, [nc1, 2 nc1): owner's row
     __shared__ double part[QR_NCH * QR_MAXS];
     __shared__ double wv[QR_MAXS];
-    __shared__ double taus[QR_MAXS], vjs[QR_MAXS];
+    __shared__ double taus[QR_MAXS];
     __shared__ float nrmf[QR_MAXS];
     __shared__ int permv[QR_MAXS];
     __shared__ double bc[4];
@@ -245,32 +247,33 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
             for (int o = 8; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
             if (lane == 0) {
                 const double al = ro[nc1];
-                double tau = 0.0, beta = al, vj = 0.0;
+                double tau = 0.0, beta = al, scal = 0.0;
                 if (s2 > 0.0) {
                     const double nrm = sqrt(fma(al, al, s2));
                     beta = al >= 0.0 ? -nrm : nrm;
-                    tau = 1.0 / (nrm * (nrm + fabs(al)));
-                    vj = al - beta;
+                    tau = (beta - al) / beta;
+                    scal = 1.0 / (al - beta);
                 }
-                bc[0] = tau; bc[1] = beta; bc[2] = vj;
+                bc[0] = tau; bc[1] = beta; bc[2] = scal; bc[3] = al;
                 taus[j] = tau;
-                vjs[j] = vj;
             }
         } else {
             peer_sums(rd, 1, nc1, 32, nt - 32, wv);
         }
         __syncthreads();
-        const double tau = bc[0], beta = bc[1], vj = bc[2];
-        // w_c = tau (D_c - beta P_c); pivot norms lose the new row of R, R_jc = P_c - v_j w_c
+        const double tau = bc[0], beta = bc[1], scal = bc[2], al = bc[3];
+        // w_c = tau v^T A_c = tau (P_c + (D_c - alpha P_c) / (alpha - beta)); pivot norms lose
+        // the new row of R, R_jc = P_c - w_c; v stored in place: x_i / (alpha - beta)
         for (int cc = 1 + tid; cc < nc1; cc += nt) {
             const double Pc = ro[nc1 + cc];
-            const double w = tau * fma(-beta, Pc, wv[cc]);
+            const double w = tau * fma(scal, fma(-al, Pc, wv[cc]), Pc);
             wv[cc] = w;
             if (piv) {
-                const float rf = (float)(fma(-vj, w, Pc) * scr);
+                const float rf = (float)((Pc - w) * scr);
                 nrmf[j + cc] = fmaxf(nrmf[j + cc] - rf * rf, 0.f);
             }
         }
+        for (int i = max(r0, j + 1) + tid; i < r1; i += nt) A(i, j) *= scal;
         if (owner && tid == 0) A(j, j) = beta;
         __syncthreads();
         const int nrows = max(0, r1 - ib), nc = nc1 - 1;
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
             int RT, ng, il, g;
             row_layout(nrows, RT, ng, il, g);
             for (int i = ib + il; i < r1; i += RT) {
-                const double v = (i == j) ? vj : A(i, j);
+                const double v = (i == j) ? 1.0 : A(i, j);
                 for (int cc = 1 + g; cc < nc1; cc += ng) A(i, j + cc) = fma(-v, wv[cc], A(i, j + cc));
             }
         }
@@ -298,13 +301,12 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
         for (int j = kmax - 1; j >= 0; --j) {
             const double tau = taus[j];
             if (tau == 0.0) continue;   // uniform across the cluster
-            const double vj = vjs[j];
             double *rd = red[xch & 1];
             const int ib = max(r0, j), ncq = s - j;
             column_sums(j, ncq, ib, [&](int c, int i0, int i1) {
                 double pd = 0.0;
                 int i = i0;
-                if (i == j && i < i1) { pd = vj * Q(j, c); ++i; }
+                if (i == j && i < i1) { pd = Q(j, c); ++i; }
                 for (; i < i1; ++i) pd = fma(A(i, j), Q(i, c), pd);
                 return pd;
             }, rd);
@@ -319,7 +321,7 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
                 int RT, ng, il, g;
                 row_layout(nrows, RT, ng, il, g);
                 for (int i = ib + il; i < r1; i += RT) {
-                    const double v = (i == j) ? vj : A(i, j);
+                    const double v = (i == j) ? 1.0 : A(i, j);
                     for (int cc = g; cc < ncq; cc += ng) Q(i, j + cc) = fma(-v, wv[cc], Q(i, j + cc));
                 }
             }

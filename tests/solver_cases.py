@@ -14,6 +14,8 @@ CASES = {
     "mln_convdiff_n40": (lambda: W.convdiff3d(40, 2, None), W.SolverParams('mln', 10, 0, 12, 16, 1e-8, seed=8), False),
     "adjoint_convdiff_n30": (lambda: W.convdiff3d(30, 4, None), W.SolverParams('rhosvd', 10, 64, 5, 15, 1e-8, seed=9), True),
     "exhaustion_convdiff_n16": (lambda: W.convdiff3d(16, 5, None), W.SolverParams('rhosvd', 4, 10, 5, 40, 1e-14, seed=1), False),
+    "point_source_n64": (lambda: W.poisson3d_point(64, None, 8, "p64"),
+                         W.SolverParams('rhosvd', 32, 64, 5, 6, 1e-8, eta=0.4, ktrunc=1, seed=2), False),
 }
 
 

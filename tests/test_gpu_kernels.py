@@ -115,10 +115,17 @@ def _rs_case(name):
     if name == "order4":
         n = [12, 11, 10, 9]
         return [(1.0, rand_tucker(n, [3, 3, 3, 3], 15)), (2.0, rand_tucker(n, [2, 2, 2, 2], 16))], 4, 3
+    if name == "point_source":
+        # L(b) for the Poisson operator and b = (ones / sqrt(n)) (x) e_1 (x) e_1: factors with
+        # identical interior rows and exact zeros, so every range-finder matrix has exact rank
+        # 2 and the Householder steps past it act on rounding noise that shrinks step by step
+        n = 64
+        wl = W.poisson3d_point(n, None, 8, "p")
+        return [(1.0, t) for t in OO.apply_op(wl.op, wl.b)], 32, 5
     raise KeyError(name)
 
 
-@pytest.mark.parametrize("case", ["exact_lowrank", "truncating", "small_n", "matvec_terms", "order4"])
+@pytest.mark.parametrize("case", ["exact_lowrank", "truncating", "small_n", "matvec_terms", "order4", "point_source"])
 def test_roundsum(P, case):
     terms, R, p = _rs_case(case)
     n = terms[0][1].n
