@@ -1,4 +1,5 @@
-"""RHOSVD-Tucker sGMRES (Algorithm 2), MLN-Tucker sGMRES (Algorithm 6), dense sGMRES (Eq. (2.8)).
+"""RHOSVD-Tucker GMRES (Algorithm 1), RHOSVD-Tucker sGMRES (Algorithm 2), MLN-Tucker sGMRES
+(Algorithm 6), dense sGMRES (Eq. (2.8)).
 
 Test infrastructure only.  Readings of points the paper leaves open:
   * x_0 = 0, so V_1 = B / ||B||;
@@ -13,7 +14,9 @@ Test infrastructure only.  Readings of points the paper leaves open:
     (seed, STREAM_KRYLOV, 0, mode);
   * Algorithm 6: Psi_k has r + p columns (Section 3.3); b_s = ||B|| diag(G_Psi(V_1)) so that
     b_s = S^T vec(B) as in Algorithm 2; after the window's MLN_Sum the sum is recovered
-    (MLN_Recovery) before its norm is taken and V_{i+1} is formed.
+    (MLN_Recovery) before its norm is taken and V_{i+1} is formed;
+  * Algorithm 1: the same breakdown reading (the Hessenberg least-squares problem is solved
+    with its zero last row, then the solve ends); it stops when res_k < tol (no eta factor).
 """
 from __future__ import annotations
 
@@ -116,6 +119,59 @@ def rhosvd_sgmres(op: Operator, b: Tucker, prm: SolverParams, transpose: bool = 
             break
     basis = zs if precond is not None else v
     x = rs([(float(y[i]), basis[i]) for i in range(k)])
+    return Result(x, k, status, hist, y, ranks, sizes, v)
+
+
+def rhosvd_gmres(op: Operator, b: Tucker, prm: SolverParams, transpose: bool = False,
+                 bf16_sketch: bool = False, maxit: Optional[int] = None) -> Result:
+    """Algorithm 1: GMRES with full Arnoldi orthogonalisation, every sum through RoundSum.
+    h_{j,k} = <V_j, W> for all j <= k from the same W (classical Gram-Schmidt, one RoundSum of
+    k + 1 terms); h_{k+1,k} = ||W||; y_k = argmin ||beta e_1 - H_{1:k+1,1:k} y||; the relative
+    residual res_k = ||beta e_1 - H y_k|| / beta."""
+    d, n = b.d, b.n
+    maxit = prm.maxit if maxit is None else maxit
+    call = [0]
+    sizes: List[int] = []
+
+    def rs(terms):
+        sr = (effective_sketch_size(terms, prm.oversample_p, prm.rank_cap, prm.round_tol)
+              if prm.adaptive_rank else prm.rank_cap + prm.oversample_p)
+        mats = [sketch_matrix(prm.seed, STREAM_ROUNDSUM, call[0], k, n[k], sr, bf16_sketch)
+                for k in range(d)]
+        call[0] += 1
+        sizes.append(sr)
+        return roundsum(terms, mats, prm.rank_cap, prm.round_tol)
+
+    beta = norm(b)
+    v = [scale(b, 1.0 / beta)]
+    h = np.zeros((maxit + 1, maxit))
+    hist: List[float] = []
+    ranks: List[List[int]] = []
+    status = NOT_CONVERGED
+    y = np.zeros(0)
+    k = 0
+    for k in range(1, maxit + 1):
+        w = rs([(1.0, t) for t in apply_op(op, v[-1], transpose)])
+        w0 = norm(w)
+        hs = [inner(v[j], w) for j in range(k)]
+        w = rs([(1.0, w)] + [(-hj, v[j]) for j, hj in enumerate(hs)])
+        nw = norm(w)
+        h[:k, k - 1] = hs
+        h[k, k - 1] = nw
+        rhs = np.zeros(k + 1)
+        rhs[0] = beta
+        y = np.linalg.lstsq(h[:k + 1, :k], rhs, rcond=None)[0]
+        res = float(np.linalg.norm(rhs - h[:k + 1, :k] @ y)) / beta
+        hist.append(res)
+        if nw <= 1e-14 * w0:
+            status = BREAKDOWN
+            break
+        v.append(scale(w, 1.0 / nw))
+        ranks.append(v[-1].r)
+        if res < prm.tol:
+            status = CONVERGED
+            break
+    x = rs([(float(y[i]), v[i]) for i in range(k)])
     return Result(x, k, status, hist, y, ranks, sizes, v)
 
 

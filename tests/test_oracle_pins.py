@@ -469,3 +469,68 @@ def test_preconditioned_poisson_reaches_1e6_quickly():
     res = S.rhosvd_sgmres(wl.op, wl.b, prm, precond=OP.expsum_preconditioner(n, 3, 8))
     assert res.status == S.CONVERGED and res.iters <= 12
     assert RS.true_residual(wl.op, res.x, wl.b) < 1e-5
+
+
+# ------------------------------------------------------------------------------ Algorithm 1
+def _dense_op(n, seed):
+    rng = np.random.default_rng(seed)
+    mats = []
+    for k in range(3):
+        a = rng.standard_normal((n, n)) / np.sqrt(n) + 3.0 * np.eye(n)
+        mats.append(W.ModeMat('D', n, 0, 0, a))
+    return W.Operator(
+        3, [n] * 3, [1.0, 1.0, 1.0],
+        [[mats[0], W.identity(n), W.identity(n)], [W.identity(n), mats[1], W.identity(n)],
+         [W.identity(n), W.identity(n), mats[2]]])
+
+
+def test_tucker_gmres_untruncated_matches_scipy_gmres():
+    """Untruncated Algorithm 1 (rank cap = n, tiny tolerance) is exact GMRES: its residual
+    history equals scipy's unrestarted GMRES on the dense Kronecker matrix (an independent
+    Arnoldi implementation)."""
+    from scipy.sparse.linalg import gmres
+    n = 6
+    op = _dense_op(n, 3)
+    b = W.random_tucker([n] * 3, [2, 2, 2], 41)
+    prm = W.SolverParams('gmres', n, 0, n, 12, 1e-14, round_tol=1e-15, seed=1)
+    res = S.rhosvd_gmres(op, b, prm)
+    a = O.dense_matrix(op)
+    bv = T.full(b).reshape(-1, order='F')
+    hist = []
+    gmres(a, bv, rtol=1e-14, atol=0.0, restart=200, maxiter=1, callback=lambda r: hist.append(r),
+          callback_type='pr_norm')
+    k = min(len(hist), len(res.res_hist))
+    assert k >= 8
+    assert np.allclose(res.res_hist[:k], hist[:k], rtol=1e-6, atol=1e-12)
+
+
+def test_tucker_gmres_two_eigenvalues_converges_in_two_steps():
+    """A diagonalisable operator with two distinct eigenvalues: the minimal polynomial has
+    degree 2, so GMRES is exact at iteration 2 (and the solution is the exact inverse)."""
+    n = 5
+    dvals = np.where(np.arange(n) % 2 == 0, 1.0, 3.0)
+    d0 = W.ModeMat('D', n, 0, 0, np.diag(dvals))
+    op = W.Operator(3, [n] * 3, [1.0], [[d0, W.identity(n), W.identity(n)]])   # eigenvalues 1, 3
+    b = W.random_tucker([n] * 3, [2, 2, 2], 42)
+    prm = W.SolverParams('gmres', n, 0, n, 10, 1e-12, round_tol=1e-15, seed=2)
+    res = S.rhosvd_gmres(op, b, prm)
+    assert res.iters <= 2 and res.res_hist[-1] < 1e-12
+    xs = T.ttm(T.full(b), np.diag(1.0 / dvals), 0)
+    assert np.linalg.norm(T.full(res.x) - xs) <= 1e-11 * np.linalg.norm(xs)
+
+
+def test_tucker_gmres_residuals_do_not_increase_and_beat_short_recurrence():
+    """Full GMRES minimises the residual over the whole Krylov space: its history is
+    non-increasing, and (untruncated) never above the sketched short-recurrence method's
+    true residual at the same iteration."""
+    n = 6
+    op = _dense_op(n, 4)
+    b = W.random_tucker([n] * 3, [1, 2, 1], 43)
+    prm = W.SolverParams('gmres', n, 0, n, 15, 1e-14, round_tol=1e-15, seed=3)
+    res = S.rhosvd_gmres(op, b, prm)
+    hsts = np.array(res.res_hist)
+    assert np.all(np.diff(hsts) <= 1e-12)
+    prm2 = W.SolverParams('rhosvd', n, 64, n, 15, 1e-14, ktrunc=2, round_tol=1e-15, seed=3)
+    for k in [3, 6, 10]:
+        r2 = S.rhosvd_sgmres(op, b, prm2, maxit=k)
+        assert hsts[k - 1] <= RS.true_residual(op, r2.x, b) * (1 + 1e-8)
