@@ -444,6 +444,19 @@ def secondary(P, W, torch):
     entry["unpreconditioned"] = {"iters": rep.iters, "status": rep.status, "seconds": round(dt, 4),
                                  "true_rel_residual": P.tk_residual(dop, x, b)}
     out["poisson3d_point_n1000_expsum_q8"] = entry
+    # Algorithm 1 (full Arnoldi) against Algorithm 2 (short recurrence), same RoundSum settings
+    wl = W.workload("convdiff3d_n256")
+    dop = P.DeviceOperator(wl.op)
+    b = P.DeviceTucker.from_numpy(wl.b.core, wl.b.factors)
+    cmp = {}
+    for variant, prm in [("gmres (Algorithm 1)", W.SolverParams('gmres', 32, 0, 5, 30, 1e-6, seed=0)),
+                         ("sgmres (Algorithm 2)", W.SolverParams('rhosvd', 32, 128, 5, 30, 1e-6, seed=0))]:
+        opts = P.Options.from_params(prm)
+        P.tk_solve(dop, b, opts)
+        x, rep, dt = _timed_solve(P, torch, dop, b, opts)
+        cmp[variant] = {"iters": rep.iters, "seconds": round(dt, 4), "iters_per_s": round(rep.iters / dt, 2),
+                        "res_hist_last": rep.res_hist[-1], "true_rel_residual": P.tk_residual(dop, x, b)}
+    out["gmres_vs_sgmres_convdiff3d_n256_30it"] = cmp
     out["time_to_1e-6"] = time_to_tol(P, W, torch)
     # gradient of 0.5||x - x_ref||^2 w.r.t. theta and b: forward solve + adjoint solve + contractions
     wl = W.workload("deblur3d_n128")

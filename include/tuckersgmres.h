@@ -76,12 +76,14 @@ typedef struct {
     const tk_modemat *mats;
 } tk_operator;
 
-enum { TK_RHOSVD_SGMRES = 0, TK_MLN_SGMRES = 1 };
+/* TK_RHOSVD_GMRES: Algorithm 1 (full Arnoldi, least squares on the Hessenberg matrix; the
+ * comparator of the paper's experiments; sketch_s, ktrunc and eta unused, stops at res < tol). */
+enum { TK_RHOSVD_SGMRES = 0, TK_MLN_SGMRES = 1, TK_RHOSVD_GMRES = 2 };
 enum { TK_FP64 = 0, TK_MIXED = 1 };
 
 /* Solver options (Algorithm 2 inputs; Algorithm 6 inputs). */
 typedef struct {
-    int32_t variant;        /* TK_RHOSVD_SGMRES or TK_MLN_SGMRES                                  */
+    int32_t variant;        /* TK_RHOSVD_SGMRES, TK_MLN_SGMRES or TK_RHOSVD_GMRES                 */
     int32_t rank_cap;       /* RHOSVD: multilinear rank cap; MLN: Nystrom target rank r           */
     int32_t sketch_s;       /* RHOSVD: Krylov sketch size s (MLN uses r + p)                      */
     int32_t oversample_p;   /* RHOSVD: RoundSum oversampling (paper: 5); MLN: Nystrom p            */
@@ -130,8 +132,9 @@ int tk_profile(tk_handle *h, int32_t enable);
  * The returned string is owned by the handle and valid until the next call on it. */
 const char *tk_profile_report(tk_handle *h);
 
-/* tk_solve: RHOSVD-Tucker sGMRES (Algorithm 2) or MLN-Tucker sGMRES (Algorithm 6) for
- * L(X) = B (or L^T(X) = B when opts->transpose).  x_out is caller-allocated with
+/* tk_solve: RHOSVD-Tucker sGMRES (Algorithm 2), MLN-Tucker sGMRES (Algorithm 6) or
+ * RHOSVD-Tucker GMRES (Algorithm 1, opts->variant) for L(X) = B (or L^T(X) = B when
+ * opts->transpose).  x_out is caller-allocated with
  * x_out->r[k] = rank_cap for every mode (core rank_cap^d, factors n_k x rank_cap); the
  * solution is written zero-padded and report->out_rank holds its multilinear rank.
  * Synchronizes `stream`.  Returns TK_OK / TK_NOT_CONVERGED / TK_BREAKDOWN /

@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "libtuckersgmres.so")
 TK_OK, TK_NOT_CONVERGED, TK_BREAKDOWN, TK_SKETCH_EXHAUSTED = 0, 1, 2, 3
 TK_EINVAL, TK_ENOMEM, TK_ECUDA, TK_EINTERNAL = -1, -2, -3, -4
 TK_IDENTITY, TK_BANDED, TK_DENSE = 0, 1, 2
-TK_RHOSVD_SGMRES, TK_MLN_SGMRES = 0, 1
+TK_RHOSVD_SGMRES, TK_MLN_SGMRES, TK_RHOSVD_GMRES = 0, 1, 2
 TK_FP64, TK_MIXED = 0, 1
 
 EXPORTS = ["tk_create", "tk_destroy", "tk_last_error", "tk_solve", "tk_apply", "tk_roundsum",

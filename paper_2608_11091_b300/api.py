@@ -210,7 +210,7 @@ class DeviceOperator:
 
 @dataclass
 class Options:
-    variant: str = "rhosvd"          # 'rhosvd' (Algorithm 2) or 'mln' (Algorithm 6)
+    variant: str = "rhosvd"          # 'rhosvd' (Algorithm 2), 'mln' (Algorithm 6) or 'gmres' (Algorithm 1)
     rank_cap: int = 8
     sketch_s: int = 64
     oversample_p: int = 5
@@ -235,7 +235,7 @@ class Options:
 
     def c(self) -> L.tk_opts:
         s = L.tk_opts()
-        s.variant = L.TK_RHOSVD_SGMRES if self.variant == "rhosvd" else L.TK_MLN_SGMRES
+        s.variant = {"rhosvd": L.TK_RHOSVD_SGMRES, "mln": L.TK_MLN_SGMRES, "gmres": L.TK_RHOSVD_GMRES}[self.variant]
         s.rank_cap, s.sketch_s, s.oversample_p = self.rank_cap, self.sketch_s, self.oversample_p
         s.ktrunc, s.maxit, s.adaptive_rank = self.ktrunc, self.maxit, int(self.adaptive_rank)
         s.precision = L.TK_MIXED if self.precision == "mixed" else L.TK_FP64
@@ -258,7 +258,8 @@ class Report:
 
 def tk_solve(op: DeviceOperator, b: DeviceTucker, opts: Options, x: Optional[DeviceTucker] = None,
              stream=None, device: Optional[int] = None):
-    """RHOSVD-Tucker sGMRES (Algorithm 2) or MLN-Tucker sGMRES (Algorithm 6). Returns (x, Report)."""
+    """RHOSVD-Tucker sGMRES (Algorithm 2), MLN-Tucker sGMRES (Algorithm 6) or RHOSVD-Tucker GMRES
+    (Algorithm 1), by opts.variant. Returns (x, Report)."""
     h = handle(device)
     if x is None:
         x = DeviceTucker.empty(b.n, [opts.rank_cap] * b.d, device=b.core.device)

@@ -249,6 +249,114 @@ static void solve_rhosvd(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tuck
 }
 
 // ------------------------------------------------------------------------------------------
+// RHOSVD-Tucker GMRES (Algorithm 1): full Arnoldi, every sum through RoundSum, least squares on
+// the Hessenberg matrix (the incremental Householder kernel with M = H, b = beta e_1)
+// ------------------------------------------------------------------------------------------
+static void solve_gmres(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucker *b, const tk_opts &o,
+                        tk_tucker *x, SolveOut &so, double *pinned) {
+    ScopedMark solve_mark(*c.arena);
+    const int d = pb.d, R = o.rank_cap, sr = o.rank_cap + o.oversample_p;
+    const int kmax = o.maxit, ld = kmax + 1;
+    TK_REQUIRE(sr <= 96, "RoundSum sketch size rank_cap + p must be <= 96");
+    TK_REQUIRE(kmax <= 4095, "maxit must be <= 4095");
+    const int bf16 = o.precision == TK_MIXED ? 1 : 0;
+    double *sc = c.arena->alloc(SC_N);
+    fill(c, sc, SC_N, 0.0);
+    const TTerm B = term_of(b);
+    inner_batch(c, pb, {InnerJob{B, B, sc + SC_BETA2}});
+    sqrt_scalar(c, sc + SC_BETA2, sc + SC_BETA);
+    std::vector<TTerm> V;
+    {
+        TTerm v1 = B;
+        double *core = c.arena->alloc(prodi(B.r, d));
+        scale_by(c, core, b->core, prodi(B.r, d), sc + SC_BETA, 1);
+        v1.core = core;
+        V.push_back(v1);
+    }
+    // Hessenberg matrix H ((kmax + 1) x kmax, column-major) and beta e_1
+    double *H = c.arena->alloc((size_t)ld * kmax);
+    fill(c, H, (long long)ld * kmax, 0.0);
+    double *e1 = c.arena->alloc(ld);
+    fill(c, e1, ld, 0.0);
+    copy(c, e1, sc + SC_BETA, 1);
+    LSState ls{};
+    ls.H = c.arena->alloc((size_t)ld * kmax);
+    ls.tau = c.arena->alloc(kmax);
+    ls.qtb = c.arena->alloc(ld);
+    ls.y = c.arena->alloc(kmax);
+    ls.res = sc + SC_RES;
+    readback(c, pinned, sc, 4);
+    const double beta = pinned[SC_BETA];
+    TK_REQUIRE(std::isfinite(beta) && beta > 0.0, "right-hand side is zero or not finite");
+
+    so.status = TK_NOT_CONVERGED;
+    int k = 0;
+    uint64_t call = 0;
+    for (k = 1; k <= kmax; ++k) {
+        Slot vn = alloc_slot(c, pb, R);
+        {
+            ScopedMark it(*c.arena);
+            std::vector<TTerm> terms = apply_operator(c, pb, op, V.back(), o.transpose);
+            Slot wmv = alloc_slot(c, pb, R);
+            roundsum(c, pb, terms, RSConfig{sr, R, o.round_tol, o.seed, call++, bf16}, wmv.out(pb));
+            const TTerm W = wmv.term(pb, R);
+            dot(c, W.core, W.core, prodi(W.r, d), sc + SC_NW0SQ);
+            double *hcol = H + (size_t)(k - 1) * ld;
+            std::vector<InnerJob> ij;
+            for (int j = 1; j <= k; ++j) ij.push_back(InnerJob{V[j - 1], W, hcol + (j - 1)});
+            inner_batch(c, pb, ij);
+            std::vector<TTerm> orth{W};
+            for (int j = 1; j <= k; ++j) {
+                TTerm t = V[j - 1];
+                t.coef = -1.0;
+                t.coef_dev = hcol + (j - 1);
+                orth.push_back(t);
+            }
+            roundsum(c, pb, orth, RSConfig{sr, R, o.round_tol, o.seed, call++, bf16}, vn.out(pb));
+            const long long csz = prodi(W.r, d);
+            dot(c, vn.core, vn.core, csz, sc + SC_NWSQ);
+            sqrt_scalar(c, sc + SC_NWSQ, sc + SC_NW);
+            copy(c, hcol + k, sc + SC_NW, 1);                      // h_{k+1,k} = ||W||
+            ls_update(c, H, e1, ld, k - 1, k, ls, k == 1);
+            scale_by(c, vn.core, vn.core, csz, sc + SC_NW, 1);
+            readback(c, pinned, sc, 8);
+        }
+        const double res = pinned[SC_RES] / beta;
+        TK_REQUIRE(std::isfinite(res), "non-finite residual");
+        so.hist.push_back(res);
+        so.sres = res;
+        if (std::sqrt(std::max(pinned[SC_NWSQ], 0.0)) <= 1e-14 * std::sqrt(std::max(pinned[SC_NW0SQ], 0.0))) {
+            so.status = TK_BREAKDOWN;
+            break;
+        }
+        V.push_back(vn.term(pb, R));
+        if (res < o.tol) {
+            so.status = TK_OK;
+            break;
+        }
+    }
+    if (k > kmax) k = kmax;
+    so.iters = k;
+    std::vector<TTerm> fin;
+    for (int i = 0; i < k; ++i) {
+        TTerm t = V[i];
+        t.coef = 1.0;
+        t.coef_dev = ls.y + i;
+        fin.push_back(t);
+    }
+    TOut xo{};
+    xo.core = x->core;
+    for (int kk = 0; kk < d; ++kk) xo.f[kk] = x->factor[kk];
+    int *rk = c.arena->alloc_int(TK_MAX_D);
+    xo.rank_dev = rk;
+    roundsum(c, pb, fin, RSConfig{sr, R, o.round_tol, o.seed, call++, bf16}, xo);
+    int hr[TK_MAX_D];
+    TK_CUDA(cudaMemcpyAsync(hr, rk, sizeof(int) * d, cudaMemcpyDeviceToHost, c.st));
+    TK_CUDA(cudaStreamSynchronize(c.st));
+    for (int kk = 0; kk < d; ++kk) so.ranks[kk] = hr[kk];
+}
+
+// ------------------------------------------------------------------------------------------
 // MLN-Tucker sGMRES (Algorithm 6, without the memory-saving truncation)
 // ------------------------------------------------------------------------------------------
 struct Sk {
@@ -660,7 +768,8 @@ static int solve_entry(tk_handle *h, const tk_operator *op, const tk_operator *p
             TK_REQUIRE(x_out->n[k] == b->n[k], "x_out: mode size differs from b");
             TK_REQUIRE(x_out->r[k] == o.rank_cap, "x_out: every rank must equal rank_cap");
         }
-        TK_REQUIRE(o.variant == TK_RHOSVD_SGMRES || o.variant == TK_MLN_SGMRES, "unknown variant");
+        TK_REQUIRE(o.variant == TK_RHOSVD_SGMRES || o.variant == TK_MLN_SGMRES || o.variant == TK_RHOSVD_GMRES,
+                   "unknown variant");
         TK_REQUIRE(o.rank_cap >= 1 && o.oversample_p >= 0 && o.maxit >= 1, "bad rank_cap / p / maxit");
         TK_REQUIRE(o.precision == TK_FP64 || o.precision == TK_MIXED, "bad precision");
         TK_REQUIRE(o.adaptive_rank == 0, "adaptive sketch size is not available in this build");
@@ -679,6 +788,8 @@ static int solve_entry(tk_handle *h, const tk_operator *op, const tk_operator *p
         }
         if (o.variant == TK_RHOSVD_SGMRES)
             solve_rhosvd(c, pb, od, b, o, x_out, so, h->pinned, pc ? &pd : nullptr);
+        else if (o.variant == TK_RHOSVD_GMRES)
+            solve_gmres(c, pb, od, b, o, x_out, so, h->pinned);
         else
             solve_mln(c, pb, od, b, o, x_out, so, h->pinned);
         TK_CUDA(cudaEventRecord(e1, c.st));

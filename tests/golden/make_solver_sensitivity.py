@@ -45,6 +45,8 @@ def _solve(wl, prm, noise, seed, transpose=False, bf16=False, precond=None):
     try:
         if prm.variant == "rhosvd":
             return OS.rhosvd_sgmres(wl.op, wl.b, prm, transpose=transpose, bf16_sketch=bf16, precond=precond)
+        if prm.variant == "gmres":
+            return OS.rhosvd_gmres(wl.op, wl.b, prm, transpose=transpose, bf16_sketch=bf16)
         return OS.mln_sgmres(wl.op, wl.b, prm, transpose=transpose)
     finally:
         OS.roundsum, OS.mln_recovery = rs, rec

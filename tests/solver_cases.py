@@ -16,6 +16,13 @@ CASES = {
     "exhaustion_convdiff_n16": (lambda: W.convdiff3d(16, 5, None), W.SolverParams('rhosvd', 4, 10, 5, 40, 1e-14, seed=1), False),
     "point_source_n64": (lambda: W.poisson3d_point(64, None, 8, "p64"),
                          W.SolverParams('rhosvd', 32, 64, 5, 6, 1e-8, eta=0.4, ktrunc=1, seed=2), False),
+    # Algorithm 1 (full Arnoldi through RoundSum)
+    "gmres_poisson3d_n20_r12": (lambda: W.poisson3d(20, 1, 3, None, "p20"),
+                                W.SolverParams('gmres', 12, 0, 5, 30, 1e-9, seed=4), False),
+    "gmres_convdiff_ragged": (lambda: W.convdiff3d(37, 3, None, rhs_rank=2),
+                              W.SolverParams('gmres', 7, 0, 6, 15, 1e-8, seed=6), False),
+    "gmres_adjoint_convdiff_n30": (lambda: W.convdiff3d(30, 4, None), W.SolverParams('gmres', 10, 0, 5, 12, 1e-8, seed=9),
+                                   True),
 }
 
 

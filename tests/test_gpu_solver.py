@@ -45,6 +45,8 @@ def _run(P, wl, params, transpose=False):
     x, rep = P.tk_solve(P.DeviceOperator(wl.op), to_dev(wl.b), opts)
     if params.variant == "rhosvd":
         ref = OS.rhosvd_sgmres(wl.op, wl.b, params, transpose=transpose)
+    elif params.variant == "gmres":
+        ref = OS.rhosvd_gmres(wl.op, wl.b, params, transpose=transpose)
     else:
         ref = OS.mln_sgmres(wl.op, wl.b, params, transpose=transpose)
     return x, rep, ref
@@ -99,6 +101,22 @@ def test_rejects_bad_options(P):
             P.tk_solve(dop, b, P.Options.from_params(wl.params, **over))
 
 
+def test_gmres_breakdown_on_eigentensor(P):
+    """Algorithm 1 on an eigentensor of the 3-D Laplacian: L(V_1) is a multiple of V_1, so W
+    vanishes after the first orthogonalisation (lucky breakdown) and x is exact."""
+    n = 24
+    i = np.arange(1, n + 1)
+    v = np.sqrt(2.0 / (n + 1)) * np.sin(np.outer(i, i) * np.pi / (n + 1))
+    lam = 2 - 2 * np.cos(i * np.pi / (n + 1))
+    op = W.kronecker_sum_operator([W.second_difference(n)], 3)
+    b = W.Tucker(np.full((1, 1, 1), 3.0), [v[:, [2]], v[:, [0]], v[:, [5]]])
+    params = W.SolverParams('gmres', 4, 0, 5, 10, 1e-12)
+    x, rep = P.tk_solve(P.DeviceOperator(op), to_dev(b), P.Options.from_params(params))
+    assert rep.status == "breakdown" and rep.iters == 1
+    ref = W.Tucker(b.core / (lam[2] + lam[0] + lam[5]), b.factors)
+    assert rel_diff(to_host(x), ref) <= 1e-12
+
+
 @pytest.mark.parametrize("name,iters", [("convdiff3d_n256", 12), ("poisson3d_n1024", 3), ("deblur3d_n128", 6),
                                         ("varcoef4d_n128", 3)])
 def test_full_size_prefix_parity(P, name, iters):
@@ -106,5 +124,14 @@ def test_full_size_prefix_parity(P, name, iters):
     wl = W.workload(name)
     params = wl.params
     params.maxit = iters
+    x, rep, ref = _run(P, wl, params)
+    _check(x, rep, ref)
+
+
+def test_gmres_full_size_prefix_parity(P):
+    """Algorithm 1 on the convection-diffusion workload at full size (n = 256, 6 terms, cap 32):
+    the first iterations, every one orthogonalised against the whole basis."""
+    wl = W.workload("convdiff3d_n256")
+    params = W.SolverParams('gmres', 32, 0, 5, 8, 1e-6, seed=0)
     x, rep, ref = _run(P, wl, params)
     _check(x, rep, ref)
