@@ -63,3 +63,12 @@ def mln_recovery(sk: Sketch, psis: Sequence[np.ndarray]) -> Tucker:
         us.append(f[k] @ pinv_upper(rr))
         qs.append(q)
     return Tucker(multi_ttm(g_psi, [q.T for q in qs]), us)
+
+
+def mln_downsample(sk: Sketch, rt_sol: int, r_sol: int) -> Sketch:
+    """Memory-efficient truncation of a stored sketch (Section 3.3): the leading
+    rt_sol x ... x rt_sol block of G_Psi and the leading r_sol columns of every F_k.  Equal to
+    sketching with the leading rt_sol columns of each Psi_k from the start (the Khatri-Rao
+    column l of F_k uses column l of every other Psi_j)."""
+    g, f = sk
+    return g[(slice(0, rt_sol),) * g.ndim].copy(), [fk[:, :r_sol].copy() for fk in f]

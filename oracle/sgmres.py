@@ -27,7 +27,7 @@ import numpy as np
 
 from workloads import (STREAM_KRYLOV, STREAM_ROUNDSUM, Operator, SolverParams, Tucker,
                        sketch_matrix)
-from .mln import mln_diag, mln_recovery, mln_sketch, mln_sum
+from .mln import mln_diag, mln_downsample, mln_recovery, mln_sketch, mln_sum
 from .operators import apply_op
 from .rhosvd import effective_sketch_size, kron_sketch, roundsum
 from .tensor import inner, norm, scale
@@ -177,12 +177,21 @@ def rhosvd_gmres(op: Operator, b: Tucker, prm: SolverParams, transpose: bool = F
 
 def mln_sgmres(op: Operator, b: Tucker, prm: SolverParams, transpose: bool = False,
                maxit: Optional[int] = None) -> Result:
-    """Algorithm 6 (without the memory-saving truncation), r = rank_cap, r + p sketch columns."""
+    """Algorithm 6, r = rank_cap, r + p sketch columns.  With prm.r_sol > 0 (save_memory): once a
+    basis tensor leaves the window (iteration i > k_trunc drops V_{i - k_trunc}) its stored
+    sketch is cut to r_sol + p_sol (mln_downsample); at the end the sketches still in the
+    window are cut too, and the solution is recovered at rank r_sol with the leading
+    r_sol + p_sol columns of each Psi_k."""
     d, n = b.d, b.n
     r = prm.rank_cap
     rp = r + prm.oversample_p
     maxit = prm.maxit if maxit is None else maxit
     psis = [sketch_matrix(prm.seed, STREAM_KRYLOV, 0, k, n[k], rp) for k in range(d)]
+    save = prm.r_sol > 0
+    rt_sol = prm.r_sol + prm.p_sol
+    if save:
+        assert prm.r_sol <= r and rt_sol <= rp, "r_sol <= r and r_sol + p_sol <= r + p"
+    cut = {}
     beta = norm(b)
     v = [scale(b, 1.0 / beta)]
     sks = [mln_sketch(v[0], psis, r)]
@@ -211,10 +220,19 @@ def mln_sgmres(op: Operator, b: Tucker, prm: SolverParams, transpose: bool = Fal
             break
         v.append(scale(w, 1.0 / nw))
         sks.append(mln_sketch(v[-1], psis, r))
+        if save and i > prm.ktrunc:
+            sks[i - prm.ktrunc - 1] = mln_downsample(sks[i - prm.ktrunc - 1], rt_sol, prm.r_sol)
+            cut[i - prm.ktrunc - 1] = True
         if res / beta_s < prm.eta * prm.tol:
             status = CONVERGED
             break
-    x = mln_recovery(mln_sum([(float(y[m]), sks[m]) for m in range(i)]), psis)
+    if save:
+        for m in range(i):
+            if not cut.get(m, False):
+                sks[m] = mln_downsample(sks[m], rt_sol, prm.r_sol)
+        x = mln_recovery(mln_sum([(float(y[m]), sks[m]) for m in range(i)]), [ps[:, :rt_sol] for ps in psis])
+    else:
+        x = mln_recovery(mln_sum([(float(y[m]), sks[m]) for m in range(i)]), psis)
     return Result(x, i, status, hist, y, basis=v)
 
 

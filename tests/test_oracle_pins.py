@@ -534,3 +534,38 @@ def test_tucker_gmres_residuals_do_not_increase_and_beat_short_recurrence():
     for k in [3, 6, 10]:
         r2 = S.rhosvd_sgmres(op, b, prm2, maxit=k)
         assert hsts[k - 1] <= RS.true_residual(op, r2.x, b) * (1 + 1e-8)
+
+
+# ------------------------------------------------------------------------------ memory-efficient MLN
+def test_mln_downsample_equals_sketch_with_leading_columns():
+    """Cutting a stored sketch to (r_sol + p_sol, r_sol) equals sketching with the leading
+    r_sol + p_sol columns of every Psi_k and target rank r_sol (Section 3.3)."""
+    from oracle import mln as M
+    n = [9, 8, 7]
+    x = W.random_tucker(n, [3, 4, 2], 51)
+    rng = np.random.default_rng(52)
+    r, p, r_sol, p_sol = 5, 6, 3, 2
+    psis = [rng.standard_normal((nk, r + p)) for nk in n]
+    full = M.mln_downsample(M.mln_sketch(x, psis, r), r_sol + p_sol, r_sol)
+    small = M.mln_sketch(x, [ps[:, :r_sol + p_sol] for ps in psis], r_sol)
+    assert np.allclose(full[0], small[0], atol=1e-13)
+    for a, b in zip(full[1], small[1]):
+        assert np.allclose(a, b, atol=1e-13)
+
+
+def test_mln_save_memory_exact_for_low_rank_solution():
+    """A problem whose Krylov vectors stay within multilinear rank r_sol: the memory-efficient
+    variant returns the same solution as the full one (the cut sketches still determine the
+    rank-r_sol tensors exactly), with every stored sketch cut."""
+    n = 7
+    d0 = W.ModeMat('D', n, 0, 0, np.diag(np.linspace(1.0, 2.0, n)))
+    op = W.Operator(3, [n] * 3, [1.0], [[d0, W.identity(n), W.identity(n)]])
+    b = W.random_tucker([n] * 3, [1, 1, 1], 53)
+    prm_full = W.SolverParams('mln', 4, 0, 8, 6, 1e-12, ktrunc=2, seed=5)
+    prm_save = W.SolverParams('mln', 4, 0, 8, 6, 1e-12, ktrunc=2, seed=5, r_sol=3, p_sol=3)
+    a = S.mln_sgmres(op, b, prm_full)
+    s_ = S.mln_sgmres(op, b, prm_save)
+    assert a.iters == s_.iters and np.allclose(a.res_hist, s_.res_hist, rtol=1e-12)
+    xa, xs = T.full(a.x), T.full(s_.x)
+    assert np.linalg.norm(xa - xs) <= 1e-10 * np.linalg.norm(xa)
+    assert max(s_.x.r) <= 3

@@ -262,6 +262,8 @@ class SolverParams:
     round_tol: float = 1e-12
     seed: int = 0
     adaptive_rank: bool = False
+    r_sol: int = 0          # MLN memory-efficient variant (Section 3.3): solution rank r_sol,
+    p_sol: int = 0          # stored sketches cut to r_sol + p_sol (0: off)
 
 
 @dataclass
