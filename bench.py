@@ -444,6 +444,23 @@ def secondary(P, W, torch):
     entry["unpreconditioned"] = {"iters": rep.iters, "status": rep.status, "seconds": round(dt, 4),
                                  "true_rel_residual": P.tk_residual(dop, x, b)}
     out["poisson3d_point_n1000_expsum_q8"] = entry
+    # MLN-Tucker sGMRES, full vs memory-efficient sketches (Section 3.3, r_sol = p_sol = 12)
+    wl = W.workload("varcoef4d_n128")
+    dop = P.DeviceOperator(wl.op)
+    b = P.DeviceTucker.from_numpy(wl.b.core, wl.b.factors)
+    mem = {}
+    r, p, n, d = wl.params.rank_cap, wl.params.oversample_p, wl.b.n[0], wl.b.d
+    for label, rs, ps in [("full", 0, 0), ("save_memory r_sol=12 p_sol=12", 12, 12)]:
+        prm = copy.copy(wl.params)
+        prm.r_sol, prm.p_sol = rs, ps
+        opts = P.Options.from_params(prm)
+        P.tk_solve(dop, b, opts)
+        x, rep, dt = _timed_solve(P, torch, dop, b, opts)
+        side, cols = (r + p, r) if rs == 0 else (rs + ps, rs)
+        mem[label] = {"iters": rep.iters, "seconds": round(dt, 4), "iters_per_s": round(rep.iters / dt, 2),
+                      "stored_sketch_bytes_per_iteration": 8 * (side ** d + d * n * cols),
+                      "true_rel_residual": P.tk_residual(dop, x, b), "out_rank": rep.out_rank}
+    out["mln_memory_varcoef4d_n128"] = mem
     # Algorithm 1 (full Arnoldi) against Algorithm 2 (short recurrence), same RoundSum settings
     wl = W.workload("convdiff3d_n256")
     dop = P.DeviceOperator(wl.op)

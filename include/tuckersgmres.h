@@ -92,6 +92,10 @@ typedef struct {
     int32_t adaptive_rank;  /* RHOSVD: 1 = effective-rank sketch size (Section 3.1), 0 = r + p    */
     int32_t precision;      /* TK_FP64 or TK_MIXED                                                 */
     int32_t transpose;      /* 1 = solve the adjoint system L^T(X) = B                            */
+    int32_t mln_r_sol;      /* MLN memory-efficient variant (Section 3.3): 0 = off; else the     */
+    int32_t mln_p_sol;      /* solution rank r_sol <= rank_cap and p_sol, r_sol + p_sol <= r + p:  */
+                            /* stored sketches leaving the window are cut to r_sol + p_sol, the   */
+                            /* solution is recovered at rank r_sol (x_out zero-padded)            */
     int32_t reserved;
     double tol;             /* tolerance                                                           */
     double eta;             /* sketched correction factor: stop when res_k < eta * tol             */

@@ -223,12 +223,15 @@ class Options:
     adaptive_rank: bool = False
     precision: str = "fp64"          # 'fp64' or 'mixed'
     transpose: bool = False
+    r_sol: int = 0                   # MLN memory-efficient variant: solution rank (0: off)
+    p_sol: int = 0                   # ... and the stored sketches' extra columns
 
     @staticmethod
     def from_params(p, **over) -> "Options":
         o = Options(variant=p.variant, rank_cap=p.rank_cap, sketch_s=p.sketch_s,
                     oversample_p=p.oversample_p, ktrunc=p.ktrunc, maxit=p.maxit, tol=p.tol,
-                    eta=p.eta, round_tol=p.round_tol, seed=p.seed, adaptive_rank=p.adaptive_rank)
+                    eta=p.eta, round_tol=p.round_tol, seed=p.seed, adaptive_rank=p.adaptive_rank,
+                    r_sol=getattr(p, "r_sol", 0), p_sol=getattr(p, "p_sol", 0))
         for k, v in over.items():
             setattr(o, k, v)
         return o
@@ -240,6 +243,7 @@ class Options:
         s.ktrunc, s.maxit, s.adaptive_rank = self.ktrunc, self.maxit, int(self.adaptive_rank)
         s.precision = L.TK_MIXED if self.precision == "mixed" else L.TK_FP64
         s.transpose = int(self.transpose)
+        s.mln_r_sol, s.mln_p_sol = int(self.r_sol), int(self.p_sol)
         s.tol, s.eta, s.round_tol, s.seed = self.tol, self.eta, self.round_tol, self.seed
         return s
 

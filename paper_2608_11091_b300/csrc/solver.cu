@@ -409,8 +409,34 @@ static void solve_mln(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucker 
         v1.core = core;
         V.push_back(v1);
     }
-    std::vector<Sk> sks;
-    sks.push_back(alloc_sk(c, pb, r, rp));
+    // Stored sketches.  Default: every sketch kept at full size.  Memory-efficient variant
+    // (Section 3.3): full-size sketches live in a ring of ktrunc + 1 slots; the sketch of V_m is
+    // cut to (r_sol + p_sol)^d and n x r_sol just before its slot is reused (it has left the
+    // window by then), into a compact store.
+    const bool save = o.mln_r_sol > 0;
+    const int rs = o.mln_r_sol, rts = o.mln_r_sol + o.mln_p_sol, K = o.ktrunc;
+    if (save) TK_REQUIRE(rs <= r && o.mln_p_sol >= 0 && rts <= rp, "MLN: need r_sol <= r and r_sol + p_sol <= r + p");
+    std::vector<Sk> sks;                 // index m: sketch of V_{m+1} (full size, or its ring slot)
+    std::vector<Sk> ring;
+    std::vector<Sk> cut;                 // compact sketches (save), index m
+    std::vector<char> is_cut;
+    auto cut_sketch = [&](int m) {
+        Sk t{};
+        t.g = c.arena->alloc((size_t)std::llround(std::pow((double)rts, d)));
+        int rd[TK_MAX_D], rsrc[TK_MAX_D];
+        for (int k = 0; k < d; ++k) { rd[k] = rts; rsrc[k] = rp; }
+        copy_core_pad(c, t.g, rd, sks[m].g, rsrc, d);
+        for (int k = 0; k < d; ++k) {
+            t.F[k] = c.arena->alloc((size_t)pb.n[k] * rs);
+            copy(c, t.F[k], sks[m].F[k], (long long)pb.n[k] * rs);
+        }
+        if ((int)cut.size() <= m) { cut.resize(m + 1); is_cut.resize(m + 1, 0); }
+        cut[m] = t;
+        is_cut[m] = 1;
+    };
+    if (save)
+        for (int q = 0; q <= K; ++q) ring.push_back(alloc_sk(c, pb, r, rp));
+    sks.push_back(save ? ring[0] : alloc_sk(c, pb, r, rp));
     mln_sketch_sum(c, pb, {V[0]}, psi, r, p, sks[0].g, sks[0].F, 0.0);
     double *bs = c.arena->alloc(rp);
     superdiag(c, sks[0].g, rp, d, bs, 1.0, sc + SC_BETA);
@@ -433,7 +459,14 @@ static void solve_mln(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucker 
     int i = 0;
     for (i = 1; i <= kmax; ++i) {
         Slot vn = alloc_slot(c, pb, r);
-        Sk skn = alloc_sk(c, pb, r, rp);
+        Sk skn;
+        if (save) {
+            // the slot for the sketch of V_{i+1} holds that of V_{i-K}, outside every later window
+            if (i - K - 1 >= 0) cut_sketch(i - K - 1);
+            skn = ring[i % (K + 1)];
+        } else {
+            skn = alloc_sk(c, pb, r, rp);
+        }
         {
             ScopedMark it(*c.arena);
             std::vector<TTerm> terms = apply_operator(c, pb, op, V.back(), o.transpose);
@@ -484,6 +517,40 @@ static void solve_mln(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucker 
     }
     if (i > kmax) i = kmax;
     so.iters = i;
+    if (save) {
+        // X~ = MLN_Recovery(MLN_Sum(cut sketches 1..i, y)) at rank r_sol with the leading
+        // r_sol + p_sol columns of each Psi_k, zero-padded into x_out
+        for (int m = 0; m < i; ++m)
+            if ((int)is_cut.size() <= m || !is_cut[m]) cut_sketch(m);
+        const long long gs = (long long)std::llround(std::pow((double)rts, d));
+        Sk sol{};
+        sol.g = c.arena->alloc(gs);
+        for (int k = 0; k < d; ++k) sol.F[k] = c.arena->alloc((size_t)pb.n[k] * rs);
+        std::vector<const double *> xs, cd;
+        std::vector<double> cf;
+        for (int m = 0; m < i; ++m) { xs.push_back(cut[m].g); cf.push_back(1.0); cd.push_back(ls.y + m); }
+        axpy_list(c, sol.g, gs, 0.0, xs, cf, cd);
+        for (int k = 0; k < d; ++k) {
+            std::vector<const double *> fx;
+            for (int m = 0; m < i; ++m) fx.push_back(cut[m].F[k]);
+            axpy_list(c, sol.F[k], (long long)pb.n[k] * rs, 0.0, fx, cf, cd);
+        }
+        TOut tmp{};
+        long long cs = 1;
+        for (int k = 0; k < d; ++k) cs *= rs;
+        tmp.core = c.arena->alloc(cs);
+        for (int k = 0; k < d; ++k) tmp.f[k] = c.arena->alloc((size_t)pb.n[k] * rs);
+        tmp.rank_dev = nullptr;
+        mln_recovery(c, pb, sol.g, sol.F, psi, rs, o.mln_p_sol, tmp);
+        int rd[TK_MAX_D], rsrc[TK_MAX_D];
+        for (int k = 0; k < d; ++k) { rd[k] = r; rsrc[k] = rs; }
+        copy_core_pad(c, x->core, rd, tmp.core, rsrc, d);
+        for (int k = 0; k < d; ++k)
+            copy_pad(c, x->factor[k], pb.n[k], pb.n[k], r, tmp.f[k], pb.n[k], pb.n[k], rs);
+        TK_CUDA(cudaStreamSynchronize(c.st));
+        for (int k = 0; k < d; ++k) so.ranks[k] = rs;
+        return;
+    }
     // X~ = MLN_Recovery(MLN_Sum(sketches 1..i, y))
     Sk sol = alloc_sk(c, pb, r, rp);
     {

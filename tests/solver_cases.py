@@ -16,6 +16,11 @@ CASES = {
     "exhaustion_convdiff_n16": (lambda: W.convdiff3d(16, 5, None), W.SolverParams('rhosvd', 4, 10, 5, 40, 1e-14, seed=1), False),
     "point_source_n64": (lambda: W.poisson3d_point(64, None, 8, "p64"),
                          W.SolverParams('rhosvd', 32, 64, 5, 6, 1e-8, eta=0.4, ktrunc=1, seed=2), False),
+    # MLN memory-efficient variant (Section 3.3): stored sketches cut to r_sol + p_sol
+    "mln_save_varcoef4d_n16": (lambda: W.varcoef4d(16, 1, None),
+                               W.SolverParams('mln', 6, 0, 6, 10, 1e-8, seed=7, r_sol=4, p_sol=4), False),
+    "mln_save_convdiff_n40": (lambda: W.convdiff3d(40, 2, None),
+                              W.SolverParams('mln', 10, 0, 12, 16, 1e-8, ktrunc=3, seed=8, r_sol=8, p_sol=8), False),
     # Algorithm 1 (full Arnoldi through RoundSum)
     "gmres_poisson3d_n20_r12": (lambda: W.poisson3d(20, 1, 3, None, "p20"),
                                 W.SolverParams('gmres', 12, 0, 5, 30, 1e-9, seed=4), False),

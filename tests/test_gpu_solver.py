@@ -135,3 +135,16 @@ def test_gmres_full_size_prefix_parity(P):
     params = W.SolverParams('gmres', 32, 0, 5, 8, 1e-6, seed=0)
     x, rep, ref = _run(P, wl, params)
     _check(x, rep, ref)
+
+
+def test_mln_save_memory_full_size_prefix(P):
+    """The 4D variable-coefficient workload (n = 128, r = 24, p = 36) in the memory-efficient
+    form with r_sol = p_sol = 12 (the paper's p_sol = r_sol), first iterations at full size; the
+    stored sketches shrink from 60^4 to 24^4 and the workspace with them."""
+    wl = W.workload("varcoef4d_n128")
+    params = wl.params
+    params.maxit = 4
+    params.r_sol, params.p_sol = 12, 12
+    x, rep, ref = _run(P, wl, params)
+    _check(x, rep, ref)
+    assert rep.out_rank == [12, 12, 12, 12]
