@@ -54,6 +54,38 @@ def _ls(mcols: List[np.ndarray], bs: np.ndarray):
     return y, float(np.linalg.norm(m @ y - bs))
 
 
+GCV_POINTS = 121
+
+
+def gcv_grid(sigma_max: float) -> np.ndarray:
+    """The lambda values GCV chooses from (reading: the paper does not state the search):
+    sigma_max 10^(-12 + 12 g / 120), g = 0 .. 120."""
+    return sigma_max * 10.0 ** (-12.0 + 12.0 * np.arange(GCV_POINTS) / (GCV_POINTS - 1))
+
+
+def gcv_function(sig: np.ndarray, bhat: np.ndarray, rho2: float, m: int, lam: float) -> float:
+    """GCV (Golub, Heath, Wahba 1979) of the Tikhonov problem min ||M y - b||^2 + lam^2 ||y||^2
+    from the SVD of M (singular values sig, bhat = U^T b, rho2 = ||b||^2 - ||bhat||^2):
+    ||(I - A_lam) b||^2 / trace(I - A_lam)^2, A_lam = M (M^T M + lam^2 I)^-1 M^T, m rows."""
+    f = sig ** 2 / (sig ** 2 + lam ** 2)
+    num = float(np.sum(((1.0 - f) * bhat) ** 2) + rho2)
+    return num / (m - float(np.sum(f))) ** 2
+
+
+def ls_tikhonov(m_mat: np.ndarray, b: np.ndarray):
+    """Projected Tikhonov step (Section 4.3, Eq. for the sketched / Hessenberg problem): lambda by
+    GCV over gcv_grid (ties: the smaller lambda), then y = V diag(sig / (sig^2 + lam^2)) U^T b.
+    Returns y, ||M y - b||, lambda."""
+    u, sig, vt = np.linalg.svd(m_mat, full_matrices=False)
+    bhat = u.T @ b
+    rho2 = max(float(b @ b - bhat @ bhat), 0.0)
+    grid = gcv_grid(float(sig[0]) if sig.size else 0.0)
+    vals = [gcv_function(sig, bhat, rho2, m_mat.shape[0], lam) for lam in grid]
+    lam = float(grid[int(np.argmin(vals))])
+    y = vt.T @ (sig / (sig ** 2 + lam ** 2) * bhat)
+    return y, float(np.linalg.norm(m_mat @ y - b)), lam
+
+
 def rhosvd_sgmres(op: Operator, b: Tucker, prm: SolverParams, transpose: bool = False,
                   bf16_sketch: bool = False, maxit: Optional[int] = None,
                   precond: Optional[Operator] = None) -> Result:
@@ -107,7 +139,10 @@ def rhosvd_sgmres(op: Operator, b: Tucker, prm: SolverParams, transpose: bool = 
         hs = [inner(v[j - 1], w) for j in window]
         w = rs([(1.0, w)] + [(-h, v[j - 1]) for h, j in zip(hs, window)])
         nw = norm(w)
-        y, res = _ls(mcols, bs)
+        if prm.tikhonov:
+            y, res, _ = ls_tikhonov(np.stack(mcols, axis=1), bs)
+        else:
+            y, res = _ls(mcols, bs)
         hist.append(res / beta_s)
         if nw <= 1e-14 * w0:
             status = BREAKDOWN
@@ -160,8 +195,12 @@ def rhosvd_gmres(op: Operator, b: Tucker, prm: SolverParams, transpose: bool = F
         h[k, k - 1] = nw
         rhs = np.zeros(k + 1)
         rhs[0] = beta
-        y = np.linalg.lstsq(h[:k + 1, :k], rhs, rcond=None)[0]
-        res = float(np.linalg.norm(rhs - h[:k + 1, :k] @ y)) / beta
+        if prm.tikhonov:
+            y, res, _ = ls_tikhonov(h[:k + 1, :k], rhs)
+            res /= beta
+        else:
+            y = np.linalg.lstsq(h[:k + 1, :k], rhs, rcond=None)[0]
+            res = float(np.linalg.norm(rhs - h[:k + 1, :k] @ y)) / beta
         hist.append(res)
         if nw <= 1e-14 * w0:
             status = BREAKDOWN
@@ -213,7 +252,10 @@ def mln_sgmres(op: Operator, b: Tucker, prm: SolverParams, transpose: bool = Fal
         gw = mln_sum([(1.0, gw)] + [(-h, sks[j - 1]) for h, j in zip(hs, window)])
         w = mln_recovery(gw, psis)
         nw = norm(w)
-        y, res = _ls(mcols, bs)
+        if prm.tikhonov:
+            y, res, _ = ls_tikhonov(np.stack(mcols, axis=1), bs)
+        else:
+            y, res = _ls(mcols, bs)
         hist.append(res / beta_s)
         if nw <= 1e-14 * w0:
             status = BREAKDOWN

@@ -569,3 +569,59 @@ def test_mln_save_memory_exact_for_low_rank_solution():
     xa, xs = T.full(a.x), T.full(s_.x)
     assert np.linalg.norm(xa - xs) <= 1e-10 * np.linalg.norm(xa)
     assert max(s_.x.r) <= 3
+
+
+# ------------------------------------------------------------------------------ Tikhonov + GCV
+def test_gcv_function_matches_influence_matrix_definition():
+    """The SVD form of the GCV function equals its definition with the explicit influence
+    matrix A = M (M^T M + lam^2 I)^-1 M^T (dense), at several lambda."""
+    rng = np.random.default_rng(61)
+    m_mat = rng.standard_normal((40, 9)) @ np.diag(10.0 ** -np.arange(9))
+    b = rng.standard_normal(40)
+    u, sig, vt = np.linalg.svd(m_mat, full_matrices=False)
+    bhat = u.T @ b
+    rho2 = b @ b - bhat @ bhat
+    for lam in [1e-6, 1e-3, 1e-1, 1.0]:
+        a = m_mat @ np.linalg.solve(m_mat.T @ m_mat + lam ** 2 * np.eye(9), m_mat.T)
+        r = b - a @ b
+        ref = (r @ r) / np.trace(np.eye(40) - a) ** 2
+        assert np.isclose(S.gcv_function(sig, bhat, rho2, 40, lam), ref, rtol=1e-8)
+
+
+def test_tikhonov_solution_is_the_augmented_least_squares_solution():
+    """y_lambda solves min ||[M; lambda I] y - [b; 0]|| (the normal equations of the penalised
+    problem), and the chosen lambda minimises GCV over the grid."""
+    rng = np.random.default_rng(62)
+    m_mat = rng.standard_normal((30, 8)) @ np.diag(10.0 ** -(0.5 * np.arange(8)))
+    b = m_mat @ rng.standard_normal(8) + 1e-3 * rng.standard_normal(30)
+    y, res, lam = S.ls_tikhonov(m_mat, b)
+    aug = np.vstack([m_mat, lam * np.eye(8)])
+    ref = np.linalg.lstsq(aug, np.concatenate([b, np.zeros(8)]), rcond=None)[0]
+    assert np.allclose(y, ref, rtol=1e-9, atol=1e-12)
+    assert np.isclose(res, np.linalg.norm(m_mat @ y - b), rtol=1e-12)
+    u, sig, vt = np.linalg.svd(m_mat, full_matrices=False)
+    bhat = u.T @ b
+    vals = [S.gcv_function(sig, bhat, b @ b - bhat @ bhat, 30, l) for l in S.gcv_grid(sig[0])]
+    assert np.isclose(S.gcv_function(sig, bhat, b @ b - bhat @ bhat, 30, lam), min(vals))
+    assert 0 < lam < sig[0]
+
+
+def test_tikhonov_gcv_regularises_a_noisy_ill_posed_solve():
+    """Noisy deblurring (n = 12): with GCV-Tikhonov in the least-squares step the error to the
+    true solution after many iterations stays near its best value, while the unregularised
+    iteration drifts away (semi-convergence)."""
+    n = 12
+    wl = W.deblur3d(n, 0, None, lam=1e-4, x_rank=2)
+    rng = np.random.default_rng(63)
+    bf = T.full(wl.b)
+    bf = bf + 0.02 * np.linalg.norm(bf) / np.sqrt(bf.size) * rng.standard_normal(bf.shape)
+    core = bf.copy()
+    facs = [np.eye(n) for _ in range(3)]
+    b = W.Tucker(core, facs)
+    xt = T.full(wl.x_true)
+    errs = {}
+    for tik in [False, True]:
+        prm = W.SolverParams('gmres', n, 0, 5, 30, 1e-14, round_tol=1e-15, seed=1, tikhonov=tik)
+        res = S.rhosvd_gmres(wl.op, b, prm)
+        errs[tik] = np.linalg.norm(T.full(res.x) - xt) / np.linalg.norm(xt)
+    assert errs[True] < 0.5 * errs[False]

@@ -264,6 +264,7 @@ class SolverParams:
     adaptive_rank: bool = False
     r_sol: int = 0          # MLN memory-efficient variant (Section 3.3): solution rank r_sol,
     p_sol: int = 0          # stored sketches cut to r_sol + p_sol (0: off)
+    tikhonov: bool = False  # projected Tikhonov with the GCV parameter in every least-squares step
 
 
 @dataclass
