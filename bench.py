@@ -444,6 +444,24 @@ def secondary(P, W, torch):
     entry["unpreconditioned"] = {"iters": rep.iters, "status": rep.status, "seconds": round(dt, 4),
                                  "true_rel_residual": P.tk_residual(dop, x, b)}
     out["poisson3d_point_n1000_expsum_q8"] = entry
+    # noisy deblurring (2% noise), relative reconstruction error with and without projected
+    # Tikhonov + GCV in the least-squares step (Section 4.3)
+    wl = W.deblur3d_noisy(64, 0, None)
+    dop = P.DeviceOperator(wl.op)
+    b = P.DeviceTucker.from_numpy(wl.b.core, wl.b.factors)
+    xt = P.DeviceTucker.from_numpy(wl.x_true.core, wl.x_true.factors)
+    xt_norm = P.tk_sum_norm([xt], [1.0])
+    reg = {}
+    for label, prm in [("sgmres", W.SolverParams('rhosvd', 32, 128, 5, 60, 1e-12, seed=0)),
+                       ("sgmres+tikhonov_gcv", W.SolverParams('rhosvd', 32, 128, 5, 60, 1e-12, seed=0, tikhonov=True)),
+                       ("gmres", W.SolverParams('gmres', 32, 0, 5, 40, 1e-12, seed=0)),
+                       ("gmres+tikhonov_gcv", W.SolverParams('gmres', 32, 0, 5, 40, 1e-12, seed=0, tikhonov=True))]:
+        opts = P.Options.from_params(prm)
+        P.tk_solve(dop, b, opts)
+        x, rep, dt = _timed_solve(P, torch, dop, b, opts)
+        reg[label] = {"iters": rep.iters, "seconds": round(dt, 4),
+                      "rel_reconstruction_error": P.tk_sum_norm([x, xt], [1.0, -1.0]) / xt_norm}
+    out["regularisation_deblur3d_noisy_n64"] = reg
     # MLN-Tucker sGMRES, full vs memory-efficient sketches (Section 3.3, r_sol = p_sol = 12)
     wl = W.workload("varcoef4d_n128")
     dop = P.DeviceOperator(wl.op)

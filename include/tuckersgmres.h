@@ -96,7 +96,9 @@ typedef struct {
     int32_t mln_p_sol;      /* solution rank r_sol <= rank_cap and p_sol, r_sol + p_sol <= r + p:  */
                             /* stored sketches leaving the window are cut to r_sol + p_sol, the   */
                             /* solution is recovered at rank r_sol (x_out zero-padded)            */
-    int32_t reserved;
+    int32_t gcv_tikhonov;   /* 1: projected Tikhonov in every least-squares step, the parameter    */
+                            /* chosen by GCV over sigma_max 10^(-12+12g/120), g = 0..120          */
+                            /* (Section 4.3); needs at most 96 iterations                          */
     double tol;             /* tolerance                                                           */
     double eta;             /* sketched correction factor: stop when res_k < eta * tol             */
     double round_tol;       /* ST-HOSVD tolerance epsilon (RoundSum)                               */

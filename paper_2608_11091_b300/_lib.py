@@ -49,7 +49,7 @@ class tk_opts(ctypes.Structure):
                 ("ktrunc", ctypes.c_int32), ("maxit", ctypes.c_int32),
                 ("adaptive_rank", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("transpose", ctypes.c_int32), ("mln_r_sol", ctypes.c_int32),
-                ("mln_p_sol", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("mln_p_sol", ctypes.c_int32), ("gcv_tikhonov", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("eta", ctypes.c_double),
                 ("round_tol", ctypes.c_double), ("seed", ctypes.c_uint64)]
 

@@ -225,13 +225,15 @@ class Options:
     transpose: bool = False
     r_sol: int = 0                   # MLN memory-efficient variant: solution rank (0: off)
     p_sol: int = 0                   # ... and the stored sketches' extra columns
+    tikhonov: bool = False           # projected Tikhonov with the GCV parameter (Section 4.3)
 
     @staticmethod
     def from_params(p, **over) -> "Options":
         o = Options(variant=p.variant, rank_cap=p.rank_cap, sketch_s=p.sketch_s,
                     oversample_p=p.oversample_p, ktrunc=p.ktrunc, maxit=p.maxit, tol=p.tol,
                     eta=p.eta, round_tol=p.round_tol, seed=p.seed, adaptive_rank=p.adaptive_rank,
-                    r_sol=getattr(p, "r_sol", 0), p_sol=getattr(p, "p_sol", 0))
+                    r_sol=getattr(p, "r_sol", 0), p_sol=getattr(p, "p_sol", 0),
+                    tikhonov=bool(getattr(p, "tikhonov", False)))
         for k, v in over.items():
             setattr(o, k, v)
         return o
@@ -244,6 +246,7 @@ class Options:
         s.precision = L.TK_MIXED if self.precision == "mixed" else L.TK_FP64
         s.transpose = int(self.transpose)
         s.mln_r_sol, s.mln_p_sol = int(self.r_sol), int(self.p_sol)
+        s.gcv_tikhonov = int(self.tikhonov)
         s.tol, s.eta, s.round_tol, s.seed = self.tol, self.eta, self.round_tol, self.seed
         return s
 

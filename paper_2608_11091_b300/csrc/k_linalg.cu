@@ -747,6 +747,49 @@ __device__ int jacobi64(double *A, double *V, double *nrm2, int s, double tol, d
     return steps;
 }
 
+// One step of the polar iteration with its second-order term: X = Y (I + E)^(-1/2) ~
+// Y (I - E / 2 + 3 E^2 / 8) with Y = double(V32), E = Y^T Y - I (|E| ~ s 2^-24 for an FP32
+// product of rotations, so the E^3 term is below FP64 rounding; E^2 in FP32).  Y, Z: s x s FP64
+// scratch; X receives the result and may hold V32 itself (V32 is copied out before X is used
+// for the FP32 copies of E and E^2).
+__device__ void polar_step(const float *V32, double *X, double *Y, double *Z, int s) {
+    const int tid = threadIdx.x, nt = blockDim.x, ss = s * s;
+    for (int e = tid; e < ss; e += nt) Y[e] = (double)V32[e];
+    __syncthreads();
+    float *ef = reinterpret_cast<float *>(X), *e2f = ef + ss;
+    for (int e = tid; e < ss; e += nt) {
+        const int i = e % s, j = e / s;
+        if (i > j) continue;
+        double t = 0.0;
+        for (int k = 0; k < s; ++k) t = fma(Y[k + i * s], Y[k + j * s], t);
+        const double ev = t - ((i == j) ? 1.0 : 0.0);
+        Z[i + j * s] = ev;
+        Z[j + i * s] = ev;
+        ef[i + j * s] = (float)ev;
+        ef[j + i * s] = (float)ev;
+    }
+    __syncthreads();
+    for (int e = tid; e < ss; e += nt) {
+        const int i = e % s, j = e / s;
+        float acc = 0.f;
+        for (int k = 0; k < s; ++k) acc = fmaf(ef[i + k * s], ef[k + j * s], acc);
+        e2f[e] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < ss; e += nt) {
+        const int i = e % s, j = e / s;
+        Z[e] = ((i == j) ? 1.0 : 0.0) - 0.5 * Z[e] + 0.375 * (double)e2f[e];
+    }
+    __syncthreads();
+    for (int e = tid; e < ss; e += nt) {
+        const int i = e % s, j = e / s;
+        double t = 0.0;
+        for (int k = 0; k < s; ++k) t = fma(Y[i + k * s], Z[k + j * s], t);
+        X[e] = t;   // X's FP32 contents were last read before the previous barrier
+    }
+    __syncthreads();
+}
+
 // SVD of a small square matrix R (upper triangle read) to FP64 accuracy.  Two modes:
 //
 // ST-HOSVD (J.perm set): R comes from the column-pivoted QR C^T P = Q R of a core unfolding;
@@ -807,46 +850,8 @@ __global__ void __launch_bounds__(1024) k_svd(const __grid_constant__ SVDJobs jo
     const int n32 = jacobi32(A32, V32, nrm32, s, 8.0f * sqrtf((float)s) * 0x1p-24f,
                              graded ? 0x1p-100f : fro * 0x1p-40f, 20, &flag);
     if (tid == 0) g_svd_sweeps[2 * blockIdx.x] = n32;
-    // phase 2: V = double(V32) into Y, orthonormalised by one step of the polar iteration with
-    // its second-order term: V = Y (I + E)^(-1/2) ~ Y (I - E / 2 + 3 E^2 / 8), E = Y^T Y - I
-    // (|E| ~ s 2^-24, so the E^3 term is below FP64 rounding; E^2 in FP32).  E (symmetric)
-    // into Z, FP32 copies of E and E^2 into X, Z <- I - E / 2 + 3 E^2 / 8, X = Y Z.
-    for (int e = tid; e < ss; e += nt) Y[e] = (double)V32[e];
-    __syncthreads();
-    {
-        float *ef = reinterpret_cast<float *>(X), *e2f = ef + ss;
-        for (int e = tid; e < ss; e += nt) {
-            const int i = e % s, j = e / s;
-            if (i > j) continue;
-            double t = 0.0;
-            for (int k = 0; k < s; ++k) t = fma(Y[k + i * s], Y[k + j * s], t);
-            const double ev = t - ((i == j) ? 1.0 : 0.0);
-            Z[i + j * s] = ev;
-            Z[j + i * s] = ev;
-            ef[i + j * s] = (float)ev;
-            ef[j + i * s] = (float)ev;
-        }
-        __syncthreads();
-        for (int e = tid; e < ss; e += nt) {
-            const int i = e % s, j = e / s;
-            float acc = 0.f;
-            for (int k = 0; k < s; ++k) acc = fmaf(ef[i + k * s], ef[k + j * s], acc);
-            e2f[e] = acc;
-        }
-        __syncthreads();
-        for (int e = tid; e < ss; e += nt) {
-            const int i = e % s, j = e / s;
-            Z[e] = ((i == j) ? 1.0 : 0.0) - 0.5 * Z[e] + 0.375 * (double)e2f[e];
-        }
-        __syncthreads();
-        for (int e = tid; e < ss; e += nt) {
-            const int i = e % s, j = e / s;
-            double t = 0.0;
-            for (int k = 0; k < s; ++k) t = fma(Y[i + k * s], Z[k + j * s], t);
-            X[e] = t;   // X's FP32 contents were last read before the previous barrier
-        }
-        __syncthreads();
-    }
+    // phase 2: V = double(V32), orthonormalised (polar step) into X
+    polar_step(V32, X, Y, Z, s);
     // phase 3: A = B V into Y (B triangular: R^T lower, R upper)
     for (int e = tid; e < ss; e += nt) {
         const int i = e % s, j = e / s;
@@ -969,6 +974,133 @@ __global__ void __launch_bounds__(1024) k_svd(const __grid_constant__ SVDJobs jo
             P[i + (long long)jj * s] = t;
         }
     }
+}
+
+// Projected Tikhonov with the GCV parameter (Section 4.3) on the least-squares state of k_ls:
+// M = Q R (R k x k upper triangle of st.H, ld ldr), Q^T b = st.qtb, rho = ||tail of Q^T b|| =
+// *st.res.  SVD of R (the same FP32 sweeps, polar step and FP64 sweeps as k_svd, V kept):
+// A = R V has columns sigma_j u_j, so t_j = a_j^T c = sigma_j (U^T b)_j.  GCV over
+// lambda_g = sigma_max 10^(-12 + 12 g / 120), g = 0..120 (Golub, Heath and Wahba):
+//   G(lambda) = [sum_j (lambda^2 t_j / (sigma_j (sigma_j^2 + lambda^2)))^2 + rho^2]
+//               / (m - sum_j sigma_j^2 / (sigma_j^2 + lambda^2))^2,
+// smallest value (ties: the smaller lambda).  Then y = V diag(1 / (sigma^2 + lambda^2)) t
+// overwrites st.y and ||M y - b|| = (||R y - c||^2 + rho^2)^(1/2) overwrites *st.res.
+constexpr int GCV_POINTS = 121;
+__global__ void __launch_bounds__(1024) k_tikhonov(LSState st, int ldr, int k, int m, double *lambda_out) {
+    extern __shared__ double sm[];
+    const int s = k, ss = s * s;
+    double *X = sm, *Y = sm + ss, *Z = sm + 2 * ss;
+    __shared__ double sig[SVD_MAXS], tv[SVD_MAXS], cvec[SVD_MAXS], yv[SVD_MAXS];
+    __shared__ double gval[GCV_POINTS];
+    __shared__ double nrm64[SVD_MAXS];
+    __shared__ float nrm32[SVD_MAXS];
+    __shared__ double gpart[JNP * (SVD_MAXS / 2 + 1)];
+    __shared__ double cpar[SVD_MAXS / 2 + 1], spar[SVD_MAXS / 2 + 1];
+    __shared__ int act[SVD_MAXS / 2 + 1];
+    __shared__ int flag;
+    __shared__ float fscr[40];
+    __shared__ int iscr[40];
+    __shared__ double scr[40];
+    __shared__ double lam_s, rho2_s;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    auto Rat = [&](int i, int c) -> double { return i <= c ? st.H[i + (long long)c * ldr] : 0.0; };
+    if (tid == 0) { const double r = *st.res; rho2_s = r * r; }
+    for (int i = tid; i < s; i += nt) cvec[i] = st.qtb[i];
+    // SVD of R: scaled FP32 sweeps with V, polar step, A = R V, FP64 sweeps with V
+    int emax = 0;
+    for (int e = tid; e < ss; e += nt) emax = max(emax, (__double2hiint(Rat(e % s, e / s)) >> 20) & 0x7ff);
+    emax = min(block_max_i(emax, iscr), 2044);
+    const double inv = __hiloint2double((2045 - emax) << 20, 0);
+    const double mx = __hiloint2double((emax + 1) << 20, 0);
+    float *A32 = reinterpret_cast<float *>(X), *V32 = A32 + ss;
+    for (int e = tid; e < ss; e += nt) {
+        A32[e] = (float)(Rat(e % s, e / s) * inv);
+        V32[e] = (e % s == e / s) ? 1.f : 0.f;
+    }
+    float frop = 0.f;
+    for (int e = tid; e < ss; e += nt) frop = fmaf(A32[e], A32[e], frop);
+    __syncthreads();
+    const float fro = block_sum_f(frop, fscr);
+    jacobi32(A32, V32, nrm32, s, 8.0f * sqrtf((float)s) * 0x1p-24f, fro * 0x1p-40f, 20, &flag);
+    polar_step(V32, X, Y, Z, s);
+    for (int e = tid; e < ss; e += nt) {
+        const int i = e % s, j = e / s;
+        double t = 0.0;
+        for (int kk = i; kk < s; ++kk) t = fma(Rat(i, kk), X[kk + j * s], t);
+        Y[e] = t;
+    }
+    __syncthreads();
+    const double fro_r = (double)fro * mx * mx;
+    const double floor2 = fro_r * (double)s * s * 0x1p-106;
+    int nsw = 0;
+    jacobi64<true>(Y, X, nrm64, s, 4.0 * sqrt((double)s) * 0x1p-53, floor2, 16, &flag, gpart, cpar, spar, act,
+                   Z, nullptr, nullptr, &nsw);
+    // singular values, t_j = a_j^T c
+    for (int j = tid; j < s; j += nt) {
+        sig[j] = sqrt(nrm64[j]);
+        double t = 0.0;
+        for (int i = 0; i < s; ++i) t = fma(Y[i + j * s], cvec[i], t);
+        tv[j] = t;
+    }
+    __syncthreads();
+    double smax = 0.0;
+    for (int j = 0; j < s; ++j) smax = fmax(smax, sig[j]);
+    const double rho2 = rho2_s;
+    for (int g = tid; g < GCV_POINTS; g += nt) {
+        const double lam = smax * pow(10.0, -12.0 + 12.0 * g / (GCV_POINTS - 1));
+        const double l2 = lam * lam;
+        double num = rho2, tr = (double)m;
+        for (int j = 0; j < s; ++j) {
+            const double s2 = sig[j] * sig[j], den = s2 + l2;
+            if (sig[j] > 0.0) {
+                const double q = l2 * tv[j] / (sig[j] * den);
+                num = fma(q, q, num);
+                tr -= s2 / den;
+            }
+        }
+        gval[g] = num / (tr * tr);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int best = 0;
+        for (int g = 1; g < GCV_POINTS; ++g)
+            if (gval[g] < gval[best]) best = g;
+        lam_s = smax * pow(10.0, -12.0 + 12.0 * best / (GCV_POINTS - 1));
+        if (lambda_out) *lambda_out = lam_s;
+    }
+    __syncthreads();
+    const double l2 = lam_s * lam_s;
+    for (int i = tid; i < s; i += nt) {
+        double t = 0.0;
+        for (int j = 0; j < s; ++j) {
+            const double den = sig[j] * sig[j] + l2;
+            if (den > 0.0) t = fma(X[i + j * s], tv[j] / den, t);
+        }
+        yv[i] = t;
+        st.y[i] = t;
+    }
+    __syncthreads();
+    double r2 = 0.0;
+    for (int i = tid; i < s; i += nt) {
+        double t = -cvec[i];
+        for (int l = i; l < s; ++l) t = fma(Rat(i, l), yv[l], t);
+        r2 = fma(t, t, r2);
+    }
+    r2 = block_sum(r2, scr);
+    if (tid == 0) *st.res = sqrt(r2 + rho2);
+}
+
+void tikhonov_gcv(Ctx &c, const LSState &st, int ldr, int k, int m, double *lambda_out) {
+    TK_REQUIRE(k >= 1 && k <= SVD_MAXS, "Tikhonov/GCV: at most 96 least-squares columns");
+    static bool attr_set = false;
+    if (!attr_set) {
+        TK_CUDA(cudaFuncSetAttribute(k_tikhonov, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     3 * SVD_MAXS * SVD_MAXS * (int)sizeof(double)));
+        attr_set = true;
+    }
+    c.pre_launch();
+    k_tikhonov<<<1, 1024, 3 * (size_t)k * k * sizeof(double), c.st>>>(st, ldr, k, m, lambda_out);
+    c.check_launch("tikhonov", 12.0 * k * (double)k * k);
 }
 
 static void svd_launch(Ctx &c, SVDJobs &J, int smax) {

@@ -209,6 +209,7 @@ static void solve_rhosvd(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tuck
             dot(c, vn.core, vn.core, csz, sc + SC_NWSQ);
             sqrt_scalar(c, sc + SC_NWSQ, sc + SC_NW);
             ls_update(c, M, bs, s, k - 1, k, ls, k == 1);
+            if (o.gcv_tikhonov) tikhonov_gcv(c, ls, s, k, s, nullptr);
             scale_by(c, vn.core, vn.core, csz, sc + SC_NW, 1);
             readback(c, pinned, sc, 8);
         }
@@ -318,6 +319,7 @@ static void solve_gmres(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucke
             sqrt_scalar(c, sc + SC_NWSQ, sc + SC_NW);
             copy(c, hcol + k, sc + SC_NW, 1);                      // h_{k+1,k} = ||W||
             ls_update(c, H, e1, ld, k - 1, k, ls, k == 1);
+            if (o.gcv_tikhonov) tikhonov_gcv(c, ls, ld, k, k + 1, nullptr);
             scale_by(c, vn.core, vn.core, csz, sc + SC_NW, 1);
             readback(c, pinned, sc, 8);
         }
@@ -496,6 +498,7 @@ static void solve_mln(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucker 
             inner_batch(c, pb, {InnerJob{Wn, Wn, sc + SC_NWSQ}});
             sqrt_scalar(c, sc + SC_NWSQ, sc + SC_NW);
             ls_update(c, M, bs, rp, i - 1, i, ls, i == 1);
+            if (o.gcv_tikhonov) tikhonov_gcv(c, ls, rp, i, rp, nullptr);
             scale_by(c, vn.core, vn.core, csz, sc + SC_NW, 1);
             mln_sketch_sum(c, pb, {Wn}, psi, r, p, skn.g, skn.F, 0.0);
             readback(c, pinned, sc, 8);
@@ -840,6 +843,8 @@ static int solve_entry(tk_handle *h, const tk_operator *op, const tk_operator *p
         TK_REQUIRE(o.rank_cap >= 1 && o.oversample_p >= 0 && o.maxit >= 1, "bad rank_cap / p / maxit");
         TK_REQUIRE(o.precision == TK_FP64 || o.precision == TK_MIXED, "bad precision");
         TK_REQUIRE(o.adaptive_rank == 0, "adaptive sketch size is not available in this build");
+        TK_REQUIRE(o.gcv_tikhonov == 0 || o.gcv_tikhonov == 1, "gcv_tikhonov must be 0 or 1");
+        TK_REQUIRE(!o.gcv_tikhonov || o.maxit <= 96, "Tikhonov/GCV: maxit must be <= 96");
         TK_REQUIRE(o.tol > 0.0 && o.eta > 0.0 && o.round_tol >= 0.0, "bad tolerances");
         if (o.variant == TK_RHOSVD_SGMRES) TK_REQUIRE(o.sketch_s >= 2 && o.sketch_s <= 4096, "sketch_s must be 2..4096");
         Ctx c = make_ctx(h, stream);

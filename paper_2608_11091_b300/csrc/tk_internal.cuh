@@ -203,6 +203,9 @@ struct LSState {
 // Processes columns [c0, k) of M (s x k, lda = s) and solves for y_k.
 void ls_update(Ctx &c, const double *M, const double *b, int s, int c0, int k, const LSState &st,
                int init_qtb);
+// Projected Tikhonov with the GCV-chosen parameter on the current least-squares state (k columns,
+// R in st.H with leading dimension ldr, m rows of the problem): overwrites st.y and *st.res.
+void tikhonov_gcv(Ctx &c, const LSState &st, int ldr, int k, int m, double *lambda_out);
 
 // ------------------------------------------------------------------------------------------
 // Elementwise / structured kernels

@@ -21,6 +21,13 @@ CASES = {
                                W.SolverParams('mln', 6, 0, 6, 10, 1e-8, seed=7, r_sol=4, p_sol=4), False),
     "mln_save_convdiff_n40": (lambda: W.convdiff3d(40, 2, None),
                               W.SolverParams('mln', 10, 0, 12, 16, 1e-8, ktrunc=3, seed=8, r_sol=8, p_sol=8), False),
+    # projected Tikhonov with the GCV parameter (Section 4.3), noisy deblurring
+    "tik_sgmres_deblur_n24": (lambda: W.deblur3d_noisy(24, 3, None),
+                              W.SolverParams('rhosvd', 12, 64, 5, 20, 1e-8, seed=3, tikhonov=True), False),
+    "tik_gmres_deblur_n16": (lambda: W.deblur3d_noisy(16, 4, None),
+                             W.SolverParams('gmres', 10, 0, 5, 15, 1e-8, seed=4, tikhonov=True), False),
+    "tik_mln_deblur_n16": (lambda: W.deblur3d_noisy(16, 5, None),
+                           W.SolverParams('mln', 8, 0, 16, 12, 1e-8, seed=5, tikhonov=True), False),
     # Algorithm 1 (full Arnoldi through RoundSum)
     "gmres_poisson3d_n20_r12": (lambda: W.poisson3d(20, 1, 3, None, "p20"),
                                 W.SolverParams('gmres', 12, 0, 5, 30, 1e-9, seed=4), False),
