@@ -18,6 +18,7 @@ seeds); there is no data-path collective.
 from __future__ import annotations
 
 import argparse
+import copy
 import json
 import os
 import statistics
