@@ -342,10 +342,12 @@ def time_to_tol(P, W, torch, tol=1e-6):
     """Time to true relative residual <= tol, FP64 vs mixed, on the problems that reach it at
     these ranks: Poisson with the exponential-sum preconditioner (Section 3.4), the paper's
     point-source setting at n = 1000 and the rank-1 Poisson workload at n = 32.  Forward: the
-    preconditioned solve.  Adjoint: the gradient of 0.5 ||x - x_ref||^2 w.r.t. the operator
-    coefficients and b (x_ref = ||x|| / 2 times the unit tensor (1/sqrt(n))^(x)3, a smooth target,
-    so the adjoint right-hand side x - x_ref is as smooth as x): one transposed preconditioned solve
-    to the same tolerance plus the adjoint contractions.  Wall time, device synchronised."""
+    preconditioned solve.  Adjoint: the gradient of the quantity of interest l = <w, x>
+    (w = the unit tensor (1/sqrt(n))^(x)3, smooth and rank 1) w.r.t. the operator coefficients
+    and b: one transposed preconditioned solve L^T mu = w to the same tolerance plus the adjoint
+    contractions.  (A loss like 0.5 ||x - x_ref||^2 has the adjoint right-hand side x - x_ref, whose
+    rank is already at the cap, so its adjoint solution cannot be represented to 1e-6.)  Wall time,
+    device synchronised."""
     import copy
     res = {}
     cases = [("poisson3d_point_n1000_q8", W.workload("poisson3d_point_n1000"), 8),
@@ -359,11 +361,9 @@ def time_to_tol(P, W, torch, tol=1e-6):
         dop = P.DeviceOperator(wl.op)
         b = P.DeviceTucker.from_numpy(wl.b.core, wl.b.factors)
         pc = P.tk_expsum_laplacian(n, wl.b.d, q)
-        x0, _ = P.tk_solve_precond(dop, pc, b, P.Options.from_params(prm))
-        xnorm = P.tk_sum_norm([x0], [1.0])
         import numpy as np
         unit = np.ones((n, 1)) / np.sqrt(n)
-        xr = P.DeviceTucker.from_numpy(np.full((1,) * wl.b.d, 0.5 * xnorm), [unit] * wl.b.d)
+        wq = P.DeviceTucker.from_numpy(np.ones((1,) * wl.b.d), [unit] * wl.b.d)
         entry = {}
         for form in ["fp64", "mixed"]:
             opts = P.Options.from_params(prm, precision=form)
@@ -376,8 +376,7 @@ def time_to_tol(P, W, torch, tol=1e-6):
                 x, rep = P.tk_solve_precond(dop, pc, b, opts)
                 torch.cuda.synchronize()
                 t1 = time.perf_counter()
-                g = P.autograd.tucker_difference(x, xr)
-                mu, rep_a = P.tk_solve_precond(dop, pc, g, adj)
+                mu, rep_a = P.tk_solve_precond(dop, pc, wq, adj)
                 P.tk_adjoint_grads(dop, mu, x, b)
                 torch.cuda.synchronize()
                 t2 = time.perf_counter()
@@ -447,22 +446,23 @@ def secondary(P, W, torch):
     out["poisson3d_point_n1000_expsum_q8"] = entry
     # noisy deblurring (2% noise), relative reconstruction error with and without projected
     # Tikhonov + GCV in the least-squares step (Section 4.3)
-    wl = W.deblur3d_noisy(64, 0, None)
+    wl = W.deblur3d_noisy(32, 0, None)
     dop = P.DeviceOperator(wl.op)
     b = P.DeviceTucker.from_numpy(wl.b.core, wl.b.factors)
     xt = P.DeviceTucker.from_numpy(wl.x_true.core, wl.x_true.factors)
     xt_norm = P.tk_sum_norm([xt], [1.0])
     reg = {}
-    for label, prm in [("sgmres", W.SolverParams('rhosvd', 32, 128, 5, 60, 1e-12, seed=0)),
-                       ("sgmres+tikhonov_gcv", W.SolverParams('rhosvd', 32, 128, 5, 60, 1e-12, seed=0, tikhonov=True)),
-                       ("gmres", W.SolverParams('gmres', 32, 0, 5, 40, 1e-12, seed=0)),
-                       ("gmres+tikhonov_gcv", W.SolverParams('gmres', 32, 0, 5, 40, 1e-12, seed=0, tikhonov=True))]:
-        opts = P.Options.from_params(prm)
-        P.tk_solve(dop, b, opts)
-        x, rep, dt = _timed_solve(P, torch, dop, b, opts)
-        reg[label] = {"iters": rep.iters, "seconds": round(dt, 4),
-                      "rel_reconstruction_error": P.tk_sum_norm([x, xt], [1.0, -1.0]) / xt_norm}
-    out["regularisation_deblur3d_noisy_n64"] = reg
+    for label, variant, s_, tik in [("sgmres", 'rhosvd', 128, False), ("sgmres+tikhonov_gcv", 'rhosvd', 128, True),
+                                    ("gmres", 'gmres', 0, False), ("gmres+tikhonov_gcv", 'gmres', 0, True)]:
+        errs = {}
+        for it in [10, 20, 40]:
+            prm = W.SolverParams(variant, 32, s_, 5, it, 1e-12, seed=0, tikhonov=tik)
+            opts = P.Options.from_params(prm)
+            x, rep, dt = _timed_solve(P, torch, dop, b, opts)
+            errs[f"rre_at_{it}"] = round(P.tk_sum_norm([x, xt], [1.0, -1.0]) / xt_norm, 4)
+            errs[f"seconds_{it}"] = round(dt, 4)
+        reg[label] = errs
+    out["regularisation_deblur3d_noisy_n32"] = reg
     # MLN-Tucker sGMRES, full vs memory-efficient sketches (Section 3.3, r_sol = p_sol = 12)
     wl = W.workload("varcoef4d_n128")
     dop = P.DeviceOperator(wl.op)
