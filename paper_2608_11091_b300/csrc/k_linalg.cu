@@ -1103,6 +1103,282 @@ void tikhonov_gcv(Ctx &c, const LSState &st, int ldr, int k, int m, double *lamb
     c.check_launch("tikhonov", 12.0 * k * (double)k * k);
 }
 
+// ST-HOSVD SVD (graded mode) on a cluster of SCL CTAs.  The FP32 sweeps are a chain of
+// barrier-separated rounds and stay on CTA 0; the FP64 phase after them is dense matrix work
+// (polar step, A = B V, Gram checks, first-order corrections), which on one SM runs at one SM's
+// FP64 rate.  Here every CTA owns a block of cb = ceil(s / SCL) columns and computes those
+// columns of E = Y^T Y - I, of V = Y Z, of A = B V, of H = A^T A, of T and of A (I + D), reading
+// the full operand it needs from its peers' shared memory after a cluster barrier.  The control
+// decisions (converged, separated) are made identically by every CTA from the gathered flags, so
+// all CTAs pass the same cluster barriers.  A check that finds a non-separated pair hands the
+// current A to CTA 0, which finishes with sweeps exactly as the single-CTA kernel does.
+// Shared memory per CTA: X | Y | Z, s x s doubles each:
+//   X: CTA 0's FP32 A and V during the sweeps; afterwards [0, s cb) this CTA's columns (V, then
+//      A) and, behind them, an FP32 publish area (s cb floats: columns of E, then of T);
+//   Y: full copies (Y = double(V32), then the gathered A);
+//   Z: [0, s cb) work columns (E, Z, H, T, D) and, behind them, FP32 full gathers (s^2 floats).
+constexpr int SCL = 8;
+__global__ void __launch_bounds__(1024) k_svd_cl(const __grid_constant__ SVDJobs jobs) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int q = (int)cl.block_rank();
+    const SVDJob &J = jobs.j[blockIdx.x / SCL];
+    extern __shared__ double sm[];
+    const int s = J.s, ss = s * s;
+    double *X = sm, *Y = sm + ss, *Z = sm + 2 * ss;
+    const int cb = (s + SCL - 1) / SCL;
+    const int c0 = min(s, q * cb), c1 = min(s, c0 + cb), nc = c1 - c0;
+    double *Acol = X;                                            // s x cb (this CTA's columns)
+    float *pub = reinterpret_cast<float *>(X + (size_t)s * cb);  // s x cb floats
+    double *W_ = Z;                                              // s x cb work columns
+    float *full32 = reinterpret_cast<float *>(Z + (size_t)s * cb);   // s x s floats
+    __shared__ double dcol[SVD_MAXS], dall[SVD_MAXS];
+    __shared__ double sig[SVD_MAXS], rsig[SVD_MAXS];
+    __shared__ long long skey[SVD_MAXS];
+    __shared__ int order[SVD_MAXS];
+    __shared__ int flag, kept, fl_more, fl_bad;
+    __shared__ int cflags[2];                                    // published: more, bad
+    __shared__ float fscr[40];
+    __shared__ int iscr[40];
+    __shared__ double nrm64[SVD_MAXS];
+    __shared__ float nrm32[SVD_MAXS];
+    __shared__ double gpart[JNP * (SVD_MAXS / 2 + 1)];
+    __shared__ double cpar[SVD_MAXS / 2 + 1], spar[SVD_MAXS / 2 + 1];
+    __shared__ int act[SVD_MAXS / 2 + 1];
+    __shared__ double scal[2];                                   // CTA 0: mx, fro
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
+    auto Bat = [&](int i, int c) -> double {                     // B = R^T (lower triangle)
+        return (c <= i && c < J.ldr) ? J.R[c + (long long)i * J.ldr] : 0.0;
+    };
+    auto owner = [&](int col) { return col / cb; };
+    // ---- phase 1 (CTA 0): scaled FP32 sweeps
+    if (q == 0) {
+        float *A32 = reinterpret_cast<float *>(X), *V32 = A32 + ss;
+        int emax = 0;
+        for (int e = tid; e < ss; e += nt) emax = max(emax, (__double2hiint(Bat(e % s, e / s)) >> 20) & 0x7ff);
+        emax = min(block_max_i(emax, iscr), 2044);
+        const double inv = __hiloint2double((2045 - emax) << 20, 0);
+        for (int e = tid; e < ss; e += nt) {
+            A32[e] = (float)(Bat(e % s, e / s) * inv);
+            V32[e] = (e % s == e / s) ? 1.f : 0.f;
+        }
+        float frop = 0.f;
+        for (int e = tid; e < ss; e += nt) frop = fmaf(A32[e], A32[e], frop);
+        __syncthreads();
+        const float fro = block_sum_f(frop, fscr);
+        const int n32 = jacobi32(A32, V32, nrm32, s, 8.0f * sqrtf((float)s) * 0x1p-24f, 0x1p-100f, 20, &flag);
+        if (tid == 0) {
+            g_svd_sweeps[2 * (blockIdx.x / SCL)] = n32;
+            scal[0] = __hiloint2double((emax + 1) << 20, 0);
+            scal[1] = (double)fro;
+        }
+    }
+    cl.sync();                                                                    // (1)
+    // ---- phase 2: Y = double(V32) everywhere; E columns
+    {
+        const float *V32r = reinterpret_cast<const float *>(cl.map_shared_rank(X, 0)) + ss;
+        for (int e = tid; e < ss; e += nt) Y[e] = (double)V32r[e];
+        if (tid < 2) scal[tid] = cl.map_shared_rank(scal, 0)[tid];
+    }
+    cl.sync();                                                                    // (2) CTA 0's X free
+    const double mx = scal[0], fro = scal[1];
+    for (int e = tid; e < s * nc; e += nt) {
+        const int i = e % s, jl = e / s, j = c0 + jl;
+        double t = 0.0;
+        for (int k = 0; k < s; ++k) t = fma(Y[k + i * s], Y[k + j * s], t);
+        const double ev = t - (i == j ? 1.0 : 0.0);
+        W_[i + jl * s] = ev;
+        pub[i + jl * s] = (float)ev;
+    }
+    cl.sync();                                                                    // (3)
+    for (int e = tid; e < ss; e += nt) {                          // gather E (FP32) in full
+        const int i = e % s, k = e / s, o = owner(k);
+        full32[e] = reinterpret_cast<const float *>(cl.map_shared_rank(X + (size_t)s * cb, o))[i + (k - o * cb) * s];
+    }
+    __syncthreads();
+    for (int e = tid; e < s * nc; e += nt) {                      // Z = I - E / 2 + 3 E^2 / 8
+        const int i = e % s, jl = e / s, j = c0 + jl;
+        float acc = 0.f;
+        for (int k = 0; k < s; ++k) acc = fmaf(full32[i + k * s], full32[k + j * s], acc);
+        W_[i + jl * s] = (i == j ? 1.0 : 0.0) - 0.5 * W_[i + jl * s] + 0.375 * (double)acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < s * nc; e += nt) {                      // V columns = Y Z, then A = B V
+        const int i = e % s, jl = e / s;
+        double t = 0.0;
+        for (int k = 0; k < s; ++k) t = fma(Y[i + k * s], W_[k + jl * s], t);
+        Acol[i + jl * s] = t;
+    }
+    __syncthreads();
+    for (int e = tid; e < s * nc; e += nt) {
+        const int i = e % s, jl = e / s;
+        double t = 0.0;
+        for (int k = 0; k <= i; ++k) t = fma(Bat(i, k), Acol[k + jl * s], t);
+        W_[i + jl * s] = t;
+    }
+    __syncthreads();
+    for (int e = tid; e < s * nc; e += nt) Acol[e] = W_[e];
+    // ---- phase 3: Gram checks and first-order corrections, column-parallel
+    const double fro_r = fro * mx * mx;
+    const double floor2 = fro_r * (double)s * s * 0x1p-106;
+    const double tol = 4.0 * sqrt((double)s) * 0x1p-53, chk2 = 16.0 * tol * tol;
+    bool sweep_fallback = false;
+    for (int step = 0; step <= 16; ++step) {
+        cl.sync();                                                                // A columns final
+        for (int e = tid; e < ss; e += nt) {                      // gather A in full into Y
+            const int i = e % s, k = e / s, o = owner(k);
+            Y[e] = cl.map_shared_rank(Acol, o)[i + (k - o * cb) * s];
+        }
+        __syncthreads();
+        for (int e = tid; e < s * nc; e += nt) {                  // H columns
+            const int i = e % s, jl = e / s, j = c0 + jl;
+            double t = 0.0;
+            for (int r = 0; r < s; ++r) t = fma(Y[r + i * s], Y[r + j * s], t);
+            W_[i + jl * s] = t;
+            if (i == j) dcol[jl] = t;
+        }
+        __syncthreads();
+        cl.sync();                                                                // diagonals published
+        for (int j = tid; j < s; j += nt) {
+            const int o = owner(j);
+            dall[j] = cl.map_shared_rank(dcol, o)[j - o * cb];
+        }
+        if (tid == 0) { fl_more = 0; fl_bad = 0; }
+        __syncthreads();
+        for (int e = tid; e < s * nc; e += nt) {                  // T columns and flags
+            const int i = e % s, jl = e / s, j = c0 + jl;
+            double t = 0.0;
+            if (i != j) {
+                const double di = dall[i], dj = dall[j], g = W_[i + jl * s];
+                if (di > floor2 && dj > floor2 && g * g > chk2 * di * dj) {
+                    fl_more = 1;
+                    if (fabs(g) <= 1e-3 * fabs(dj - di)) t = g / (dj - di);
+                    else fl_bad = 1;
+                }
+            }
+            W_[i + jl * s] = t;
+            pub[i + jl * s] = (float)t;
+        }
+        __syncthreads();
+        if (tid == 0) { cflags[0] = fl_more; cflags[1] = fl_bad; }
+        cl.sync();                                                                // flags, T published
+        int more = 0, bad = 0;
+        for (int o = 0; o < SCL; ++o) {
+            const int *cf = cl.map_shared_rank(cflags, o);
+            more |= cf[0];
+            bad |= cf[1];
+        }
+        if (!more || step == 16) break;
+        if (bad) { sweep_fallback = true; break; }
+        for (int e = tid; e < ss; e += nt) {                      // gather T (FP32) in full
+            const int i = e % s, k = e / s, o = owner(k);
+            full32[e] = reinterpret_cast<const float *>(cl.map_shared_rank(X + (size_t)s * cb, o))[i + (k - o * cb) * s];
+        }
+        __syncthreads();
+        for (int e = tid; e < s * nc; e += nt) {                  // D = T + T^2 / 2
+            const int i = e % s, jl = e / s, j = c0 + jl;
+            float acc = 0.f;
+            for (int k = 0; k < s; ++k) acc = fmaf(full32[i + k * s], full32[k + j * s], acc);
+            W_[i + jl * s] += 0.5 * (double)acc;
+        }
+        __syncthreads();
+        double r[SVD_REGS];
+#pragma unroll
+        for (int k = 0; k < SVD_REGS; ++k) {                      // A columns <- A + A D
+            const int e = tid + k * nt;
+            r[k] = 0.0;
+            if (e < s * nc) {
+                const int i = e % s, jl = e / s;
+                double acc = Acol[e];
+                for (int kk = 0; kk < s; ++kk) acc = fma(Y[i + kk * s], W_[kk + jl * s], acc);
+                r[k] = acc;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < SVD_REGS; ++k) {
+            const int e = tid + k * nt;
+            if (e < s * nc) Acol[e] = r[k];
+        }
+    }
+    // ---- tail on CTA 0 (Y holds the gathered A of the last check)
+    if (q == 0) {
+        if (sweep_fallback) {
+            int nsw = 0;
+            jacobi64<false>(Y, nullptr, nrm64, s, tol, floor2, 16, &flag, gpart, cpar, spar, act, Z, nullptr,
+                            nullptr, &nsw);
+            for (int j = tid; j < s; j += nt) dall[j] = nrm64[j];
+            __syncthreads();
+        }
+        for (int c = tid; c < s; c += nt) {
+            const double v = sqrt(fmax(dall[c], 0.0));
+            sig[c] = v;
+            skey[c] = __double_as_longlong(v);
+            rsig[c] = v > 0.0 ? 1.0 / v : 0.0;
+        }
+        __syncthreads();
+        for (int c = tid; c < s; c += nt) {
+            int pos = 0;
+            const long long kc = skey[c];
+            for (int o = 0; o < s; ++o)
+                if (skey[o] > kc || (skey[o] == kc && o < c)) ++pos;
+            order[pos] = c;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            int r = min(s, J.rank_cap);
+            if (J.normsq) {
+                const double thr = J.eps2_over_d * (*J.normsq);
+                double suf[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const int pos = k * 32 + lane;
+                    double v = pos < s ? fmax(dall[order[pos]], 0.0) : 0.0;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const double u = __shfl_down_sync(0xffffffffu, v, o);
+                        if (lane + o < 32) v += u;
+                    }
+                    suf[k] = v;
+                }
+                const double c2 = __shfl_sync(0xffffffffu, suf[2], 0);
+                const double c1 = __shfl_sync(0xffffffffu, suf[1], 0) + c2;
+                suf[1] += c2;
+                suf[0] += c1;
+                int best = s;
+#pragma unroll
+                for (int k = 2; k >= 0; --k) {
+                    const int pos = k * 32 + lane;
+                    const unsigned msk = __ballot_sync(0xffffffffu, pos >= 1 && pos < s && suf[k] <= thr);
+                    if (msk) best = k * 32 + __ffs(msk) - 1;
+                }
+                r = min(best, J.rank_cap);
+            }
+            r = max(r, 1);
+            if (lane == 0) {
+                kept = r;
+                if (J.rank) *J.rank = r;
+            }
+        }
+        __syncthreads();
+        const int r = kept;
+        if (J.sigma)
+            for (int c = tid; c < s; c += nt) J.sigma[c] = sig[order[c]];
+        if (J.W) {
+            const double fl = sqrt(floor2);
+            for (int e = tid; e < s * J.wcols; e += nt) {
+                const int i = e % s, c = e / s;
+                double v = 0.0;
+                if (c < r) {
+                    const int o = order[c];
+                    if (sig[o] > fl) v = Y[i + o * s] * rsig[o];
+                }
+                J.W[J.perm[i] + (long long)c * s] = v;
+            }
+        }
+    }
+    cl.sync();   // keep shared memory alive until every peer has finished reading it
+}
+
 static void svd_launch(Ctx &c, SVDJobs &J, int smax) {
     const size_t smem = 3 * (size_t)smax * smax * sizeof(double);
     static bool attr_set = false;
@@ -1122,7 +1398,51 @@ static void svd_launch(Ctx &c, SVDJobs &J, int smax) {
     c.check_launch("svd", flops);
 }
 
+static void svd_cl_launch(Ctx &c, SVDJobs &J, int smax) {
+    const size_t smem = 3 * (size_t)smax * smax * sizeof(double);
+    static bool attr_set = false;
+    if (!attr_set) {
+        TK_CUDA(cudaFuncSetAttribute(k_svd_cl, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     3 * SVD_MAXS * SVD_MAXS * (int)sizeof(double)));
+        attr_set = true;
+    }
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3((unsigned)(SCL * J.n), 1, 1);
+    cfg.blockDim = dim3(1024, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c.st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = SCL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    c.pre_launch();
+    TK_CUDA(cudaLaunchKernelEx(&cfg, k_svd_cl, J));
+    double flops = 0.0;
+    for (int i = 0; i < J.n; ++i) flops += 12.0 * J.j[i].s * (double)J.j[i].s * J.j[i].s;
+    c.check_launch("svd", flops);
+}
+
 void svd_jacobi(Ctx &c, const std::vector<SVDJob> &jobs) {
+    // graded (ST-HOSVD) jobs of at least 2 SCL columns: the clustered kernel
+    bool all_graded = !jobs.empty();
+    for (const SVDJob &j : jobs) all_graded = all_graded && j.perm != nullptr && j.s >= 2 * SCL;
+    if (all_graded) {
+        for (size_t base = 0; base < jobs.size(); base += TK_MAX_D) {
+            SVDJobs J{};
+            J.n = (int)std::min<size_t>(TK_MAX_D, jobs.size() - base);
+            int smax = 1;
+            for (int i = 0; i < J.n; ++i) {
+                J.j[i] = jobs[base + i];
+                TK_REQUIRE(J.j[i].s <= SVD_MAXS, "SVD: size must be 1..96");
+                smax = std::max(smax, J.j[i].s);
+            }
+            svd_cl_launch(c, J, smax);
+        }
+        return;
+    }
     for (size_t base = 0; base < jobs.size(); base += TK_MAX_D) {
         SVDJobs J{};
         J.n = (int)std::min<size_t>(TK_MAX_D, jobs.size() - base);
