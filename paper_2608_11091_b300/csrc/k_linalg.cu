@@ -18,7 +18,6 @@ namespace cg = cooperative_groups;
 namespace tk {
 
 constexpr int QR_MAXS = 256;
-constexpr int QR_NCH = 8;        // row chunks per column in the QR partial sums
 constexpr int SVD_MAXS = 96;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -95,7 +94,6 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
     double *Al = dyn;                              // nr x s, ld rb_cap
     double *Ql = dyn + (size_t)rb_cap * s;         // nr x s, ld rb_cap
     __shared__ double red[2][2 * QR_MAXS];         // [0, nc1): partial sums, [nc1, 2 nc1): owner's row
-    __shared__ double part[QR_NCH * QR_MAXS];
     __shared__ double wv[QR_MAXS];
     __shared__ double taus[QR_MAXS];
     __shared__ float nrmf[QR_MAXS];
@@ -117,23 +115,19 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
         }
     __syncthreads();
     int xch = 0;   // exchanges so far (selects the buffer)
-    // partial sums over this CTA's rows [ib, r1) for columns j0 .. j0 + ncols - 1: one thread per
-    // (column, row chunk) calls chunk(c, i0, i1) (a plain FMA loop), chunks combined per column
-    // into out[]
-    auto column_sums = [&](int j0, int ncols, int ib, auto chunk, double *out) {
-        const int nrows = max(0, r1 - ib);
-        const int nch = max(1, min(QR_NCH, nt / max(ncols, 1)));
-        const int rch = (nrows + nch - 1) / nch;
-        for (int e = tid; e < ncols * nch; e += nt) {
-            const int cc = e % ncols, ch = e / ncols;
-            const int i0 = ib + ch * rch, i1 = min(r1, i0 + rch);
-            part[ch * QR_MAXS + cc] = chunk(j0 + cc, i0, i1);
-        }
-        __syncthreads();
-        for (int cc = tid; cc < ncols; cc += nt) {
-            double t = part[cc];
-            for (int ch = 1; ch < nch; ++ch) t += part[ch * QR_MAXS + cc];
-            out[cc] = t;
+    // partial sums over this CTA's rows for columns j0 .. j0 + ncols - 1 into out[]: a group of
+    // eight lanes per column, the rows strided by eight across the group (sum(c, first, 8) is a
+    // plain FMA loop), combined by three xor shuffles: no block barrier and no serial combine.
+    // Every warp runs the same number of passes, so all its lanes reach the shuffles.
+    auto column_sums = [&](int j0, int ncols, auto sum, double *out) {
+        const int grp = tid >> 3, gl = tid & 7, ngrp = nt >> 3;
+        for (int cc0 = 0; cc0 < ncols; cc0 += ngrp) {
+            const int cc = cc0 + grp;
+            double pd = cc < ncols ? sum(j0 + cc, gl) : 0.0;
+            pd += __shfl_xor_sync(0xffffffffu, pd, 1);
+            pd += __shfl_xor_sync(0xffffffffu, pd, 2);
+            pd += __shfl_xor_sync(0xffffffffu, pd, 4);
+            if (cc < ncols && gl == 0) out[cc] = pd;
         }
     };
     // rows across threads, trailing columns in groups: thread (row lane il, group g) updates
@@ -162,9 +156,9 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
     if (piv) {
         for (int c = tid; c < s; c += nt) permv[c] = c;
         double *rd = red[xch & 1];
-        column_sums(0, s, r0, [&](int c, int i0, int i1) {
+        column_sums(0, s, [&](int c, int g) {
             double pd = 0.0;
-            for (int i = i0; i < i1; ++i) { const double x = A(i, c); pd = fma(x, x, pd); }
+            for (int i = r0 + g; i < r1; i += 8) { const double x = A(i, c); pd = fma(x, x, pd); }
             return pd;
         }, rd);
         cl.sync();
@@ -226,12 +220,12 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
         double *rd = red[xch & 1];
         // rd[0] = sigma2 part (rows > j), rd[cc] = D_{j+cc} part (rows >= j); owner: its row j
         const int ib = max(r0, j);
-        column_sums(j, nc1, ib, [&](int c, int i0, int i1) {
+        column_sums(j, nc1, [&](int c, int g) {
             double pd = 0.0;
             if (c == j) {
-                for (int i = max(i0, j + 1); i < i1; ++i) { const double x = A(i, j); pd = fma(x, x, pd); }
+                for (int i = max(ib, j + 1) + g; i < r1; i += 8) { const double x = A(i, j); pd = fma(x, x, pd); }
             } else {
-                for (int i = i0; i < i1; ++i) pd = fma(A(i, j), A(i, c), pd);
+                for (int i = ib + g; i < r1; i += 8) pd = fma(A(i, j), A(i, c), pd);
             }
             return pd;
         }, rd);
@@ -243,10 +237,10 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
         if (warp == 0) {
             // sigma2 over the peers (lane = peer, C <= 16), alpha from the owner, the scalars
             double s2 = lane < C ? cl.map_shared_rank(rd, lane)[0] : 0.0;
+            const double al = ro[nc1];          // issued beside the sigma2 loads
 #pragma unroll
             for (int o = 8; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
             if (lane == 0) {
-                const double al = ro[nc1];
                 double tau = 0.0, beta = al, scal = 0.0;
                 if (s2 > 0.0) {
                     const double nrm = sqrt(fma(al, al, s2));
@@ -303,11 +297,9 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
             if (tau == 0.0) continue;   // uniform across the cluster
             double *rd = red[xch & 1];
             const int ib = max(r0, j), ncq = s - j;
-            column_sums(j, ncq, ib, [&](int c, int i0, int i1) {
+            column_sums(j, ncq, [&](int c, int g) {
                 double pd = 0.0;
-                int i = i0;
-                if (i == j && i < i1) { pd = Q(j, c); ++i; }
-                for (; i < i1; ++i) pd = fma(A(i, j), Q(i, c), pd);
+                for (int i = ib + g; i < r1; i += 8) pd = fma(i == j ? 1.0 : A(i, j), Q(i, c), pd);
                 return pd;
             }, rd);
             cl.sync();
