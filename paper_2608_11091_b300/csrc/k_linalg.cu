@@ -469,26 +469,41 @@ __device__ __forceinline__ void rr_pair(int round, int pr, int sp, int &p, int &
 }
 
 // FP32 one-sided (Hestenes) Jacobi on the columns of A (s x s, column-major, shared memory),
-// rotations accumulated into V.  One warp per pair with the rows across lanes; the butterfly
-// reduction leaves a_p . a_q in every lane, so every lane forms the rotation itself (fast
-// FP32 intrinsics: the FP32 phase only has to bring the columns close to orthogonal, the
-// FP64 phase finishes).  A pair is rotated when |a_p . a_q| > tol ||a_p|| ||a_q|| and both
-// squared norms exceed `floor2`.  Convergence is checked after every sweep on the full Gram
-// matrix A^T A (one dot product per thread), which replaces a final rotation-free sweep.
-// Column squared norms are kept in `nrm2` (Rutishauser's updates inside a sweep, exact from
-// the Gram check between sweeps).  Returns the number of sweeps.
-__device__ int jacobi32(float *A, float *V, float *nrm2, int s, float tol, float floor2, int max_sweeps,
-                        int *flag) {
+// rotations accumulated into V.  A round of the sweep is latency bound (dot product, butterfly,
+// rotation, barrier, s - 1 rounds in a row), so each pair takes a group of G lanes with up to
+// J32R rows per lane held in registers: 32 / G pairs share a warp and only ceil(np G / 32) warps
+// issue the round, synchronised by a named barrier.  The butterfly leaves a_p . a_q in every lane
+// of the group and every lane forms the rotation itself, with fast FP32 intrinsics: this phase
+// only has to bring the columns close to orthogonal, the FP64 phase finishes.  A pair is rotated
+// when |a_p . a_q| > tol ||a_p|| ||a_q|| and both squared norms exceed `floor2`.  Convergence is
+// checked after every sweep on the full Gram matrix A^T A (one dot product per thread), which
+// replaces a final rotation-free sweep.  Column squared norms are kept in `nrm2` (Rutishauser's
+// updates inside a sweep, exact from the Gram check between sweeps).  Returns the number of sweeps.
+constexpr int J32R = 5;
+__device__ __forceinline__ float dot_rows(const float *x, const float *y, int s) {
+    float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+    int i = 0;
+    for (; i + 3 < s; i += 4) {
+        t0 = fmaf(x[i], y[i], t0);
+        t1 = fmaf(x[i + 1], y[i + 1], t1);
+        t2 = fmaf(x[i + 2], y[i + 2], t2);
+        t3 = fmaf(x[i + 3], y[i + 3], t3);
+    }
+    for (; i < s; ++i) t0 = fmaf(x[i], y[i], t0);
+    return (t0 + t1) + (t2 + t3);
+}
+template <int G>
+__device__ int jacobi32_g(float *A, float *V, float *nrm2, int s, float tol, float floor2, int max_sweeps,
+                          int *flag) {
+    constexpr int PPW = 32 / G;                      // pairs per warp
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5, nt = blockDim.x;
+    const int gl = lane & (G - 1), slot = lane / G;
     const int sp = s + (s & 1), np = sp / 2;
+    const int nact = min(nw, (np + PPW - 1) / PPW);  // warps holding a pair
     int sweeps = 0;
     for (;;) {
         // Gram check: squared norms first, then every pair p < q
-        for (int c = tid; c < s; c += nt) {
-            float t = 0.f;
-            for (int i = 0; i < s; ++i) t = fmaf(A[i + c * s], A[i + c * s], t);
-            nrm2[c] = t;
-        }
+        for (int c = tid; c < s; c += nt) nrm2[c] = dot_rows(A + c * s, A + c * s, s);
         if (tid == 0) *flag = 0;
         __syncthreads();
         for (int e = tid; e < s * s; e += nt) {
@@ -496,8 +511,7 @@ __device__ int jacobi32(float *A, float *V, float *nrm2, int s, float tol, float
             if (p >= q) continue;
             const float al = nrm2[p], be = nrm2[q];
             if (al <= floor2 || be <= floor2) continue;
-            float g = 0.f;
-            for (int i = 0; i < s; ++i) g = fmaf(A[i + p * s], A[i + q * s], g);
+            const float g = dot_rows(A + p * s, A + q * s, s);
             // 4x the rotation tolerance: the check's dot product is summed in another order
             // than the sweep's, and a pair between the two must not keep the loop alive
             if (fabsf(g) > 4.f * tol * __fsqrt_rn(al) * __fsqrt_rn(be)) *flag = 1;
@@ -507,39 +521,74 @@ __device__ int jacobi32(float *A, float *V, float *nrm2, int s, float tol, float
         __syncthreads();
         if (!more || sweeps >= max_sweeps || sp < 2) break;
         ++sweeps;
-        for (int round = 0; round < sp - 1; ++round) {
-            for (int pr = warp; pr < np; pr += nw) {
-                int p, q;
-                rr_pair(round, pr, sp, p, q);
-                if (q >= s) continue;
-                const float al = nrm2[p], be = nrm2[q];
-                if (al <= floor2 || be <= floor2) continue;
-                float ga = 0.f;
-                for (int i = lane; i < s; i += 32) ga = fmaf(A[i + p * s], A[i + q * s], ga);
-                ga = warp_sum_t(ga);
-                if (!(fabsf(ga) > tol * __fsqrt_rn(al) * __fsqrt_rn(be))) continue;
-                const float zeta = __fdividef(be - al, 2.f * ga);
-                const float az = fabsf(zeta);
-                const float t = az < 1e18f ? copysignf(1.f, zeta) / (az + __fsqrt_rn(fmaf(zeta, zeta, 1.f)))
-                                           : 0.5f / zeta;
-                const float cs = rsqrtf(fmaf(t, t, 1.f)), sn = cs * t;
-                for (int i = lane; i < s; i += 32) {
-                    const float a = A[i + p * s], b = A[i + q * s];
-                    A[i + p * s] = cs * a - sn * b;
-                    A[i + q * s] = sn * a + cs * b;
-                    const float va = V[i + p * s], vb = V[i + q * s];
-                    V[i + p * s] = cs * va - sn * vb;
-                    V[i + q * s] = sn * va + cs * vb;
+        if (warp < nact) {
+            for (int round = 0; round < sp - 1; ++round) {
+                // every lane of the warp runs the same trip count, so the butterfly below is
+                // warp-uniform; a group without a live pair carries zeros through it
+                for (int base = warp * PPW; base < np; base += nw * PPW) {
+                    const int pr = base + slot;
+                    int p = 0, q = 0;
+                    bool live = pr < np;
+                    if (live) {
+                        rr_pair(round, pr, sp, p, q);
+                        live = q < s;
+                    }
+                    float a[J32R], b[J32R], va[J32R], vb[J32R];
+#pragma unroll
+                    for (int k = 0; k < J32R; ++k) {
+                        const int i = gl + G * k;
+                        a[k] = b[k] = va[k] = vb[k] = 0.f;
+                        if (live && i < s) {
+                            a[k] = A[i + p * s];
+                            b[k] = A[i + q * s];
+                            va[k] = V[i + p * s];
+                            vb[k] = V[i + q * s];
+                        }
+                    }
+                    const float al = live ? nrm2[p] : 0.f, be = live ? nrm2[q] : 0.f;
+                    float ga = 0.f;
+#pragma unroll
+                    for (int k = 0; k < J32R; ++k) ga = fmaf(a[k], b[k], ga);
+#pragma unroll
+                    for (int o = G / 2; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
+                    if (!live || al <= floor2 || be <= floor2) continue;
+                    // norms above floor2 = 2^-100 or a positive fraction of ||A||_F^2: normal
+                    // numbers, so x * rsqrt(x) is a safe square root
+                    if (!(fabsf(ga) > tol * (al * rsqrtf(al)) * (be * rsqrtf(be)))) continue;
+                    const float zeta = __fdividef(be - al, 2.f * ga);
+                    const float az = fabsf(zeta), z1 = fmaf(zeta, zeta, 1.f);
+                    const float t = az < 1e18f ? __fdividef(copysignf(1.f, zeta), az + z1 * rsqrtf(z1))
+                                               : __fdividef(0.5f, zeta);
+                    const float cs = rsqrtf(fmaf(t, t, 1.f)), sn = cs * t;
+#pragma unroll
+                    for (int k = 0; k < J32R; ++k) {
+                        const int i = gl + G * k;
+                        if (i < s) {
+                            A[i + p * s] = cs * a[k] - sn * b[k];
+                            A[i + q * s] = sn * a[k] + cs * b[k];
+                            V[i + p * s] = cs * va[k] - sn * vb[k];
+                            V[i + q * s] = sn * va[k] + cs * vb[k];
+                        }
+                    }
+                    if (gl == 0) {
+                        nrm2[p] = fmaxf(al - t * ga, 0.f);
+                        nrm2[q] = be + t * ga;
+                    }
                 }
-                if (lane == 0) {
-                    nrm2[p] = fmaxf(al - t * ga, 0.f);
-                    nrm2[q] = be + t * ga;
-                }
+                asm volatile("bar.sync 1, %0;" ::"r"(nact * 32) : "memory");
             }
-            __syncthreads();
         }
+        __syncthreads();
     }
     return sweeps;
+}
+// s <= G J32R rows per group; SVD_MAXS = 96 needs G = 32 at most
+__device__ int jacobi32(float *A, float *V, float *nrm2, int s, float tol, float floor2, int max_sweeps,
+                        int *flag) {
+    if (s <= 4 * J32R) return jacobi32_g<4>(A, V, nrm2, s, tol, floor2, max_sweeps, flag);
+    if (s <= 8 * J32R) return jacobi32_g<8>(A, V, nrm2, s, tol, floor2, max_sweeps, flag);
+    if (s <= 16 * J32R) return jacobi32_g<16>(A, V, nrm2, s, tol, floor2, max_sweeps, flag);
+    return jacobi32_g<32>(A, V, nrm2, s, tol, floor2, max_sweeps, flag);
 }
 
 // FP64 phase of the one-sided Jacobi SVD.  Every FP64 warp instruction occupies an SMSP's FP64
@@ -1380,7 +1429,8 @@ static void svd_launch(Ctx &c, SVDJobs &J, int smax) {
         attr_set = true;
     }
     c.pre_launch();
-    // 1024 threads: the FP32 sweeps run one warp per pair, and s <= 64 gives at most 32 pairs
+    // 1024 threads: enough for one Gram-check dot product per thread and for every FP32 pair
+    // group (at most 48 pairs at s = 96)
     // per round (512 threads would serialise pairs on a warp and double each round's latency)
     k_svd<<<J.n, 1024, smem, c.st>>>(J);
     // algorithmic work: Golub and Van Loan's count for the singular values and one set of
