@@ -1431,7 +1431,6 @@ static void svd_launch(Ctx &c, SVDJobs &J, int smax) {
     c.pre_launch();
     // 1024 threads: enough for one Gram-check dot product per thread and for every FP32 pair
     // group (at most 48 pairs at s = 96)
-    // per round (512 threads would serialise pairs on a warp and double each round's latency)
     k_svd<<<J.n, 1024, smem, c.st>>>(J);
     // algorithmic work: Golub and Van Loan's count for the singular values and one set of
     // singular vectors of an s x s matrix, 12 s^3
