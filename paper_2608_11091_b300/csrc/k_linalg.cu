@@ -95,6 +95,7 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
     double *Ql = dyn + (size_t)rb_cap * s;         // nr x s, ld rb_cap
     __shared__ double red[2][2 * QR_MAXS];         // [0, nc1): partial sums, [nc1, 2 nc1): owner's row
     __shared__ double wv[QR_MAXS];
+    __shared__ double prow[QR_MAXS];               // owner's row j of the step (local copy)
     __shared__ double taus[QR_MAXS];
     __shared__ float nrmf[QR_MAXS];
     __shared__ int permv[QR_MAXS];
@@ -139,14 +140,23 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
         g = tid / RT;
     };
     // sum over the cluster of rd[lo .. hi) of every peer into dst[lo .. hi): four threads per
-    // entry, each over a quarter of the peers, combined by two shuffles within the group
-    auto peer_sums = [&](const double *rd, int lo, int hi, int t0, int nthr, double *dst) {
+    // entry, each over a quarter of the peers (C <= 16: at most four loads, all issued before
+    // the first add), combined by two shuffles within the group
+    // (optional: the group's first thread also copies rowsrc[cc] into rowdst[cc], a load issued
+    // with the others)
+    auto peer_sums = [&](const double *rd, int lo, int hi, int t0, int nthr, double *dst,
+                         const double *rowsrc = nullptr, double *rowdst = nullptr) {
         const int n4 = (hi - lo) * 4;
         for (int e = tid - t0; e >= 0 && e < ((n4 + 31) & ~31); e += nthr) {
             const int cc = lo + e / 4, g = e & 3;
-            double d = 0.0;
-            if (e < n4)
-                for (int qq = g; qq < C; qq += 4) d += cl.map_shared_rank(rd, qq)[cc];
+            double v[4] = {0.0, 0.0, 0.0, 0.0};
+            if (e < n4) {
+                if (rowsrc && g == 0) rowdst[cc] = rowsrc[cc];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (g + 4 * u < C) v[u] = cl.map_shared_rank(rd, g + 4 * u)[cc];
+            }
+            double d = (v[0] + v[1]) + (v[2] + v[3]);
             d += __shfl_xor_sync(0xffffffffu, d, 1);
             d += __shfl_xor_sync(0xffffffffu, d, 2);
             if (e < n4 && g == 0) dst[cc] = d;
@@ -165,10 +175,12 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
         ++xch;
         peer_sums(rd, 0, s, 0, nt, wv);
         __syncthreads();
-        if (tid == 0) {
+        if (warp == 0) {                 // largest squared column norm: one warp of shuffles
             double mxn = 0.0;
-            for (int c = 0; c < s; ++c) mxn = fmax(mxn, wv[c]);
-            bc[0] = mxn > 0.0 ? 1.0 / mxn : 1.0;
+            for (int c = lane; c < s; c += 32) mxn = fmax(mxn, wv[c]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mxn = fmax(mxn, __shfl_xor_sync(0xffffffffu, mxn, o));
+            if (lane == 0) bc[0] = mxn > 0.0 ? 1.0 / mxn : 1.0;
         }
         __syncthreads();
         sc2 = bc[0];
@@ -252,14 +264,14 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
                 taus[j] = tau;
             }
         } else {
-            peer_sums(rd, 1, nc1, 32, nt - 32, wv);
+            peer_sums(rd, 1, nc1, 32, nt - 32, wv, ro + nc1, prow);   // owner's row P_c beside them
         }
         __syncthreads();
         const double tau = bc[0], beta = bc[1], scal = bc[2], al = bc[3];
         // w_c = tau v^T A_c = tau (P_c + (D_c - alpha P_c) / (alpha - beta)); pivot norms lose
         // the new row of R, R_jc = P_c - w_c; v stored in place: x_i / (alpha - beta)
         for (int cc = 1 + tid; cc < nc1; cc += nt) {
-            const double Pc = ro[nc1 + cc];
+            const double Pc = prow[cc];
             const double w = tau * fma(scal, fma(-al, Pc, wv[cc]), Pc);
             wv[cc] = w;
             if (piv) {
@@ -307,14 +319,12 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
             peer_sums(rd, 0, ncq, 0, nt, wv);
             __syncthreads();
             const int nrows = r1 - ib;
-            for (int cc = tid; cc < ncq; cc += nt) wv[cc] *= tau;
-            __syncthreads();
             if (nrows > 0) {
                 int RT, ng, il, g;
                 row_layout(nrows, RT, ng, il, g);
                 for (int i = ib + il; i < r1; i += RT) {
-                    const double v = (i == j) ? 1.0 : A(i, j);
-                    for (int cc = g; cc < ncq; cc += ng) Q(i, j + cc) = fma(-v, wv[cc], Q(i, j + cc));
+                    const double tv = tau * ((i == j) ? 1.0 : A(i, j));   // Q_c -= (tau v) (v^T Q_c)
+                    for (int cc = g; cc < ncq; cc += ng) Q(i, j + cc) = fma(-tv, wv[cc], Q(i, j + cc));
                 }
             }
             __syncthreads();
