@@ -3,10 +3,11 @@
 //
 // One launch runs up to GEMM_MAXPROB problems, each a sum over up to GEMM_MAXSEG segments
 // (so a sum of Tucker terms reduces over the concatenated K without atomics).  Tiles are
-// 32 x 32 with 256 threads, 2 x 2 FP64 outputs per thread.  Problems whose reduction
+// 32 x 32 with 256 threads, 2 x 2 FP64 outputs per thread (warps outside a partial tile idle).  Problems whose reduction
 // dimension is long relative to their tile count split K over a thread-block cluster of
-// up to 8 CTAs; the partial tiles are summed through distributed shared memory in a fixed
-// rank order, so results are deterministic run to run.
+// up to 8 CTAs (the factor chosen per problem, so that small grids still occupy the SMs); the
+// partial tiles are summed through distributed shared memory in a fixed rank order, so results
+// are deterministic run to run.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -38,16 +39,32 @@ __global__ void __launch_bounds__(256) k_gemm_group(const __grid_constant__ GGro
 
     const int tid = threadIdx.x;
     const int tx = tid % 16, ty = tid / 16;
+    // Every thread owns a 2 x 2 block.  A warp spans either 4 rows x 32 columns (rows split
+    // across warps) or 32 rows x 4 columns; the tile takes the split along its shorter valid
+    // extent, and a warp whose rows (columns) all lie outside C skips the FMAs: an FP64 warp
+    // instruction costs the same whatever its lanes hold, and the sketch width r + p rarely
+    // fills the last tile (37 = 32 + 5).
+    const int mv = min(BM, P.M - m0), nv = min(BN, P.N - n0);
+    const bool colsplit = nv < mv;
+    const int r0 = colsplit ? tx * 2 : ty * 2, c0 = colsplit ? ty * 2 : tx * 2;
+    const bool active = (colsplit ? (tid >> 5) * 4 < nv : (tid >> 5) * 4 < mv);
     double acc00 = 0, acc01 = 0, acc10 = 0, acc11 = 0;
 
+    // split-K: part `part` of `ksplit` takes an equal share of the concatenated reduction
+    // (all segments end to end), so short segments are not cut into mostly empty slabs
+    int ktot = 0;
+    for (int si = 0; si < P.nseg; ++si) ktot += P.seg[si].K;
+    const int kcs = (ktot + ksplit - 1) / ksplit;
+    const int kg0 = part * kcs, kg1 = min(ktot, kg0 + kcs);
+    int koff = 0;
     for (int si = 0; si < P.nseg; ++si) {
         const GSeg &S = P.seg[si];
+        const int kb = max(kg0 - koff, 0), ke = min(kg1 - koff, S.K);
+        koff += S.K;
+        if (kb >= ke) continue;   // uniform across the CTA
         const double cf = S.coef * (S.coef_dev ? *S.coef_dev : 1.0);
         const double *A = S.A + (long long)b * P.sA;
         const double *B = S.B + (long long)b * P.sB;
-        const int kc = (S.K + ksplit - 1) / ksplit;
-        const int kb = part * kc;
-        const int ke = min(S.K, kb + kc);
         for (int k0 = kb; k0 < ke; k0 += BK) {
 #pragma unroll
             for (int rep = 0; rep < 2; ++rep) {
@@ -68,14 +85,16 @@ __global__ void __launch_bounds__(256) k_gemm_group(const __grid_constant__ GGro
                 Bs[kk][nn] = w;
             }
             __syncthreads();
+            if (active) {
 #pragma unroll
-            for (int kk = 0; kk < BK; ++kk) {
-                const double a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
-                const double b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
-                acc00 = fma(a0, b0, acc00);
-                acc01 = fma(a0, b1, acc01);
-                acc10 = fma(a1, b0, acc10);
-                acc11 = fma(a1, b1, acc11);
+                for (int kk = 0; kk < BK; ++kk) {
+                    const double a0 = As[kk][r0], a1 = As[kk][r0 + 1];
+                    const double b0 = Bs[kk][c0], b1 = Bs[kk][c0 + 1];
+                    acc00 = fma(a0, b0, acc00);
+                    acc01 = fma(a0, b1, acc01);
+                    acc10 = fma(a1, b0, acc10);
+                    acc11 = fma(a1, b1, acc11);
+                }
             }
             __syncthreads();
         }
@@ -88,7 +107,7 @@ __global__ void __launch_bounds__(256) k_gemm_group(const __grid_constant__ GGro
         for (int i = 0; i < 2; ++i)
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                const int gm = m0 + ty * 2 + i, gn = n0 + tx * 2 + j;
+                const int gm = m0 + r0 + i, gn = n0 + c0 + j;
                 if (gm < P.M && gn < P.N) {
                     double *c = C + gm + (long long)gn * P.ldc;
                     *c = P.beta == 0.0 ? acc[i][j] : fma(P.beta, *c, acc[i][j]);
@@ -98,10 +117,10 @@ __global__ void __launch_bounds__(256) k_gemm_group(const __grid_constant__ GGro
     }
     // split-K: reduce partial tiles across the cluster in rank order
     cg::cluster_group cl = cg::this_cluster();
-    red[ty * 2][tx * 2] = acc00;
-    red[ty * 2][tx * 2 + 1] = acc01;
-    red[ty * 2 + 1][tx * 2] = acc10;
-    red[ty * 2 + 1][tx * 2 + 1] = acc11;
+    red[r0][c0] = acc00;
+    red[r0][c0 + 1] = acc01;
+    red[r0 + 1][c0] = acc10;
+    red[r0 + 1][c0 + 1] = acc11;
     cl.sync();
     const int rows = BM / ksplit;
     for (int e = tid; e < rows * BN; e += 256) {
@@ -174,7 +193,7 @@ void Gemm::flush_group(std::vector<GProb> &probs, int ksplit) {
         cfg.numAttrs = 1;
         c_.pre_launch();
         TK_CUDA(cudaLaunchKernelEx(&cfg, k_gemm_group, g, ksplit));
-        c_.check_launch("gemm", flops);
+        c_.check_launch(tag_, flops);
     }
     probs.clear();
 }
@@ -182,26 +201,34 @@ void Gemm::flush_group(std::vector<GProb> &probs, int ksplit) {
 void Gemm::run() {
     // Problems writing the same C (segment chunks) must run in order: split the pending list
     // into waves where no C repeats.
-    std::vector<GProb> wave_split, wave_plain;
+    std::vector<std::vector<GProb>> waves(1);
     std::vector<double *> seen;
-    auto flush = [&]() {
-        flush_group(wave_split, 8);
-        flush_group(wave_plain, 1);
-        seen.clear();
-    };
     for (const GProb &p : pending_) {
-        if (std::find(seen.begin(), seen.end(), p.C) != seen.end()) flush();
+        if (std::find(seen.begin(), seen.end(), p.C) != seen.end()) {
+            waves.emplace_back();
+            seen.clear();
+        }
         seen.push_back(p.C);
-        long long kmax = 0;
-        for (int s = 0; s < p.nseg; ++s) kmax += p.seg[s].K;
-        const long long tiles = (long long)p.tiles_m * p.tiles_n * p.batch;
-        // split K when the reduction is long and the tile count small
-        if (kmax >= 256 && tiles * 8 <= 4LL * c_.num_sms)
-            wave_split.push_back(p);
-        else
-            wave_plain.push_back(p);
+        waves.back().push_back(p);
     }
-    flush();
+    for (const std::vector<GProb> &wave : waves) {
+        // a small grid runs each tile's BK-slab chain on an otherwise idle SM: split K (powers
+        // of two, BM divisible by the factor) while the wave's grid stays within two CTAs per
+        // SM, each problem only as far as every part keeps at least 8 of its reduction
+        long long tiles = 0;
+        for (const GProb &p : wave) tiles += (long long)p.tiles_m * p.tiles_n * p.batch;
+        int wmax = 0;
+        while (wmax < 3 && tiles * (2LL << wmax) <= 2LL * c_.num_sms) ++wmax;
+        std::vector<GProb> by_split[4];            // split factors 1, 2, 4, 8
+        for (const GProb &p : wave) {
+            long long ktot = 0;
+            for (int s = 0; s < p.nseg; ++s) ktot += p.seg[s].K;
+            int w = 0;
+            while (w < wmax && ktot >= 8LL * (2 << w)) ++w;
+            by_split[w].push_back(p);
+        }
+        for (int w = 3; w >= 0; --w) flush_group(by_split[w], 1 << w);
+    }
     pending_.clear();
 }
 

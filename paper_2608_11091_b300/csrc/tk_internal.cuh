@@ -124,7 +124,8 @@ struct GGroup {
 // Host-side builder that chunks problems/segments into launches.
 class Gemm {
 public:
-    explicit Gemm(Ctx &c) : c_(c) {}
+    // `tag`: the profiler's name for this builder's launches (the contraction it serves)
+    explicit Gemm(Ctx &c, const char *tag = "gemm") : c_(c), tag_(tag) {}
     // C = beta C + sum coef_s op(A_s) op(B_s).  Segments beyond GEMM_MAXSEG are chunked.
     struct Seg {
         const double *A; int lda;
@@ -145,6 +146,7 @@ public:
 
 private:
     Ctx &c_;
+    const char *tag_;
     std::vector<GProb> pending_;
     void flush_group(std::vector<GProb> &probs, int ksplit);
 };

@@ -24,7 +24,7 @@ static long long prod(const int *v, int a, int b) {
 void mttkrp_batch(Ctx &c, int d, int s, const std::vector<MttJob> &jobs, bool tensor_cores) {
     struct St { std::vector<int> dims, modes; const double *T; };
     std::vector<St> st(jobs.size());
-    Gemm g(c);
+    Gemm g(c, "gemm_mttkrp");
     std::vector<TcProb> tc;
     for (size_t i = 0; i < jobs.size(); ++i) {
         const MttJob &J = jobs[i];
@@ -93,7 +93,7 @@ void ttm_groups(Ctx &c, int d, const std::vector<TtmGroup> &groups) {
             st[gi].push_back(s);
         }
     for (int k = 0; k < d - 1; ++k) {
-        Gemm g(c);
+        Gemm g(c, "gemm_ttm");
         for (size_t gi = 0; gi < groups.size(); ++gi) {
             const TtmGroup &G = groups[gi];
             for (size_t ji = 0; ji < G.jobs.size(); ++ji) {
@@ -113,7 +113,7 @@ void ttm_groups(Ctx &c, int d, const std::vector<TtmGroup> &groups) {
         }
         g.run();
     }
-    Gemm g(c);
+    Gemm g(c, "gemm_ttm");
     const int k = d - 1;
     for (size_t gi = 0; gi < groups.size(); ++gi) {
         const TtmGroup &G = groups[gi];
@@ -143,7 +143,7 @@ void ttm_groups(Ctx &c, int d, const std::vector<TtmGroup> &groups) {
 // ------------------------------------------------------------------------------------------
 void inner_batch(Ctx &c, const Dims &pb, const std::vector<InnerJob> &jobs) {
     const int d = pb.d;
-    Gemm g(c);
+    Gemm g(c, "gemm_inner");
     std::vector<std::vector<double *>> P(jobs.size());
     for (size_t i = 0; i < jobs.size(); ++i) {
         const InnerJob &J = jobs[i];
@@ -185,7 +185,7 @@ void inner_batch(Ctx &c, const Dims &pb, const std::vector<InnerJob> &jobs) {
 void kron_sketch_batch(Ctx &c, const Dims &pb, const std::vector<TTerm> &xs,
                        const double *const *S, int s, double *const *outs) {
     const int d = pb.d;
-    Gemm g(c);
+    Gemm g(c, "gemm_sketch");
     std::vector<MttJob> mj(xs.size());
     for (size_t i = 0; i < xs.size(); ++i) {
         MttJob &J = mj[i];
@@ -213,7 +213,7 @@ std::vector<TTerm> apply_operator(Ctx &c, const Dims &pb, const OpDesc &op, cons
     const int d = pb.d;
     std::vector<TTerm> out(op.nterms);
     std::vector<BandJob> bj;
-    Gemm g(c);
+    Gemm g(c, "gemm_apply");
     // distinct (matrix, mode) pairs produce one factor each
     std::map<std::pair<const void *, int>, double *> made;
     for (int t = 0; t < op.nterms; ++t) {
@@ -272,7 +272,7 @@ void roundsum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const RSC
     const bool mixed = cfg.bf16_sketch != 0;
     std::vector<std::vector<const double *>> M(N, std::vector<const double *>(d));
     {
-        Gemm g(c);
+        Gemm g(c, "gemm_factor_sketch");
         std::vector<TcProb> tc;
         std::map<const double *, double *> made[TK_MAX_D];
         for (int i = 0; i < N; ++i)
@@ -310,7 +310,7 @@ void roundsum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const RSC
     // 4. Y_k = sum_i c_i U_k^(i) Z_k^(i)   (n_k x sr)
     double *Y[TK_MAX_D], *Q[TK_MAX_D];
     {
-        Gemm g(c);
+        Gemm g(c, "gemm_range");
         for (int k = 0; k < d; ++k) {
             Y[k] = c.arena->alloc((size_t)pb.n[k] * sr);
             std::vector<Gemm::Seg> segs;
@@ -334,7 +334,7 @@ void roundsum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const RSC
     // 6. projections P_k^(i) = U^_k^T U_k^(i)   (sr x r_k^(i))
     std::vector<std::vector<const double *>> P(N, std::vector<const double *>(d));
     {
-        Gemm g(c);
+        Gemm g(c, "gemm_proj");
         std::map<const double *, double *> made[TK_MAX_D];
         for (int i = 0; i < N; ++i)
             for (int k = 0; k < d; ++k) {
@@ -389,7 +389,7 @@ void roundsum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const RSC
         sj.normsq = normsq; sj.eps2_over_d = cfg.eps * cfg.eps / d; sj.rank_cap = R;
         svd_jacobi(c, {sj});
         double *Cn = (k == d - 1) ? out.core : c.arena->alloc(a * R * rest);
-        Gemm g(c);
+        Gemm g(c, "gemm_hosvd");
         if (k == 0)
             g.add1(R, (int)rest, sk, 1, 0, W[k], sk, C, sk, Cn, R);
         else
@@ -401,7 +401,7 @@ void roundsum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const RSC
     }
     // 9. output factors U^_k W_k   (n_k x R)
     {
-        Gemm g(c);
+        Gemm g(c, "gemm_factors");
         for (int k = 0; k < d; ++k) g.add1(pb.n[k], R, sr, 0, 0, Q[k], pb.n[k], W[k], sr, out.f[k], pb.n[k]);
         g.run();
     }
@@ -419,7 +419,7 @@ void mln_sketch_sum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, con
     // U_Psi,k^(i) = Psi_k^T U_k^(i)  ((r+p) x r_k); Ubar^T = first r rows, transposed on use
     std::vector<std::vector<const double *>> UP(N, std::vector<const double *>(d));
     {
-        Gemm g(c);
+        Gemm g(c, "gemm_mln");
         std::map<const double *, double *> made[TK_MAX_D];
         for (int i = 0; i < N; ++i)
             for (int k = 0; k < d; ++k) {
@@ -479,7 +479,7 @@ void mln_sketch_sum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, con
         mttkrp_batch(c, d, r, mj);
     }
     {
-        Gemm g(c);
+        Gemm g(c, "gemm_mln");
         for (int k = 0; k < d; ++k) {
             std::vector<Gemm::Seg> segs;
             for (int i = 0; i < N; ++i)
@@ -498,7 +498,7 @@ void mln_recovery(Ctx &c, const Dims &pb, const double *gpsi, const double *cons
     const int d = pb.d, rp = r + p;
     double *PF[TK_MAX_D], *Qk[TK_MAX_D], *Rp[TK_MAX_D];
     {
-        Gemm g(c);
+        Gemm g(c, "gemm_mln");
         for (int k = 0; k < d; ++k) {
             PF[k] = c.arena->alloc((size_t)rp * r);
             g.add1(rp, r, pb.n[k], 1, 0, psi[k], pb.n[k], F[k], pb.n[k], PF[k], rp);
@@ -524,7 +524,7 @@ void mln_recovery(Ctx &c, const Dims &pb, const double *gpsi, const double *cons
         pinv_small(c, Rs, ld, r, Rp, d, r * 0x1p-52);
     }
     {
-        Gemm g(c);
+        Gemm g(c, "gemm_mln");
         for (int k = 0; k < d; ++k) g.add1(pb.n[k], r, r, 0, 0, F[k], pb.n[k], Rp[k], r, out.f[k], pb.n[k]);
         g.run();
     }
