@@ -225,7 +225,8 @@ int tk_philox(tk_handle *h, uint64_t seed, uint64_t stream_id, uint64_t first, i
               uint32_t *out, void *stream);
 
 /* tk_sketched_ls: y = argmin ||M y - b||_2 for M (device, s x k column-major, lda = s),
- * b (device, s), via Householder QR (Algorithm 2 least-squares step); writes y (device, k)
+ * b (device, s), via Householder QR (Algorithm 2 least-squares step; the reflectors applied in
+ * compact WY form for k <= 256, one at a time beyond); writes y (device, k)
  * and the residual norm ||M y - b|| to *res (device).  Enqueues only.  Requires k < s <= 1024. */
 int tk_sketched_ls(tk_handle *h, const double *M, const double *b, int32_t s, int32_t k,
                    double *y, double *res, void *stream);
@@ -235,8 +236,8 @@ int tk_sketched_ls(tk_handle *h, const double *M, const double *b, int32_t s, in
  * memory up front for its own allocator, or a latency-critical loop that cannot accept
  * cudaMalloc's implicit device synchronisation).  The paper has no counterpart; this is an
  * interface for such callers.  It takes no handle and allocates nothing: its workspace is a
- * fixed 513 KiB array in the library's device image (reflectors s x k, tau, Q^T b at
- * s <= 512, k <= 128), resident on every GPU that loads the library until the process exits.
+ * fixed 645 KiB array in the library's device image (reflectors s x k, tau, Q^T b and the
+ * k x k compact-WY factor at s <= 512, k <= 128), resident on every GPU that loads the library until the process exits.
  * M (device, s x k column-major), b (device, s), y (device, k) and res (device, 1) belong to
  * the caller.  Sizes with k < 1, k >= s, s > 512 or k > 128 return TK_EINVAL; a CUDA failure
  * returns TK_ECUDA (no message: there is no handle).  The first call on a device looks up the

@@ -26,16 +26,22 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Sum over the block, result returned to every thread.  `scratch` holds >= 33 doubles.
+// Sum over the block, result returned to every thread.  `scratch` holds >= 33 doubles.  The
+// warp partials are combined once by warp 0 (an FP64 warp instruction costs the same whatever
+// its lanes hold, so every thread re-adding them would cost nw times as much).
 __device__ double block_sum(double v, double *scratch) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     v = warp_sum(v);
     __syncthreads();
     if (lane == 0) scratch[warp] = v;
     __syncthreads();
-    double t = 0.0;
-    for (int w = 0; w < nw; ++w) t += scratch[w];
-    return t;
+    if (warp == 0) {
+        double t = lane < nw ? scratch[lane] : 0.0;
+        t = warp_sum(t);
+        if (lane == 0) scratch[32] = t;
+    }
+    __syncthreads();
+    return scratch[32];
 }
 
 // Householder vector in LAPACK dlarfg form: given alpha and sigma2 = ||x||^2 of the part
@@ -1591,11 +1597,160 @@ __global__ void __launch_bounds__(512) k_ls(const double *M, const double *b, in
     if (tid == 0) *st.res = sqrt(r);
 }
 
+// Incremental Householder least squares in compact WY form (Schreiber and Van Loan): the
+// product H_0 ... H_{c-1} of the stored reflectors is I - V T V^T, V unit lower trapezoidal
+// (column j: 1 in row j, v_j below), T upper triangular, grown by one column per reflector:
+// T[0:c, c] = -tau_c T[0:c, 0:c] (V^T v_c), T[c][c] = tau_c.  A new column h is reduced as
+// Q^T h = h - V (T^T (V^T h)): three matrix-vector products whose loads are all independent,
+// instead of c reflector steps each waiting on the previous one.  Reflectors, tau and Q^T b are
+// stored exactly as by the sequential form, so either form may continue the other's state.
+// Back substitution (k <= LSW_BSK): R packed into shared memory, one warp, rows across lanes.
+constexpr int LSW_BSK = 96;
+constexpr int LSW_SHM = LSW_BSK * (LSW_BSK + 1) / 2;           // >= LSW_MAXS + 2 LSW_MAXK
+static_assert(LSW_SHM >= LSW_MAXS + 2 * LSW_MAXK, "shared work area too small");
+__global__ void __launch_bounds__(512) k_ls_wy(const double *M, const double *b, int s, int c0, int k,
+                                               LSState st, int init_qtb) {
+    __shared__ double shm[LSW_SHM];
+    __shared__ double scratch[40];
+    __shared__ double bc[4];
+    double *hs = shm, *z = shm + LSW_MAXS, *u = z + LSW_MAXK;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5, nt = blockDim.x;
+    double *H = st.H, *T = st.T;
+    const long long ldt = st.ldt;
+    if (init_qtb)
+        for (int i = tid; i < s; i += nt) st.qtb[i] = b[i];
+    for (int col = c0; col < k; ++col) {
+        for (int i = tid; i < s; i += nt) hs[i] = M[i + (long long)col * s];
+        __syncthreads();
+        if (col > 0) {
+            // z = V^T h: a warp per reflector, rows across lanes (v_j: 1 in row j, stored below)
+            for (int j = warp; j < col; j += nw) {
+                const double *v = H + (long long)j * s;
+                double p = 0.0;
+                for (int i = j + lane; i < s; i += 32) p = fma(i == j ? 1.0 : v[i], hs[i], p);
+                p = warp_sum(p);
+                if (lane == 0) z[j] = p;
+            }
+            __syncthreads();
+            // u = T^T z
+            for (int j = tid; j < col; j += nt) {
+                const double *tc = T + j * ldt;
+                double a = 0.0;
+                for (int i = 0; i <= j; ++i) a = fma(tc[i], z[i], a);
+                u[j] = a;
+            }
+            __syncthreads();
+            // h -= V u
+            for (int i = tid; i < s; i += nt) {
+                const int jm = min(i, col - 1);
+                double a = 0.0;
+                for (int j = 0; j <= jm; ++j) a = fma(j == i ? 1.0 : H[i + (long long)j * s], u[j], a);
+                hs[i] -= a;
+            }
+            __syncthreads();
+        }
+        // reflector of h[col:]
+        double p = 0.0;
+        for (int i = col + 1 + tid; i < s; i += nt) p = fma(hs[i], hs[i], p);
+        p = block_sum(p, scratch);
+        if (tid == 0) {
+            double tau, beta, scal;
+            householder(hs[col], p, tau, beta, scal);
+            bc[0] = tau; bc[1] = scal; bc[2] = beta;
+            st.tau[col] = tau;
+        }
+        __syncthreads();
+        const double tau = bc[0], scal = bc[1], beta = bc[2];
+        for (int i = col + 1 + tid; i < s; i += nt) hs[i] *= scal;
+        __syncthreads();
+        for (int i = tid; i < s; i += nt) H[i + (long long)col * s] = (i == col) ? beta : hs[i];
+        // new column of T from y = V^T v_col (rows >= col of the earlier reflectors)
+        if (col > 0) {
+            for (int j = warp; j < col; j += nw) {
+                const double *v = H + (long long)j * s;
+                double q = 0.0;
+                for (int i = col + lane; i < s; i += 32) q = fma(v[i], i == col ? 1.0 : hs[i], q);
+                q = warp_sum(q);
+                if (lane == 0) z[j] = q;
+            }
+            __syncthreads();
+            for (int i = tid; i < col; i += nt) {
+                double a = 0.0;
+                for (int l = i; l < col; ++l) a = fma(T[i + l * ldt], z[l], a);
+                T[i + col * ldt] = -tau * a;
+            }
+        }
+        if (tid == 0) T[col + col * ldt] = tau;
+        // Q^T b: the new reflector
+        double q = 0.0;
+        for (int i = col + tid; i < s; i += nt) q = fma(i == col ? 1.0 : hs[i], st.qtb[i], q);
+        q = block_sum(q, scratch);
+        const double f = tau * q;
+        for (int i = col + tid; i < s; i += nt) st.qtb[i] -= (i == col ? 1.0 : hs[i]) * f;
+        __syncthreads();
+    }
+    // back substitution R y = (Q^T b)[0:k]
+    if (k <= LSW_BSK) {
+        double *Rp = shm;                                        // packed upper triangle
+        for (int e = tid; e < k * k; e += nt) {
+            const int i = e % k, j = e / k;
+            if (i <= j) Rp[j * (j + 1) / 2 + i] = H[i + (long long)j * s];
+        }
+        __syncthreads();
+        if (warp == 0) {
+            constexpr int RPL = (LSW_BSK + 31) / 32;             // rows per lane
+            double cv[RPL], dr[RPL];
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) {
+                const int i = lane + 32 * r;
+                cv[r] = i < k ? st.qtb[i] : 0.0;
+                const double d = i < k ? Rp[i * (i + 1) / 2 + i] : 0.0;
+                dr[r] = d != 0.0 ? 1.0 / d : 0.0;               // a zero pivot gives y_j = 0
+            }
+            for (int j = k - 1; j >= 0; --j) {
+                const int rj = j >> 5;
+                double own = 0.0;
+#pragma unroll
+                for (int r = 0; r < RPL; ++r)
+                    if (r == rj) own = cv[r] * dr[r];
+                const double yj = __shfl_sync(0xffffffffu, own, j & 31);
+                if (lane == (j & 31)) st.y[j] = yj;
+                const double *rc = Rp + j * (j + 1) / 2;
+#pragma unroll
+                for (int r = 0; r < RPL; ++r) {
+                    const int i = lane + 32 * r;
+                    if (i < j) cv[r] = fma(-rc[i], yj, cv[r]);
+                }
+            }
+        }
+    } else {
+        for (int i = tid; i < k; i += nt) st.y[i] = st.qtb[i];
+        __syncthreads();
+        for (int j = k - 1; j >= 0; --j) {
+            if (tid == 0) {
+                const double rjj = H[j + (long long)j * s];
+                st.y[j] = rjj != 0.0 ? st.y[j] / rjj : 0.0;
+            }
+            __syncthreads();
+            const double yj = st.y[j];
+            for (int i = tid; i < j; i += nt) st.y[i] -= H[i + (long long)j * s] * yj;
+            __syncthreads();
+        }
+    }
+    double r = 0.0;
+    for (int i = k + tid; i < s; i += nt) r = fma(st.qtb[i], st.qtb[i], r);
+    r = block_sum(r, scratch);
+    if (tid == 0) *st.res = sqrt(r);
+}
+
 void ls_update(Ctx &c, const double *M, const double *b, int s, int c0, int k, const LSState &st,
                int init_qtb) {
     TK_REQUIRE(s >= 1 && s <= 4096 && k >= 1 && k < s + 1, "least squares: bad size");
     c.pre_launch();
-    k_ls<<<1, 512, 0, c.st>>>(M, b, s, c0, k, st, init_qtb);
+    if (st.T && s <= LSW_MAXS && k <= LSW_MAXK && k <= st.ldt)
+        k_ls_wy<<<1, 512, 0, c.st>>>(M, b, s, c0, k, st, init_qtb);
+    else
+        k_ls<<<1, 512, 0, c.st>>>(M, b, s, c0, k, st, init_qtb);
     c.check_launch("ls");
 }
 

@@ -17,16 +17,19 @@
 #include "tk_internal.cuh"
 
 namespace tk {
-// The incremental Householder least-squares kernel of k_linalg.cu.
-__global__ void k_ls(const double *M, const double *b, int s, int c0, int k, LSState st, int init_qtb);
+// The compact WY Householder least-squares kernel of k_linalg.cu.
+__global__ void k_ls_wy(const double *M, const double *b, int s, int c0, int k, LSState st, int init_qtb);
 }  // namespace tk
 
 namespace {
 
 constexpr int kMaxRows = 512;   // largest s accepted
 constexpr int kMaxCols = 128;   // largest k accepted
-// Reflectors (s x k, leading dimension s), tau (k) and Q^T b (s) at their largest sizes.
-constexpr size_t kScratchDoubles = (size_t)kMaxRows * kMaxCols + kMaxCols + kMaxRows;
+static_assert(kMaxRows <= tk::LSW_MAXS && kMaxCols <= tk::LSW_MAXK, "limits beyond the WY kernel's");
+// Reflectors (s x k, leading dimension s), tau (k), Q^T b (s) and the WY factor T (k x k,
+// leading dimension kMaxCols) at their largest sizes.
+constexpr size_t kScratchDoubles =
+    (size_t)kMaxRows * kMaxCols + kMaxCols + kMaxRows + (size_t)kMaxCols * kMaxCols;
 
 static __device__ __align__(256) double g_ls_scratch[kScratchDoubles];
 
@@ -68,10 +71,13 @@ extern "C" int tk_sketched_ls_static(const double *M, const double *b, int32_t s
     st.H = base;
     st.tau = base + (size_t)kMaxRows * kMaxCols;
     st.qtb = st.tau + kMaxCols;
+    st.T = st.qtb + kMaxRows;
+    st.ldt = kMaxCols;
     st.y = y;
     st.res = res;
     // Every scratch word the kernel reads it has written earlier in the same call (Q^T b is
-    // initialised from b, each reflector column before use), so nothing needs clearing.
-    tk::k_ls<<<1, 512, 0, static_cast<cudaStream_t>(stream)>>>(M, b, s, 0, k, st, 1);
+    // initialised from b, each reflector column and each column of T before use), so nothing
+    // needs clearing.
+    tk::k_ls_wy<<<1, 512, 0, static_cast<cudaStream_t>(stream)>>>(M, b, s, 0, k, st, 1);
     return cudaGetLastError() == cudaSuccess ? TK_OK : TK_ECUDA;
 }

@@ -169,6 +169,8 @@ static void solve_rhosvd(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tuck
     ls.tau = c.arena->alloc(kmax);
     ls.qtb = c.arena->alloc(s);
     ls.y = c.arena->alloc(kmax);
+    ls.T = c.arena->alloc((size_t)kmax * kmax);
+    ls.ldt = kmax;
     ls.res = sc + SC_RES;
 
     so.status = kmax < o.maxit ? TK_SKETCH_EXHAUSTED : TK_NOT_CONVERGED;
@@ -285,6 +287,8 @@ static void solve_gmres(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucke
     ls.tau = c.arena->alloc(kmax);
     ls.qtb = c.arena->alloc(ld);
     ls.y = c.arena->alloc(kmax);
+    ls.T = c.arena->alloc((size_t)kmax * kmax);
+    ls.ldt = kmax;
     ls.res = sc + SC_RES;
     readback(c, pinned, sc, 4);
     const double beta = pinned[SC_BETA];
@@ -455,6 +459,8 @@ static void solve_mln(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucker 
     ls.tau = c.arena->alloc(kmax);
     ls.qtb = c.arena->alloc(rp);
     ls.y = c.arena->alloc(kmax);
+    ls.T = c.arena->alloc((size_t)kmax * kmax);
+    ls.ldt = kmax;
     ls.res = sc + SC_RES;
 
     so.status = kmax < o.maxit ? TK_SKETCH_EXHAUSTED : TK_NOT_CONVERGED;
@@ -1099,6 +1105,10 @@ int tk_sketched_ls(tk_handle *h, const double *M, const double *b, int32_t s, in
         st.H = c.arena->alloc((size_t)s * k);
         st.tau = c.arena->alloc(k);
         st.qtb = c.arena->alloc(s);
+        if (k <= LSW_MAXK) {
+            st.T = c.arena->alloc((size_t)k * k);
+            st.ldt = k;
+        }
         st.y = y;
         st.res = res;
         ls_update(c, M, b, s, 0, k, st, 1);

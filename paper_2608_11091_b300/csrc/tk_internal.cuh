@@ -201,7 +201,11 @@ struct LSState {
     double *qtb;      // s: Q^T b (rows updated incrementally)
     double *y;        // kmax
     double *res;      // 1: ||M y - b||
+    double *T;        // optional, kmax x kmax (ld ldt): the compact WY factor of the reflectors
+    int ldt;
 };
+// Compact WY least squares (T set, s <= LSW_MAXS rows, k <= LSW_MAXK columns).
+constexpr int LSW_MAXS = 1024, LSW_MAXK = 256;
 // Processes columns [c0, k) of M (s x k, lda = s) and solves for y_k.
 void ls_update(Ctx &c, const double *M, const double *b, int s, int c0, int k, const LSState &st,
                int init_qtb);
