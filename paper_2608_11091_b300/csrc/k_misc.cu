@@ -1,7 +1,11 @@
 // Structured and elementwise kernels of the Tucker sGMRES hot path.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "tk_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace tk {
 
@@ -309,20 +313,37 @@ struct DotJobs {
     DotJob j[32];
 };
 
+// One 8-CTA cluster per dot product: each CTA sums a contiguous eighth (one SM's FP64 pipe
+// would otherwise take every FMA), warp 0 combines its warps, and CTA 0 adds the eight
+// partials in rank order, so the result depends only on n, never on the batching.
+constexpr int DOT_CL = 8;
 __global__ void __launch_bounds__(1024) k_dots(const __grid_constant__ DotJobs J) {
-    const DotJob &D = J.j[blockIdx.x];
+    cg::cluster_group cl = cg::this_cluster();
+    const int q = (int)cl.block_rank();
+    const DotJob &D = J.j[blockIdx.x / DOT_CL];
+    const long long chunk = (D.n + DOT_CL - 1) / DOT_CL;
+    const long long i0 = q * chunk, i1 = min(D.n, i0 + chunk);
     double acc = 0.0;
-    for (long long i = threadIdx.x; i < D.n; i += blockDim.x) acc = fma(D.x[i], D.y[i], acc);
-    __shared__ double sh[32];
+    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc = fma(D.x[i], D.y[i], acc);
+    __shared__ double sh[33];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) sh[warp] = acc;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (warp == 0) {
+        double t = lane < nw ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) sh[32] = t;
+    }
+    cl.sync();
+    if (q == 0 && threadIdx.x == 0) {
         double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        for (int r = 0; r < DOT_CL; ++r) t += cl.map_shared_rank(sh, r)[32];
         *D.out = t;
     }
+    cl.sync();   // keep every CTA's partial alive until CTA 0 has read it
 }
 
 void dots(Ctx &c, const std::vector<DotJob> &jobs) {
@@ -330,8 +351,19 @@ void dots(Ctx &c, const std::vector<DotJob> &jobs) {
         DotJobs J{};
         J.n = (int)std::min<size_t>(32, jobs.size() - base);
         for (int i = 0; i < J.n; ++i) J.j[i] = jobs[base + i];
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)(J.n * DOT_CL), 1, 1);
+        cfg.blockDim = dim3(1024, 1, 1);
+        cfg.stream = c.st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = DOT_CL;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
         c.pre_launch();
-        k_dots<<<J.n, 1024, 0, c.st>>>(J);
+        TK_CUDA(cudaLaunchKernelEx(&cfg, k_dots, J));
         c.check_launch("dots");
     }
 }
