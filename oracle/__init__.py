@@ -10,7 +10,10 @@ Plain, slow and written to be checked against the paper by eye:
   operators.py Section 1 Eq.(1.2) separable operators applied to Tucker tensors
   rhosvd.py    Section 3.1       RoundSum: Khatri-Rao sketched randomized HOSVD + ST-HOSVD
   mln.py       Section 3.3       MLN_Sketch / MLN_Sum / MLN_Recovery (Algorithms 3-5)
-  sgmres.py    Algorithms 2, 6   RHOSVD-Tucker sGMRES, MLN-Tucker sGMRES; dense sGMRES (Eq. 2.8)
+  sgmres.py    Algorithms 1, 2, 6   RHOSVD-Tucker GMRES and sGMRES, MLN-Tucker sGMRES (with the
+               memory-efficient sketches); dense sGMRES (Eq. 2.8); Section 4.3 projected
+               Tikhonov with the GCV parameter
+  precond.py   Section 3.4       exponential-sum inverse Laplacian, the flexible iteration's preconditioner
   residual.py  Algorithm 1-2 output contract   true relative residual in Tucker form
   adjoint.py   (no counterpart in the paper)   gradients of a loss through the solve
 
