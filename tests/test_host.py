@@ -97,3 +97,39 @@ def test_replica_aggregation_over_two_gloo_ranks():
 def test_single_process_aggregation_is_identity():
     import bench
     assert bench.aggregate_over_ranks(1.5, 7, "cpu") == (1.5, 7.0)
+
+
+def _bench(args, env_extra=None, timeout=300):
+    import json
+    import subprocess
+    import sys
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=timeout)
+    lines = [ln for ln in p.stdout.splitlines() if ln.startswith("{")]
+    return p.returncode, [json.loads(ln) for ln in lines]
+
+
+def test_reference_arm_json_contract():
+    """bench.py --impl reference: the oracle timed on the host cores, one JSON line with the
+    contract's keys (the reference arm of the benchmark, no GPU involved)."""
+    rc, lines = _bench(["--impl", "reference", "--steps", "1", "--warmup", "0"])
+    assert rc == 0 and len(lines) == 1
+    d = lines[0]
+    for key in ["metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"]:
+        assert key in d, key
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "iters/s"
+    assert d["config"]["workload"] == "convdiff3d_n256"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_reference_arm_other_ranks_do_no_work():
+    """Under torchrun only rank 0 runs and prints the reference line; the others exit 0 silently."""
+    rc, lines = _bench(["--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0"],
+                       {"RANK": "1", "LOCAL_RANK": "1", "WORLD_SIZE": "2"}, timeout=120)
+    assert rc == 0 and lines == []
