@@ -133,3 +133,34 @@ def test_reference_arm_other_ranks_do_no_work():
     rc, lines = _bench(["--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0"],
                        {"RANK": "1", "LOCAL_RANK": "1", "WORLD_SIZE": "2"}, timeout=120)
     assert rc == 0 and lines == []
+
+
+def test_ctypes_structs_match_the_header_layout(tmp_path):
+    """Every struct the binding mirrors has, in the C header compiled by gcc, the same size and
+    the same field offsets as its ctypes definition: a field added, dropped, retyped or moved on
+    one side only would otherwise corrupt every call silently."""
+    import shutil
+    import subprocess
+    from paper_2608_11091_b300 import _lib as L
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    structs = {name: getattr(L, name) for name in ["tk_tucker", "tk_modemat", "tk_operator", "tk_opts", "tk_report"]}
+    src = ['#include <stddef.h>', '#include <stdio.h>', '#include "tuckersgmres.h"', 'int main(void) {']
+    for name, cls in structs.items():
+        src.append(f'  printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            src.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    src.append('  return 0;\n}')
+    c_file, exe = tmp_path / "layout.c", tmp_path / "layout"
+    c_file.write_text("\n".join(src) + "\n")
+    subprocess.run([gcc, "-std=c11", "-Wall", "-I", os.path.join(ROOT, "include"), str(c_file), "-o", str(exe)],
+                   check=True, capture_output=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        name, field, value = line.split()
+        got[(name, field)] = int(value)
+    for name, cls in structs.items():
+        assert got[(name, "sizeof")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
