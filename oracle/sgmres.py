@@ -72,15 +72,17 @@ def gcv_function(sig: np.ndarray, bhat: np.ndarray, rho2: float, m: int, lam: fl
     return num / (m - float(np.sum(f))) ** 2
 
 
-def ls_tikhonov(m_mat: np.ndarray, b: np.ndarray):
+def ls_tikhonov(m_mat: np.ndarray, b: np.ndarray, rows: Optional[int] = None):
     """Projected Tikhonov step (Section 4.3, Eq. for the sketched / Hessenberg problem): lambda by
     GCV over gcv_grid (ties: the smaller lambda), then y = V diag(sig / (sig^2 + lam^2)) U^T b.
-    Returns y, ||M y - b||, lambda."""
+    GCV counts the problem's rows (m_mat's, unless `rows` is given).  Returns y, ||M y - b||,
+    lambda."""
     u, sig, vt = np.linalg.svd(m_mat, full_matrices=False)
     bhat = u.T @ b
     rho2 = max(float(b @ b - bhat @ bhat), 0.0)
     grid = gcv_grid(float(sig[0]) if sig.size else 0.0)
-    vals = [gcv_function(sig, bhat, rho2, m_mat.shape[0], lam) for lam in grid]
+    m = m_mat.shape[0] if rows is None else rows
+    vals = [gcv_function(sig, bhat, rho2, m, lam) for lam in grid]
     lam = float(grid[int(np.argmin(vals))])
     y = vt.T @ (sig / (sig ** 2 + lam ** 2) * bhat)
     return y, float(np.linalg.norm(m_mat @ y - b)), lam
@@ -88,9 +90,13 @@ def ls_tikhonov(m_mat: np.ndarray, b: np.ndarray):
 
 def rhosvd_sgmres(op: Operator, b: Tucker, prm: SolverParams, transpose: bool = False,
                   bf16_sketch: bool = False, maxit: Optional[int] = None,
-                  precond: Optional[Operator] = None) -> Result:
+                  precond: Optional[Operator] = None, gcv_rows: str = "sketch") -> Result:
     """Algorithm 2.  bf16_sketch rounds RoundSum's Gaussian matrices to bfloat16 values (the
     mixed-precision form stores them so); the arithmetic stays FP64.
+
+    gcv_rows (with prm.tikhonov): the row count GCV uses for the sketched problem, "sketch" (s,
+    the reading the library implements) or "projected" (k + 1, the dimension of the span of
+    [M_k, S b] in which the sketched residual lives; the alternative reading, oracle only).
 
     precond: a separable operator M applied with truncation, Z_k = RoundSum(M(V_k)), in the
     flexible form of Section 3.4: the Krylov columns sketch RoundSum(L(Z_k)) and the solution is
@@ -140,7 +146,8 @@ def rhosvd_sgmres(op: Operator, b: Tucker, prm: SolverParams, transpose: bool = 
         w = rs([(1.0, w)] + [(-h, v[j - 1]) for h, j in zip(hs, window)])
         nw = norm(w)
         if prm.tikhonov:
-            y, res, _ = ls_tikhonov(np.stack(mcols, axis=1), bs)
+            y, res, _ = ls_tikhonov(np.stack(mcols, axis=1), bs,
+                                    rows=len(mcols) + 1 if gcv_rows == "projected" else None)
         else:
             y, res = _ls(mcols, bs)
         hist.append(res / beta_s)
@@ -215,12 +222,12 @@ def rhosvd_gmres(op: Operator, b: Tucker, prm: SolverParams, transpose: bool = F
 
 
 def mln_sgmres(op: Operator, b: Tucker, prm: SolverParams, transpose: bool = False,
-               maxit: Optional[int] = None) -> Result:
+               maxit: Optional[int] = None, gcv_rows: str = "sketch") -> Result:
     """Algorithm 6, r = rank_cap, r + p sketch columns.  With prm.r_sol > 0 (save_memory): once a
     basis tensor leaves the window (iteration i > k_trunc drops V_{i - k_trunc}) its stored
     sketch is cut to r_sol + p_sol (mln_downsample); at the end the sketches still in the
     window are cut too, and the solution is recovered at rank r_sol with the leading
-    r_sol + p_sol columns of each Psi_k."""
+    r_sol + p_sol columns of each Psi_k.  gcv_rows: as for rhosvd_sgmres ("sketch": r + p rows)."""
     d, n = b.d, b.n
     r = prm.rank_cap
     rp = r + prm.oversample_p
@@ -253,7 +260,8 @@ def mln_sgmres(op: Operator, b: Tucker, prm: SolverParams, transpose: bool = Fal
         w = mln_recovery(gw, psis)
         nw = norm(w)
         if prm.tikhonov:
-            y, res, _ = ls_tikhonov(np.stack(mcols, axis=1), bs)
+            y, res, _ = ls_tikhonov(np.stack(mcols, axis=1), bs,
+                                    rows=len(mcols) + 1 if gcv_rows == "projected" else None)
         else:
             y, res = _ls(mcols, bs)
         hist.append(res / beta_s)

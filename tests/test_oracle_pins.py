@@ -649,3 +649,21 @@ def test_coarse_rhs_compression_removes_semi_convergence():
     assert raw[2] > raw[1]                       # semi-convergence without compression
     assert comp[0] > comp[1] > comp[2]           # monotone with compression
     assert comp[2] < min(raw)
+
+
+def test_gcv_counting_projected_rows_regularises_the_sketched_solve():
+    """Section 4.3 for the sketched variants: the sketched residual lives in the (k + 1)-dimensional
+    span of [M_k, S b].  GCV counting those k + 1 rows, as it counts Algorithm 1's k + 1 Hessenberg
+    rows, keeps Algorithm 2's error flat from 20 to 40 iterations on noisy deblurring (n = 32);
+    counting the sketch's s = 128 rows (the reading the library implements) lets it grow."""
+    wl = W.deblur3d_noisy(32, 0, None)
+    xt = T.full(wl.x_true)
+    errs = {}
+    for rows in ["sketch", "projected"]:
+        errs[rows] = []
+        for it in [20, 40]:
+            prm = W.SolverParams('rhosvd', 32, 128, 5, it, 1e-12, seed=0, tikhonov=True)
+            x = S.rhosvd_sgmres(wl.op, wl.b, prm, gcv_rows=rows).x
+            errs[rows].append(np.linalg.norm(T.full(x) - xt) / np.linalg.norm(xt))
+    assert errs["sketch"][1] > 1.1 * errs["sketch"][0]
+    assert errs["projected"][1] < 1.02 * errs["projected"][0]
