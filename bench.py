@@ -1,19 +1,25 @@
 #!/usr/bin/env python
-"""Throughput of Tucker-format sketched GMRES on B300.
+"""Time to relative residual 1e-6 of Tucker-format sketched GMRES on B300, mixed+adjoint vs FP64.
 
-One step = one complete RHOSVD-Tucker sGMRES solve (Algorithm 2) of the workload: every
-iteration's Tucker matvec, RoundSum recompression, Kronecker sketch, short-recurrence
-orthogonalisation and sketched least-squares update, then the final RoundSum assembly.
-The metric is Krylov iterations per second (higher is better); the timed steps run with the
-inputs resident in HBM and L2 flushed (256 MiB write) between steps.  `e2e` repeats the
-steps through the public API with the right-hand side and the operator copied from pinned
-host memory and the solution copied back inside the timed region.
+Workload (the largest configuration): 3-D Poisson, n = 1024 per mode (N = 1.07e9, never formed),
+right-hand side of multilinear rank (8,8,8) with seeded smooth factors, rank cap 64, Krylov
+sketch s = 256, RoundSum oversampling 5, flexible RHOSVD-Tucker sGMRES (Algorithm 2) with the
+exponential-sum inverse-Laplacian preconditioner of Section 3.4 (q = 16, 33 terms), tol 1e-6.
+
+One step = one gradient evaluation: the forward solve to the tolerance, the adjoint solve
+L^T mu = w of the quantity of interest l = <w, x> (w smooth, rank 1) to the same tolerance and the
+adjoint contractions dl/dtheta, dl/dG_b, dl/dU_b (every step of the path in the library's
+kernels).  `value` is the seconds per step of the mixed form (BF16 sketches and tensor-core
+products with FP32 accumulation, FP64 QR/SVD/least squares); `config.fp64_seconds` is the same
+step in plain FP64 and `config.mixed_speedup` their ratio.  Inputs are resident in HBM and L2 is
+flushed (256 MiB write) between steps; `e2e` repeats the step through the public API with the
+right-hand side, operator and weight copied from pinned host memory and x, mu and the gradients
+read back inside the timed region.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
---impl reference times the FP64 CPU oracle on the same workload (a bounded sample of
-iterations per step).  Under torchrun every rank runs independent replicas (different
-seeds); there is no data-path collective.
+--impl reference times the FP64 CPU oracle on the same step.  Under torchrun every rank runs
+independent replicas (different seeds); there is no data-path collective.
 """
 from __future__ import annotations
 
@@ -21,6 +27,7 @@ import argparse
 import copy
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -30,7 +37,9 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-DEFAULT_WORKLOAD = "convdiff3d_n256"
+DEFAULT_WORKLOAD = "poisson3d_n1024"
+PRECOND_Q = 16
+TOL = 1e-6
 METRIC = "time to rel. residual 1e-6 and iters/s: mixed+adjoint vs plain FP64 on 1 B300"
 
 
@@ -42,6 +51,7 @@ def parse():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-extras", action="store_true", help="skip the cpu_baseline and secondary workloads")
+    ap.add_argument("--profile-only", action="store_true", help="one step of each form with the kernel profile")
     return ap.parse_args()
 
 
@@ -120,59 +130,159 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------
-def oracle_timing(name: str, seed: int, budget_s: float):
-    """The FP64 oracle as it stands, on this host: Krylov iterations/s over a bounded sample."""
-    import workloads as W
-    from oracle import sgmres as OS
+def host_cpu() -> dict:
+    model = platform.processor() or ""
     try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    try:
+        import numpy  # noqa: F401  (loads the BLAS whose thread pool the oracle uses)
         from threadpoolctl import threadpool_info
         cores = max([int(i.get("num_threads", 1)) for i in threadpool_info()] + [1])
     except Exception:
         cores = os.cpu_count() or 1
+    return {"cpu_model": model, "cores": cores, "nproc": os.cpu_count()}
+
+
+def qoi_weight_np(n: int, d: int):
+    """w of the quantity of interest l = <w, x>: the smooth rank-1 tensor (1/sqrt(n))^(x)d."""
+    import numpy as np
+    import workloads as W
+    return W.Tucker(np.ones((1,) * d), [np.ones((n, 1)) / np.sqrt(n)] * d)
+
+
+def oracle_step(name: str, seed: int, maxit=None):
+    """The FP64 oracle as it stands on this host: the step the GPU arm times (forward solve to the
+    tolerance, adjoint solve, adjoint contractions) with the same preconditioner and streams.
+    Returns (seconds, forward iterations, adjoint iterations)."""
+    import workloads as W
+    from oracle import adjoint as OA
+    from oracle import precond as OP
+    from oracle import sgmres as OS
     wl = W.workload(name, seed=seed)
-    prm = wl.params
-    iters, t0 = 0, time.perf_counter()
-    runs = 0
-    while True:
-        per = min(prm.maxit, 12)
-        r = (OS.rhosvd_sgmres if prm.variant == "rhosvd" else OS.mln_sgmres)(wl.op, wl.b, prm, maxit=per)
-        iters += r.iters
-        runs += 1
-        if time.perf_counter() - t0 >= budget_s:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": iters / dt, "unit": "iters/s", "cores": cores, "kind": "oracle",
-            "sample": f"{runs} solve(s) of {name} truncated at {min(prm.maxit, 12)} iterations "
-                      f"(numpy FP64, {iters} iterations in {dt:.1f} s)"}
+    prm = copy.copy(wl.params)
+    prm.tol = TOL
+    if maxit:
+        prm.maxit = maxit
+    t0 = time.perf_counter()
+    pc = OP.expsum_preconditioner(wl.b.n[0], wl.b.d, PRECOND_Q)
+    fw = OS.rhosvd_sgmres(wl.op, wl.b, prm, precond=pc)
+    ad = OS.rhosvd_sgmres(wl.op, qoi_weight_np(wl.b.n[0], wl.b.d), prm, transpose=True, precond=pc)
+    OA.theta_gradients(wl.op, fw.x, ad.x)
+    OA.core_gradient(ad.x, wl.b)
+    OA.factor_gradients(ad.x, wl.b)
+    return time.perf_counter() - t0, fw.iters, ad.iters
+
+
+def oracle_baseline(name: str, budget_s: float, gpu_iters: int):
+    """Bounded sample for cpu_baseline: oracle steps cut at 1 iteration per solve until the budget
+    is used, giving seconds per Krylov iteration; scaled to the seconds the full step needs at the
+    iteration count the GPU FP64 step took."""
+    host = host_cpu()
+    t, its, n = 0.0, 0, 0
+    while t < budget_s or n == 0:
+        dt, fi, ai = oracle_step(name, 0, maxit=1)
+        t += dt
+        its += fi + ai
+        n += 1
+    per_it = t / its
+    return {"value": per_it * gpu_iters, "unit": "s", "cores": host["cores"], "kind": "oracle",
+            "cpu_model": host["cpu_model"], "nproc": host["nproc"],
+            "sample": f"{n} oracle step(s) of {name} cut at 1 forward + 1 adjoint iteration (numpy FP64, "
+                      f"{t:.1f} s, {per_it:.3f} s per Krylov iteration), scaled to the {gpu_iters} iterations "
+                      f"of the GPU FP64 step"}
 
 
 def run_reference(args):
     ws, rank, _ = dist_info()
     if rank != 0:
         return
-    import workloads as W  # noqa: F401
-    vals = []
-    budget = 8.0
+    host = host_cpu()
+    budget, times, its = 240.0, [], []
+    t_start = time.perf_counter()
     for i in range(args.warmup + args.steps):
-        r = oracle_timing(args.workload, 0, budget if i >= args.warmup else 1.0)
-        if i >= args.warmup:
-            vals.append(r)
-    value = statistics.median([v["value"] for v in vals])
-    line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1000.0 * budget, "higher_is_better": True,
+        if i > 0 and time.perf_counter() - t_start > budget:
+            break                      # bounded: at least one full step is always timed
+        dt, fi, ai = oracle_step(args.workload, 0)
+        if i >= args.warmup or i == 0:
+            times.append(dt)
+            its.append(fi + ai)
+    value = statistics.median(times)
+    line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus, "steps": len(times),
+            "warmup": args.warmup, "ms_per_step": 1000.0 * value, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": args.workload, "solver": "RHOSVD-Tucker sGMRES (Algorithm 2)",
-                       "parallelism": "host cores"},
-            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": vals[0]["cores"], "kind": "oracle",
-                             "sample": vals[0]["sample"]},
-            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": {"workload": args.workload, "solver": "flexible RHOSVD-Tucker sGMRES (Algorithm 2), "
+                                                             "exponential-sum preconditioner q = 16",
+                       "step": "forward solve + adjoint solve + adjoint contractions to rel. residual 1e-6",
+                       "iters_per_step": statistics.median(its), "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": host["cores"], "kind": "oracle",
+                             "cpu_model": host["cpu_model"],
+                             "sample": f"{len(times)} full oracle step(s) (numpy FP64; the run is cut after "
+                                       f"{budget:.0f} s, at least one step)"},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
 # ------------------------------------------------------------------------------------------
 def tucker_bytes(t) -> int:
     return 8 * (t.core.numel() + sum(u.numel() for u in t.factors))
+
+
+class Problem:
+    """The benchmark problem on the device: operator, right-hand side, preconditioner, weight w."""
+
+    def __init__(self, P, W, name, seed):
+        import numpy as np
+        self.wl = W.workload(name, seed=seed)
+        self.prm = copy.copy(self.wl.params)
+        self.prm.tol = TOL
+        n, d = self.wl.b.n[0], self.wl.b.d
+        self.dop = P.DeviceOperator(self.wl.op)
+        self.b = P.DeviceTucker.from_numpy(self.wl.b.core, self.wl.b.factors)
+        wq = qoi_weight_np(n, d)
+        self.w = P.DeviceTucker.from_numpy(wq.core, wq.factors)
+        self.pc = P.tk_expsum_laplacian(n, d, PRECOND_Q)
+        R = self.prm.rank_cap
+        self.x = P.DeviceTucker.empty(self.b.n, [R] * d)
+        self.mu = P.DeviceTucker.empty(self.b.n, [R] * d)
+        self.np = np
+
+    def step(self, P, form):
+        opts = P.Options.from_params(self.prm, precision=form)
+        x, rep = P.tk_solve_precond(self.dop, self.pc, self.b, opts, x=self.x)
+        adj = copy.copy(opts)
+        adj.transpose = True
+        mu, rep_a = P.tk_solve_precond(self.dop, self.pc, self.w, adj, x=self.mu)
+        grads = P.tk_adjoint_grads(self.dop, mu, x, self.b)
+        return rep, rep_a, grads
+
+
+def kernel_table(prof, peaks):
+    """Per kernel: launches, device time, share, and its roofline: FP64 pipe (GEMM, QR, SVD and
+    contraction kernels, algorithmic FP64 flops), BF16 tensor pipe (gemm_tc) or HBM (streaming
+    kernels, algorithmic bytes).  Small launches are latency bound far below these peaks."""
+    total = sum(v[1] for v in prof.values()) or 1.0
+    out = {}
+    for name, (n, ms, fl, by) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
+        e = {"launches": n, "ms": round(ms, 4), "share": round(ms / total, 4), "avg_us": round(1000 * ms / n, 2)}
+        if name == "gemm_tc" and fl > 0:
+            a = fl / (ms * 1e-3) / 1e12
+            e.update({"bound": "tensor", "achieved": round(a, 4), "unit": "TFLOP/s",
+                      "frac": round(a / peaks["bf16_tflops"], 5)})
+        elif fl > 0 and (name.startswith("gemm") or name in ("qr", "svd", "tikhonov", "hadamard")):
+            a = fl / (ms * 1e-3) / 1e12
+            e.update({"bound": "alu", "achieved": round(a, 4), "unit": "TFLOP/s",
+                      "frac": round(a / peaks["fp64_tflops"], 5)})
+        elif by > 0:
+            a = by / (ms * 1e-3) / 1e9
+            e.update({"bound": "hbm", "achieved": round(a, 2), "unit": "GB/s", "frac": round(a / peaks["hbm_gbs"], 5)})
+        out[name] = e
+    return out
 
 
 def run_native(args):
@@ -189,14 +299,12 @@ def run_native(args):
     import workloads as W
 
     name = args.workload
-    wl = W.workload(name, seed=rank)
-    prm = wl.params
-    dop = P.DeviceOperator(wl.op)
-    b = P.DeviceTucker.from_numpy(wl.b.core, wl.b.factors)
-    opts = P.Options.from_params(prm)
-    x = P.DeviceTucker.empty(b.n, [opts.rank_cap] * b.d)
+    prob = Problem(P, W, name, seed=rank)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
+    mp = _peaks()
+    peaks = {"fp64_tflops": P.tk_fma_peak(True), "fp32_tflops": P.tk_fma_peak(False),
+             "bf16_tflops": mp.get("bf16_tflops", 1800.0), "hbm_gbs": mp.get("hbm_gbs", 6400.0)}
 
     def barrier():
         torch.cuda.synchronize()
@@ -204,93 +312,126 @@ def run_native(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(args.warmup):
-        P.tk_solve(dop, b, opts, x=x)
+    def timed(form, steps):
+        evs, its, launches, reps = [], 0, 0, None
+        for i in range(steps):
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rep, rep_a, _ = prob.step(P, form)
+            e1.record(stream)
+            evs.append((e0, e1))
+            its += rep.iters + rep_a.iters
+            launches += rep.kernel_launches + rep_a.kernel_launches
+            reps = (rep, rep_a)
+        barrier()
+        return sum(a.elapsed_time(bb) for a, bb in evs) / 1000.0, its, launches, reps
 
+    for _ in range(args.warmup):
+        prob.step(P, "mixed")
+        prob.step(P, "fp64")
     sampler = ClockSampler(local)
     sampler.start()
     barrier()
-    evs = []
-    iters = launches = 0
-    statuses = []
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        _, rep = P.tk_solve(dop, b, opts, x=x)
-        e1.record(stream)
-        evs.append((e0, e1))
-        iters += rep.iters
-        launches += rep.kernel_launches
-        statuses.append(rep.status)
-    barrier()
+    t_mixed, it_mixed, launches, (rep_m, rep_ma) = timed("mixed", args.steps)
+    k64 = max(1, min(args.steps, 5))
+    t_fp64, it_fp64, _, (rep_f, rep_fa) = timed("fp64", k64)
     clocks = sampler.stop()
-    ms = sum(a.elapsed_time(bb) for a, bb in evs)
-    t_local = ms / 1000.0
-    t_all, it_all = aggregate_over_ranks(t_local, iters, "cuda")
-    value = it_all / t_all
+    t_all, steps_all = aggregate_over_ranks(t_mixed, args.steps, "cuda")
+    sec_mixed = t_all / args.steps            # max over ranks of the per-step time
+    sec_fp64 = t_fp64 / k64
+    # the 1e-6 the step reached: true relative residuals of the last step's x and mu
+    prob.step(P, "mixed")
+    tr_x = P.tk_residual(prob.dop, prob.x, prob.b)
+    tr_mu = P.tk_residual(prob.dop, prob.mu, prob.w, transpose=True)
+    prob.step(P, "fp64")
+    tr_x64 = P.tk_residual(prob.dop, prob.x, prob.b)
+    tr_mu64 = P.tk_residual(prob.dop, prob.mu, prob.w, transpose=True)
 
     # ---------------- e2e through the public API with host buffers
     host_b = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-              for a in [np.asfortranarray(wl.b.core).ravel(order='F')] + [f.ravel(order='F') for f in wl.b.factors]]
-    dev_b = [b.core] + b.factors
+              for a in [np.asfortranarray(prob.wl.b.core).ravel(order='F')] +
+              [f.ravel(order='F') for f in prob.wl.b.factors]]
+    dev_b = [prob.b.core] + prob.b.factors
+    wq = qoi_weight_np(prob.wl.b.n[0], prob.wl.b.d)
+    host_w = [torch.from_numpy(np.ascontiguousarray(a.ravel(order='F'))).pin_memory()
+              for a in [wq.core] + wq.factors]
+    dev_w = [prob.w.core] + prob.w.factors
     host_ops = []
-    for key, t in dop._keep[0].items():
+    for key, t in prob.dop._keep[0].items():
         host_ops.append((torch.from_numpy(np.ascontiguousarray(t.cpu().numpy().ravel(order='F'))).pin_memory(), t))
-    host_x = [torch.empty(t.numel(), dtype=torch.float64).pin_memory() for t in [x.core] + x.factors]
-    h2d = sum(h.numel() * 8 for h in host_b) + sum(h.numel() * 8 for h, _ in host_ops)
-    d2h = sum(h.numel() * 8 for h in host_x)
+    outs_shape = [prob.x.core] + prob.x.factors + [prob.mu.core] + prob.mu.factors
+    host_out = [torch.empty(t.numel(), dtype=torch.float64).pin_memory() for t in outs_shape]
+    nb = prob.wl.b
+    host_g = [torch.empty(int(np.prod(nb.core.shape)), dtype=torch.float64).pin_memory()] + \
+             [torch.empty(f.size, dtype=torch.float64).pin_memory() for f in nb.factors]
+
+    def flat(d):
+        return d.permute(*reversed(range(d.dim()))).reshape(-1)
+
+    h2d = sum(h.numel() * 8 for h in host_b + host_w) + sum(h.numel() * 8 for h, _ in host_ops)
+    d2h = sum(h.numel() * 8 for h in host_out + host_g) + 8 * prob.wl.op.nterms
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    it_e2e = 0
     e0.record(stream)
     for i in range(args.steps):
-        for h, d in zip(host_b, dev_b):
-            d.permute(*reversed(range(d.dim()))).reshape(-1).copy_(h, non_blocking=True)
+        for h, d in list(zip(host_b, dev_b)) + list(zip(host_w, dev_w)):
+            flat(d).copy_(h, non_blocking=True)
         for h, d in host_ops:
-            d.permute(*reversed(range(d.dim()))).reshape(-1).copy_(h, non_blocking=True)
-        _, rep = P.tk_solve(dop, b, opts, x=x)
-        it_e2e += rep.iters
-        for h, d in zip(host_x, [x.core] + x.factors):
-            h.copy_(d.permute(*reversed(range(d.dim()))).reshape(-1), non_blocking=True)
+            flat(d).copy_(h, non_blocking=True)
+        _, _, (dth, dcore, dfac) = prob.step(P, "mixed")
+        for h, d in zip(host_out, outs_shape):
+            h.copy_(flat(d), non_blocking=True)
+        for h, d in zip(host_g, [dcore] + dfac):
+            h.copy_(flat(d), non_blocking=True)
     e1.record(stream)
     barrier()
-    e2e_t = e0.elapsed_time(e1) / 1000.0
-    e2e_tmax, e2e_iters = aggregate_over_ranks(e2e_t, it_e2e, "cuda")
-    e2e_val = e2e_iters / e2e_tmax
+    e2e_t, _ = aggregate_over_ranks(e0.elapsed_time(e1) / 1000.0, args.steps, "cuda")
+    e2e_val = e2e_t / args.steps
 
-    # ---------------- per-kernel device time (library event profiler), one more solve
-    P.tk_profile(True)
-    P.tk_profile_report()
-    _, prep = P.tk_solve(dop, b, opts, x=x)
-    prof = P.tk_profile_report()
-    P.tk_profile(False)
-    total_k = sum(v[1] for v in prof.values())
-    kernels = {k: {"launches": n, "ms": round(m, 4), "share": round(m / total_k, 4) if total_k else None,
-                   "tflops": round(f / (m * 1e-3) / 1e12, 4) if f > 0 and m > 0 else None}
-               for k, (n, m, f) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
-    roofline = roofline_from_profile(prof, wl, opts, prep)
+    # ---------------- per-kernel device time (library event profiler), one step of each form
+    profs = {}
+    for form in ("mixed", "fp64"):
+        P.tk_profile(True)
+        P.tk_profile_report()
+        prob.step(P, form)
+        profs[form] = P.tk_profile_report()
+        P.tk_profile(False)
+    kernels = kernel_table(profs["mixed"], peaks)
+    roofline = roofline_from_profile(profs["mixed"], peaks)
 
     extras = {}
     if rank == 0 and not args.no_extras:
         extras = secondary(P, W, torch)
+        extras["kernels_fp64_step"] = kernel_table(profs["fp64"], peaks)
 
     if rank == 0:
-        cpu = None if args.no_extras else oracle_timing(name, 0, 10.0)
+        cpu = None if args.no_extras else oracle_baseline(name, 20.0, rep_f.iters + rep_fa.iters)
         line = {
-            "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": name, "solver": "RHOSVD-Tucker sGMRES (Algorithm 2)",
-                       "n": wl.b.n, "rhs_rank": wl.b.r, "rank_cap": prm.rank_cap, "sketch_s": prm.sketch_s,
-                       "oversample_p": prm.oversample_p, "ktrunc": prm.ktrunc, "maxit": prm.maxit,
-                       "iters_per_step": iters / args.steps, "status": statuses[-1],
-                       "operator_terms": wl.op.nterms, "l2": "flushed between steps (256 MiB write)",
+            "metric": METRIC, "value": sec_mixed, "unit": "s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * sec_mixed, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16/fp32 products, f64 QR/SVD/LS",
+            "data": "synthetic",
+            "config": {"workload": name, "solver": "flexible RHOSVD-Tucker sGMRES (Algorithm 2), exponential-sum "
+                                                   f"preconditioner q = {PRECOND_Q} ({2 * PRECOND_Q + 1} terms)",
+                       "step": "forward solve + adjoint solve + adjoint contractions to rel. residual 1e-6",
+                       "n": prob.wl.b.n, "rhs_rank": prob.wl.b.r, "rhs": "seeded smooth factors",
+                       "rank_cap": prob.prm.rank_cap, "sketch_s": prob.prm.sketch_s,
+                       "oversample_p": prob.prm.oversample_p, "ktrunc": prob.prm.ktrunc, "tol": TOL,
+                       "mixed_seconds": round(sec_mixed, 5), "fp64_seconds": round(sec_fp64, 5),
+                       "mixed_speedup": round(sec_fp64 / sec_mixed, 4),
+                       "mixed_iters": [rep_m.iters, rep_ma.iters], "fp64_iters": [rep_f.iters, rep_fa.iters],
+                       "mixed_iters_per_s": round(it_mixed / t_mixed, 2), "fp64_iters_per_s": round(it_fp64 / t_fp64, 2),
+                       "true_rel_residual": {"mixed_x": tr_x, "mixed_mu": tr_mu, "fp64_x": tr_x64, "fp64_mu": tr_mu64},
+                       "reached_1e-6": bool(max(tr_x, tr_mu, tr_x64, tr_mu64) <= TOL),
+                       "solves_per_s_all_ranks": round(2 * steps_all / t_all, 3),
+                       "l2": "flushed between steps (256 MiB write)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "clocks": clocks,
             "gpu_launches": launches,
-            "e2e": {"value": e2e_val, "unit": "iters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_val, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "roofline": roofline,
+            "peaks": {k: round(v, 3) for k, v in peaks.items()},
             "kernels": kernels,
             "cpu_baseline": cpu,
             "extras": extras,
@@ -308,25 +449,27 @@ def _peaks():
         return {}
 
 
-FP64_PEAK_TFLOPS = 1.25   # B300 FP64 nominal (148 SMs x DFMA rate at 2032 MHz); 1.13 measured by a DFMA loop
-
-
-def roofline_from_profile(prof, wl, opts, rep):
-    """Dominant kernel (by device time) with its algorithmic FP64 rate against the FP64 ALU peak."""
+def roofline_from_profile(prof, peaks):
+    """Dominant kernel (by device time) of the step with its algorithmic rate against its pipe's
+    measured peak: FP64 FMA rate (tk_fma_peak, measured in this run), BF16 tensor (MEASURED_PEAKS
+    burst figure) or HBM copy bandwidth."""
     if not prof:
         return None
-    name, (n, ms, fl) = max(prof.items(), key=lambda kv: kv[1][1])
-    total = sum(v[1] for v in prof.values())
-    out = {"kernel": name, "launches": n, "avg_us": round(1000.0 * ms / max(n, 1), 3),
-           "share": round(ms / total, 4) if total else None, "traffic": None}
-    if fl > 0:
-        achieved = fl / (ms * 1e-3) / 1e12
-        out.update({"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "flops_per_launch": fl / max(n, 1),
-                    "peak_source": "FP64 nominal (148 SMs x 2 DFMA/clk x 2032 MHz); measured DFMA loop 1.13"})
-    else:
-        out.update({"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": None,
-                    "note": "iterative kernel: no algorithmic flop count"})
+    tab = kernel_table(prof, peaks)
+    name = max(prof.items(), key=lambda kv: kv[1][1])[0]
+    e = tab[name]
+    n, ms, fl, by = prof[name]
+    out = {"kernel": name, "launches": n, "avg_us": e["avg_us"], "share": e["share"], "traffic": None,
+           "bound": e.get("bound"), "achieved": e.get("achieved"), "unit": e.get("unit"), "frac": e.get("frac")}
+    if e.get("bound") == "alu":
+        out.update({"peak": round(peaks["fp64_tflops"], 4), "flops_per_launch": fl / max(n, 1),
+                    "peak_source": "FP64 FMA rate measured in this run (tk_fma_peak, 8 DFMA chains per thread)"})
+    elif e.get("bound") == "tensor":
+        out.update({"peak": peaks["bf16_tflops"], "flops_per_launch": fl / max(n, 1),
+                    "peak_source": "MEASURED_PEAKS bf16_tflops (cuBLAS bf16 GEMM burst)"})
+    elif e.get("bound") == "hbm":
+        out.update({"peak": peaks["hbm_gbs"], "bytes_per_launch": by / max(n, 1),
+                    "peak_source": "MEASURED_PEAKS hbm_gbs (copy)"})
     return out
 
 
@@ -371,83 +514,45 @@ def regularisation_study(P, W, torch):
     return reg
 
 
-def time_to_tol(P, W, torch, tol=1e-6):
-    """Time to true relative residual <= tol, FP64 vs mixed, on the problems that reach it at
-    these ranks: Poisson with the exponential-sum preconditioner (Section 3.4), the paper's
-    point-source setting at n = 1000 and the rank-1 Poisson workload at n = 32.  Forward: the
-    preconditioned solve.  Adjoint: the gradient of the quantity of interest l = <w, x>
-    (w = the unit tensor (1/sqrt(n))^(x)3, smooth and rank 1) w.r.t. the operator coefficients
-    and b: one transposed preconditioned solve L^T mu = w to the same tolerance plus the adjoint
-    contractions.  (A loss like 0.5 ||x - x_ref||^2 has the adjoint right-hand side x - x_ref, whose
-    rank is already at the cap, so its adjoint solution cannot be represented to 1e-6.)  Wall time,
-    device synchronised."""
-    import copy
-    res = {}
-    cases = [("poisson3d_point_n1000_q8", W.workload("poisson3d_point_n1000"), 8),
-             ("poisson3d_n32_cap12_q8", W.workload("poisson3d_n32"), 8)]
-    for name, wl, q in cases:
-        prm = copy.copy(wl.params)
-        if name.startswith("poisson3d_n32"):
-            prm = W.SolverParams('rhosvd', 12, 64, 5, 30, tol, seed=0)
-        prm.tol = tol
-        n = wl.b.n[0]
-        dop = P.DeviceOperator(wl.op)
-        b = P.DeviceTucker.from_numpy(wl.b.core, wl.b.factors)
-        pc = P.tk_expsum_laplacian(n, wl.b.d, q)
-        import numpy as np
-        unit = np.ones((n, 1)) / np.sqrt(n)
-        wq = P.DeviceTucker.from_numpy(np.ones((1,) * wl.b.d), [unit] * wl.b.d)
-        entry = {}
-        for form in ["fp64", "mixed"]:
-            opts = P.Options.from_params(prm, precision=form)
-            adj = copy.copy(opts)
-            adj.transpose = True
-
-            def run():
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                x, rep = P.tk_solve_precond(dop, pc, b, opts)
-                torch.cuda.synchronize()
-                t1 = time.perf_counter()
-                mu, rep_a = P.tk_solve_precond(dop, pc, wq, adj)
-                P.tk_adjoint_grads(dop, mu, x, b)
-                torch.cuda.synchronize()
-                t2 = time.perf_counter()
-                return x, rep, rep_a, t1 - t0, t2 - t1
-
-            run()   # warm-up
-            x, rep, rep_a, tf, tb = run()
-            tr = P.tk_residual(dop, x, b)
-            entry[form] = {"forward_s": round(tf, 4), "forward_iters": rep.iters, "true_rel_residual": tr,
-                           "reached": bool(tr <= tol), "adjoint_s": round(tb, 4), "adjoint_iters": rep_a.iters,
-                           "forward_plus_adjoint_s": round(tf + tb, 4)}
-        entry["mixed_over_fp64_speedup"] = round(entry["fp64"]["forward_plus_adjoint_s"] /
-                                                 entry["mixed"]["forward_plus_adjoint_s"], 3)
-        res[name] = entry
-    return res
-
-
 def secondary(P, W, torch):
     """Other workloads of the method, FP64 and mixed form, one solve each after a warm-up
-    (reported, not the headline), and the cost of a gradient (forward + adjoint solve)."""
+    (reported, not the headline): iterations/s, true residual, and the mixed result's distance
+    from the FP64 one (relative Tucker-form difference of the solutions; the two forms draw
+    different sketch matrices, so this is the randomized compression's own spread plus the
+    reduced-precision error)."""
     out = {}
-    for name in ["convdiff3d_n256", "poisson3d_n32", "deblur3d_n128", "varcoef4d_n128", "poisson3d_n1024"]:
+    for name in ["convdiff3d_n256", "poisson3d_n32", "deblur3d_n128", "varcoef4d_n128", "poisson3d_n1024_gaussian"]:
         wl = W.workload(name)
         prm = wl.params
-        if name == "poisson3d_n1024":
+        pc = None
+        if name == "poisson3d_n1024_gaussian":
             prm.maxit = 10
+            pc = P.tk_expsum_laplacian(wl.b.n[0], wl.b.d, PRECOND_Q)
         dop = P.DeviceOperator(wl.op)
         b = P.DeviceTucker.from_numpy(wl.b.core, wl.b.factors)
         entry = {"variant": prm.variant}
         forms = ["fp64", "mixed"] if prm.variant == "rhosvd" else ["fp64"]
+        xs = {}
         for form in forms:
             opts = P.Options.from_params(prm, precision=form)
-            P.tk_solve(dop, b, opts)                     # warm-up (workspace, module load)
-            x, rep, dt = _timed_solve(P, torch, dop, b, opts)
+
+            def solve():
+                if pc is None:
+                    return P.tk_solve(dop, b, opts)
+                return P.tk_solve_precond(dop, pc, b, opts)
+            solve()                     # warm-up (workspace, module load)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            x, rep = solve()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            xs[form] = x
             tr = P.tk_residual(dop, x, b)
             entry[form] = {"iters": rep.iters, "status": rep.status, "seconds": round(dt, 4),
-                           "iters_per_s": round(rep.iters / dt, 2), "sketched_res": rep.sketched_res,
-                           "true_rel_residual": tr, "time_to_1e-6_s": round(dt, 4) if tr <= 1e-6 else None}
+                           "iters_per_s": round(rep.iters / dt, 2), "sketched_res": float(f"{rep.sketched_res:.4g}"),
+                           "true_rel_residual": float(f"{tr:.4g}")}
+        if len(xs) == 2:
+            entry["mixed_vs_fp64_rel_diff_x"] = float(f"{P.tk_sum_norm([xs['mixed'], xs['fp64']], [1.0, -1.0]) / P.tk_sum_norm([xs['fp64']], [1.0]):.3g}")
         out[name] = entry
     # the paper's preconditioned Poisson setting: exponential-sum preconditioner (Section 3.4),
     # flexible iteration, rank-1 point-source right-hand side, n = 1000
@@ -508,7 +613,6 @@ def secondary(P, W, torch):
         cmp[variant] = {"iters": rep.iters, "seconds": round(dt, 4), "iters_per_s": round(rep.iters / dt, 2),
                         "res_hist_last": rep.res_hist[-1], "true_rel_residual": P.tk_residual(dop, x, b)}
     out["gmres_vs_sgmres_convdiff3d_n256_30it"] = cmp
-    out["time_to_1e-6"] = time_to_tol(P, W, torch)
     # gradient of 0.5||x - x_ref||^2 w.r.t. theta and b: forward solve + adjoint solve + contractions
     wl = W.workload("deblur3d_n128")
     prm = wl.params
@@ -540,6 +644,8 @@ def secondary(P, W, torch):
 
 def main():
     args = parse()
+    if args.impl == "native" and args.profile_only:
+        args.no_extras = True
     if args.impl == "reference":
         run_reference(args)
     else:

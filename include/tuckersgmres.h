@@ -36,6 +36,8 @@ typedef enum {
     TK_NOT_CONVERGED = 1,       /* maxit iterations ran; x is the last iterate                */
     TK_BREAKDOWN = 2,           /* ||W|| ~ 0: the Krylov space is invariant; x is final       */
     TK_SKETCH_EXHAUSTED = 3,    /* the iteration count reached sketch size - 1                */
+    TK_SUSPENDED = 4,           /* opts->stop_after iterations ran; the Krylov state is held  */
+                                /* by the handle (tk_checkpoint_save), x is not written       */
     TK_EINVAL = -1,             /* invalid argument (shape, kind, null pointer, size limit)   */
     TK_ENOMEM = -2,             /* device allocation failed                                   */
     TK_ECUDA = -3,              /* a CUDA runtime call or kernel launch failed                 */
@@ -99,6 +101,18 @@ typedef struct {
     int32_t gcv_tikhonov;   /* 1: projected Tikhonov in every least-squares step, the parameter    */
                             /* chosen by GCV over sigma_max 10^(-12+12g/120), g = 0..120          */
                             /* (Section 4.3); needs at most 96 iterations                          */
+    int32_t gcv_rows;       /* rows m in GCV's trace(I - A_lambda) for the sketched variants:     */
+                            /* 0 = k + 1 (the dimension of span[M_k, S b], where the sketched     */
+                            /* residual lives; the count Algorithm 1 uses for its k + 1 x k        */
+                            /* Hessenberg matrix), 1 = every row of the sketch (s, or r + p)      */
+    int32_t stop_after;     /* > 0: suspend after this many iterations of this call if the solve  */
+                            /* has not ended (status TK_SUSPENDED; the handle keeps the Krylov    */
+                            /* state); 0 = run to the end                                          */
+    int32_t resume;         /* 1: continue the solve suspended in this handle (same operator, b,   */
+                            /* preconditioner and options apart from stop_after / resume /        */
+                            /* true_residual); the continued iterations are bit-for-bit those of  */
+                            /* an uninterrupted solve                                              */
+    int32_t true_residual;  /* 1: report->true_res = ||L(x) - b|| / ||b|| of the returned x       */
     double tol;             /* tolerance                                                           */
     double eta;             /* sketched correction factor: stop when res_k < eta * tol             */
     double round_tol;       /* ST-HOSVD tolerance epsilon (RoundSum)                               */
@@ -116,6 +130,7 @@ typedef struct {
     double ms_total;                /* device time of the solve (CUDA events)                   */
     int64_t workspace_bytes;        /* device workspace held by the handle after the solve       */
     int64_t kernel_launches;        /* kernels the library launched for this call                */
+    double true_res;                /* ||L(x) - b|| / ||b|| when opts->true_residual, else -1      */
 } tk_report;
 
 typedef struct tk_handle tk_handle;
@@ -133,10 +148,18 @@ const char *tk_last_error(const tk_handle *h);
  * counterpart; this is measurement plumbing. */
 int tk_profile(tk_handle *h, int32_t enable);
 /* tk_profile_report: per-kernel totals since the last report, one line per kernel name:
- * "<name> <launches> <total_ms> <algorithmic_flops>\n" (flops counted from the shapes for the
- * GEMM and QR kernels, 0 for the others); resets the totals.  Synchronizes on the recorded events.
+ * "<name> <launches> <total_ms> <algorithmic_flops> <algorithmic_bytes>\n" (flops counted from
+ * the shapes for the GEMM, QR, SVD and contraction kernels; bytes, each operand read once and each
+ * result written once, for the streaming kernels; 0 where not defined); resets the totals.  Synchronizes on the recorded events.
  * The returned string is owned by the handle and valid until the next call on it. */
 const char *tk_profile_report(tk_handle *h);
+
+/* tk_fma_peak: measured FMA throughput of the handle's device in TFLOP/s (fp64 = 1: FP64 DFMA,
+ * 0: FP32 FFMA), written to *tflops_host: 8 independent FMA chains per thread over 8 CTAs of
+ * 256 threads per SM, best of three timed launches after a warm-up launch (CUDA events).  The
+ * paper has no counterpart; it is the denominator of the library's ALU rooflines.
+ * Synchronizes. */
+int tk_fma_peak(tk_handle *h, int32_t fp64, double *tflops_host, void *stream);
 
 /* tk_solve: RHOSVD-Tucker sGMRES (Algorithm 2), MLN-Tucker sGMRES (Algorithm 6) or
  * RHOSVD-Tucker GMRES (Algorithm 1, opts->variant) for L(X) = B (or L^T(X) = B when
@@ -154,6 +177,32 @@ int tk_solve(tk_handle *h, const tk_operator *op, const tk_tucker *b, const tk_o
  * tk_solve; TK_EINVAL for the MLN variant or a NULL precond. */
 int tk_solve_precond(tk_handle *h, const tk_operator *op, const tk_operator *precond, const tk_tucker *b,
                      const tk_opts *opts, tk_tucker *x_out, tk_report *report, void *stream);
+
+/* tk_checkpoint_save / tk_checkpoint_load: the Krylov state of a solve suspended by
+ * opts->stop_after (status TK_SUSPENDED) as an opaque byte string in host memory, so that a
+ * long solve can stop and continue later, in another handle or another process (the paper
+ * has no counterpart; the state is the loop variables of Algorithms 1, 2 and 6 after
+ * iteration k).  Contents: the Krylov tensors the remaining iterations and the final sum
+ * read (Algorithm 2: V_1..V_{k+1}, and Z_1..Z_k in the flexible form; Algorithm 1: V_1..V_{k+1}
+ * with the Hessenberg matrix; Algorithm 6: the window's tensors and every stored sketch, cut
+ * or full), the sketched columns M and b_s, the least-squares factorisation (reflectors, tau,
+ * Q^T b, the compact WY factor), the residual history and the RoundSum call counter; the
+ * Gaussian sketch matrices are regenerated from the seed.  The string also records the
+ * problem's shape and options, and a resume with different ones fails with TK_EINVAL.
+ *   save: with buf == NULL writes only the size to *size_out; otherwise copies the state into
+ *         buf (host, cap bytes; TK_EINVAL when cap is too small or no solve is suspended).
+ *   load: replaces the handle's suspended state by buf (host, size bytes; the format is
+ *         checked, TK_EINVAL if it is not a checkpoint of this library).
+ * A following tk_solve / tk_solve_precond with opts->resume = 1 continues the solve; its
+ * iterations and result are bit-for-bit those of the uninterrupted solve.  Synchronizes. */
+int tk_checkpoint_save(tk_handle *h, void *buf, int64_t cap, int64_t *size_out);
+int tk_checkpoint_load(tk_handle *h, const void *buf, int64_t size);
+
+/* tk_set_workspace_limit: cap the device workspace the handle may hold (bytes; 0 = no cap).
+ * A call that would need more fails with TK_ENOMEM before launching work that depends on the
+ * missing memory, and the handle stays usable.  The paper has no counterpart; this is the hook
+ * through which callers (and the tests) bound the library's device memory. */
+int tk_set_workspace_limit(tk_handle *h, int64_t bytes);
 
 /* tk_expsum_laplacian: the exponential-sum approximation of the inverse Laplacian
  * (Section 3.4): Delta_d^{-1} ~ sum_{h=-q}^{q} c_h E_h x ... x E_h with E_h = exp(-t_h T_n),
@@ -242,7 +291,9 @@ int tk_sketched_ls(tk_handle *h, const double *M, const double *b, int32_t s, in
  * the caller.  Sizes with k < 1, k >= s, s > 512 or k > 128 return TK_EINVAL; a CUDA failure
  * returns TK_ECUDA (no message: there is no handle).  The first call on a device looks up the
  * array's device address on that device (cudaGetSymbolAddress, with the device current); make
- * that first call before any stream capture.  Every call shares the one array and it keeps the
+ * that first call before any stream capture.  The address is kept for the life of the process:
+ * after cudaDeviceReset of a device it no longer names the array, so do not call this entry
+ * point on a device that has been reset.  Every call shares the one array and it keeps the
  * last call's contents, so calls that may overlap on the GPU (different streams, or devices
  * sharing a context) race: serialise them.  Enqueues only. */
 int tk_sketched_ls_static(const double *M, const double *b, int32_t s, int32_t k, double *y,

@@ -90,13 +90,14 @@ def ls_tikhonov(m_mat: np.ndarray, b: np.ndarray, rows: Optional[int] = None):
 
 def rhosvd_sgmres(op: Operator, b: Tucker, prm: SolverParams, transpose: bool = False,
                   bf16_sketch: bool = False, maxit: Optional[int] = None,
-                  precond: Optional[Operator] = None, gcv_rows: str = "sketch") -> Result:
+                  precond: Optional[Operator] = None, gcv_rows: Optional[str] = None) -> Result:
     """Algorithm 2.  bf16_sketch rounds RoundSum's Gaussian matrices to bfloat16 values (the
     mixed-precision form stores them so); the arithmetic stays FP64.
 
-    gcv_rows (with prm.tikhonov): the row count GCV uses for the sketched problem, "sketch" (s,
-    the reading the library implements) or "projected" (k + 1, the dimension of the span of
-    [M_k, S b] in which the sketched residual lives; the alternative reading, oracle only).
+    gcv_rows (with prm.tikhonov; None: prm.gcv_rows): the row count m GCV uses for the sketched
+    problem (Section 4.3 leaves it open), "projected" (k + 1, the dimension of the span of
+    [M_k, S b] in which the sketched residual lives, as Algorithm 1's k + 1 x k Hessenberg
+    problem has k + 1 rows) or "sketch" (s, every row of the sketched problem).
 
     precond: a separable operator M applied with truncation, Z_k = RoundSum(M(V_k)), in the
     flexible form of Section 3.4: the Krylov columns sketch RoundSum(L(Z_k)) and the solution is
@@ -104,6 +105,7 @@ def rhosvd_sgmres(op: Operator, b: Tucker, prm: SolverParams, transpose: bool = 
     d, n = b.d, b.n
     s = prm.sketch_s
     maxit = prm.maxit if maxit is None else maxit
+    gcv_rows = getattr(prm, "gcv_rows", "projected") if gcv_rows is None else gcv_rows
     call = [0]
 
     def draw(sr: int):
@@ -222,13 +224,14 @@ def rhosvd_gmres(op: Operator, b: Tucker, prm: SolverParams, transpose: bool = F
 
 
 def mln_sgmres(op: Operator, b: Tucker, prm: SolverParams, transpose: bool = False,
-               maxit: Optional[int] = None, gcv_rows: str = "sketch") -> Result:
+               maxit: Optional[int] = None, gcv_rows: Optional[str] = None) -> Result:
     """Algorithm 6, r = rank_cap, r + p sketch columns.  With prm.r_sol > 0 (save_memory): once a
     basis tensor leaves the window (iteration i > k_trunc drops V_{i - k_trunc}) its stored
     sketch is cut to r_sol + p_sol (mln_downsample); at the end the sketches still in the
     window are cut too, and the solution is recovered at rank r_sol with the leading
     r_sol + p_sol columns of each Psi_k.  gcv_rows: as for rhosvd_sgmres ("sketch": r + p rows)."""
     d, n = b.d, b.n
+    gcv_rows = getattr(prm, "gcv_rows", "projected") if gcv_rows is None else gcv_rows
     r = prm.rank_cap
     rp = r + prm.oversample_p
     maxit = prm.maxit if maxit is None else maxit

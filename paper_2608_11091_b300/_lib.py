@@ -11,7 +11,7 @@ TK_MAX_D = 8
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtuckersgmres.so")
 
-TK_OK, TK_NOT_CONVERGED, TK_BREAKDOWN, TK_SKETCH_EXHAUSTED = 0, 1, 2, 3
+TK_OK, TK_NOT_CONVERGED, TK_BREAKDOWN, TK_SKETCH_EXHAUSTED, TK_SUSPENDED = 0, 1, 2, 3, 4
 TK_EINVAL, TK_ENOMEM, TK_ECUDA, TK_EINTERNAL = -1, -2, -3, -4
 TK_IDENTITY, TK_BANDED, TK_DENSE = 0, 1, 2
 TK_RHOSVD_SGMRES, TK_MLN_SGMRES, TK_RHOSVD_GMRES = 0, 1, 2
@@ -21,7 +21,8 @@ EXPORTS = ["tk_create", "tk_destroy", "tk_last_error", "tk_solve", "tk_apply", "
            "tk_kron_sketch", "tk_inner", "tk_residual", "tk_gaussian", "tk_philox",
            "tk_sketched_ls", "tk_mln_roundsum", "tk_profile", "tk_profile_report",
            "tk_sketched_ls_static", "tk_sum_norm", "tk_adjoint_grads", "tk_solve_precond",
-           "tk_expsum_laplacian"]
+           "tk_expsum_laplacian", "tk_checkpoint_save", "tk_checkpoint_load", "tk_set_workspace_limit",
+           "tk_fma_peak"]
 
 
 class tk_tucker(ctypes.Structure):
@@ -50,6 +51,8 @@ class tk_opts(ctypes.Structure):
                 ("adaptive_rank", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("transpose", ctypes.c_int32), ("mln_r_sol", ctypes.c_int32),
                 ("mln_p_sol", ctypes.c_int32), ("gcv_tikhonov", ctypes.c_int32),
+                ("gcv_rows", ctypes.c_int32), ("stop_after", ctypes.c_int32),
+                ("resume", ctypes.c_int32), ("true_residual", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("eta", ctypes.c_double),
                 ("round_tol", ctypes.c_double), ("seed", ctypes.c_uint64)]
 
@@ -62,7 +65,8 @@ class tk_report(ctypes.Structure):
                 ("out_rank", ctypes.c_int32 * TK_MAX_D),
                 ("ms_total", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64),
+                ("true_res", ctypes.c_double)]
 
 
 _lib = None
@@ -102,6 +106,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tk_solve_precond": (ctypes.c_int, [vp, P(tk_operator), P(tk_operator), P(tk_tucker), P(tk_opts), P(tk_tucker),
                                             P(tk_report), vp]),
         "tk_expsum_laplacian": (ctypes.c_int, [vp, i64, i32, P(vp), dp, vp]),
+        "tk_checkpoint_save": (ctypes.c_int, [vp, vp, i64, P(i64)]),
+        "tk_checkpoint_load": (ctypes.c_int, [vp, vp, i64]),
+        "tk_set_workspace_limit": (ctypes.c_int, [vp, i64]),
+        "tk_fma_peak": (ctypes.c_int, [vp, i32, dp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

@@ -17,7 +17,7 @@ import torch
 from . import _lib as L
 
 STATUS = {L.TK_OK: "converged", L.TK_NOT_CONVERGED: "not_converged", L.TK_BREAKDOWN: "breakdown",
-          L.TK_SKETCH_EXHAUSTED: "sketch_exhausted"}
+          L.TK_SKETCH_EXHAUSTED: "sketch_exhausted", L.TK_SUSPENDED: "suspended"}
 
 
 class TuckerError(RuntimeError):
@@ -226,6 +226,10 @@ class Options:
     r_sol: int = 0                   # MLN memory-efficient variant: solution rank (0: off)
     p_sol: int = 0                   # ... and the stored sketches' extra columns
     tikhonov: bool = False           # projected Tikhonov with the GCV parameter (Section 4.3)
+    gcv_rows: str = "projected"      # GCV's row count for the sketched variants: 'projected' (k + 1) or 'sketch'
+    stop_after: int = 0              # > 0: suspend after this many iterations (tk_checkpoint_save)
+    resume: bool = False             # continue the solve suspended in the handle
+    true_residual: bool = False      # report the true relative residual of x
 
     @staticmethod
     def from_params(p, **over) -> "Options":
@@ -233,7 +237,8 @@ class Options:
                     oversample_p=p.oversample_p, ktrunc=p.ktrunc, maxit=p.maxit, tol=p.tol,
                     eta=p.eta, round_tol=p.round_tol, seed=p.seed, adaptive_rank=p.adaptive_rank,
                     r_sol=getattr(p, "r_sol", 0), p_sol=getattr(p, "p_sol", 0),
-                    tikhonov=bool(getattr(p, "tikhonov", False)))
+                    tikhonov=bool(getattr(p, "tikhonov", False)),
+                    gcv_rows=getattr(p, "gcv_rows", "projected"))
         for k, v in over.items():
             setattr(o, k, v)
         return o
@@ -247,6 +252,10 @@ class Options:
         s.transpose = int(self.transpose)
         s.mln_r_sol, s.mln_p_sol = int(self.r_sol), int(self.p_sol)
         s.gcv_tikhonov = int(self.tikhonov)
+        if self.gcv_rows not in ("projected", "sketch"):
+            raise TuckerError("gcv_rows must be 'projected' or 'sketch'")
+        s.gcv_rows = 0 if self.gcv_rows == "projected" else 1
+        s.stop_after, s.resume, s.true_residual = int(self.stop_after), int(self.resume), int(self.true_residual)
         s.tol, s.eta, s.round_tol, s.seed = self.tol, self.eta, self.round_tol, self.seed
         return s
 
@@ -261,6 +270,7 @@ class Report:
     ms_total: float
     workspace_bytes: int
     kernel_launches: int
+    true_res: float = -1.0
 
 
 def tk_solve(op: DeviceOperator, b: DeviceTucker, opts: Options, x: Optional[DeviceTucker] = None,
@@ -279,7 +289,7 @@ def tk_solve(op: DeviceOperator, b: DeviceTucker, opts: Options, x: Optional[Dev
                         ctypes.byref(rep), _stream(stream))
     h.check(rc, "tk_solve")
     r = Report(rep.iters, STATUS[rep.status], rep.sketched_res, list(hist[:rep.iters]),
-               list(rep.out_rank[:b.d]), rep.ms_total, rep.workspace_bytes, rep.kernel_launches)
+               list(rep.out_rank[:b.d]), rep.ms_total, rep.workspace_bytes, rep.kernel_launches, rep.true_res)
     return x, r
 
 
@@ -299,8 +309,39 @@ def tk_solve_precond(op: DeviceOperator, precond: DeviceOperator, b: DeviceTucke
                                 ctypes.byref(xc), ctypes.byref(rep), _stream(stream))
     h.check(rc, "tk_solve_precond")
     r = Report(rep.iters, STATUS[rep.status], rep.sketched_res, list(hist[:rep.iters]),
-               list(rep.out_rank[:b.d]), rep.ms_total, rep.workspace_bytes, rep.kernel_launches)
+               list(rep.out_rank[:b.d]), rep.ms_total, rep.workspace_bytes, rep.kernel_launches, rep.true_res)
     return x, r
+
+
+def tk_checkpoint_save(device: Optional[int] = None) -> bytes:
+    """The Krylov state of the solve suspended in this device's handle (opts.stop_after), as bytes."""
+    h = handle(device)
+    size = ctypes.c_int64()
+    h.check(h.lib.tk_checkpoint_save(h.h, None, 0, ctypes.byref(size)), "tk_checkpoint_save")
+    buf = ctypes.create_string_buffer(size.value)
+    h.check(h.lib.tk_checkpoint_save(h.h, buf, size.value, ctypes.byref(size)), "tk_checkpoint_save")
+    return buf.raw[:size.value]
+
+
+def tk_checkpoint_load(state: bytes, device: Optional[int] = None):
+    """Install a saved Krylov state in this device's handle; a solve with opts.resume continues it."""
+    h = handle(device)
+    buf = ctypes.create_string_buffer(bytes(state), len(state))
+    h.check(h.lib.tk_checkpoint_load(h.h, buf, len(state)), "tk_checkpoint_load")
+
+
+def tk_fma_peak(fp64: bool = True, device: Optional[int] = None, stream=None) -> float:
+    """Measured FMA throughput of the device in TFLOP/s (FP64 or FP32), the ALU roofline's peak."""
+    h = handle(device)
+    out = ctypes.c_double()
+    h.check(h.lib.tk_fma_peak(h.h, int(bool(fp64)), ctypes.byref(out), _stream(stream)), "tk_fma_peak")
+    return out.value
+
+
+def tk_set_workspace_limit(nbytes: int, device: Optional[int] = None):
+    """Cap the device workspace of this device's handle (0: no cap); beyond it calls fail with TK_ENOMEM."""
+    h = handle(device)
+    h.check(h.lib.tk_set_workspace_limit(h.h, int(nbytes)), "tk_set_workspace_limit")
 
 
 def tk_expsum_laplacian(n: int, d: int, q: int, device="cuda", stream=None) -> DeviceOperator:
@@ -322,13 +363,14 @@ def tk_profile(enable: bool, device: Optional[int] = None):
 
 
 def tk_profile_report(device: Optional[int] = None) -> Dict[str, tuple]:
-    """{kernel name: (launches, total ms, algorithmic FP64 flops)} since the last report (then reset)."""
+    """{kernel name: (launches, total ms, algorithmic flops, algorithmic bytes)} since the last
+    report (then reset)."""
     h = handle(device)
     txt = h.lib.tk_profile_report(h.h).decode()
     out = {}
     for line in txt.strip().splitlines():
-        name, n, ms, fl = line.split()
-        out[name] = (int(n), float(ms), float(fl))
+        name, n, ms, fl, by = line.split()
+        out[name] = (int(n), float(ms), float(fl), float(by))
     return out
 
 
@@ -431,12 +473,21 @@ def tk_philox(seed: int, stream_id: int, first: int, nblocks: int, device="cuda"
     return out[:4 * nblocks]
 
 
+def _check_ls_args(M: torch.Tensor, b: torch.Tensor):
+    """M: float64 CUDA s x k column-major; b: float64 CUDA contiguous vector of length s, same device."""
+    if M.dim() != 2 or M.dtype != torch.float64 or not M.is_cuda or not is_fortran(M):
+        raise TuckerError("M must be a float64 CUDA matrix in column-major layout")
+    if b.dtype != torch.float64 or not b.is_cuda or b.device != M.device or not b.is_contiguous():
+        raise TuckerError("b must be a contiguous float64 CUDA vector on M's device")
+    if b.numel() != M.shape[0]:
+        raise TuckerError(f"b has {b.numel()} entries, M has {M.shape[0]} rows")
+
+
 def tk_sketched_ls(M: torch.Tensor, b: torch.Tensor, stream=None):
     """y = argmin ||M y - b|| (Householder), M s x k column-major. Returns (y, residual norm)."""
     h = handle()
+    _check_ls_args(M, b)
     s, k = int(M.shape[0]), int(M.shape[1])
-    if not is_fortran(M):
-        raise TuckerError("M must be column-major")
     y = torch.empty(k, dtype=torch.float64, device=M.device)
     res = torch.empty(1, dtype=torch.float64, device=M.device)
     h.check(h.lib.tk_sketched_ls(h.h, ctypes.c_void_p(M.data_ptr()), ctypes.c_void_p(b.data_ptr()), s, k,
@@ -449,9 +500,8 @@ def tk_sketched_ls_static(M: torch.Tensor, b: torch.Tensor, stream=None):
     """tk_sketched_ls without any device allocation by the library (fixed device workspace;
     s <= 512, k <= 128; concurrent calls race).  Returns (y, residual norm)."""
     lib = L.load()
+    _check_ls_args(M, b)
     s, k = int(M.shape[0]), int(M.shape[1])
-    if not is_fortran(M):
-        raise TuckerError("M must be column-major")
     y = torch.empty(k, dtype=torch.float64, device=M.device)
     res = torch.empty(1, dtype=torch.float64, device=M.device)
     rc = lib.tk_sketched_ls_static(ctypes.c_void_p(M.data_ptr()), ctypes.c_void_p(b.data_ptr()), s, k,

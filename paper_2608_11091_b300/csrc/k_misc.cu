@@ -9,12 +9,12 @@ namespace cg = cooperative_groups;
 
 namespace tk {
 
-void Ctx::check_launch(const char *what, double flops) {
+void Ctx::check_launch(const char *what, double flops, double bytes) {
     ++launches;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         throw Error{TK_ECUDA, std::string("launch of ") + what + ": " + cudaGetErrorString(e)};
-    if (prof) prof->end(st, what, flops);
+    if (prof) prof->end(st, what, flops, bytes);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -38,10 +38,10 @@ void Profiler::begin(cudaStream_t st) {
     TK_CUDA(cudaEventRecord(open_, st));
 }
 
-void Profiler::end(cudaStream_t st, const char *name, double flops) {
+void Profiler::end(cudaStream_t st, const char *name, double flops, double bytes) {
     cudaEvent_t b = get();
     TK_CUDA(cudaEventRecord(b, st));
-    recs_.push_back(Rec{name, open_, b, flops});
+    recs_.push_back(Rec{name, open_, b, flops, bytes});
 }
 
 void Profiler::collect() {
@@ -51,8 +51,12 @@ void Profiler::collect() {
         TK_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
         bool found = false;
         for (auto &t : tot_)
-            if (t.first == r.name) { t.second.n += 1; t.second.ms += ms; t.second.flops += r.flops; found = true; break; }
-        if (!found) { Tot t; t.n = 1; t.ms = ms; t.flops = r.flops; tot_.push_back({r.name, t}); }
+            if (t.first == r.name) {
+                t.second.n += 1; t.second.ms += ms; t.second.flops += r.flops; t.second.bytes += r.bytes;
+                found = true;
+                break;
+            }
+        if (!found) { Tot t; t.n = 1; t.ms = ms; t.flops = r.flops; t.bytes = r.bytes; tot_.push_back({r.name, t}); }
     }
     recs_.clear();
     used_ = 0;
@@ -63,7 +67,7 @@ std::string Profiler::report_and_reset() {
     std::string s;
     for (auto &t : tot_)
         s += t.first + " " + std::to_string(t.second.n) + " " + std::to_string(t.second.ms) + " " +
-             std::to_string(t.second.flops) + "\n";
+             std::to_string(t.second.flops) + " " + std::to_string(t.second.bytes) + "\n";
     tot_.clear();
     return s;
 }
@@ -87,7 +91,13 @@ void *Arena::alloc_bytes(size_t bytes) {
         ++cur_;
         off_ = 0;
     }
-    const size_t sz = std::max(bytes, size_t(256) << 20);
+    size_t sz = std::max(bytes, size_t(256) << 20);
+    if (limit_) {
+        const size_t held = capacity();
+        if (held + bytes > limit_)
+            throw Error{TK_ENOMEM, "device workspace limit of " + std::to_string(limit_) + " bytes reached"};
+        sz = std::min(sz, limit_ - held);
+    }
     char *p = nullptr;
     if (cudaMalloc(&p, sz) != cudaSuccess) {
         cudaGetLastError();
@@ -233,14 +243,17 @@ void band_apply(Ctx &c, const std::vector<BandJob> &jobs) {
         BandJobs J{};
         J.n = (int)std::min<size_t>(32, jobs.size() - base);
         long long mx = 1;
+        double bytes = 0.0;
         for (int i = 0; i < J.n; ++i) {
             J.j[i] = jobs[base + i];
-            mx = std::max(mx, (long long)J.j[i].n * J.j[i].r);
+            const BandJob &b = J.j[i];
+            mx = std::max(mx, (long long)b.n * b.r);
+            bytes += 8.0 * ((double)b.n * b.r * 2 + (double)(b.kl + b.ku + 1) * b.n);
         }
         const long long blocks = std::min<long long>((mx + 255) / 256, 2048);
         c.pre_launch();
         k_band<<<dim3((unsigned)blocks, J.n), 256, 0, c.st>>>(J);
-        c.check_launch("band");
+        c.check_launch("band", 0.0, bytes);
     }
 }
 
@@ -273,14 +286,18 @@ void hadamard_contract(Ctx &c, const std::vector<HadJob> &jobs) {
         HadJobs J{};
         J.n = (int)std::min<size_t>(32, jobs.size() - base);
         long long mx = 1;
+        double bytes = 0.0, flops = 0.0;
         for (int i = 0; i < J.n; ++i) {
             J.j[i] = jobs[base + i];
-            mx = std::max(mx, (long long)J.j[i].a * J.j[i].cc * J.j[i].s);
+            const HadJob &h = J.j[i];
+            mx = std::max(mx, (long long)h.a * h.cc * h.s);
+            bytes += 8.0 * ((double)h.a * h.b * h.cc * h.s + (double)h.b * h.s + (double)h.a * h.cc * h.s);
+            flops += 2.0 * h.a * h.b * h.cc * (double)h.s;
         }
         const long long blocks = std::min<long long>((mx + 255) / 256, 4096);
         c.pre_launch();
         k_hadamard<<<dim3((unsigned)blocks, J.n), 256, 0, c.st>>>(J);
-        c.check_launch("hadamard");
+        c.check_launch("hadamard", flops, bytes);
     }
 }
 
@@ -302,7 +319,7 @@ void gather_unfold_t(Ctx &c, const double *C, double *out, long long a, int sk, 
     const long long blocks = std::min<long long>((total + 255) / 256, 4096);
     c.pre_launch();
     k_gather_unfold_t<<<(unsigned)std::max<long long>(blocks, 1), 256, 0, c.st>>>(C, out, a, sk, rest);
-    c.check_launch("gather");
+    c.check_launch("gather", 0.0, 16.0 * (double)total);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -350,7 +367,11 @@ void dots(Ctx &c, const std::vector<DotJob> &jobs) {
     for (size_t base = 0; base < jobs.size(); base += 32) {
         DotJobs J{};
         J.n = (int)std::min<size_t>(32, jobs.size() - base);
-        for (int i = 0; i < J.n; ++i) J.j[i] = jobs[base + i];
+        double bytes = 0.0;
+        for (int i = 0; i < J.n; ++i) {
+            J.j[i] = jobs[base + i];
+            bytes += 16.0 * (double)J.j[i].n;
+        }
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3((unsigned)(J.n * DOT_CL), 1, 1);
         cfg.blockDim = dim3(1024, 1, 1);
@@ -364,7 +385,7 @@ void dots(Ctx &c, const std::vector<DotJob> &jobs) {
         cfg.numAttrs = 1;
         c.pre_launch();
         TK_CUDA(cudaLaunchKernelEx(&cfg, k_dots, J));
-        c.check_launch("dots");
+        c.check_launch("dots", 0.0, bytes);
     }
 }
 
@@ -629,8 +650,57 @@ void axpy_list(Ctx &c, double *y, long long n, double beta, const std::vector<co
         const long long blocks = std::max<long long>(1, std::min<long long>((work + 255) / 256, (long long)c.num_sms * 8));
         c.pre_launch();
         k_axpy_list<<<(unsigned)blocks, 256, 0, c.st>>>(y, n, base == 0 ? beta : 1.0, J, aligned ? 1 : 0);
-        c.check_launch("axpy_list");
+        // x_j read, y written, and y read unless it is overwritten (beta = 0 in the first chunk)
+        const double reads_y = (base == 0 && beta == 0.0) ? 0.0 : 1.0;
+        c.check_launch("axpy_list", 2.0 * J.n * (double)n, 8.0 * (double)n * (J.n + 1 + reads_y));
     }
+}
+
+// ------------------------------------------------------------------------------------------
+// FMA-rate probe: the denominator of the FP64 (and FP32) ALU rooflines, measured on the device
+// the library runs on.  Every thread runs 8 independent FMA chains (x <- x a + b, |a| < 1 keeps
+// them bounded) for `iters` steps; the grid covers every SM with several CTAs so the pipes are
+// the limit, not latency.  Algorithmic flops: 2 x 8 x iters per thread.
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_peak(T *out, int iters, T a, T b) {
+    T x[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = (T)(threadIdx.x + 1) * (T)1e-3 + (T)j;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = fma(x[j], a, b);
+    }
+    T acc = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc += x[j];
+    if (acc == (T)-1.2345) out[blockIdx.x] = acc;   // never true; keeps the chains live
+}
+
+double fma_peak_tflops(Ctx &c, int fp64) {
+    const int blocks = c.num_sms * 8, threads = 256, iters = fp64 ? 2048 : 65536;
+    void *out = c.arena->alloc(blocks);
+    cudaEvent_t e0, e1;
+    TK_CUDA(cudaEventCreate(&e0));
+    TK_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {   // the first launch warms the clocks; best of the rest
+        TK_CUDA(cudaEventRecord(e0, c.st));
+        if (fp64)
+            k_fma_peak<double><<<blocks, threads, 0, c.st>>>((double *)out, iters, 0.999999, 1e-7);
+        else
+            k_fma_peak<float><<<blocks, threads, 0, c.st>>>((float *)out, iters, 0.999999f, 1e-7f);
+        TK_CUDA(cudaGetLastError());
+        TK_CUDA(cudaEventRecord(e1, c.st));
+        TK_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        TK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) best = std::min(best, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const double flops = 2.0 * 8.0 * iters * (double)blocks * threads;
+    return flops / (best * 1e-3) / 1e12;
 }
 
 }  // namespace tk

@@ -14,6 +14,7 @@ struct tk_handle {
     tk::Profiler prof;
     bool prof_on = false;
     std::string prof_text;
+    std::vector<char> ckpt;     // Krylov state of a suspended solve (empty: none)
 };
 
 namespace tk {
@@ -117,11 +118,97 @@ static Slot alloc_slot(Ctx &c, const Dims &pb, int R) {
 }
 
 // ------------------------------------------------------------------------------------------
+// Suspended solves: the loop state after iteration k as a byte string (host memory).  A
+// suspension copies the device state out; a resume allocates the same buffers and copies it
+// back, then the loop continues with the same kernels on the same values.
+// ------------------------------------------------------------------------------------------
+struct BlobW {
+    std::vector<char> &b;
+    void host(const void *p, size_t n) {
+        const char *q = static_cast<const char *>(p);
+        b.insert(b.end(), q, q + n);
+    }
+    template <class T> void val(const T &v) { host(&v, sizeof(T)); }
+    void dev(Ctx &c, const void *d, size_t n) {
+        const size_t o = b.size();
+        b.resize(o + n);
+        if (n) {
+            TK_CUDA(cudaMemcpyAsync(b.data() + o, d, n, cudaMemcpyDeviceToHost, c.st));
+            TK_CUDA(cudaStreamSynchronize(c.st));
+        }
+    }
+    void devd(Ctx &c, const double *d, long long n) { dev(c, d, (size_t)n * sizeof(double)); }
+};
+
+struct BlobR {
+    const std::vector<char> &b;
+    size_t pos;
+    void host(void *p, size_t n) {
+        TK_REQUIRE(pos + n <= b.size(), "checkpoint: truncated state");
+        std::memcpy(p, b.data() + pos, n);
+        pos += n;
+    }
+    template <class T> T val() {
+        T v;
+        host(&v, sizeof(T));
+        return v;
+    }
+    void dev(Ctx &c, void *d, size_t n) {
+        TK_REQUIRE(pos + n <= b.size(), "checkpoint: truncated state");
+        if (n) TK_CUDA(cudaMemcpyAsync(d, b.data() + pos, n, cudaMemcpyHostToDevice, c.st));
+        pos += n;
+    }
+    void devd(Ctx &c, double *d, long long n) { dev(c, d, (size_t)n * sizeof(double)); }
+};
+
+// Where a solve takes its state from (resume) and puts it (suspension).
+struct Ckpt {
+    const std::vector<char> *in = nullptr;
+    size_t in_pos = 0;
+    std::vector<char> *out = nullptr;
+    int stop_after = 0;
+};
+
+static void put_slot(BlobW &w, Ctx &c, const Dims &pb, int R, const Slot &sl) {
+    int rr[TK_MAX_D];
+    for (int k = 0; k < pb.d; ++k) rr[k] = R;
+    w.devd(c, sl.core, prodi(rr, pb.d));
+    for (int k = 0; k < pb.d; ++k) w.devd(c, sl.f[k], (long long)pb.n[k] * R);
+    w.dev(c, sl.rank, sizeof(int) * TK_MAX_D);
+}
+
+static Slot get_slot(BlobR &r, Ctx &c, const Dims &pb, int R) {
+    Slot sl = alloc_slot(c, pb, R);
+    int rr[TK_MAX_D];
+    for (int k = 0; k < pb.d; ++k) rr[k] = R;
+    r.devd(c, sl.core, prodi(rr, pb.d));
+    for (int k = 0; k < pb.d; ++k) r.devd(c, sl.f[k], (long long)pb.n[k] * R);
+    r.dev(c, sl.rank, sizeof(int) * TK_MAX_D);
+    return sl;
+}
+
+static void put_ls(BlobW &w, Ctx &c, const LSState &ls, int rows, int kmax) {
+    w.devd(c, ls.H, (long long)rows * kmax);
+    w.devd(c, ls.tau, kmax);
+    w.devd(c, ls.qtb, rows);
+    w.devd(c, ls.y, kmax);
+    w.devd(c, ls.T, (long long)kmax * kmax);
+}
+
+static void get_ls(BlobR &r, Ctx &c, const LSState &ls, int rows, int kmax) {
+    r.devd(c, ls.H, (long long)rows * kmax);
+    r.devd(c, ls.tau, kmax);
+    r.devd(c, ls.qtb, rows);
+    r.devd(c, ls.y, kmax);
+    r.devd(c, ls.T, (long long)kmax * kmax);
+}
+
+// ------------------------------------------------------------------------------------------
 // RHOSVD-Tucker sGMRES (Algorithm 2)
 // ------------------------------------------------------------------------------------------
 static void solve_rhosvd(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucker *b,
                          const tk_opts &o, tk_tucker *x, SolveOut &so, double *pinned,
-                         const OpDesc *precond = nullptr) {
+                         const OpDesc *precond, Ckpt &ck) {
     ScopedMark solve_mark(*c.arena);
     const int d = pb.d, R = o.rank_cap, s = o.sketch_s, sr = o.rank_cap + o.oversample_p;
     const int kmax = std::min(o.maxit, s - 1);
@@ -143,26 +230,8 @@ static void solve_rhosvd(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tuck
         gaussian(c, o.seed, sids, cnt, S, d, 0);
     }
     const TTerm B = term_of(b);
-    inner_batch(c, pb, {InnerJob{B, B, sc + SC_BETA2}});
-    sqrt_scalar(c, sc + SC_BETA2, sc + SC_BETA);
-    // V_1 = B / beta  (own core copy, factors borrowed from B)
     std::vector<TTerm> V;
-    {
-        TTerm v1 = B;
-        double *core = c.arena->alloc(prodi(B.r, d));
-        scale_by(c, core, b->core, prodi(B.r, d), sc + SC_BETA, 1);
-        v1.core = core;
-        V.push_back(v1);
-    }
     double *bs = c.arena->alloc(s);
-    kron_sketch_batch(c, pb, {B}, S, s, &bs);
-    dot(c, bs, bs, s, sc + SC_BS2);
-    sqrt_scalar(c, sc + SC_BS2, sc + SC_BS);
-    readback(c, pinned, sc, 4);
-    const double beta_s = pinned[SC_BS];
-    TK_REQUIRE(std::isfinite(pinned[SC_BETA]) && pinned[SC_BETA] > 0.0, "right-hand side is zero or not finite");
-    TK_REQUIRE(std::isfinite(beta_s) && beta_s > 0.0, "sketch of the right-hand side is zero or not finite");
-
     double *M = c.arena->alloc((size_t)s * kmax);
     LSState ls{};
     ls.H = c.arena->alloc((size_t)s * kmax);
@@ -172,12 +241,83 @@ static void solve_rhosvd(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tuck
     ls.T = c.arena->alloc((size_t)kmax * kmax);
     ls.ldt = kmax;
     ls.res = sc + SC_RES;
+    // V_1 = B / beta  (own core copy, factors borrowed from B)
+    TTerm v1 = B;
+    double *v1core = c.arena->alloc(prodi(B.r, d));
+    v1.core = v1core;
+    V.push_back(v1);
+    std::vector<int *> vrank{nullptr}, zrank;   // rank arrays of the slots behind V and Z
+    int k0 = 0;
+    uint64_t call = 0;
+    std::vector<TTerm> Z;   // flexible preconditioning (Section 3.4): Z_k = RoundSum(M(V_k))
+    double beta_s;
+    if (ck.in) {
+        BlobR r{*ck.in, ck.in_pos};
+        k0 = r.val<int>();
+        call = r.val<uint64_t>();
+        so.hist.resize(k0);
+        r.host(so.hist.data(), sizeof(double) * k0);
+        r.devd(c, sc, SC_N);
+        r.devd(c, v1core, prodi(B.r, d));
+        r.devd(c, bs, s);
+        r.devd(c, M, (long long)s * kmax);
+        get_ls(r, c, ls, s, kmax);
+        for (int j = 2; j <= k0 + 1; ++j) {
+            const Slot sl = get_slot(r, c, pb, R);
+            V.push_back(sl.term(pb, R));
+            vrank.push_back(sl.rank);
+        }
+        if (precond)
+            for (int j = 1; j <= k0; ++j) {
+                const Slot sl = get_slot(r, c, pb, R);
+                Z.push_back(sl.term(pb, R));
+                zrank.push_back(sl.rank);
+            }
+        TK_REQUIRE(r.pos == ck.in->size(), "checkpoint: state does not match this solve");
+        readback(c, pinned, sc, 4);
+        beta_s = pinned[SC_BS];
+    } else {
+        inner_batch(c, pb, {InnerJob{B, B, sc + SC_BETA2}});
+        sqrt_scalar(c, sc + SC_BETA2, sc + SC_BETA);
+        scale_by(c, v1core, b->core, prodi(B.r, d), sc + SC_BETA, 1);
+        kron_sketch_batch(c, pb, {B}, S, s, &bs);
+        dot(c, bs, bs, s, sc + SC_BS2);
+        sqrt_scalar(c, sc + SC_BS2, sc + SC_BS);
+        readback(c, pinned, sc, 4);
+        beta_s = pinned[SC_BS];
+        TK_REQUIRE(std::isfinite(pinned[SC_BETA]) && pinned[SC_BETA] > 0.0, "right-hand side is zero or not finite");
+        TK_REQUIRE(std::isfinite(beta_s) && beta_s > 0.0, "sketch of the right-hand side is zero or not finite");
+    }
+    auto suspend = [&](int k) {
+        BlobW w{*ck.out};
+        w.val(k);
+        w.val(call);
+        w.host(so.hist.data(), sizeof(double) * k);
+        w.devd(c, sc, SC_N);
+        w.devd(c, v1core, prodi(B.r, d));
+        w.devd(c, bs, s);
+        w.devd(c, M, (long long)s * kmax);
+        put_ls(w, c, ls, s, kmax);
+        for (int j = 2; j <= k + 1; ++j) {
+            Slot sl{};
+            sl.core = const_cast<double *>(V[j - 1].core);
+            for (int kk = 0; kk < d; ++kk) sl.f[kk] = const_cast<double *>(V[j - 1].f[kk]);
+            sl.rank = vrank[j - 1];
+            put_slot(w, c, pb, R, sl);
+        }
+        if (precond)
+            for (int j = 1; j <= k; ++j) {
+                Slot sl{};
+                sl.core = const_cast<double *>(Z[j - 1].core);
+                for (int kk = 0; kk < d; ++kk) sl.f[kk] = const_cast<double *>(Z[j - 1].f[kk]);
+                sl.rank = zrank[j - 1];
+                put_slot(w, c, pb, R, sl);
+            }
+    };
 
     so.status = kmax < o.maxit ? TK_SKETCH_EXHAUSTED : TK_NOT_CONVERGED;
     int k = 0;
-    uint64_t call = 0;
-    std::vector<TTerm> Z;   // flexible preconditioning (Section 3.4): Z_k = RoundSum(M(V_k))
-    for (k = 1; k <= kmax; ++k) {
+    for (k = k0 + 1; k <= kmax; ++k) {
         Slot vn = alloc_slot(c, pb, R);
         if (precond) {
             Slot zs = alloc_slot(c, pb, R);
@@ -185,6 +325,7 @@ static void solve_rhosvd(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tuck
             std::vector<TTerm> mterms = apply_operator(c, pb, *precond, V.back(), o.transpose);
             roundsum(c, pb, mterms, RSConfig{sr, R, o.round_tol, o.seed, call++, bf16}, zs.out(pb));
             Z.push_back(zs.term(pb, R));
+            zrank.push_back(zs.rank);
         }
         {
             ScopedMark it(*c.arena);
@@ -211,12 +352,12 @@ static void solve_rhosvd(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tuck
             dot(c, vn.core, vn.core, csz, sc + SC_NWSQ);
             sqrt_scalar(c, sc + SC_NWSQ, sc + SC_NW);
             ls_update(c, M, bs, s, k - 1, k, ls, k == 1);
-            if (o.gcv_tikhonov) tikhonov_gcv(c, ls, s, k, s, nullptr);
+            if (o.gcv_tikhonov) tikhonov_gcv(c, ls, s, k, o.gcv_rows ? s : k + 1, nullptr);
             scale_by(c, vn.core, vn.core, csz, sc + SC_NW, 1);
             readback(c, pinned, sc, 8);
         }
         const double res = pinned[SC_RES] / beta_s;
-        TK_REQUIRE(std::isfinite(res), "non-finite sketched residual");
+        TK_REQUIRE(std::isfinite(res), "sketched residual is not finite (non-finite input or overflow)");
         so.hist.push_back(res);
         so.sres = res;
         if (std::sqrt(std::max(pinned[SC_NWSQ], 0.0)) <= 1e-14 * std::sqrt(std::max(pinned[SC_NW0SQ], 0.0))) {
@@ -224,13 +365,21 @@ static void solve_rhosvd(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tuck
             break;
         }
         V.push_back(vn.term(pb, R));
+        vrank.push_back(vn.rank);
         if (res < o.eta * o.tol) {
             so.status = TK_OK;
             break;
         }
+        if (ck.stop_after > 0 && k - k0 >= ck.stop_after && k < kmax) {
+            suspend(k);
+            so.status = TK_SUSPENDED;
+            so.iters = k;
+            return;
+        }
     }
     if (k > kmax) k = kmax;
     so.iters = k;
+    if (!so.hist.empty()) so.sres = so.hist.back();
     // X~ = RoundSum(sum_i y_i V_i)  (flexible form: sum_i y_i Z_i)
     std::vector<TTerm> fin;
     for (int i = 0; i < k; ++i) {
@@ -256,7 +405,7 @@ static void solve_rhosvd(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tuck
 // the Hessenberg matrix (the incremental Householder kernel with M = H, b = beta e_1)
 // ------------------------------------------------------------------------------------------
 static void solve_gmres(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucker *b, const tk_opts &o,
-                        tk_tucker *x, SolveOut &so, double *pinned) {
+                        tk_tucker *x, SolveOut &so, double *pinned, Ckpt &ck) {
     ScopedMark solve_mark(*c.arena);
     const int d = pb.d, R = o.rank_cap, sr = o.rank_cap + o.oversample_p;
     const int kmax = o.maxit, ld = kmax + 1;
@@ -266,22 +415,15 @@ static void solve_gmres(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucke
     double *sc = c.arena->alloc(SC_N);
     fill(c, sc, SC_N, 0.0);
     const TTerm B = term_of(b);
-    inner_batch(c, pb, {InnerJob{B, B, sc + SC_BETA2}});
-    sqrt_scalar(c, sc + SC_BETA2, sc + SC_BETA);
     std::vector<TTerm> V;
-    {
-        TTerm v1 = B;
-        double *core = c.arena->alloc(prodi(B.r, d));
-        scale_by(c, core, b->core, prodi(B.r, d), sc + SC_BETA, 1);
-        v1.core = core;
-        V.push_back(v1);
-    }
+    std::vector<int *> vrank{nullptr};
+    TTerm v1 = B;
+    double *v1core = c.arena->alloc(prodi(B.r, d));
+    v1.core = v1core;
+    V.push_back(v1);
     // Hessenberg matrix H ((kmax + 1) x kmax, column-major) and beta e_1
     double *H = c.arena->alloc((size_t)ld * kmax);
-    fill(c, H, (long long)ld * kmax, 0.0);
     double *e1 = c.arena->alloc(ld);
-    fill(c, e1, ld, 0.0);
-    copy(c, e1, sc + SC_BETA, 1);
     LSState ls{};
     ls.H = c.arena->alloc((size_t)ld * kmax);
     ls.tau = c.arena->alloc(kmax);
@@ -290,14 +432,61 @@ static void solve_gmres(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucke
     ls.T = c.arena->alloc((size_t)kmax * kmax);
     ls.ldt = kmax;
     ls.res = sc + SC_RES;
-    readback(c, pinned, sc, 4);
-    const double beta = pinned[SC_BETA];
-    TK_REQUIRE(std::isfinite(beta) && beta > 0.0, "right-hand side is zero or not finite");
+    int k0 = 0;
+    uint64_t call = 0;
+    double beta;
+    if (ck.in) {
+        BlobR r{*ck.in, ck.in_pos};
+        k0 = r.val<int>();
+        call = r.val<uint64_t>();
+        so.hist.resize(k0);
+        r.host(so.hist.data(), sizeof(double) * k0);
+        r.devd(c, sc, SC_N);
+        r.devd(c, v1core, prodi(B.r, d));
+        r.devd(c, H, (long long)ld * kmax);
+        r.devd(c, e1, ld);
+        get_ls(r, c, ls, ld, kmax);
+        for (int j = 2; j <= k0 + 1; ++j) {
+            const Slot sl = get_slot(r, c, pb, R);
+            V.push_back(sl.term(pb, R));
+            vrank.push_back(sl.rank);
+        }
+        TK_REQUIRE(r.pos == ck.in->size(), "checkpoint: state does not match this solve");
+        readback(c, pinned, sc, 4);
+        beta = pinned[SC_BETA];
+    } else {
+        inner_batch(c, pb, {InnerJob{B, B, sc + SC_BETA2}});
+        sqrt_scalar(c, sc + SC_BETA2, sc + SC_BETA);
+        scale_by(c, v1core, b->core, prodi(B.r, d), sc + SC_BETA, 1);
+        fill(c, H, (long long)ld * kmax, 0.0);
+        fill(c, e1, ld, 0.0);
+        copy(c, e1, sc + SC_BETA, 1);
+        readback(c, pinned, sc, 4);
+        beta = pinned[SC_BETA];
+        TK_REQUIRE(std::isfinite(beta) && beta > 0.0, "right-hand side is zero or not finite");
+    }
+    auto suspend = [&](int k) {
+        BlobW w{*ck.out};
+        w.val(k);
+        w.val(call);
+        w.host(so.hist.data(), sizeof(double) * k);
+        w.devd(c, sc, SC_N);
+        w.devd(c, v1core, prodi(B.r, d));
+        w.devd(c, H, (long long)ld * kmax);
+        w.devd(c, e1, ld);
+        put_ls(w, c, ls, ld, kmax);
+        for (int j = 2; j <= k + 1; ++j) {
+            Slot sl{};
+            sl.core = const_cast<double *>(V[j - 1].core);
+            for (int kk = 0; kk < d; ++kk) sl.f[kk] = const_cast<double *>(V[j - 1].f[kk]);
+            sl.rank = vrank[j - 1];
+            put_slot(w, c, pb, R, sl);
+        }
+    };
 
     so.status = TK_NOT_CONVERGED;
     int k = 0;
-    uint64_t call = 0;
-    for (k = 1; k <= kmax; ++k) {
+    for (k = k0 + 1; k <= kmax; ++k) {
         Slot vn = alloc_slot(c, pb, R);
         {
             ScopedMark it(*c.arena);
@@ -328,7 +517,7 @@ static void solve_gmres(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucke
             readback(c, pinned, sc, 8);
         }
         const double res = pinned[SC_RES] / beta;
-        TK_REQUIRE(std::isfinite(res), "non-finite residual");
+        TK_REQUIRE(std::isfinite(res), "residual is not finite (non-finite input or overflow)");
         so.hist.push_back(res);
         so.sres = res;
         if (std::sqrt(std::max(pinned[SC_NWSQ], 0.0)) <= 1e-14 * std::sqrt(std::max(pinned[SC_NW0SQ], 0.0))) {
@@ -336,13 +525,21 @@ static void solve_gmres(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucke
             break;
         }
         V.push_back(vn.term(pb, R));
+        vrank.push_back(vn.rank);
         if (res < o.tol) {
             so.status = TK_OK;
             break;
         }
+        if (ck.stop_after > 0 && k - k0 >= ck.stop_after && k < kmax) {
+            suspend(k);
+            so.status = TK_SUSPENDED;
+            so.iters = k;
+            return;
+        }
     }
     if (k > kmax) k = kmax;
     so.iters = k;
+    if (!so.hist.empty()) so.sres = so.hist.back();
     std::vector<TTerm> fin;
     for (int i = 0; i < k; ++i) {
         TTerm t = V[i];
@@ -383,12 +580,13 @@ void axpy_list(Ctx &c, double *y, long long n, double beta, const std::vector<co
                const std::vector<double> &coef, const std::vector<const double *> &coef_dev);
 
 static void solve_mln(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucker *b, const tk_opts &o,
-                      tk_tucker *x, SolveOut &so, double *pinned) {
+                      tk_tucker *x, SolveOut &so, double *pinned, Ckpt &ck) {
     ScopedMark solve_mark(*c.arena);
     const int d = pb.d, r = o.rank_cap, p = o.oversample_p, rp = r + p;
     const int kmax = std::min(o.maxit, rp - 1);
     TK_REQUIRE(r >= 1 && p >= 0 && r <= 96, "MLN: rank must be 1..96");
     TK_REQUIRE(o.ktrunc >= 1 && o.ktrunc <= 64, "ktrunc must be 1..64");
+    TK_REQUIRE(o.precision == TK_FP64, "MLN-Tucker sGMRES runs in FP64 only (precision must be TK_FP64)");
     long long gsz = 1, csz = 1;
     for (int k = 0; k < d; ++k) { gsz *= rp; csz *= r; }
     double *sc = c.arena->alloc(SC_N);
@@ -405,16 +603,12 @@ static void solve_mln(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucker 
         gaussian(c, o.seed, sids, cnt, psi, d, 0);
     }
     const TTerm B = term_of(b);
-    inner_batch(c, pb, {InnerJob{B, B, sc + SC_BETA2}});
-    sqrt_scalar(c, sc + SC_BETA2, sc + SC_BETA);
     std::vector<TTerm> V;
-    {
-        TTerm v1 = B;
-        double *core = c.arena->alloc(prodi(B.r, d));
-        scale_by(c, core, b->core, prodi(B.r, d), sc + SC_BETA, 1);
-        v1.core = core;
-        V.push_back(v1);
-    }
+    std::vector<int *> vrank{nullptr};
+    TTerm v1 = B;
+    double *v1core = c.arena->alloc(prodi(B.r, d));
+    v1.core = v1core;
+    V.push_back(v1);
     // Stored sketches.  Default: every sketch kept at full size.  Memory-efficient variant
     // (Section 3.3): full-size sketches live in a ring of ktrunc + 1 slots; the sketch of V_m is
     // cut to (r_sol + p_sol)^d and n x r_sol just before its slot is reused (it has left the
@@ -422,37 +616,31 @@ static void solve_mln(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucker 
     const bool save = o.mln_r_sol > 0;
     const int rs = o.mln_r_sol, rts = o.mln_r_sol + o.mln_p_sol, K = o.ktrunc;
     if (save) TK_REQUIRE(rs <= r && o.mln_p_sol >= 0 && rts <= rp, "MLN: need r_sol <= r and r_sol + p_sol <= r + p");
+    long long gcut = 1;
+    for (int k = 0; k < d; ++k) gcut *= rts;
     std::vector<Sk> sks;                 // index m: sketch of V_{m+1} (full size, or its ring slot)
     std::vector<Sk> ring;
     std::vector<Sk> cut;                 // compact sketches (save), index m
     std::vector<char> is_cut;
-    auto cut_sketch = [&](int m) {
+    auto alloc_cut = [&](int m) -> Sk & {
         Sk t{};
-        t.g = c.arena->alloc((size_t)std::llround(std::pow((double)rts, d)));
-        int rd[TK_MAX_D], rsrc[TK_MAX_D];
-        for (int k = 0; k < d; ++k) { rd[k] = rts; rsrc[k] = rp; }
-        copy_core_pad(c, t.g, rd, sks[m].g, rsrc, d);
-        for (int k = 0; k < d; ++k) {
-            t.F[k] = c.arena->alloc((size_t)pb.n[k] * rs);
-            copy(c, t.F[k], sks[m].F[k], (long long)pb.n[k] * rs);
-        }
+        t.g = c.arena->alloc(gcut);
+        for (int k = 0; k < d; ++k) t.F[k] = c.arena->alloc((size_t)pb.n[k] * rs);
         if ((int)cut.size() <= m) { cut.resize(m + 1); is_cut.resize(m + 1, 0); }
         cut[m] = t;
         is_cut[m] = 1;
+        return cut[m];
+    };
+    auto cut_sketch = [&](int m) {
+        Sk &t = alloc_cut(m);
+        int rd[TK_MAX_D], rsrc[TK_MAX_D];
+        for (int k = 0; k < d; ++k) { rd[k] = rts; rsrc[k] = rp; }
+        copy_core_pad(c, t.g, rd, sks[m].g, rsrc, d);
+        for (int k = 0; k < d; ++k) copy(c, t.F[k], sks[m].F[k], (long long)pb.n[k] * rs);
     };
     if (save)
         for (int q = 0; q <= K; ++q) ring.push_back(alloc_sk(c, pb, r, rp));
-    sks.push_back(save ? ring[0] : alloc_sk(c, pb, r, rp));
-    mln_sketch_sum(c, pb, {V[0]}, psi, r, p, sks[0].g, sks[0].F, 0.0);
     double *bs = c.arena->alloc(rp);
-    superdiag(c, sks[0].g, rp, d, bs, 1.0, sc + SC_BETA);
-    dot(c, bs, bs, rp, sc + SC_BS2);
-    sqrt_scalar(c, sc + SC_BS2, sc + SC_BS);
-    readback(c, pinned, sc, 4);
-    const double beta_s = pinned[SC_BS];
-    TK_REQUIRE(std::isfinite(pinned[SC_BETA]) && pinned[SC_BETA] > 0.0, "right-hand side is zero or not finite");
-    TK_REQUIRE(std::isfinite(beta_s) && beta_s > 0.0, "sketch of the right-hand side is zero or not finite");
-
     double *M = c.arena->alloc((size_t)rp * kmax);
     LSState ls{};
     ls.H = c.arena->alloc((size_t)rp * kmax);
@@ -462,10 +650,95 @@ static void solve_mln(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucker 
     ls.T = c.arena->alloc((size_t)kmax * kmax);
     ls.ldt = kmax;
     ls.res = sc + SC_RES;
+    int i0 = 0;
+    double beta_s;
+    auto full_sk = [&](int m) { return save ? ring[m % (K + 1)] : alloc_sk(c, pb, r, rp); };
+    if (ck.in) {
+        BlobR rd{*ck.in, ck.in_pos};
+        i0 = rd.val<int>();
+        so.hist.resize(i0);
+        rd.host(so.hist.data(), sizeof(double) * i0);
+        rd.devd(c, sc, SC_N);
+        rd.devd(c, bs, rp);
+        rd.devd(c, M, (long long)rp * kmax);
+        get_ls(rd, c, ls, rp, kmax);
+        // the window of iteration i0 + 1: V_{j0} .. V_{i0+1}
+        const int j0 = std::max(1, i0 + 1 - o.ktrunc + 1);
+        if (j0 == 1) rd.devd(c, v1core, prodi(B.r, d));
+        for (int j = 2; j <= i0 + 1; ++j) {
+            if (j < j0) {               // outside every later window: never read again
+                V.push_back(TTerm{});
+                vrank.push_back(nullptr);
+                continue;
+            }
+            const Slot sl = get_slot(rd, c, pb, r);
+            V.push_back(sl.term(pb, r));
+            vrank.push_back(sl.rank);
+        }
+        for (int m = 0; m <= i0; ++m) {
+            const char isc = rd.val<char>();
+            if (isc) {
+                Sk &t = alloc_cut(m);
+                rd.devd(c, t.g, gcut);
+                for (int k = 0; k < d; ++k) rd.devd(c, t.F[k], (long long)pb.n[k] * rs);
+                sks.push_back(Sk{});     // its ring slot has been reused
+            } else {
+                Sk t = full_sk(m);
+                rd.devd(c, t.g, gsz);
+                for (int k = 0; k < d; ++k) rd.devd(c, t.F[k], (long long)pb.n[k] * r);
+                sks.push_back(t);
+            }
+        }
+        TK_REQUIRE(rd.pos == ck.in->size(), "checkpoint: state does not match this solve");
+        readback(c, pinned, sc, 4);
+        beta_s = pinned[SC_BS];
+    } else {
+        inner_batch(c, pb, {InnerJob{B, B, sc + SC_BETA2}});
+        sqrt_scalar(c, sc + SC_BETA2, sc + SC_BETA);
+        scale_by(c, v1core, b->core, prodi(B.r, d), sc + SC_BETA, 1);
+        sks.push_back(full_sk(0));
+        mln_sketch_sum(c, pb, {V[0]}, psi, r, p, sks[0].g, sks[0].F, 0.0);
+        superdiag(c, sks[0].g, rp, d, bs, 1.0, sc + SC_BETA);
+        dot(c, bs, bs, rp, sc + SC_BS2);
+        sqrt_scalar(c, sc + SC_BS2, sc + SC_BS);
+        readback(c, pinned, sc, 4);
+        beta_s = pinned[SC_BS];
+        TK_REQUIRE(std::isfinite(pinned[SC_BETA]) && pinned[SC_BETA] > 0.0, "right-hand side is zero or not finite");
+        TK_REQUIRE(std::isfinite(beta_s) && beta_s > 0.0, "sketch of the right-hand side is zero or not finite");
+    }
+    auto suspend = [&](int i) {
+        BlobW w{*ck.out};
+        w.val(i);
+        w.host(so.hist.data(), sizeof(double) * i);
+        w.devd(c, sc, SC_N);
+        w.devd(c, bs, rp);
+        w.devd(c, M, (long long)rp * kmax);
+        put_ls(w, c, ls, rp, kmax);
+        const int j0 = std::max(1, i + 1 - o.ktrunc + 1);
+        if (j0 == 1) w.devd(c, v1core, prodi(B.r, d));
+        for (int j = std::max(2, j0); j <= i + 1; ++j) {
+            Slot sl{};
+            sl.core = const_cast<double *>(V[j - 1].core);
+            for (int k = 0; k < d; ++k) sl.f[k] = const_cast<double *>(V[j - 1].f[k]);
+            sl.rank = vrank[j - 1];
+            put_slot(w, c, pb, r, sl);
+        }
+        for (int m = 0; m <= i; ++m) {
+            const char isc = (m < (int)is_cut.size() && is_cut[m]) ? 1 : 0;
+            w.val(isc);
+            if (isc) {
+                w.devd(c, cut[m].g, gcut);
+                for (int k = 0; k < d; ++k) w.devd(c, cut[m].F[k], (long long)pb.n[k] * rs);
+            } else {
+                w.devd(c, sks[m].g, gsz);
+                for (int k = 0; k < d; ++k) w.devd(c, sks[m].F[k], (long long)pb.n[k] * r);
+            }
+        }
+    };
 
     so.status = kmax < o.maxit ? TK_SKETCH_EXHAUSTED : TK_NOT_CONVERGED;
     int i = 0;
-    for (i = 1; i <= kmax; ++i) {
+    for (i = i0 + 1; i <= kmax; ++i) {
         Slot vn = alloc_slot(c, pb, r);
         Sk skn;
         if (save) {
@@ -504,13 +777,13 @@ static void solve_mln(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucker 
             inner_batch(c, pb, {InnerJob{Wn, Wn, sc + SC_NWSQ}});
             sqrt_scalar(c, sc + SC_NWSQ, sc + SC_NW);
             ls_update(c, M, bs, rp, i - 1, i, ls, i == 1);
-            if (o.gcv_tikhonov) tikhonov_gcv(c, ls, rp, i, rp, nullptr);
+            if (o.gcv_tikhonov) tikhonov_gcv(c, ls, rp, i, o.gcv_rows ? rp : i + 1, nullptr);
             scale_by(c, vn.core, vn.core, csz, sc + SC_NW, 1);
             mln_sketch_sum(c, pb, {Wn}, psi, r, p, skn.g, skn.F, 0.0);
             readback(c, pinned, sc, 8);
         }
         const double res = pinned[SC_RES] / beta_s;
-        TK_REQUIRE(std::isfinite(res), "non-finite sketched residual");
+        TK_REQUIRE(std::isfinite(res), "sketched residual is not finite (non-finite input or overflow)");
         so.hist.push_back(res);
         so.sres = res;
         if (std::sqrt(std::max(pinned[SC_NWSQ], 0.0)) <= 1e-14 * std::sqrt(std::max(pinned[SC_NW0SQ], 0.0))) {
@@ -518,27 +791,34 @@ static void solve_mln(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucker 
             break;
         }
         V.push_back(vn.term(pb, r));
+        vrank.push_back(vn.rank);
         sks.push_back(skn);
         if (res < o.eta * o.tol) {
             so.status = TK_OK;
             break;
         }
+        if (ck.stop_after > 0 && i - i0 >= ck.stop_after && i < kmax) {
+            suspend(i);
+            so.status = TK_SUSPENDED;
+            so.iters = i;
+            return;
+        }
     }
     if (i > kmax) i = kmax;
     so.iters = i;
+    if (!so.hist.empty()) so.sres = so.hist.back();
     if (save) {
         // X~ = MLN_Recovery(MLN_Sum(cut sketches 1..i, y)) at rank r_sol with the leading
         // r_sol + p_sol columns of each Psi_k, zero-padded into x_out
         for (int m = 0; m < i; ++m)
             if ((int)is_cut.size() <= m || !is_cut[m]) cut_sketch(m);
-        const long long gs = (long long)std::llround(std::pow((double)rts, d));
         Sk sol{};
-        sol.g = c.arena->alloc(gs);
+        sol.g = c.arena->alloc(gcut);
         for (int k = 0; k < d; ++k) sol.F[k] = c.arena->alloc((size_t)pb.n[k] * rs);
         std::vector<const double *> xs, cd;
         std::vector<double> cf;
         for (int m = 0; m < i; ++m) { xs.push_back(cut[m].g); cf.push_back(1.0); cd.push_back(ls.y + m); }
-        axpy_list(c, sol.g, gs, 0.0, xs, cf, cd);
+        axpy_list(c, sol.g, gcut, 0.0, xs, cf, cd);
         for (int k = 0; k < d; ++k) {
             std::vector<const double *> fx;
             for (int m = 0; m < i; ++m) fx.push_back(cut[m].F[k]);
@@ -830,6 +1110,34 @@ const char *tk_profile_report(tk_handle *h) {
     return h->prof_text.c_str();
 }
 
+// The problem a checkpoint belongs to: shapes and options (stop_after, resume and
+// true_residual excluded).  A resume must present the same.
+struct CkFinger {
+    uint32_t magic, version;
+    int32_t d, precond, nterms, pc_nterms;
+    int64_t n[TK_MAX_D], br[TK_MAX_D];
+    tk_opts o;
+};
+constexpr uint32_t CK_MAGIC = 0x4b434b54u;   // "TKCK"
+constexpr uint32_t CK_VERSION = 1;
+
+static CkFinger finger_of(const tk_tucker *b, const tk_opts &o, const OpDesc &od, const OpDesc *pd) {
+    CkFinger f;
+    std::memset(&f, 0, sizeof f);
+    f.magic = CK_MAGIC;
+    f.version = CK_VERSION;
+    f.d = b->d;
+    f.precond = pd != nullptr;
+    f.nterms = od.nterms;
+    f.pc_nterms = pd ? pd->nterms : 0;
+    for (int k = 0; k < b->d; ++k) { f.n[k] = b->n[k]; f.br[k] = b->r[k]; }
+    f.o = o;
+    f.o.stop_after = 0;
+    f.o.resume = 0;
+    f.o.true_residual = 0;
+    return f;
+}
+
 static int solve_entry(tk_handle *h, const tk_operator *op, const tk_operator *pc, const tk_tucker *b,
                        const tk_opts *opts, tk_tucker *x_out, tk_report *report, void *stream) {
     return guarded(h, [&]() -> int {
@@ -850,26 +1158,44 @@ static int solve_entry(tk_handle *h, const tk_operator *op, const tk_operator *p
         TK_REQUIRE(o.precision == TK_FP64 || o.precision == TK_MIXED, "bad precision");
         TK_REQUIRE(o.adaptive_rank == 0, "adaptive sketch size is not available in this build");
         TK_REQUIRE(o.gcv_tikhonov == 0 || o.gcv_tikhonov == 1, "gcv_tikhonov must be 0 or 1");
+        TK_REQUIRE(o.gcv_rows == 0 || o.gcv_rows == 1, "gcv_rows must be 0 or 1");
         TK_REQUIRE(!o.gcv_tikhonov || o.maxit <= 96, "Tikhonov/GCV: maxit must be <= 96");
         TK_REQUIRE(o.tol > 0.0 && o.eta > 0.0 && o.round_tol >= 0.0, "bad tolerances");
+        TK_REQUIRE(o.stop_after >= 0 && (o.resume == 0 || o.resume == 1), "bad stop_after / resume");
         if (o.variant == TK_RHOSVD_SGMRES) TK_REQUIRE(o.sketch_s >= 2 && o.sketch_s <= 4096, "sketch_s must be 2..4096");
+        OpDesc pd;
+        if (pc) {
+            TK_REQUIRE(o.variant == TK_RHOSVD_SGMRES, "preconditioning is available for RHOSVD-Tucker sGMRES");
+            pd = op_of(pc, pb);
+        }
+        const CkFinger fp = finger_of(b, o, od, pc ? &pd : nullptr);
+        Ckpt ck;
+        std::vector<char> next;
+        if (o.resume) {
+            TK_REQUIRE(h->ckpt.size() >= sizeof(CkFinger), "resume: no suspended solve in this handle");
+            TK_REQUIRE(std::memcmp(h->ckpt.data(), &fp, sizeof(CkFinger)) == 0,
+                       "resume: the suspended solve had another shape, variant or options");
+            ck.in = &h->ckpt;
+            ck.in_pos = sizeof(CkFinger);
+        }
+        if (o.stop_after > 0) {
+            ck.stop_after = o.stop_after;
+            next.resize(sizeof(CkFinger));
+            std::memcpy(next.data(), &fp, sizeof(CkFinger));
+            ck.out = &next;
+        }
         Ctx c = make_ctx(h, stream);
         cudaEvent_t e0, e1;
         TK_CUDA(cudaEventCreate(&e0));
         TK_CUDA(cudaEventCreate(&e1));
         TK_CUDA(cudaEventRecord(e0, c.st));
         SolveOut so;
-        OpDesc pd;
-        if (pc) {
-            TK_REQUIRE(o.variant == TK_RHOSVD_SGMRES, "preconditioning is available for RHOSVD-Tucker sGMRES");
-            pd = op_of(pc, pb);
-        }
         if (o.variant == TK_RHOSVD_SGMRES)
-            solve_rhosvd(c, pb, od, b, o, x_out, so, h->pinned, pc ? &pd : nullptr);
+            solve_rhosvd(c, pb, od, b, o, x_out, so, h->pinned, pc ? &pd : nullptr, ck);
         else if (o.variant == TK_RHOSVD_GMRES)
-            solve_gmres(c, pb, od, b, o, x_out, so, h->pinned);
+            solve_gmres(c, pb, od, b, o, x_out, so, h->pinned, ck);
         else
-            solve_mln(c, pb, od, b, o, x_out, so, h->pinned);
+            solve_mln(c, pb, od, b, o, x_out, so, h->pinned, ck);
         TK_CUDA(cudaEventRecord(e1, c.st));
         TK_CUDA(cudaEventSynchronize(e1));
         if (o.precision == TK_MIXED && tc_error_flag(true) != 0)
@@ -878,6 +1204,8 @@ static int solve_entry(tk_handle *h, const tk_operator *op, const tk_operator *p
         cudaEventElapsedTime(&ms, e0, e1);
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        if (so.status == TK_SUSPENDED) h->ckpt.swap(next);
+        else if (o.resume) h->ckpt.clear();
         report->iters = so.iters;
         report->status = so.status;
         report->sketched_res = so.sres;
@@ -888,6 +1216,9 @@ static int solve_entry(tk_handle *h, const tk_operator *op, const tk_operator *p
         report->ms_total = ms;
         report->workspace_bytes = (int64_t)h->arena.capacity();
         report->kernel_launches = c.launches;
+        report->true_res = -1.0;
+        if (o.true_residual && so.status != TK_SUSPENDED)
+            report->true_res = true_residual(c, pb, od, x_out, b, o.transpose);
         return so.status;
     });
 }
@@ -901,6 +1232,47 @@ int tk_solve_precond(tk_handle *h, const tk_operator *op, const tk_operator *pre
                      const tk_opts *opts, tk_tucker *x_out, tk_report *report, void *stream) {
     if (!precond) return TK_EINVAL;
     return solve_entry(h, op, precond, b, opts, x_out, report, stream);
+}
+
+int tk_checkpoint_save(tk_handle *h, void *buf, int64_t cap, int64_t *size_out) {
+    return guarded(h, [&]() -> int {
+        TK_REQUIRE(!h->ckpt.empty(), "checkpoint_save: no suspended solve in this handle");
+        if (size_out) *size_out = (int64_t)h->ckpt.size();
+        if (!buf) return TK_OK;
+        TK_REQUIRE(cap >= (int64_t)h->ckpt.size(), "checkpoint_save: buffer too small");
+        std::memcpy(buf, h->ckpt.data(), h->ckpt.size());
+        return TK_OK;
+    });
+}
+
+int tk_checkpoint_load(tk_handle *h, const void *buf, int64_t size) {
+    return guarded(h, [&]() -> int {
+        TK_REQUIRE(buf != nullptr && size >= (int64_t)sizeof(CkFinger), "checkpoint_load: no state given");
+        CkFinger f;
+        std::memcpy(&f, buf, sizeof f);
+        TK_REQUIRE(f.magic == CK_MAGIC && f.version == CK_VERSION, "checkpoint_load: not a checkpoint of this library");
+        const char *p = static_cast<const char *>(buf);
+        h->ckpt.assign(p, p + size);
+        return TK_OK;
+    });
+}
+
+int tk_fma_peak(tk_handle *h, int32_t fp64, double *tflops_host, void *stream) {
+    return guarded(h, [&]() -> int {
+        TK_REQUIRE(tflops_host != nullptr, "fma_peak: null output");
+        Ctx c = make_ctx(h, stream);
+        ScopedMark mark(h->arena);
+        *tflops_host = fma_peak_tflops(c, fp64 ? 1 : 0);
+        return TK_OK;
+    });
+}
+
+int tk_set_workspace_limit(tk_handle *h, int64_t bytes) {
+    return guarded(h, [&]() -> int {
+        TK_REQUIRE(bytes >= 0, "workspace limit must be >= 0");
+        h->arena.set_limit((size_t)bytes);
+        return TK_OK;
+    });
 }
 
 int tk_expsum_laplacian(tk_handle *h, int64_t n, int32_t q, double *const *mats, double *coef_host, void *stream) {

@@ -46,11 +46,14 @@ public:
     void release(Mark m) { cur_ = m.chunk; off_ = m.off; }
     void reset() { cur_ = 0; off_ = 0; }
     size_t capacity() const;
+    // cap on the device memory the arena may hold (0: none); a growth beyond it throws TK_ENOMEM
+    void set_limit(size_t bytes) { limit_ = bytes; }
 
 private:
     struct Chunk { char *base; size_t size; };
     std::vector<Chunk> chunks_;
     size_t cur_ = 0, off_ = 0;
+    size_t limit_ = 0;
 };
 
 struct ScopedMark {
@@ -66,17 +69,17 @@ class Profiler {
 public:
     ~Profiler();
     void begin(cudaStream_t st);
-    void end(cudaStream_t st, const char *name, double flops);
+    void end(cudaStream_t st, const char *name, double flops, double bytes = 0.0);
     void collect();                       // requires the recorded work to have completed
     std::string report_and_reset();       // "name launches total_ms" lines
 private:
     cudaEvent_t get();
     std::vector<cudaEvent_t> pool_;
     size_t used_ = 0;
-    struct Rec { const char *name; cudaEvent_t a, b; double flops; };
+    struct Rec { const char *name; cudaEvent_t a, b; double flops, bytes; };
     std::vector<Rec> recs_;
     cudaEvent_t open_ = nullptr;
-    struct Tot { long long n = 0; double ms = 0.0, flops = 0.0; };
+    struct Tot { long long n = 0; double ms = 0.0, flops = 0.0, bytes = 0.0; };
     std::vector<std::pair<std::string, Tot>> tot_;
 };
 
@@ -88,8 +91,9 @@ struct Ctx {
     int num_sms = 148;
     Profiler *prof = nullptr;
     void pre_launch() { if (prof) prof->begin(st); }
-    // `flops`: algorithmic FP64 operations of the launch (0 where not defined)
-    void check_launch(const char *what, double flops = 0.0);
+    // `flops`: algorithmic operations of the launch, `bytes`: algorithmic memory traffic (each
+    // operand read once, each result written once); 0 where not defined
+    void check_launch(const char *what, double flops = 0.0, double bytes = 0.0);
 };
 
 // ------------------------------------------------------------------------------------------
@@ -262,6 +266,8 @@ void sqrt_scalar(Ctx &c, const double *in, double *out);
 void sine_basis(Ctx &c, double *V, int n, double t);
 // p = I (n x n)
 void set_identity(Ctx &c, double *p, int n);
+// measured FMA rate of the device in TFLOP/s (fp64 = 1: FP64, 0: FP32)
+double fma_peak_tflops(Ctx &c, int fp64);
 // dst (cols x rows, ld ldd) = src(rows x cols, ld lds)^T
 void transpose_block(Ctx &c, double *dst, int ldd, const double *src, int lds, int rows, int cols);
 // upper triangle (rows x cols) of src into dst, zeros below the diagonal

@@ -24,6 +24,9 @@ CASES = {
     # projected Tikhonov with the GCV parameter (Section 4.3), noisy deblurring
     "tik_sgmres_deblur_n24": (lambda: W.deblur3d_noisy(24, 3, None),
                               W.SolverParams('rhosvd', 12, 64, 5, 20, 1e-8, seed=3, tikhonov=True), False),
+    "tik_sgmres_deblur_n24_sketchrows": (lambda: W.deblur3d_noisy(24, 3, None),
+                                         W.SolverParams('rhosvd', 12, 64, 5, 20, 1e-8, seed=3, tikhonov=True,
+                                                        gcv_rows="sketch"), False),
     "tik_gmres_deblur_n16": (lambda: W.deblur3d_noisy(16, 4, None),
                              W.SolverParams('gmres', 10, 0, 5, 15, 1e-8, seed=4, tikhonov=True), False),
     "tik_mln_deblur_n16": (lambda: W.deblur3d_noisy(16, 5, None),

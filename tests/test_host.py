@@ -114,14 +114,14 @@ def _bench(args, env_extra=None, timeout=300):
 def test_reference_arm_json_contract():
     """bench.py --impl reference: the oracle timed on the host cores, one JSON line with the
     contract's keys (the reference arm of the benchmark, no GPU involved)."""
-    rc, lines = _bench(["--impl", "reference", "--steps", "1", "--warmup", "0"])
+    rc, lines = _bench(["--impl", "reference", "--steps", "1", "--warmup", "0", "--workload", "poisson3d_smooth_n64"])
     assert rc == 0 and len(lines) == 1
     d = lines[0]
     for key in ["metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
                 "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"]:
         assert key in d, key
-    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "iters/s"
-    assert d["config"]["workload"] == "convdiff3d_n256"
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "s" and d["higher_is_better"] is False
+    assert d["config"]["workload"] == "poisson3d_smooth_n64"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"]["value"] == d["value"]

@@ -36,3 +36,54 @@ def test_static_workspace_rejects_sizes_beyond_its_limits():
         b = P.to_fortran(np.ones(s), "cuda")
         with pytest.raises(P.TuckerError):
             P.tk_sketched_ls_static(M, b)
+
+
+_FRESH_PROCESS = r"""
+import ctypes, sys
+import numpy as np
+lib = ctypes.CDLL(sys.argv[1])                 # the library (and through it the CUDA runtime)
+rt = ctypes.CDLL("libcudart.so.13")
+vp, sz = ctypes.c_void_p, ctypes.c_size_t
+assert rt.cudaSetDevice(0) == 0 and rt.cudaFree(None) == 0      # context, modules loaded eagerly
+rng = np.random.default_rng(5)
+s, k = 200, 60
+host = {"M": np.asfortranarray(rng.standard_normal((s, k))), "b": rng.standard_normal(s),
+        "y": np.zeros(k), "res": np.zeros(1)}
+dev = {}
+for name, a in host.items():
+    p = vp()
+    assert rt.cudaMalloc(ctypes.byref(p), sz(a.nbytes)) == 0
+    assert rt.cudaMemcpy(p, a.ctypes.data_as(vp), sz(a.nbytes), 1) == 0          # host to device
+    dev[name] = p
+h = vp()
+assert lib.tk_create(ctypes.byref(h), 0) == 0
+# the regular entry point first: its launch reserves what the least-squares kernel needs (and
+# its handle allocates its own workspace), so what follows isolates the static entry point
+assert lib.tk_sketched_ls(h, dev["M"], dev["b"], s, k, dev["y"], dev["res"], None) == 0
+assert rt.cudaDeviceSynchronize() == 0
+free, total = sz(), sz()
+assert rt.cudaMemGetInfo(ctypes.byref(free), ctypes.byref(total)) == 0
+free0 = free.value
+for _ in range(3):
+    assert lib.tk_sketched_ls_static(dev["M"], dev["b"], s, k, dev["y"], dev["res"], None) == 0
+assert rt.cudaDeviceSynchronize() == 0
+assert rt.cudaMemGetInfo(ctypes.byref(free), ctypes.byref(total)) == 0
+print("FREE", free0, free.value)
+"""
+
+
+def test_static_workspace_allocates_nothing_in_a_fresh_process():
+    """In a new process without PyTorch, with the library's device image loaded eagerly at
+    context creation, the first calls of the static entry point leave the device's free memory
+    unchanged: the entry point allocates nothing itself."""
+    import os
+    import subprocess
+    import sys
+    import paper_2608_11091_b300 as P
+    env = dict(os.environ, CUDA_MODULE_LOADING="EAGER")
+    out = subprocess.run([sys.executable, "-c", _FRESH_PROCESS, P.LIB_PATH], capture_output=True, text=True,
+                         env=env, timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = [ln for ln in out.stdout.splitlines() if ln.startswith("FREE")][-1]
+    free0, free1 = (int(v) for v in line.split()[1:])
+    assert free1 == free0, (free0, free1)

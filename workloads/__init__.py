@@ -246,6 +246,24 @@ def random_tucker(n: Sequence[int], r: Sequence[int], seed: int) -> Tucker:
     return Tucker(core, factors)
 
 
+def smooth_tucker(n: Sequence[int], r: Sequence[int], seed: int, decay: float = 2.0) -> Tucker:
+    """Tucker tensor with i.i.d. N(0,1) core and smooth factors: column c of U_k is
+    sum_j g_jc j^(-decay) sqrt(2/(n+1)) sin(j i pi/(n+1)) (i, j = 1..n_k, g_jc i.i.d. N(0,1)),
+    normalised to unit norm: a seeded random function whose sine coefficients decay like
+    j^(-decay), the kind of source a PDE right-hand side is."""
+    rng = np.random.default_rng(seed)
+    core = rng.standard_normal(tuple(r))
+    factors = []
+    for nk, rk in zip(n, r):
+        i = np.arange(1, nk + 1)
+        basis = np.sqrt(2.0 / (nk + 1)) * np.sin(np.outer(i, i) * np.pi / (nk + 1))
+        coef = rng.standard_normal((nk, rk)) * (i[:, None].astype(float) ** -decay)
+        u = basis @ coef
+        u /= np.linalg.norm(u, axis=0, keepdims=True)
+        factors.append(u)
+    return Tucker(core, factors)
+
+
 # ----------------------------------------------------------------------------------
 # The five synthetic workloads
 # ----------------------------------------------------------------------------------
@@ -265,6 +283,8 @@ class SolverParams:
     r_sol: int = 0          # MLN memory-efficient variant (Section 3.3): solution rank r_sol,
     p_sol: int = 0          # stored sketches cut to r_sol + p_sol (0: off)
     tikhonov: bool = False  # projected Tikhonov with the GCV parameter in every least-squares step
+    gcv_rows: str = "projected"  # GCV's row count for the sketched variants: 'projected' (k + 1) or
+                                 # 'sketch' (every row of the sketch, s or r + p)
 
 
 @dataclass
@@ -366,8 +386,22 @@ def workload(name: str, seed: int = 0) -> Workload:
         p = SolverParams('rhosvd', 32, 256, 5, 150, 1e-6, seed=seed)
         return deblur3d(128, seed, p)
     if name == "poisson3d_n1024":
+        # rank (8,8,8) seeded smooth right-hand side, solved with the exponential-sum
+        # preconditioner of q = 8 (2q+1 = 17 terms)
+        p = SolverParams('rhosvd', 64, 256, 5, 40, 1e-6, seed=seed)
+        op = kronecker_sum_operator([second_difference(1024)], 3)
+        return Workload(name, op, smooth_tucker([1024] * 3, [8] * 3, seed), p, extra={"precond_q": 8})
+    if name == "poisson3d_smooth_n64":
+        # a small instance of the same problem (test size)
+        p = SolverParams('rhosvd', 24, 64, 5, 20, 1e-6, seed=seed)
+        op = kronecker_sum_operator([second_difference(64)], 3)
+        return Workload(name, op, smooth_tucker([64] * 3, [4] * 3, seed), p, extra={"precond_q": 16})
+    if name == "poisson3d_n1024_gaussian":
+        # the same problem with white-noise (i.i.d. Gaussian, unit-norm) factors: its solution
+        # is not representable at rank 64 to 1e-6 (iteration speed only)
         p = SolverParams('rhosvd', 64, 256, 5, 100, 1e-6, seed=seed)
-        return poisson3d(1024, 8, seed, p, name)
+        return Workload(name, kronecker_sum_operator([second_difference(1024)], 3),
+                        random_tucker([1024] * 3, [8] * 3, seed), p, extra={"precond_q": 8})
     if name == "poisson3d_point_n1000":
         p = SolverParams('rhosvd', 40, 64, 40, 20, 1e-7, eta=0.4, ktrunc=1, seed=seed)
         return poisson3d_point(1000, p, 8, name)
