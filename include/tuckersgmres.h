@@ -178,6 +178,19 @@ int tk_solve(tk_handle *h, const tk_operator *op, const tk_tucker *b, const tk_o
 int tk_solve_precond(tk_handle *h, const tk_operator *op, const tk_operator *precond, const tk_tucker *b,
                      const tk_opts *opts, tk_tucker *x_out, tk_report *report, void *stream);
 
+/* tk_solve_expsum: tk_solve_precond with the exponential-sum inverse of the Laplacian of
+ * tk_expsum_laplacian (Section 3.4: 2q+1 terms c_h E_h x .. x E_h, E_h = exp(-t_h T_{n_k}) in
+ * mode k, c_h = eta t_h, t_h = exp(h eta), eta = pi / sqrt(q)) applied as the paper applies it,
+ * through the sine eigenbasis V_k of T_{n_k} (the DST-I): with U^_k = V_k^T U_k the terms of M(X)
+ * are [c_h G; diag(w_h) U^_1, ..] in that basis (w_h = exp(-t_h lambda)), RoundSum draws its
+ * Gaussian sketches S_k as usual and applies them rotated (V_k^T S_k), and the compressed
+ * factors are rotated back by V_k.  In exact arithmetic this is RoundSum(M(V_k)) with the
+ * sketches S_k, i.e. tk_solve_precond with the dense E_h; it needs three n_k x n_k products per
+ * mode per application instead of 2q+1.  Builds V_k and the weights on the device (n_k <= 16384);
+ * q = 1..64.  Otherwise as tk_solve_precond. */
+int tk_solve_expsum(tk_handle *h, const tk_operator *op, int32_t q, const tk_tucker *b, const tk_opts *opts,
+                    tk_tucker *x_out, tk_report *report, void *stream);
+
 /* tk_checkpoint_save / tk_checkpoint_load: the Krylov state of a solve suspended by
  * opts->stop_after (status TK_SUSPENDED) as an opaque byte string in host memory, so that a
  * long solve can stop and continue later, in another handle or another process (the paper

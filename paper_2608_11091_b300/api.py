@@ -313,6 +313,26 @@ def tk_solve_precond(op: DeviceOperator, precond: DeviceOperator, b: DeviceTucke
     return x, r
 
 
+def tk_solve_expsum(op: DeviceOperator, q: int, b: DeviceTucker, opts: Options, x: Optional[DeviceTucker] = None,
+                    stream=None, device: Optional[int] = None):
+    """Flexible RHOSVD-Tucker sGMRES preconditioned by the exponential-sum inverse Laplacian of
+    2q+1 terms, applied in the sine eigenbasis (Section 3.4). Returns (x, Report)."""
+    h = handle(device)
+    if x is None:
+        x = DeviceTucker.empty(b.n, [opts.rank_cap] * b.d, device=b.core.device)
+    hist = (ctypes.c_double * max(1, opts.maxit))()
+    rep = L.tk_report()
+    rep.res_hist = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
+    rep.res_hist_len = opts.maxit
+    opc, bc, oc, xc = op.c(), b.c(), opts.c(), x.c()
+    rc = h.lib.tk_solve_expsum(h.h, ctypes.byref(opc), int(q), ctypes.byref(bc), ctypes.byref(oc), ctypes.byref(xc),
+                               ctypes.byref(rep), _stream(stream))
+    h.check(rc, "tk_solve_expsum")
+    r = Report(rep.iters, STATUS[rep.status], rep.sketched_res, list(hist[:rep.iters]),
+               list(rep.out_rank[:b.d]), rep.ms_total, rep.workspace_bytes, rep.kernel_launches, rep.true_res)
+    return x, r
+
+
 def tk_checkpoint_save(device: Optional[int] = None) -> bytes:
     """The Krylov state of the solve suspended in this device's handle (opts.stop_after), as bytes."""
     h = handle(device)

@@ -554,6 +554,60 @@ void sine_basis(Ctx &c, double *V, int n, double t) {
     c.check_launch("sine_basis");
 }
 
+// ------------------------------------------------------------------------------------------
+// Row scalings of the exponential-sum preconditioner in the sine basis (memory bound)
+// ------------------------------------------------------------------------------------------
+constexpr int RS_MAXJ = 128;
+struct RowScaleJobs {
+    int n;
+    RowScaleJob j[RS_MAXJ];
+};
+
+__global__ void k_row_scale(const __grid_constant__ RowScaleJobs J) {
+    const RowScaleJob &R = J.j[blockIdx.y];
+    const long long total = (long long)R.n * R.r;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x)
+        R.out[e] = R.w[e % R.n] * R.in[e];
+}
+
+void row_scale(Ctx &c, const std::vector<RowScaleJob> &jobs) {
+    for (size_t base = 0; base < jobs.size(); base += RS_MAXJ) {
+        RowScaleJobs J{};
+        J.n = (int)std::min<size_t>(RS_MAXJ, jobs.size() - base);
+        long long mx = 1;
+        double bytes = 0.0;
+        for (int i = 0; i < J.n; ++i) {
+            J.j[i] = jobs[base + i];
+            const long long e = (long long)J.j[i].n * J.j[i].r;
+            mx = std::max(mx, e);
+            bytes += 16.0 * e + 8.0 * J.j[i].n;
+        }
+        const long long blocks = std::min<long long>((mx + 255) / 256, 512);
+        c.pre_launch();
+        k_row_scale<<<dim3((unsigned)blocks, J.n), 256, 0, c.st>>>(J);
+        c.check_launch("row_scale", 0.0, bytes);
+    }
+}
+
+__global__ void k_expsum_weights(double *w, int n, int q, double eta) {
+    const long long total = (long long)n * (2 * q + 1);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long i = e % n, h = e / n;
+        const double lam = 2.0 - 2.0 * cospi((double)(i + 1) / (n + 1));
+        w[e] = exp(-exp((double)(h - q) * eta) * lam);
+    }
+}
+
+void expsum_weights(Ctx &c, double *w, int n, int q, double eta) {
+    const long long total = (long long)n * (2 * q + 1);
+    const long long blocks = std::min<long long>((total + 255) / 256, 1024);
+    c.pre_launch();
+    k_expsum_weights<<<(unsigned)blocks, 256, 0, c.st>>>(w, n, q, eta);
+    c.check_launch("expsum_weights");
+}
+
 __global__ void k_set_identity(double *p, int n) {
     const long long total = (long long)n * n;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;

@@ -208,7 +208,7 @@ static void get_ls(BlobR &r, Ctx &c, const LSState &ls, int rows, int kmax) {
 // ------------------------------------------------------------------------------------------
 static void solve_rhosvd(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucker *b,
                          const tk_opts &o, tk_tucker *x, SolveOut &so, double *pinned,
-                         const OpDesc *precond, Ckpt &ck) {
+                         const OpDesc *precond, Ckpt &ck, const ExpSumPC *es = nullptr) {
     ScopedMark solve_mark(*c.arena);
     const int d = pb.d, R = o.rank_cap, s = o.sketch_s, sr = o.rank_cap + o.oversample_p;
     const int kmax = std::min(o.maxit, s - 1);
@@ -322,8 +322,17 @@ static void solve_rhosvd(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tuck
         if (precond) {
             Slot zs = alloc_slot(c, pb, R);
             ScopedMark it(*c.arena);
-            std::vector<TTerm> mterms = apply_operator(c, pb, *precond, V.back(), o.transpose);
-            roundsum(c, pb, mterms, RSConfig{sr, R, o.round_tol, o.seed, call++, bf16}, zs.out(pb));
+            if (es) {
+                // Section 3.4: the terms of M(V_k) in the sine eigenbasis, RoundSum with the sketches
+                // rotated into that basis and the factors rotated back (the DST-I application)
+                std::vector<TTerm> mterms = expsum_terms(c, pb, *es, V.back());
+                RSConfig rc{sr, R, o.round_tol, o.seed, call++, bf16};
+                rc.rot = es->V;
+                roundsum(c, pb, mterms, rc, zs.out(pb));
+            } else {
+                std::vector<TTerm> mterms = apply_operator(c, pb, *precond, V.back(), o.transpose);
+                roundsum(c, pb, mterms, RSConfig{sr, R, o.round_tol, o.seed, call++, bf16}, zs.out(pb));
+            }
             Z.push_back(zs.term(pb, R));
             zrank.push_back(zs.rank);
         }
@@ -1139,7 +1148,8 @@ static CkFinger finger_of(const tk_tucker *b, const tk_opts &o, const OpDesc &od
 }
 
 static int solve_entry(tk_handle *h, const tk_operator *op, const tk_operator *pc, const tk_tucker *b,
-                       const tk_opts *opts, tk_tucker *x_out, tk_report *report, void *stream) {
+                       const tk_opts *opts, tk_tucker *x_out, tk_report *report, void *stream,
+                       int expsum_q = 0) {
     return guarded(h, [&]() -> int {
         TK_REQUIRE(opts != nullptr && report != nullptr, "solve: null opts or report");
         check_tucker(b, "b");
@@ -1168,7 +1178,14 @@ static int solve_entry(tk_handle *h, const tk_operator *op, const tk_operator *p
             TK_REQUIRE(o.variant == TK_RHOSVD_SGMRES, "preconditioning is available for RHOSVD-Tucker sGMRES");
             pd = op_of(pc, pb);
         }
-        const CkFinger fp = finger_of(b, o, od, pc ? &pd : nullptr);
+        if (expsum_q) {
+            TK_REQUIRE(o.variant == TK_RHOSVD_SGMRES, "preconditioning is available for RHOSVD-Tucker sGMRES");
+            TK_REQUIRE(expsum_q >= 1 && expsum_q <= 64, "expsum: q must be 1..64");
+            for (int k = 0; k < pb.d; ++k) TK_REQUIRE(pb.n[k] <= 16384, "expsum: mode size must be <= 16384");
+            pd.nterms = 2 * expsum_q + 1;   // recorded in the checkpoint fingerprint
+        }
+        CkFinger fp = finger_of(b, o, od, (pc || expsum_q) ? &pd : nullptr);
+        if (expsum_q) fp.precond = 2;
         Ckpt ck;
         std::vector<char> next;
         if (o.resume) {
@@ -1190,8 +1207,30 @@ static int solve_entry(tk_handle *h, const tk_operator *op, const tk_operator *p
         TK_CUDA(cudaEventCreate(&e1));
         TK_CUDA(cudaEventRecord(e0, c.st));
         SolveOut so;
+        ScopedMark pc_mark(h->arena);
+        ExpSumPC es;
+        if (expsum_q) {
+            // sine eigenbasis and exponential weights per distinct mode size (Section 3.4)
+            es.q = expsum_q;
+            es.nh = 2 * expsum_q + 1;
+            const double eta = M_PI / std::sqrt((double)expsum_q);
+            for (int hh = -expsum_q; hh <= expsum_q; ++hh) es.coef.push_back(eta * std::exp(hh * eta));
+            for (int k = 0; k < pb.d; ++k) {
+                int same = -1;
+                for (int j = 0; j < k; ++j)
+                    if (pb.n[j] == pb.n[k]) { same = j; break; }
+                if (same >= 0) { es.V[k] = es.V[same]; es.w[k] = es.w[same]; continue; }
+                double *Vk = c.arena->alloc((size_t)pb.n[k] * pb.n[k]);
+                double *wk = c.arena->alloc((size_t)pb.n[k] * es.nh);
+                sine_basis(c, Vk, pb.n[k], 0.0);
+                expsum_weights(c, wk, pb.n[k], expsum_q, eta);
+                es.V[k] = Vk;
+                es.w[k] = wk;
+            }
+        }
         if (o.variant == TK_RHOSVD_SGMRES)
-            solve_rhosvd(c, pb, od, b, o, x_out, so, h->pinned, pc ? &pd : nullptr, ck);
+            solve_rhosvd(c, pb, od, b, o, x_out, so, h->pinned, (pc || expsum_q) ? &pd : nullptr, ck,
+                         expsum_q ? &es : nullptr);
         else if (o.variant == TK_RHOSVD_GMRES)
             solve_gmres(c, pb, od, b, o, x_out, so, h->pinned, ck);
         else
@@ -1232,6 +1271,15 @@ int tk_solve_precond(tk_handle *h, const tk_operator *op, const tk_operator *pre
                      const tk_opts *opts, tk_tucker *x_out, tk_report *report, void *stream) {
     if (!precond) return TK_EINVAL;
     return solve_entry(h, op, precond, b, opts, x_out, report, stream);
+}
+
+int tk_solve_expsum(tk_handle *h, const tk_operator *op, int32_t q, const tk_tucker *b, const tk_opts *opts,
+                    tk_tucker *x_out, tk_report *report, void *stream) {
+    if (q < 1) {
+        if (h) h->err = "expsum: q must be >= 1";
+        return TK_EINVAL;
+    }
+    return solve_entry(h, op, nullptr, b, opts, x_out, report, stream, q);
 }
 
 int tk_checkpoint_save(tk_handle *h, void *buf, int64_t cap, int64_t *size_out) {

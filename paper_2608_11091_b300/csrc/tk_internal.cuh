@@ -260,6 +260,11 @@ void copy_core_pad(Ctx &c, double *dst, const int *rdst, const double *src, cons
 // extract the superdiagonal G[i,..,i] of a cube with side m, d modes: out[i]
 void superdiag(Ctx &c, const double *G, int m, int d, double *out, double scale_host,
                const double *scale_dev);
+// out[i + n j] = w[i] in[i + n j]  (n x r), many jobs per launch
+struct RowScaleJob { const double *in, *w; double *out; int n, r; };
+void row_scale(Ctx &c, const std::vector<RowScaleJob> &jobs);
+// w[h n + i] = exp(-t_h lambda_i), lambda_i = 2 - 2 cos((i + 1) pi / (n + 1)), t_h = exp((h - q) eta)
+void expsum_weights(Ctx &c, double *w, int n, int q, double eta);
 // scalar helpers for the solver control flow
 void sqrt_scalar(Ctx &c, const double *in, double *out);
 // V (n x n) = sine eigenvectors of tridiag(-1,2,-1), columns scaled by exp(-t lambda_j) if t != 0

@@ -267,6 +267,16 @@ void roundsum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const RSC
         }
         gaussian(c, cfg.seed, sids, cnt, S, d, cfg.bf16_sketch);
     }
+    if (cfg.rot) {
+        // terms given in the bases Q_k: rotate the sketches, S_k <- Q_k^T S_k
+        Gemm g(c, "gemm_rotate");
+        for (int k = 0; k < d; ++k) {
+            double *Sr = c.arena->alloc((size_t)pb.n[k] * sr);
+            g.add1(pb.n[k], sr, pb.n[k], 1, 0, cfg.rot[k], pb.n[k], S[k], pb.n[k], Sr, pb.n[k]);
+            S[k] = Sr;
+        }
+        g.run();
+    }
     // 2. factor sketches M_j^(i) = U_j^(i)T S_j, shared between terms with the same factor
     // (mixed form: on tensor cores, U in three BF16 pieces, S exact in BF16)
     const bool mixed = cfg.bf16_sketch != 0;
@@ -280,9 +290,9 @@ void roundsum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const RSC
                 auto it = made[j].find(terms[i].f[j]);
                 if (it != made[j].end()) { M[i][j] = it->second; continue; }
                 double *m = c.arena->alloc((size_t)terms[i].r[j] * sr);
-                if (mixed)
+                if (mixed)   // S is exact in BF16 unless rotated
                     tc.push_back(TcProb{terms[i].f[j], S[j], m, terms[i].r[j], sr, pb.n[j], pb.n[j], pb.n[j],
-                                        terms[i].r[j], 1, 0, 3, 1, 1.0, 0.0, 0, 0, 0});
+                                        terms[i].r[j], 1, 0, 3, cfg.rot ? 3 : 1, 1.0, 0.0, 0, 0, 0});
                 else
                     g.add1(terms[i].r[j], sr, pb.n[j], 1, 0, terms[i].f[j], pb.n[j], S[j], pb.n[j], m, terms[i].r[j]);
                 made[j][terms[i].f[j]] = m;
@@ -399,12 +409,56 @@ void roundsum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const RSC
         C = Cn;
         cur[k] = R;
     }
-    // 9. output factors U^_k W_k   (n_k x R)
+    // 9. output factors U^_k W_k   (n_k x R), rotated back by Q_k when the terms were rotated
     {
         Gemm g(c, "gemm_factors");
-        for (int k = 0; k < d; ++k) g.add1(pb.n[k], R, sr, 0, 0, Q[k], pb.n[k], W[k], sr, out.f[k], pb.n[k]);
+        double *tmp[TK_MAX_D];
+        for (int k = 0; k < d; ++k) {
+            tmp[k] = cfg.rot ? c.arena->alloc((size_t)pb.n[k] * R) : out.f[k];
+            g.add1(pb.n[k], R, sr, 0, 0, Q[k], pb.n[k], W[k], sr, tmp[k], pb.n[k]);
+        }
+        g.run();
+        if (cfg.rot) {
+            Gemm g2(c, "gemm_rotate");
+            for (int k = 0; k < d; ++k)
+                g2.add1(pb.n[k], R, pb.n[k], 0, 0, cfg.rot[k], pb.n[k], tmp[k], pb.n[k], out.f[k], pb.n[k]);
+            g2.run();
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Exponential-sum preconditioner applied in the sine eigenbasis (Section 3.4: the DST-I of the
+// factor matrices): E_h U = V diag(w_h) V^T U, so the 2q+1 terms of M(X) are, in the basis V,
+// [c_h G; diag(w_h) V^T U_1, ...]: one product V^T U_k per mode and row scalings.
+// ------------------------------------------------------------------------------------------
+std::vector<TTerm> expsum_terms(Ctx &c, const Dims &pb, const ExpSumPC &es, const TTerm &x) {
+    const int d = pb.d;
+    double *Uh[TK_MAX_D];
+    {
+        Gemm g(c, "gemm_sine");
+        for (int k = 0; k < d; ++k) {
+            Uh[k] = c.arena->alloc((size_t)pb.n[k] * x.r[k]);
+            g.add1(pb.n[k], x.r[k], pb.n[k], 1, 0, es.V[k], pb.n[k], x.f[k], pb.n[k], Uh[k], pb.n[k]);
+        }
         g.run();
     }
+    std::vector<TTerm> out(es.nh);
+    std::vector<RowScaleJob> jobs;
+    for (int h = 0; h < es.nh; ++h) {
+        TTerm &T = out[h];
+        T.core = x.core;
+        T.coef = es.coef[h] * x.coef;
+        T.coef_dev = x.coef_dev;
+        for (int k = 0; k < d; ++k) {
+            T.r[k] = x.r[k];
+            double *f = c.arena->alloc((size_t)pb.n[k] * x.r[k]);
+            jobs.push_back(RowScaleJob{Uh[k], es.w[k] + (size_t)h * pb.n[k], f, pb.n[k], x.r[k]});
+            T.f[k] = f;
+        }
+    }
+    row_scale(c, jobs);
+    return out;
 }
 
 // ------------------------------------------------------------------------------------------

@@ -76,8 +76,24 @@ struct RSConfig {
     uint64_t seed;
     uint64_t call;      // RoundSum call index (stream id)
     int bf16_sketch;    // round the Gaussian matrices to bfloat16
+    // optional orthogonal n_k x n_k matrices Q_k (device): the terms are given in the basis Q_k
+    // (term factors Q_k^T U), so the sketches are rotated into it (S_k <- Q_k^T S_k) and the
+    // output factors rotated back (U <- Q_k U): the result is RoundSum of the terms Q_k U with
+    // the sketches S_k, computed without forming Q_k U
+    const double *const *rot = nullptr;
 };
 void roundsum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const RSConfig &cfg, const TOut &out);
+
+// Exponential-sum preconditioner (Section 3.4) in the sine eigenbasis of T_n: per mode the
+// basis V_k (n_k x n_k, symmetric orthogonal) and the weights w[h][i] = exp(-t_h lambda_i).
+struct ExpSumPC {
+    int q = 0, nh = 0;
+    std::vector<double> coef;              // c_h = eta t_h, h = -q..q
+    const double *V[TK_MAX_D] = {};
+    const double *w[TK_MAX_D] = {};        // nh x n_k, row h contiguous
+};
+// Terms of M(X) in the sine basis: [c_h G; diag(w_h) V_1^T U_1, ..., diag(w_h) V_d^T U_d]
+std::vector<TTerm> expsum_terms(Ctx &c, const Dims &pb, const ExpSumPC &es, const TTerm &x);
 
 void mln_sketch_sum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const double *const *psi,
                     int r, int p, double *gpsi, double *const *F, double beta);

@@ -30,6 +30,8 @@ CASES = {
                             None, (4, 5)),
     "sgmres_precond_poisson_n20": (lambda: W.poisson3d(20, 1, 3, None, "p20"),
                                    W.SolverParams('rhosvd', 12, 64, 5, 8, 1e-13, seed=4), 4, (2, 3)),
+    "sgmres_expsum_poisson_n20": (lambda: W.poisson3d(20, 1, 3, None, "p20"),
+                                  W.SolverParams('rhosvd', 12, 64, 5, 8, 1e-13, seed=4), -4, (2, 3)),
     "gmres_convdiff_n30": (lambda: W.convdiff3d(30, 4, None), W.SolverParams('gmres', 10, 0, 5, 12, 1e-12, seed=9),
                            None, (3, 4)),
     "mln_varcoef4d_n16": (lambda: W.varcoef4d(16, 1, None), W.SolverParams('mln', 6, 0, 6, 10, 1e-12, seed=7),
@@ -43,6 +45,8 @@ CASES = {
 def _solve(P, dop, pc, b, opts):
     if pc is None:
         return P.tk_solve(dop, b, opts)
+    if isinstance(pc, int):            # the sine-basis exponential sum of q terms
+        return P.tk_solve_expsum(dop, pc, b, opts)
     return P.tk_solve_precond(dop, pc, b, opts)
 
 
@@ -52,7 +56,7 @@ def test_resume_is_bit_for_bit(P, case):
     build, prm, q, (k1, k2) = CASES[case]
     wl = build()
     dop, b = P.DeviceOperator(wl.op), to_dev(wl.b)
-    pc = P.tk_expsum_laplacian(wl.b.n[0], wl.b.d, q) if q else None
+    pc = None if not q else (-q if q < 0 else P.tk_expsum_laplacian(wl.b.n[0], wl.b.d, q))
     opts = P.Options.from_params(prm)
     x_ref, rep_ref = _solve(P, dop, pc, b, opts)
     assert rep_ref.iters > k1 + k2, "the case must run past both suspensions"

@@ -82,6 +82,43 @@ def test_preconditioned_solver_parity_prefix(P, case):
     PT.check(rep, x, ref, PT.TOL, PT.TOL)
 
 
+@pytest.mark.parametrize("case", list(PRECOND_CASES))
+def test_expsum_sine_basis_solver_parity(P, case):
+    """tk_solve_expsum (the preconditioner applied in the sine eigenbasis, RoundSum with rotated
+    sketches) against the oracle's flexible iteration with the dense E_h: equal in exact
+    arithmetic, so the bounds are those of the dense path (prefix and full length)."""
+    build, prm, q = PRECOND_CASES[case]
+    wl = build()
+    prm = prm or wl.params
+    n = wl.b.n[0]
+    ref = OS.rhosvd_sgmres(wl.op, wl.b, prm, precond=OPC.expsum_preconditioner(n, wl.b.d, q))
+    x, rep = P.tk_solve_expsum(P.DeviceOperator(wl.op), q, to_dev(wl.b), P.Options.from_params(prm))
+    x_tol, h_tol = PT.full_length_bounds(case, SENS[case])
+    PT.check(rep, x, ref, x_tol, h_tol, prefix_hist=SENS[case]["prefix"])
+    pm = PT.with_maxit(prm, SENS[case]["prefix"])
+    ref = OS.rhosvd_sgmres(wl.op, wl.b, pm, precond=OPC.expsum_preconditioner(n, wl.b.d, q))
+    x, rep = P.tk_solve_expsum(P.DeviceOperator(wl.op), q, to_dev(wl.b), P.Options.from_params(pm))
+    PT.check(rep, x, ref, PT.TOL, PT.TOL)
+
+
+def test_expsum_sine_basis_transposed_and_mixed(P):
+    """The adjoint (transposed) solve and the mixed form through the sine-basis path: transposed
+    against the oracle's transposed flexible iteration (1e-10); mixed reaches the FP64 solve's
+    true residual to within 2x."""
+    wl = W.poisson3d(24, 2, 7, None, "p24")
+    prm = W.SolverParams('rhosvd', 12, 48, 5, 8, 1e-9, seed=6)
+    pc = OPC.expsum_preconditioner(24, 3, 6)
+    dop = P.DeviceOperator(wl.op)
+    p4 = PT.with_maxit(prm, 3)      # residuals still far above their rounding floor
+    x, rep = P.tk_solve_expsum(dop, 6, to_dev(wl.b), P.Options.from_params(p4, transpose=True))
+    ref = OS.rhosvd_sgmres(wl.op, wl.b, p4, transpose=True, precond=pc)
+    PT.check(rep, x, ref, PT.TOL, PT.TOL)
+    ref = OS.rhosvd_sgmres(wl.op, wl.b, prm, precond=pc)
+    xm, repm = P.tk_solve_expsum(dop, 6, to_dev(wl.b), P.Options.from_params(prm, precision="mixed"))
+    tr_m, tr_f = P.tk_residual(dop, xm, to_dev(wl.b)), ORS.true_residual(wl.op, ref.x, wl.b)
+    assert tr_m <= 2 * tr_f + 1e-9
+
+
 def test_preconditioned_point_source_true_residual(P):
     """The paper's Poisson setting (n = 1000, rank-1 point-source right-hand side): the flexible
     solver stops on the sketched residual and the true relative residual agrees with it."""
