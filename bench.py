@@ -6,10 +6,10 @@ right-hand side of multilinear rank (8,8,8) with seeded smooth factors, rank cap
 sketch s = 256, RoundSum oversampling 5, flexible RHOSVD-Tucker sGMRES (Algorithm 2) with the
 exponential-sum inverse-Laplacian preconditioner of Section 3.4 (q = 16, 33 terms), tol 1e-6.
 
-One step = one gradient evaluation: the forward solve to the tolerance, the adjoint solve
-L^T mu = w of the quantity of interest l = <w, x> (w smooth, rank 1) to the same tolerance and the
-adjoint contractions dl/dtheta, dl/dG_b, dl/dU_b (every step of the path in the library's
-kernels).  `value` is the seconds per step of the mixed form (BF16 sketches and tensor-core
+One step = one gradient evaluation: the forward solve to the tolerance and the adjoint solve
+L^T mu = w of the quantity of interest l = <w, x> (w smooth, rank 1) to the same tolerance, run
+at the same time on two streams (tk_solve_concurrent; they are independent), then the adjoint
+contractions dl/dtheta, dl/dG_b, dl/dU_b (every step of the path in the library's kernels).  `value` is the seconds per step of the mixed form (BF16 sketches and tensor-core
 products with FP32 accumulation, FP64 QR/SVD/least squares); `config.fp64_seconds` is the same
 step in plain FP64 and `config.mixed_speedup` their ratio.  Inputs are resident in HBM and L2 is
 flushed (256 MiB write) between steps; `e2e` repeats the step through the public API with the
@@ -251,12 +251,20 @@ class Problem:
         self.mu = P.DeviceTucker.empty(self.b.n, [R] * d)
         self.np = np
 
-    def step(self, P, form):
+    def step(self, P, form, concurrent=True):
+        """Forward and adjoint solves at the same time (independent: the adjoint right-hand side
+        is w), then the adjoint contractions.  concurrent=False runs them one after the other on
+        the default handle (the kernel profile is per handle)."""
         opts = P.Options.from_params(self.prm, precision=form)
-        x, rep = P.tk_solve_expsum(self.dop, PRECOND_Q, self.b, opts, x=self.x)
         adj = copy.copy(opts)
         adj.transpose = True
-        mu, rep_a = P.tk_solve_expsum(self.dop, PRECOND_Q, self.w, adj, x=self.mu)
+        if concurrent:
+            (x, rep), (mu, rep_a) = P.tk_solve_concurrent(
+                [dict(op=self.dop, b=self.b, opts=opts, expsum_q=PRECOND_Q, x=self.x),
+                 dict(op=self.dop, b=self.w, opts=adj, expsum_q=PRECOND_Q, x=self.mu)])
+        else:
+            x, rep = P.tk_solve_expsum(self.dop, PRECOND_Q, self.b, opts, x=self.x)
+            mu, rep_a = P.tk_solve_expsum(self.dop, PRECOND_Q, self.w, adj, x=self.mu)
         grads = P.tk_adjoint_grads(self.dop, mu, x, self.b)
         return rep, rep_a, grads
 
@@ -393,7 +401,7 @@ def run_native(args):
     for form in ("mixed", "fp64"):
         P.tk_profile(True)
         P.tk_profile_report()
-        prob.step(P, form)
+        prob.step(P, form, concurrent=False)
         profs[form] = P.tk_profile_report()
         P.tk_profile(False)
     kernels = kernel_table(profs["mixed"], peaks)

@@ -191,6 +191,30 @@ int tk_solve_precond(tk_handle *h, const tk_operator *op, const tk_operator *pre
 int tk_solve_expsum(tk_handle *h, const tk_operator *op, int32_t q, const tk_tucker *b, const tk_opts *opts,
                     tk_tucker *x_out, tk_report *report, void *stream);
 
+/* tk_solve_concurrent: independent solves run at the same time, each on its own host thread,
+ * handle and stream, so that their kernels overlap on the GPU (a single solve is a chain of
+ * small dependent launches that leaves most SMs idle; the forward and adjoint solves of a
+ * gradient are independent).  The paper has no counterpart.  Job i is what tk_solve
+ * (precond == NULL, expsum_q == 0), tk_solve_precond (precond set) or tk_solve_expsum
+ * (expsum_q > 0) would do with the same arguments; its return value is stored in jobs[i].status.
+ * Every job needs its own handle (TK_EINVAL otherwise; a handle is used by one thread at a time)
+ * and should have its own stream.  Returns TK_OK when every job succeeded (status >= 0), else the
+ * first negative status.  Synchronizes every job's stream.  The mixed form's tensor-core timeout
+ * flag is shared by the library, so a timeout may be reported by another concurrent mixed job. */
+typedef struct {
+    tk_handle *h;
+    const tk_operator *op;
+    const tk_operator *precond;
+    int32_t expsum_q;
+    const tk_tucker *b;
+    const tk_opts *opts;
+    tk_tucker *x_out;
+    tk_report *report;
+    void *stream;
+    int32_t status;
+} tk_solve_job;
+int tk_solve_concurrent(int32_t count, tk_solve_job *jobs);
+
 /* tk_checkpoint_save / tk_checkpoint_load: the Krylov state of a solve suspended by
  * opts->stop_after (status TK_SUSPENDED) as an opaque byte string in host memory, so that a
  * long solve can stop and continue later, in another handle or another process (the paper

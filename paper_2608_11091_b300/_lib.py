@@ -22,7 +22,7 @@ EXPORTS = ["tk_create", "tk_destroy", "tk_last_error", "tk_solve", "tk_apply", "
            "tk_sketched_ls", "tk_mln_roundsum", "tk_profile", "tk_profile_report",
            "tk_sketched_ls_static", "tk_sum_norm", "tk_adjoint_grads", "tk_solve_precond",
            "tk_expsum_laplacian", "tk_checkpoint_save", "tk_checkpoint_load", "tk_set_workspace_limit",
-           "tk_fma_peak", "tk_solve_expsum"]
+           "tk_fma_peak", "tk_solve_expsum", "tk_solve_concurrent"]
 
 
 class tk_tucker(ctypes.Structure):
@@ -55,6 +55,13 @@ class tk_opts(ctypes.Structure):
                 ("resume", ctypes.c_int32), ("true_residual", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("eta", ctypes.c_double),
                 ("round_tol", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class tk_solve_job(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_void_p), ("op", ctypes.c_void_p), ("precond", ctypes.c_void_p),
+                ("expsum_q", ctypes.c_int32), ("b", ctypes.c_void_p), ("opts", ctypes.c_void_p),
+                ("x_out", ctypes.c_void_p), ("report", ctypes.c_void_p), ("stream", ctypes.c_void_p),
+                ("status", ctypes.c_int32)]
 
 
 class tk_report(ctypes.Structure):
@@ -112,6 +119,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tk_fma_peak": (ctypes.c_int, [vp, i32, dp, vp]),
         "tk_solve_expsum": (ctypes.c_int, [vp, P(tk_operator), i32, P(tk_tucker), P(tk_opts), P(tk_tucker),
                                            P(tk_report), vp]),
+        "tk_solve_concurrent": (ctypes.c_int, [i32, P(tk_solve_job)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

@@ -333,6 +333,58 @@ def tk_solve_expsum(op: DeviceOperator, q: int, b: DeviceTucker, opts: Options, 
     return x, r
 
 
+_POOL: Dict[int, List[tuple]] = {}
+
+
+def _pool(device: int, count: int) -> List[tuple]:
+    """(handle, stream) pairs for concurrent solves on `device`: the device's default handle
+    with a stream of its own, then extra handles, each with its own stream (created once)."""
+    lst = _POOL.setdefault(device, [])
+    while len(lst) < count:
+        h = handle(device) if not lst else Handle(device)
+        lst.append((h, torch.cuda.Stream(device=device)))
+    return lst[:count]
+
+
+def tk_solve_concurrent(jobs: Sequence[dict], device: Optional[int] = None):
+    """Independent solves at the same time (tk_solve_concurrent): each job is a dict with op, b,
+    opts and optionally precond (DeviceOperator), expsum_q (int) and x (output DeviceTucker).
+    The jobs run on their own handles and streams, after the current stream's pending work.
+    Returns [(x, Report)] in job order; raises on the first failed job."""
+    dev = torch.cuda.current_device() if device is None else int(device)
+    pool = _pool(dev, len(jobs))
+    cur = torch.cuda.current_stream(dev)
+    keep, arr = [], (L.tk_solve_job * len(jobs))()
+    for i, (job, (h, st)) in enumerate(zip(jobs, pool)):
+        st.wait_stream(cur)
+        b, opts = job["b"], job["opts"]
+        x = job.get("x") or DeviceTucker.empty(b.n, [opts.rank_cap] * b.d, device=b.core.device)
+        hist = (ctypes.c_double * max(1, opts.maxit))()
+        rep = L.tk_report()
+        rep.res_hist = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
+        rep.res_hist_len = opts.maxit
+        opc, bc, oc, xc = job["op"].c(), b.c(), opts.c(), x.c()
+        pcc = job["precond"].c() if job.get("precond") is not None else None
+        keep.append((x, hist, rep, opc, bc, oc, xc, pcc))
+        J = arr[i]
+        J.h, J.op, J.b, J.opts, J.x_out = h.h, ctypes.addressof(opc), ctypes.addressof(bc), ctypes.addressof(oc), \
+            ctypes.addressof(xc)
+        J.precond = ctypes.addressof(pcc) if pcc is not None else None
+        J.expsum_q = int(job.get("expsum_q", 0))
+        J.report = ctypes.addressof(rep)
+        J.stream = st.cuda_stream
+    lib = L.load()
+    lib.tk_solve_concurrent(len(jobs), arr)
+    out = []
+    for i, (x, hist, rep, *_rest) in enumerate(keep):
+        h = pool[i][0]
+        h.check(arr[i].status, f"tk_solve_concurrent job {i}")
+        out.append((x, Report(rep.iters, STATUS[rep.status], rep.sketched_res, list(hist[:rep.iters]),
+                              list(rep.out_rank[:x.d]), rep.ms_total, rep.workspace_bytes, rep.kernel_launches,
+                              rep.true_res)))
+    return out
+
+
 def tk_checkpoint_save(device: Optional[int] = None) -> bytes:
     """The Krylov state of the solve suspended in this device's handle (opts.stop_after), as bytes."""
     h = handle(device)

@@ -18,6 +18,8 @@
 
 #include <algorithm>
 
+#include <atomic>
+
 #include "tk_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -221,7 +223,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const __grid_constant__ TcGroup
 
 void gemm_tc(Ctx &c, const std::vector<TcProb> &probs) {
     if (probs.empty()) return;
-    static bool attr_set = false;
+    static std::atomic<bool> attr_set{false};   // set once; idempotent if two threads race
     if (!attr_set) {
         TK_CUDA(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_OPS + TC_SMEM_RED));
         attr_set = true;

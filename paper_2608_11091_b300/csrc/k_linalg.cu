@@ -11,6 +11,8 @@
 
 #include <algorithm>
 
+#include <atomic>
+
 #include "tk_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -348,7 +350,7 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
 
 void qr_householder(Ctx &c, const std::vector<QRJob> &jobs) {
     if (jobs.empty()) return;
-    static bool attr_set = false;
+    static std::atomic<bool> attr_set{false};   // set once; idempotent if two threads race
     if (!attr_set) {
         TK_CUDA(cudaFuncSetAttribute(k_qr<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
         TK_CUDA(cudaFuncSetAttribute(k_qr<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
@@ -1149,7 +1151,7 @@ __global__ void __launch_bounds__(1024) k_tikhonov(LSState st, int ldr, int k, i
 
 void tikhonov_gcv(Ctx &c, const LSState &st, int ldr, int k, int m, double *lambda_out) {
     TK_REQUIRE(k >= 1 && k <= SVD_MAXS, "Tikhonov/GCV: at most 96 least-squares columns");
-    static bool attr_set = false;
+    static std::atomic<bool> attr_set{false};   // set once; idempotent if two threads race
     if (!attr_set) {
         TK_CUDA(cudaFuncSetAttribute(k_tikhonov, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      3 * SVD_MAXS * SVD_MAXS * (int)sizeof(double)));
@@ -1438,7 +1440,7 @@ __global__ void __launch_bounds__(1024) k_svd_cl(const __grid_constant__ SVDJobs
 
 static void svd_launch(Ctx &c, SVDJobs &J, int smax) {
     const size_t smem = 3 * (size_t)smax * smax * sizeof(double);
-    static bool attr_set = false;
+    static std::atomic<bool> attr_set{false};   // set once; idempotent if two threads race
     if (!attr_set) {
         TK_CUDA(cudaFuncSetAttribute(k_svd, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      3 * SVD_MAXS * SVD_MAXS * (int)sizeof(double)));
@@ -1457,7 +1459,7 @@ static void svd_launch(Ctx &c, SVDJobs &J, int smax) {
 
 static void svd_cl_launch(Ctx &c, SVDJobs &J, int smax) {
     const size_t smem = 3 * (size_t)smax * smax * sizeof(double);
-    static bool attr_set = false;
+    static std::atomic<bool> attr_set{false};   // set once; idempotent if two threads race
     if (!attr_set) {
         TK_CUDA(cudaFuncSetAttribute(k_svd_cl, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      3 * SVD_MAXS * SVD_MAXS * (int)sizeof(double)));

@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <thread>
 
 #include "tucker.cuh"
 
@@ -1280,6 +1281,40 @@ int tk_solve_expsum(tk_handle *h, const tk_operator *op, int32_t q, const tk_tuc
         return TK_EINVAL;
     }
     return solve_entry(h, op, nullptr, b, opts, x_out, report, stream, q);
+}
+
+int tk_solve_concurrent(int32_t count, tk_solve_job *jobs) {
+    if (count < 1 || !jobs) return TK_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        if (!jobs[i].h) return TK_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (jobs[j].h == jobs[i].h) {
+                jobs[i].h->err = "solve_concurrent: every job needs its own handle";
+                return TK_EINVAL;
+            }
+    }
+    auto run = [jobs](int i) {
+        tk_solve_job &J = jobs[i];
+        if (J.expsum_q > 0)
+            J.status = tk_solve_expsum(J.h, J.op, J.expsum_q, J.b, J.opts, J.x_out, J.report, J.stream);
+        else if (J.precond)
+            J.status = tk_solve_precond(J.h, J.op, J.precond, J.b, J.opts, J.x_out, J.report, J.stream);
+        else
+            J.status = tk_solve(J.h, J.op, J.b, J.opts, J.x_out, J.report, J.stream);
+    };
+    std::vector<std::thread> th;
+    int next = 1;
+    try {
+        for (; next < count; ++next) th.emplace_back(run, next);
+    } catch (const std::exception &) {
+        // no more threads: the remaining jobs run in this thread after the first
+    }
+    run(0);
+    for (int i = next; i < count; ++i) run(i);
+    for (auto &t : th) t.join();
+    for (int i = 0; i < count; ++i)
+        if (jobs[i].status < 0) return jobs[i].status;
+    return TK_OK;
 }
 
 int tk_checkpoint_save(tk_handle *h, void *buf, int64_t cap, int64_t *size_out) {

@@ -170,3 +170,25 @@ def test_non_finite_inputs_return_an_error_status(P, where):
         P.tk_solve(P.DeviceOperator(op), to_dev(b_np), P.Options.from_params(prm))
     x, rep = P.tk_solve(P.DeviceOperator(wl.op), to_dev(wl.b), P.Options.from_params(prm))
     assert rep.iters == 6 and np.isfinite(rep.sketched_res)
+
+
+def test_concurrent_solves_equal_the_serial_ones(P):
+    """tk_solve_concurrent: a forward and a transposed sine-basis solve and a plain solve run at
+    the same time on three handles and streams give, bit for bit, what each gives alone; a job with
+    bad options fails with its own status while the others complete."""
+    import torch
+    wl = W.poisson3d(24, 2, 7, None, "p24")
+    dop, b = P.DeviceOperator(wl.op), to_dev(wl.b)
+    prm = W.SolverParams('rhosvd', 12, 48, 5, 6, 1e-10, seed=6)
+    o = P.Options.from_params(prm)
+    ot = P.Options.from_params(prm, transpose=True)
+    jobs = [dict(op=dop, b=b, opts=o, expsum_q=6), dict(op=dop, b=b, opts=ot, expsum_q=6), dict(op=dop, b=b, opts=o)]
+    got = P.tk_solve_concurrent(jobs)
+    ref = [P.tk_solve_expsum(dop, 6, b, o), P.tk_solve_expsum(dop, 6, b, ot), P.tk_solve(dop, b, o)]
+    torch.cuda.synchronize()
+    for (x, rep), (xr, rr) in zip(got, ref):
+        assert rep.iters == rr.iters and rep.res_hist == rr.res_hist
+        assert torch.equal(x.core, xr.core) and all(torch.equal(u, v) for u, v in zip(x.factors, xr.factors))
+    bad = P.Options.from_params(prm, rank_cap=200)
+    with pytest.raises(P.TuckerError, match="job 1"):
+        P.tk_solve_concurrent([dict(op=dop, b=b, opts=o), dict(op=dop, b=b, opts=bad)])

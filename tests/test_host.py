@@ -145,7 +145,8 @@ def test_ctypes_structs_match_the_header_layout(tmp_path):
     gcc = shutil.which("gcc")
     if gcc is None:
         pytest.skip("no C compiler")
-    structs = {name: getattr(L, name) for name in ["tk_tucker", "tk_modemat", "tk_operator", "tk_opts", "tk_report"]}
+    structs = {name: getattr(L, name) for name in ["tk_tucker", "tk_modemat", "tk_operator", "tk_opts", "tk_report",
+                                                         "tk_solve_job"]}
     src = ['#include <stddef.h>', '#include <stdio.h>', '#include "tuckersgmres.h"', 'int main(void) {']
     for name, cls in structs.items():
         src.append(f'  printf("{name} sizeof %zu\\n", sizeof({name}));')
