@@ -91,7 +91,12 @@ typedef struct {
     int32_t oversample_p;   /* RHOSVD: RoundSum oversampling (paper: 5); MLN: Nystrom p            */
     int32_t ktrunc;         /* short-recurrence window k_trunc >= 1                               */
     int32_t maxit;          /* N_max                                                               */
-    int32_t adaptive_rank;  /* RHOSVD: 1 = effective-rank sketch size (Section 3.1), 0 = r + p    */
+    int32_t adaptive_rank;  /* RHOSVD: 1 = effective-rank sketch size (Section 3.1): each RoundSum */
+                            /* uses min(max_k r~_k, rank_cap) + p columns, r~_k the smallest r   */
+                            /* whose tail of the eigenvalues of V_k^T V_k, V_k = [|c_i| ||G_i||   */
+                            /* U_k^(i)]_i, is <= round_tol^2 of their sum (formed when V_k has   */
+                            /* <= 96 rows or columns, else r~_k = rank_cap); 0 = rank_cap + p;    */
+                            /* ignored by the MLN variant, which has no RoundSum                  */
     int32_t precision;      /* TK_FP64 or TK_MIXED                                                 */
     int32_t transpose;      /* 1 = solve the adjoint system L^T(X) = B                            */
     int32_t mln_r_sol;      /* MLN memory-efficient variant (Section 3.3): 0 = off; else the     */

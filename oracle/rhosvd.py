@@ -12,7 +12,8 @@ Readings (the paper leaves them open):
   * ST-HOSVD: modes 1..d in order, SVD of the current unfolding, kept rank
     r_k = min(rank_cap, smallest r whose tail energy sum_{j>r} sigma_j^2 <= eps^2 ||C^||^2 / d);
   * adaptive sketch size: tail energy of the Gram eigenvalues of the energy-weighted
-    concatenated factors below rank_tol^2 of their total, s = min(max_k r~_k, rank_cap) + p.
+    concatenated factors below rank_tol^2 of their total, s = min(max_k r~_k, rank_cap) + p
+    (rank_tol = the RoundSum tolerance; estimate formed when V_k has <= 96 rows or columns).
 """
 from __future__ import annotations
 
@@ -46,15 +47,28 @@ def st_hosvd(c: np.ndarray, eps: float, rank_cap: int) -> Tuple[np.ndarray, List
     return c, ws
 
 
+GRAM_MAX = 96
+
+
 def effective_sketch_size(terms: Sequence[Tuple[float, Tucker]], p: int, rank_cap: int,
-                          rank_tol: float) -> int:
-    """Sketch size from the effective rank of V_k = [||G^(i)|| U_k^(i)]_i (Section 3.1)."""
+                          rank_tol: float, gram_max: int = GRAM_MAX) -> int:
+    """Sketch size from the effective rank of V_k = [|c_i| ||G^(i)||_F U_k^(i)]_i (Section 3.1):
+    r~_k is the smallest r whose tail sum_{j > r} lambda_j of the eigenvalues of V_k^T V_k is at
+    most rank_tol^2 sum_j lambda_j, and s = min(max_k r~_k, rank_cap) + p.  Reading of a size
+    limit shared with the library: the estimate is formed only when V_k has at most gram_max
+    columns or rows (min(n_k, sum_i r_k^(i)) <= gram_max); otherwise r~_k = rank_cap."""
     d = terms[0][1].d
     rt = []
     for k in range(d):
+        n_k = terms[0][1].factors[k].shape[0]
+        if min(n_k, sum(t.factors[k].shape[1] for _, t in terms)) > gram_max:
+            rt.append(rank_cap)
+            continue
         v = np.concatenate([abs(c) * np.linalg.norm(t.core) * t.factors[k] for c, t in terms], axis=1)
-        lam = np.sort(np.linalg.eigvalsh(v.T @ v))[::-1]
-        lam = np.maximum(lam, 0.0)
+        # the eigenvalues of V_k^T V_k, taken as the squared singular values of V_k: the same
+        # numbers without the rounding of forming V_k^T V_k (which would blur every eigenvalue
+        # below ~1e-16 of the largest, and with it thresholds rank_tol < 1e-8)
+        lam = np.linalg.svd(v, compute_uv=False) ** 2
         total = lam.sum()
         tail = np.concatenate([np.cumsum(lam[::-1])[::-1], [0.0]])
         r = len(lam)

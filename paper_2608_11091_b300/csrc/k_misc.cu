@@ -590,6 +590,37 @@ void row_scale(Ctx &c, const std::vector<RowScaleJob> &jobs) {
     }
 }
 
+constexpr int WC_MAXJ = 56;   // 56 x 48 bytes of parameters per launch
+struct WeightedCopyJobs {
+    int n;
+    WeightedCopyJob j[WC_MAXJ];
+};
+
+__global__ void k_weighted_copy(const __grid_constant__ WeightedCopyJobs J) {
+    const WeightedCopyJob &W = J.j[blockIdx.y];
+    const double w = fabs(W.coef * (W.cd ? *W.cd : 1.0)) * sqrt(fmax(*W.normsq, 0.0));
+    const long long total = (long long)W.n * W.r;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x)
+        W.dst[e] = w * W.src[e];
+}
+
+void weighted_copy(Ctx &c, const std::vector<WeightedCopyJob> &jobs) {
+    for (size_t base = 0; base < jobs.size(); base += WC_MAXJ) {
+        WeightedCopyJobs J{};
+        J.n = (int)std::min<size_t>(WC_MAXJ, jobs.size() - base);
+        long long mx = 1;
+        for (int i = 0; i < J.n; ++i) {
+            J.j[i] = jobs[base + i];
+            mx = std::max(mx, (long long)J.j[i].n * J.j[i].r);
+        }
+        const long long blocks = std::min<long long>((mx + 255) / 256, 256);
+        c.pre_launch();
+        k_weighted_copy<<<dim3((unsigned)blocks, J.n), 256, 0, c.st>>>(J);
+        c.check_launch("weighted_copy");
+    }
+}
+
 __global__ void k_expsum_weights(double *w, int n, int q, double eta) {
     const long long total = (long long)n * (2 * q + 1);
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;

@@ -118,6 +118,17 @@ static Slot alloc_slot(Ctx &c, const Dims &pb, int R) {
     return s;
 }
 
+// RoundSum settings of a solve: fixed sketch size rank_cap + p, or the effective-rank estimate
+// (Section 3.1) at the relative threshold round_tol when adaptive_rank is set
+static RSConfig rs_cfg(const tk_opts &o, int sr, int R, uint64_t call, int bf16) {
+    RSConfig rc{sr, R, o.round_tol, o.seed, call, bf16};
+    if (o.adaptive_rank) {
+        rc.adaptive_p = o.oversample_p;
+        rc.rank_tol = o.round_tol;
+    }
+    return rc;
+}
+
 // ------------------------------------------------------------------------------------------
 // Suspended solves: the loop state after iteration k as a byte string (host memory).  A
 // suspension copies the device state out; a resume allocates the same buffers and copies it
@@ -332,7 +343,7 @@ static void solve_rhosvd(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tuck
                 roundsum(c, pb, mterms, rc, zs.out(pb));
             } else {
                 std::vector<TTerm> mterms = apply_operator(c, pb, *precond, V.back(), o.transpose);
-                roundsum(c, pb, mterms, RSConfig{sr, R, o.round_tol, o.seed, call++, bf16}, zs.out(pb));
+                roundsum(c, pb, mterms, rs_cfg(o, sr, R, call++, bf16), zs.out(pb));
             }
             Z.push_back(zs.term(pb, R));
             zrank.push_back(zs.rank);
@@ -341,7 +352,7 @@ static void solve_rhosvd(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tuck
             ScopedMark it(*c.arena);
             std::vector<TTerm> terms = apply_operator(c, pb, op, precond ? Z.back() : V.back(), o.transpose);
             Slot wmv = alloc_slot(c, pb, R);
-            roundsum(c, pb, terms, RSConfig{sr, R, o.round_tol, o.seed, call++, bf16}, wmv.out(pb));
+            roundsum(c, pb, terms, rs_cfg(o, sr, R, call++, bf16), wmv.out(pb));
             const TTerm W = wmv.term(pb, R);
             dot(c, W.core, W.core, prodi(W.r, d), sc + SC_NW0SQ);
             double *mcol = M + (size_t)(k - 1) * s;
@@ -357,7 +368,7 @@ static void solve_rhosvd(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tuck
                 t.coef_dev = sc + SC_H + (j - j0);
                 orth.push_back(t);
             }
-            roundsum(c, pb, orth, RSConfig{sr, R, o.round_tol, o.seed, call++, bf16}, vn.out(pb));
+            roundsum(c, pb, orth, rs_cfg(o, sr, R, call++, bf16), vn.out(pb));
             const long long csz = prodi(W.r, d);
             dot(c, vn.core, vn.core, csz, sc + SC_NWSQ);
             sqrt_scalar(c, sc + SC_NWSQ, sc + SC_NW);
@@ -403,7 +414,7 @@ static void solve_rhosvd(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tuck
     for (int kk = 0; kk < d; ++kk) xo.f[kk] = x->factor[kk];
     int *rk = c.arena->alloc_int(TK_MAX_D);
     xo.rank_dev = rk;
-    roundsum(c, pb, fin, RSConfig{sr, R, o.round_tol, o.seed, call++, bf16}, xo);
+    roundsum(c, pb, fin, rs_cfg(o, sr, R, call++, bf16), xo);
     int hr[TK_MAX_D];
     TK_CUDA(cudaMemcpyAsync(hr, rk, sizeof(int) * d, cudaMemcpyDeviceToHost, c.st));
     TK_CUDA(cudaStreamSynchronize(c.st));
@@ -502,7 +513,7 @@ static void solve_gmres(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucke
             ScopedMark it(*c.arena);
             std::vector<TTerm> terms = apply_operator(c, pb, op, V.back(), o.transpose);
             Slot wmv = alloc_slot(c, pb, R);
-            roundsum(c, pb, terms, RSConfig{sr, R, o.round_tol, o.seed, call++, bf16}, wmv.out(pb));
+            roundsum(c, pb, terms, rs_cfg(o, sr, R, call++, bf16), wmv.out(pb));
             const TTerm W = wmv.term(pb, R);
             dot(c, W.core, W.core, prodi(W.r, d), sc + SC_NW0SQ);
             double *hcol = H + (size_t)(k - 1) * ld;
@@ -516,7 +527,7 @@ static void solve_gmres(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucke
                 t.coef_dev = hcol + (j - 1);
                 orth.push_back(t);
             }
-            roundsum(c, pb, orth, RSConfig{sr, R, o.round_tol, o.seed, call++, bf16}, vn.out(pb));
+            roundsum(c, pb, orth, rs_cfg(o, sr, R, call++, bf16), vn.out(pb));
             const long long csz = prodi(W.r, d);
             dot(c, vn.core, vn.core, csz, sc + SC_NWSQ);
             sqrt_scalar(c, sc + SC_NWSQ, sc + SC_NW);
@@ -562,7 +573,7 @@ static void solve_gmres(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucke
     for (int kk = 0; kk < d; ++kk) xo.f[kk] = x->factor[kk];
     int *rk = c.arena->alloc_int(TK_MAX_D);
     xo.rank_dev = rk;
-    roundsum(c, pb, fin, RSConfig{sr, R, o.round_tol, o.seed, call++, bf16}, xo);
+    roundsum(c, pb, fin, rs_cfg(o, sr, R, call++, bf16), xo);
     int hr[TK_MAX_D];
     TK_CUDA(cudaMemcpyAsync(hr, rk, sizeof(int) * d, cudaMemcpyDeviceToHost, c.st));
     TK_CUDA(cudaStreamSynchronize(c.st));
@@ -1167,7 +1178,7 @@ static int solve_entry(tk_handle *h, const tk_operator *op, const tk_operator *p
                    "unknown variant");
         TK_REQUIRE(o.rank_cap >= 1 && o.oversample_p >= 0 && o.maxit >= 1, "bad rank_cap / p / maxit");
         TK_REQUIRE(o.precision == TK_FP64 || o.precision == TK_MIXED, "bad precision");
-        TK_REQUIRE(o.adaptive_rank == 0, "adaptive sketch size is not available in this build");
+        TK_REQUIRE(o.adaptive_rank == 0 || o.adaptive_rank == 1, "adaptive_rank must be 0 or 1");
         TK_REQUIRE(o.gcv_tikhonov == 0 || o.gcv_tikhonov == 1, "gcv_tikhonov must be 0 or 1");
         TK_REQUIRE(o.gcv_rows == 0 || o.gcv_rows == 1, "gcv_rows must be 0 or 1");
         TK_REQUIRE(!o.gcv_tikhonov || o.maxit <= 96, "Tikhonov/GCV: maxit must be <= 96");
@@ -1424,7 +1435,7 @@ int tk_roundsum(tk_handle *h, int32_t nterms, const tk_tucker *xs, const double 
         }
         const int R = opts->rank_cap;
         for (int k = 0; k < pb.d; ++k) TK_REQUIRE(out->r[k] == R, "roundsum: out ranks must equal rank_cap");
-        TK_REQUIRE(opts->adaptive_rank == 0, "adaptive sketch size is not available in this build");
+        TK_REQUIRE(opts->adaptive_rank == 0 || opts->adaptive_rank == 1, "roundsum: adaptive_rank must be 0 or 1");
         const int sr = R + opts->oversample_p;
         TK_REQUIRE(sr <= 96, "roundsum: rank_cap + p must be <= 96");
         Ctx c = make_ctx(h, stream);
@@ -1433,8 +1444,7 @@ int tk_roundsum(tk_handle *h, int32_t nterms, const tk_tucker *xs, const double 
         o.core = out->core;
         for (int k = 0; k < pb.d; ++k) o.f[k] = out->factor[k];
         o.rank_dev = c.arena->alloc_int(TK_MAX_D);
-        roundsum(c, pb, terms, RSConfig{sr, R, opts->round_tol, opts->seed, call_index,
-                                        opts->precision == TK_MIXED ? 1 : 0}, o);
+        roundsum(c, pb, terms, rs_cfg(*opts, sr, R, call_index, opts->precision == TK_MIXED ? 1 : 0), o);
         int hr[TK_MAX_D];
         TK_CUDA(cudaMemcpyAsync(hr, o.rank_dev, sizeof(int) * pb.d, cudaMemcpyDeviceToHost, c.st));
         TK_CUDA(cudaStreamSynchronize(c.st));

@@ -260,6 +260,9 @@ void copy_core_pad(Ctx &c, double *dst, const int *rdst, const double *src, cons
 // extract the superdiagonal G[i,..,i] of a cube with side m, d modes: out[i]
 void superdiag(Ctx &c, const double *G, int m, int d, double *out, double scale_host,
                const double *scale_dev);
+// dst (n x r, ld n) = |coef * (*cd or 1)| * sqrt(*normsq) * src (n x r, ld n), many jobs per launch
+struct WeightedCopyJob { const double *src; double *dst; const double *cd, *normsq; double coef; int n, r; };
+void weighted_copy(Ctx &c, const std::vector<WeightedCopyJob> &jobs);
 // out[i + n j] = w[i] in[i + n j]  (n x r), many jobs per launch
 struct RowScaleJob { const double *in, *w; double *out; int n, r; };
 void row_scale(Ctx &c, const std::vector<RowScaleJob> &jobs);

@@ -249,12 +249,104 @@ std::vector<TTerm> apply_operator(Ctx &c, const Dims &pb, const OpDesc &op, cons
 // RoundSum (Section 3.1): Khatri-Rao sketched randomized HOSVD of sum_i c_i X_i followed by
 // ST-HOSVD of the projected core.  Output zero-padded to rank R.
 // ------------------------------------------------------------------------------------------
+// ------------------------------------------------------------------------------------------
+// Effective-rank sketch size (Section 3.1): V_k = [|c_i| ||G^(i)||_F U_k^(i)]_i, its squared
+// singular values are the eigenvalues lambda of V_k^T V_k; r~_k is the smallest r with
+// sum_{j > r} lambda_j <= rank_tol^2 sum_j lambda_j and s = min(max_k r~_k, cap) + p.  Formed
+// when V_k has at most 96 columns or rows (pivoted QR of V_k or V_k^T, Jacobi SVD of its R);
+// beyond that r~_k = cap.  One read-back of the singular values per call.
+// ------------------------------------------------------------------------------------------
+int effective_sketch_size(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, int cap, int p,
+                          double rank_tol) {
+    ScopedMark mark(*c.arena);
+    const int d = pb.d, N = (int)terms.size();
+    constexpr int GMAX = 96;
+    double *ns = c.arena->alloc(N);
+    {
+        std::vector<DotJob> dj;
+        for (int i = 0; i < N; ++i) dj.push_back(DotJob{terms[i].core, terms[i].core, prod(terms[i].r, 0, d), ns + i});
+        dots(c, dj);
+    }
+    int width[TK_MAX_D], cols[TK_MAX_D];
+    bool formed[TK_MAX_D];
+    std::vector<QRJob> qj;
+    std::vector<SVDJob> sj;
+    double *sig = c.arena->alloc((size_t)d * GMAX);
+    fill(c, sig, (long long)d * GMAX, 0.0);
+    std::vector<WeightedCopyJob> wj;
+    double *Vk[TK_MAX_D];
+    for (int k = 0; k < d; ++k) {
+        width[k] = 0;
+        for (int i = 0; i < N; ++i) width[k] += terms[i].r[k];
+        formed[k] = std::min(pb.n[k], width[k]) <= GMAX;
+        if (!formed[k]) continue;
+        Vk[k] = c.arena->alloc((size_t)pb.n[k] * width[k]);
+        int off = 0;
+        for (int i = 0; i < N; ++i) {
+            wj.push_back(WeightedCopyJob{terms[i].f[k], Vk[k] + (size_t)off * pb.n[k], terms[i].coef_dev, ns + i,
+                                         terms[i].coef, pb.n[k], terms[i].r[k]});
+            off += terms[i].r[k];
+        }
+    }
+    weighted_copy(c, wj);
+    for (int k = 0; k < d; ++k) {
+        if (!formed[k]) continue;
+        // columns of the QR: the smaller side (V_k or its transpose)
+        double *A = Vk[k];
+        int m = pb.n[k];
+        cols[k] = width[k];
+        if (width[k] > pb.n[k]) {
+            A = c.arena->alloc((size_t)pb.n[k] * width[k]);
+            transpose_block(c, A, width[k], Vk[k], pb.n[k], pb.n[k], width[k]);
+            m = width[k];
+            cols[k] = pb.n[k];
+        }
+        int *perm = c.arena->alloc_int(cols[k]);
+        qj.push_back(QRJob{A, c.arena->alloc(cols[k]), nullptr, m, cols[k], perm});
+        SVDJob s{};
+        s.perm = perm;
+        s.R = A; s.ldr = m; s.s = std::min(m, cols[k]); s.W = nullptr; s.wcols = 0;
+        s.sigma = sig + (size_t)k * GMAX; s.rank = nullptr; s.normsq = nullptr; s.eps2_over_d = 0.0;
+        s.rank_cap = s.s;
+        sj.push_back(s);
+    }
+    if (!qj.empty()) {
+        qr_householder(c, qj);
+        svd_jacobi(c, sj);
+    }
+    std::vector<double> hs((size_t)d * GMAX);
+    TK_CUDA(cudaMemcpyAsync(hs.data(), sig, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, c.st));
+    TK_CUDA(cudaStreamSynchronize(c.st));
+    int rmax = 1;
+    for (int k = 0; k < d; ++k) {
+        int rk = cap;
+        if (formed[k]) {
+            const int q = std::min(pb.n[k], width[k]);
+            std::vector<double> lam(q);
+            double total = 0.0;
+            for (int j = 0; j < q; ++j) { lam[j] = hs[(size_t)k * GMAX + j] * hs[(size_t)k * GMAX + j]; total += lam[j]; }
+            // tail[r] = sum_{j >= r} lambda_j (descending order); smallest r >= 1 with tail <= thr
+            const double thr = rank_tol * rank_tol * total;
+            double tail = 0.0;
+            rk = q;
+            std::vector<double> suffix(q + 1, 0.0);
+            for (int j = q - 1; j >= 0; --j) { tail += lam[j]; suffix[j] = tail; }
+            for (int r = 1; r <= q; ++r)
+                if (suffix[r] <= thr) { rk = r; break; }
+        }
+        rmax = std::max(rmax, rk);
+    }
+    return std::min(rmax, cap) + p;
+}
+
 void roundsum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const RSConfig &cfg,
               const TOut &out) {
     ScopedMark mark(*c.arena);
-    const int d = pb.d, sr = cfg.sr, R = cfg.R;
     const int N = (int)terms.size();
     TK_REQUIRE(N >= 1, "roundsum: no terms");
+    const int d = pb.d, R = cfg.R;
+    const int sr = cfg.adaptive_p >= 0 ? effective_sketch_size(c, pb, terms, R, cfg.adaptive_p, cfg.rank_tol) : cfg.sr;
+    if (cfg.sr_used) *cfg.sr_used = sr;
     // 1. Gaussian S_k (n_k x sr), stream (seed, purpose 2, call, k)
     double *S[TK_MAX_D];
     {

@@ -81,7 +81,16 @@ struct RSConfig {
     // output factors rotated back (U <- Q_k U): the result is RoundSum of the terms Q_k U with
     // the sketches S_k, computed without forming Q_k U
     const double *const *rot = nullptr;
+    // adaptive sketch size (Section 3.1): when adaptive_p >= 0, sr is replaced by
+    // min(max_k r~_k, R) + adaptive_p, r~_k from the Gram eigenvalues of the energy-weighted
+    // concatenated factors at relative threshold rank_tol
+    int adaptive_p = -1;
+    double rank_tol = 0.0;
+    int *sr_used = nullptr;   // optional host output: the sketch size this call used
 };
+// The effective-rank sketch size of a sum (Section 3.1); see RSConfig::adaptive_p.
+int effective_sketch_size(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, int cap, int p,
+                          double rank_tol);
 void roundsum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const RSConfig &cfg, const TOut &out);
 
 // Exponential-sum preconditioner (Section 3.4) in the sine eigenbasis of T_n: per mode the

@@ -31,6 +31,12 @@ CASES = {
                              W.SolverParams('gmres', 10, 0, 5, 15, 1e-8, seed=4, tikhonov=True), False),
     "tik_mln_deblur_n16": (lambda: W.deblur3d_noisy(16, 5, None),
                            W.SolverParams('mln', 8, 0, 16, 12, 1e-8, seed=5, tikhonov=True), False),
+    # effective-rank RoundSum sketch size (Section 3.1): rank-1 right-hand side, so the early
+    # Krylov tensors have low rank and the estimate is below rank_cap + p
+    "adaptive_poisson3d_n20": (lambda: W.poisson3d(20, 1, 3, None, "p20"),
+                               W.SolverParams('rhosvd', 12, 64, 5, 10, 1e-9, seed=4, adaptive_rank=True), False),
+    "adaptive_gmres_convdiff_ragged": (lambda: W.convdiff3d(37, 3, None, rhs_rank=2),
+                                       W.SolverParams('gmres', 7, 0, 6, 10, 1e-8, seed=6, adaptive_rank=True), False),
     # Algorithm 1 (full Arnoldi through RoundSum)
     "gmres_poisson3d_n20_r12": (lambda: W.poisson3d(20, 1, 3, None, "p20"),
                                 W.SolverParams('gmres', 12, 0, 5, 30, 1e-9, seed=4), False),

@@ -143,6 +143,28 @@ def test_roundsum(P, case):
         assert np.allclose(g, np.eye(rk), atol=1e-12)
 
 
+@pytest.mark.parametrize("case,cap,smaller", [("exact_lowrank", 6, True), ("point_source", 32, True),
+                                              ("truncating", 8, False), ("matvec_terms", 30, True),
+                                              ("order4", 4, False), ("small_n", 6, False)])
+def test_adaptive_roundsum(P, case, cap, smaller):
+    """RoundSum with the effective-rank sketch size (Section 3.1): the same size as the oracle's
+    estimate (so the same Gaussian draws), the same ranks, the same tensor (1e-11).  `smaller`:
+    the estimate is below rank_cap + p (exact low-rank sums; the convection-diffusion matvec,
+    whose factors span 3 r directions per mode, formed through the transposed V_k)."""
+    terms, _, p = _rs_case(case)
+    n = terms[0][1].n
+    d = len(n)
+    seed, call, eps = 3, 7, 1e-12
+    sr = OR.effective_sketch_size(terms, p, cap, eps)
+    assert (sr < cap + p) == smaller
+    sk = [W.sketch_matrix(seed, W.STREAM_ROUNDSUM, call, k, n[k], sr) for k in range(d)]
+    ref = OR.roundsum(terms, sk, cap, eps)
+    opts = P.Options(rank_cap=cap, oversample_p=p, round_tol=eps, seed=seed, adaptive_rank=True)
+    out, ranks = P.tk_roundsum([to_dev(t) for _, t in terms], [c for c, _ in terms], opts, call)
+    assert ranks == ref.r
+    assert rel_diff(to_host(out), ref) <= 1e-11
+
+
 # ------------------------------------------------------------------------------ MLN
 @pytest.mark.parametrize("n,r,p,ranks", [([30, 31, 32], 5, 4, [[2, 3, 2], [5, 5, 5]]),
                                          ([12, 13, 14, 15], 4, 3, [[3, 3, 3, 3], [1, 1, 1, 1]])])

@@ -226,6 +226,36 @@ def test_effective_sketch_size():
     assert R.effective_sketch_size([(1.0, x)], 5, 3, 1e-10) == 3 + 5
 
 
+def test_effective_sketch_size_known_gram_spectrum():
+    """A sum whose weighted factor Gram matrix V_k^T V_k is known exactly: three terms whose
+    mode-k factors are disjoint column blocks of one orthogonal matrix (so V_k^T V_k is diagonal),
+    cores of chosen Frobenius norms and chosen coefficients.  Its eigenvalues are
+    (c_i ||G_i||)^2 with multiplicity r_i = 2, 3, 4: 100, 1 and 0.01, total 203.04; the tails
+    after 2 and 5 eigenvalues are 3.04 and 0.04.  A threshold between two tail energies fixes
+    r~ exactly: rank_tol^2 = 2.5e-3 lies between 0.04/203.04 and 3.04/203.04, so r~ = 5 (a
+    weighting by ||G|| instead of ||G||^2 in the eigenvalues, or c instead of c^2, gives 2);
+    rank_tol^2 = 0.04 gives 2; 1e-4 gives 7 (tails 0.03 and 0.02 after 6 and 7 eigenvalues);
+    2.5e-5, below one 0.01 eigenvalue's share, gives 9; then the cap and the oversampling apply."""
+    n, rs = 12, [2, 3, 4]
+    rng = np.random.default_rng(3)
+    qs = [np.linalg.qr(rng.standard_normal((n, n)))[0] for _ in range(3)]
+    weights = [10.0, 1.0, 0.1]                 # c_i ||G_i||
+    coefs = [2.0, -0.5, 4.0]
+    terms, off = [], 0
+    for r, wgt, c in zip(rs, weights, coefs):
+        core = rng.standard_normal((r, r, r))
+        core *= (wgt / abs(c)) / np.linalg.norm(core)
+        fac = [q[:, off:off + r] for q in qs]
+        terms.append((c, W.Tucker(core, fac)))
+        off += r
+    assert R.effective_sketch_size(terms, 5, 50, 0.05) == 5 + 5
+    assert R.effective_sketch_size(terms, 5, 50, 0.2) == 2 + 5
+    assert R.effective_sketch_size(terms, 5, 50, 0.01) == 7 + 5
+    assert R.effective_sketch_size(terms, 5, 50, 0.005) == 9 + 5
+    assert R.effective_sketch_size(terms, 5, 4, 0.05) == 4 + 5
+    assert R.effective_sketch_size(terms, 7, 50, 0.05, gram_max=8) == 50 + 7   # beyond the size limit
+
+
 # ------------------------------------------------------------------------------ MLN
 def test_mln_diag_is_khatri_rao_sketch():
     n, r, p = [5, 4, 6], 2, 3
