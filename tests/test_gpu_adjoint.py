@@ -128,3 +128,89 @@ def test_sum_norm_is_accurate_for_small_differences(P):
     y = W.Tucker(x.core * (1 + 1e-9), x.factors)
     v = P.tk_sum_norm([to_dev(x), to_dev(y)], [1.0, -1.0])
     assert np.isclose(v, 1e-9 * OT.norm(x), rtol=1e-5)
+
+
+# ------------------------------------------------------------------------------ full size
+def _blur_eig_inverse(n, lam, sigma=2.0):
+    """A = G x G x G + lam I with G the symmetric Gaussian Toeplitz blur: G = Q diag(g) Q^T, so
+    A^{-1} is diagonal in Q (x) Q (x) Q.  Returns a function applying A^{-1} to a dense tensor
+    and ||A^{-1}||_2 = 1 / min |g_i g_j g_k + lam|."""
+    g, q = np.linalg.eigh(W.gaussian_blur_dense(n, sigma))
+    den = g[:, None, None] * g[None, :, None] * g[None, None, :] + lam
+
+    def solve(t):
+        return OT.multi_ttm(OT.multi_ttm(t, [q.T] * 3) / den, [q] * 3)
+    return solve, 1.0 / np.min(np.abs(den))
+
+
+def _unit_weight(n):
+    return W.Tucker(np.ones((1, 1, 1)), [np.ones((n, 1)) / np.sqrt(n)] * 3)
+
+
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+def test_adjoint_closed_form_deblur_n128(P, form):
+    """The deblurring workload at full size (n = 128, G Gaussian blur sigma = 2, lam = 1e-2,
+    b = A x_true with x_true of rank (6,6,6); rank cap 32, s = 256) and the quantity of interest
+    l = <w, x>, w the smooth rank-1 tensor (1/sqrt(n))^(x)3.  Exact: mu* = A^{-T} w through G's
+    eigenbasis (A^{-1} is diagonal in Q (x) Q (x) Q), dl/db = mu*, dl/dlam = -<mu*, x> at the
+    computed x, dl/dG_b = mu* x_k U_bk^T.  The GPU's mu from the transposed solve differs from
+    mu* by A^{-T} (A^T mu - w), so |<mu - mu*, v>| <= ||v|| ||A^{-1}|| ||A^T mu - w|| for any v,
+    with the adjoint residual measured in Tucker form: every gradient is checked against its
+    closed form within that bound, and the bound itself must be small (adjoint residual < 1e-6)."""
+    n, lam = 128, 1e-2
+    wl = W.workload("deblur3d_n128")
+    prm = W.SolverParams('rhosvd', 32, 256, 5, 60, 1e-7, seed=0)
+    dop, b = P.DeviceOperator(wl.op), to_dev(wl.b)
+    wq = _unit_weight(n)
+    x, _ = P.tk_solve(dop, b, P.Options.from_params(prm, precision=form))
+    mu, rep_t = P.tk_solve(dop, to_dev(wq), P.Options.from_params(prm, precision=form, transpose=True))
+    r_mu = P.tk_residual(dop, mu, to_dev(wq), transpose=True)          # ||A^T mu - w|| / ||w||, ||w|| = 1
+    assert r_mu < 1e-6
+    dth, dG, _ = P.tk_adjoint_grads(dop, mu, x, b)
+    ainv, ainv_norm = _blur_eig_inverse(n, lam)
+    mu_star = ainv(OT.full(wq))
+    err_bound = ainv_norm * r_mu                                        # >= ||mu - mu*||
+    mu_d = OT.full(to_host(mu))
+    assert np.linalg.norm(mu_d - mu_star) <= err_bound * (1 + 1e-6) + 1e-12 * np.linalg.norm(mu_star)
+    xd = OT.full(to_host(x))
+    dlam_star = -np.sum(mu_star * xd)
+    assert abs(dth[1] - dlam_star) <= np.linalg.norm(xd) * err_bound * (1 + 1e-6) + 1e-12 * abs(dlam_star)
+    dG_star = OT.multi_ttm(mu_star, [u.T for u in wl.b.factors])
+    fac_norm = np.prod([np.linalg.norm(u, 2) for u in wl.b.factors])
+    assert np.linalg.norm(dG.cpu().numpy() - dG_star) <= fac_norm * err_bound * (1 + 1e-6) + 1e-12 * np.linalg.norm(dG_star)
+
+
+def test_adjoint_central_differences_n128(P):
+    """Full size n = 128 with a well-conditioned blur system (lam = 1, rank cap 48, where the
+    forward solve reaches a relative residual near 1e-8): the adjoint gradient of l = <w, x> along
+    a core direction delta of b, <mu, [delta; U_b]> = <dl/dG_b, delta>, against central
+    differences of the GPU forward solve (common random numbers), and the mixed form's gradient
+    against the FP64 one."""
+    n = 128
+    wl = W.deblur3d(n, 0, None, lam=1.0)
+    prm = W.SolverParams('rhosvd', 48, 128, 5, 30, 1e-13, seed=0)
+    dop = P.DeviceOperator(wl.op)
+    wq = to_dev(_unit_weight(n))
+    rng = np.random.default_rng(41)
+    delta = rng.standard_normal(wl.b.core.shape)
+    delta *= np.linalg.norm(wl.b.core) / np.linalg.norm(delta)
+
+    def qoi(core):
+        x, _ = P.tk_solve(dop, to_dev(W.Tucker(core, wl.b.factors)), P.Options.from_params(prm))
+        return P.tk_inner(wq, x)
+
+    grads = {}
+    for form in ["fp64", "mixed"]:
+        x, _ = P.tk_solve(dop, to_dev(wl.b), P.Options.from_params(prm, precision=form))
+        mu, _ = P.tk_solve(dop, wq, P.Options.from_params(prm, precision=form, transpose=True))
+        _, dG, _ = P.tk_adjoint_grads(dop, mu, x, to_dev(wl.b))
+        grads[form] = float(np.sum(dG.cpu().numpy() * delta))
+    # l is linear in b, so a central difference has no truncation error of its own at any step:
+    # a large step keeps the forward solves' ~1e-8 error from being divided by a small one
+    h = 0.5
+    fd = (qoi(wl.b.core + h * delta) - qoi(wl.b.core - h * delta)) / (2 * h)
+    # the solves are accurate to ~1e-8 relative; a random direction's derivative is ~1e-3 of
+    # l itself, so both comparisons are made on the scale of l
+    scale = abs(qoi(wl.b.core))
+    assert abs(grads["fp64"] - fd) <= 1e-6 * scale
+    assert abs(grads["mixed"] - grads["fp64"]) <= 1e-6 * scale
