@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtuckersgmres.so")
-SOURCES = ["k_gemm.cu", "k_gemm_tc.cu", "k_linalg.cu", "k_misc.cu", "tucker.cu", "solver.cu", "ls_static.cu"]
+SOURCES = ["k_gemm.cu", "k_gemm_oz.cu", "k_linalg.cu", "k_misc.cu", "tucker.cu", "solver.cu", "ls_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

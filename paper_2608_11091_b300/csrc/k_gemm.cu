@@ -212,6 +212,14 @@ void Gemm::run() {
         waves.back().push_back(p);
     }
     for (const std::vector<GProb> &wave : waves) {
+        if (tc_) {
+            std::vector<GProb> oz, rest;
+            for (const GProb &p : wave) (oz_supported(p) ? oz : rest).push_back(p);
+            gemm_oz(c_, oz, tag_);
+            if (rest.empty()) continue;
+            flush_group(rest, 1);
+            continue;
+        }
         // a small grid runs each tile's BK-slab chain on an otherwise idle SM: split K (powers
         // of two, BM divisible by the factor) while the wave's grid stays within two CTAs per
         // SM, each problem only as far as every part keeps at least 8 of its reduction

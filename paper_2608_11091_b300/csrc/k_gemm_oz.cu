@@ -1,0 +1,499 @@
+// Tensor-core GEMM of the mixed-precision form (tcgen05 + TMA, sm_103a):
+//   C = beta C + sum_s coef_s op(A_s) op(B_s)      (FP64 operands and result)
+// computed from BF16 products with FP32 accumulation, exactly, on integer slices of the
+// operands (the splitting of Ozaki, Ogita, Oishi and Rump, "Error-free transformations of
+// matrix multiplication by using fast routines of matrix multiplication and its
+// applications", Numer. Algorithms 59, 2012), restated here for BF16 tensor cores:
+//
+//  * Slicing (k_oz_split).  Per row m of an operand and per chunk c of 256 reduction indices,
+//    e = the exponent with max_k |x_mk| < 2^e.  x = 2^(e - 7) (d_0 + d_1 2^-8 + ... + d_4 2^-32)
+//    + O(2^(e - 40)) with integer digits |d_p| <= 128 (the balanced base-256 expansion of the
+//    nearest integer to x 2^(39 - e)), each exactly representable in BF16.  Digits are written as
+//    five BF16 planes, K contiguous.
+//  * Products.  For digit planes p of A and q of B, sum_k d_p g_q over a chunk of 256 is an
+//    integer; grouping the products by level L = p + q (<= 4, 15 products), each level's sum
+//    is at most (L + 1) 256 2^14 <= 2^24 in magnitude, so the FP32 accumulation in tensor memory
+//    is exact.  Products with p + q > 4 are dropped: the error is about 2^-40 relative to
+//    max|A row| max|B column| per reduction index.
+//  * Accumulation.  Per chunk the epilogue adds 2^(e_m + f_n) sum_L 2^(-8L) S_L into FP64
+//    registers (one output row per thread), then C = beta C + 2^-14 acc.
+//
+// Pipeline (k_gemm_oz, one 128 x 32 output tile per CTA, 6 warps): warp 4 lane 0 issues the TMA
+// loads (five A planes 128 x 64 and five B planes 32 x 64 per K slab of 64, 128-byte swizzle)
+// into a two-stage ring; warp 5 lane 0 issues the tcgen05.mma (M 128, N 32, K 16) into two
+// alternating sets of five accumulators in tensor memory; warps 0-3 read a finished set back
+// (tcgen05.ld) while the next chunk is multiplied.  mbarriers: full / empty per stage,
+// accumulator full / empty per set.  Every wait has an iteration limit: on expiry the kernel
+// records an error in g_oz_error and all roles stop issuing work; the CTA waits (bounded) for
+// its own copies and MMAs before freeing its tensor memory.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+
+#include "tk_internal.cuh"
+
+namespace tk {
+
+__device__ int g_oz_error;
+
+constexpr int OZ_S = 5;                               // digit planes per operand
+constexpr int OZ_L = OZ_S;                            // accumulator levels L = p + q = 0..4
+constexpr int OZ_BM = 128, OZ_BN = 32, OZ_BK = 64;    // tile and K slab
+constexpr int OZ_CHUNK = 256;                         // reduction indices per exact chunk
+constexpr int OZ_SLABS = OZ_CHUNK / OZ_BK;            // slabs per chunk
+constexpr int OZ_MAXCHUNK = 16;                       // K <= 4096
+constexpr int OZ_A_TILE = OZ_BM * OZ_BK * 2;          // 16 KB
+constexpr int OZ_B_TILE = OZ_BN * OZ_BK * 2;          // 4 KB
+constexpr int OZ_STAGE = OZ_S * (OZ_A_TILE + OZ_B_TILE);
+constexpr int OZ_STAGES = 2;
+constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE + 1024;  // + alignment slack
+constexpr int OZ_TMEM_COLS = 512;                     // 2 sets x 5 levels x 32 columns
+constexpr int OZ_SET_COLS = OZ_L * OZ_BN;
+constexpr long OZ_SPIN = 1L << 20;                    // bounded waits
+
+// ------------------------------------------------------------------------------------------
+// Slicing
+// ------------------------------------------------------------------------------------------
+struct OzSeg {
+    const double *p, *cd;
+    double coef;
+    int K, ld, koff;
+};
+
+// One operand side: `rows` logical rows (A: M x batch folded, B: N) by the concatenated K of
+// the segments; element (m, k) of segment s at local index kk is, with i = m % a, b = m / a,
+// p[i + ld kk + bstride b] (trans = 0) or p[kk + ld i + bstride b] (trans = 1), times coef (and
+// *cd when set).
+struct OzSide {
+    int rows, a, trans, nseg, Kpad, Rpad;
+    long long bstride;
+    OzSeg seg[GEMM_MAXSEG];
+    __nv_bfloat16 *planes;   // [OZ_S][Rpad][Kpad]
+    short *exps;             // [nchunk][Rpad]
+};
+
+constexpr int OZ_MAXSIDES = 24;
+struct OzSides {
+    int n;
+    OzSide s[OZ_MAXSIDES];
+};
+
+// grid (row blocks of 32, chunks, sides); 256 threads; tile 32 rows x (up to) 256 in dynamic
+// shared memory (row stride OZ_CHUNK + 1), chunk c covering [256 c, min(256 c + 256, Kpad)).
+// Integer arithmetic on the FP64 bit patterns throughout (the FP64 pipe is slow on this part):
+// e = the largest exponent field of the row's chunk minus 1022 (so |v| < 2^e); X = the nearest
+// integer to v 2^(39 - e), |X| < 2^39, from the 53-bit significand by a rounding shift; the
+// digits are X's balanced base-256 expansion, X = d_0 2^32 + d_1 2^24 + ... + d_4, |d_p| <= 128.
+constexpr int OZ_SPLIT_LD = OZ_CHUNK + 1;
+constexpr int OZ_SPLIT_SMEM = 32 * OZ_SPLIT_LD * 8;
+__global__ void __launch_bounds__(256) k_oz_split(const __grid_constant__ OzSides S) {
+    const OzSide &D = S.s[blockIdx.z];
+    const int r0 = blockIdx.x * 32, c = blockIdx.y, k0 = c * OZ_CHUNK;
+    if (r0 >= D.Rpad || k0 >= D.Kpad) return;
+    const int W = min(OZ_CHUNK, D.Kpad - k0);        // a multiple of 64
+    extern __shared__ long long oz_tile[];
+    auto t = [&](int r, int kk) -> long long & { return oz_tile[r * OZ_SPLIT_LD + kk]; };
+    __shared__ int er[32];
+    const int tid = threadIdx.x;
+    for (int e = tid; e < 32 * W; e += 256) {
+        int r, kk;
+        if (D.trans) { kk = e % W; r = e / W; } else { r = e % 32; kk = e / 32; }
+        const int m = r0 + r, k = k0 + kk;
+        double v = 0.0;
+        if (m < D.rows) {
+            for (int s = 0; s < D.nseg; ++s) {
+                const OzSeg &g = D.seg[s];
+                if (k >= g.koff && k < g.koff + g.K) {
+                    const int i = m % D.a, b = m / D.a, kl = k - g.koff;
+                    const double *src = g.p + (long long)b * D.bstride;
+                    v = D.trans ? src[kl + (long long)g.ld * i] : src[i + (long long)g.ld * kl];
+                    v *= g.coef * (g.cd ? *g.cd : 1.0);
+                    break;
+                }
+            }
+        }
+        t(r, kk) = __double_as_longlong(v);
+    }
+    __syncthreads();
+    {
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int r = warp; r < 32; r += 8) {
+            int ef = 0;
+            for (int kk = lane; kk < W; kk += 32) ef = max(ef, (int)((t(r, kk) >> 52) & 0x7FF));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) ef = max(ef, __shfl_xor_sync(0xffffffffu, ef, o));
+            // exponent field E: |v| < 2^(E - 1022) for every v of the row (0 for an all-zero
+            // or subnormal row, whose digits are then 0)
+            if (lane == 0) {
+                er[r] = ef;
+                D.exps[(long long)c * D.Rpad + r0 + r] = (short)(ef > 0 ? ef - 1022 : 0);
+            }
+        }
+    }
+    __syncthreads();
+    const long long plane = (long long)D.Rpad * D.Kpad;
+    for (int e = tid; e < 32 * W; e += 256) {
+        const int r = e / W, kk = e % W;
+        const long long bits = t(r, kk);
+        const int ef = (int)((bits >> 52) & 0x7FF);
+        long long X = 0;
+        if (ef > 0) {
+            // |v| 2^(39 - e) = m 2^(ef - 1075 + 39 - e) with m the significand, e = E - 1022:
+            // a right shift by E + 14 - ef >= 14 with rounding to nearest
+            const long long m = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+            const int sh = er[r] + 14 - ef;
+            if (sh < 63) X = (m + (1LL << (sh - 1))) >> sh;
+            if (bits < 0) X = -X;
+        }
+        __nv_bfloat16 *dst = D.planes + (long long)(r0 + r) * D.Kpad + k0 + kk;
+#pragma unroll
+        for (int p = OZ_S - 1; p >= 1; --p) {
+            const long long d = ((X + 128) & 255) - 128;        // balanced digit in [-128, 127]
+            dst[p * plane] = __float2bfloat16_rn((float)d);
+            X = (X - d) >> 8;                                    // exact: X - d = 0 mod 256
+        }
+        dst[0] = __float2bfloat16_rn((float)X);                 // |d_0| <= 128
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Main kernel
+// ------------------------------------------------------------------------------------------
+struct OzProb {                                       // CUtensorMap carries its own alignment
+    CUtensorMap tmA, tmB;                            // 3-D: (K, rows, plane), BF16, 128-B swizzle
+    const short *expA, *expB;
+    double *C;
+    double beta;
+    long long sC;
+    int M, N, a, ldc, RpadA, RpadB, nslab, nchunk;
+    int tiles_m, tiles_n, tile_begin;
+};
+
+constexpr int OZ_MAXPROB = 12;
+struct OzGroup {
+    OzProb p[OZ_MAXPROB];
+    int nprob;
+};
+
+__device__ __forceinline__ uint32_t oz_smem(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool oz_wait(uint32_t bar, uint32_t parity) {
+    for (long it = 0; it < OZ_SPIN; ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// K-major operand tile in shared memory with 128-byte swizzle (8 rows x 128 B atoms)
+__device__ __forceinline__ uint64_t oz_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;                // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;      // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                // descriptor version
+    d |= (uint64_t)2 << 61;                // 128-byte swizzle
+    return d;
+}
+
+__global__ void __launch_bounds__(192, 1) k_gemm_oz(const __grid_constant__ OzGroup g) {
+    extern __shared__ unsigned char oz_dyn[];
+    __shared__ __align__(8) uint64_t bar_full[OZ_STAGES], bar_empty[OZ_STAGES], bar_accf[2], bar_acce[2];
+    __shared__ uint32_t taddr_s;
+    __shared__ int stop_s;
+    __shared__ double fsc[OZ_MAXCHUNK][OZ_BN];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int pi = 0;
+    while (pi + 1 < g.nprob && (int)blockIdx.x >= g.p[pi + 1].tile_begin) ++pi;
+    const OzProb &P = g.p[pi];
+    const int t = blockIdx.x - P.tile_begin;
+    const int m0 = (t % P.tiles_m) * OZ_BM, n0 = (t / P.tiles_m) * OZ_BN;
+    const uint32_t base = (oz_smem(oz_dyn) + 1023u) & ~1023u;   // 1024-aligned stage ring
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(oz_smem(&taddr_s)), "r"(OZ_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < OZ_STAGES; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(oz_smem(&bar_full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(oz_smem(&bar_empty[s])));
+        }
+        for (int s = 0; s < 2; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(oz_smem(&bar_accf[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(oz_smem(&bar_acce[s])));
+        }
+        stop_s = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int e = tid; e < P.nchunk * OZ_BN; e += blockDim.x) {
+        const int c = e / OZ_BN, j = e % OZ_BN;
+        fsc[c][j] = ldexp(1.0, (int)P.expB[(long long)c * P.RpadB + n0 + j]);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = taddr_s;
+    int issued_slabs = 0;       // producer / MMA progress, for the bounded drain at exit
+
+    if (warp == 4) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            for (int k = 0; k < P.nslab; ++k) {
+                const int s = k % OZ_STAGES;
+                if (k >= OZ_STAGES && !oz_wait(oz_smem(&bar_empty[s]), ((k / OZ_STAGES) - 1) & 1)) {
+                    stop_s = 1;
+                    break;
+                }
+                if (*(volatile int *)&stop_s) break;
+                const uint32_t fb = oz_smem(&bar_full[s]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(OZ_STAGE) : "memory");
+                const uint32_t st = base + s * OZ_STAGE;
+                for (int p = 0; p < OZ_S; ++p) {
+                    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                                 ::"r"(st + p * OZ_A_TILE), "l"((uint64_t)&P.tmA), "r"(k * OZ_BK), "r"(m0), "r"(p), "r"(fb)
+                                 : "memory");
+                    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                                 ::"r"(st + OZ_S * OZ_A_TILE + p * OZ_B_TILE), "l"((uint64_t)&P.tmB), "r"(k * OZ_BK),
+                                   "r"(n0), "r"(p), "r"(fb)
+                                 : "memory");
+                }
+                issued_slabs = k + 1;
+            }
+            // drain: wait (bounded) until every issued copy has landed before the CTA exits
+            for (int k = max(0, issued_slabs - OZ_STAGES); k < issued_slabs; ++k)
+                oz_wait(oz_smem(&bar_full[k % OZ_STAGES]), (k / OZ_STAGES) & 1);
+        }
+    } else if (warp == 5) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
+                                   ((uint32_t)(OZ_BM >> 4) << 24);
+            bool ok = true;
+            for (int k = 0; k < P.nslab && ok; ++k) {
+                const int s = k % OZ_STAGES, c = k / OZ_SLABS, set = c & 1;
+                if (k % OZ_SLABS == 0 && c >= 2 && !oz_wait(oz_smem(&bar_acce[set]), ((c / 2) - 1) & 1)) ok = false;
+                if (ok && !oz_wait(oz_smem(&bar_full[s]), (k / OZ_STAGES) & 1)) ok = false;
+                if (!ok || *(volatile int *)&stop_s) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t st = base + s * OZ_STAGE;
+                for (int ks = 0; ks < OZ_BK / 16; ++ks)
+                    for (int L = 0; L < OZ_L; ++L)
+                        for (int p = 0; p <= L; ++p) {
+                            const int q = L - p;
+                            const uint64_t da = oz_desc(st + p * OZ_A_TILE + ks * 32);
+                            const uint64_t db = oz_desc(st + OZ_S * OZ_A_TILE + q * OZ_B_TILE + ks * 32);
+                            const uint32_t acc = (k % OZ_SLABS == 0 && ks == 0 && p == 0) ? 0u : 1u;
+                            const uint32_t d = taddr + set * OZ_SET_COLS + L * OZ_BN;
+                            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+                                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                                         ::"r"(d), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+                        }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             ::"r"(oz_smem(&bar_empty[s])) : "memory");
+                if (k % OZ_SLABS == OZ_SLABS - 1 || k == P.nslab - 1)
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 ::"r"(oz_smem(&bar_accf[set])) : "memory");
+                issued_slabs = k + 1;
+            }
+            if (!ok) stop_s = 1;
+            // drain: the last commit tracks every MMA issued; wait (bounded) for it
+            if (issued_slabs > 0) {
+                const int k = issued_slabs - 1;
+                oz_wait(oz_smem(&bar_empty[k % OZ_STAGES]), (k / OZ_STAGES) & 1);
+            }
+        }
+    } else {
+        // ---------------- epilogue: warps 0-3, one output row per thread
+        const int row = warp * 32 + lane, m = m0 + row;
+        double acc[OZ_BN];
+#pragma unroll
+        for (int j = 0; j < OZ_BN; ++j) acc[j] = 0.0;
+        bool ok = true;
+        for (int c = 0; c < P.nchunk; ++c) {
+            const int set = c & 1;
+            // warp-uniform outcome: the tensor-memory loads below are .sync.aligned
+            const bool arrived = __all_sync(0xffffffffu, oz_wait(oz_smem(&bar_accf[set]), (c / 2) & 1));
+            if (!arrived) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const double es = ldexp(1.0, (int)P.expA[(long long)c * P.RpadA + m]);
+            double sl[OZ_BN];
+#pragma unroll
+            for (int j = 0; j < OZ_BN; ++j) sl[j] = 0.0;
+#pragma unroll
+            for (int L = OZ_L - 1; L >= 0; --L) {
+                uint32_t r[OZ_BN];
+                const uint32_t a = taddr + ((uint32_t)(warp * 32) << 16) + set * OZ_SET_COLS + L * OZ_BN;
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                               "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                               "=r"(r[15])
+                             : "r"(a));
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                             : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+                               "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+                               "=r"(r[30]), "=r"(r[31])
+                             : "r"(a + 16));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                // sum_L 2^(-8L) S_L, lowest level first (each S_L an exact integer < 2^24)
+                const double w = ldexp(1.0, -8 * L);
+#pragma unroll
+                for (int j = 0; j < OZ_BN; ++j) sl[j] = fma(w, (double)__uint_as_float(r[j]), sl[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < OZ_BN; ++j) acc[j] = fma(es * fsc[c][j], sl[j], acc[j]);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(oz_smem(&bar_acce[set])) : "memory");
+        }
+        if (!ok) stop_s = 1;
+        // folded rows: m = i + a b  ->  C + i + ldc n + sC b
+        if (ok) {
+            if (m < P.M) {
+                const int i = m % P.a, b = m / P.a;
+                double *Cr = P.C + i + (long long)b * P.sC;
+#pragma unroll
+                for (int j = 0; j < OZ_BN; ++j) {
+                    const int n = n0 + j;
+                    if (n < P.N) {
+                        double *cp = Cr + (long long)P.ldc * n;
+                        const double v = ldexp(acc[j], -14);
+                        *cp = P.beta == 0.0 ? v : fma(P.beta, *cp, v);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && stop_s) atomicExch(&g_oz_error, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(OZ_TMEM_COLS));
+}
+
+// ------------------------------------------------------------------------------------------
+// Host side
+// ------------------------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 oz_encode_fn() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, []() {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        cudaGetLastError();
+    });
+    TK_REQUIRE(fn != nullptr, "tensor-core GEMM: cuTensorMapEncodeTiled is unavailable");
+    return fn;
+}
+
+// 3-D map over [OZ_S][rows][Kpad] BF16 planes, box (64, box_rows, 1), 128-byte swizzle
+static void oz_tensor_map(CUtensorMap *m, const __nv_bfloat16 *planes, int Kpad, int Rpad, int box_rows) {
+    const cuuint64_t dims[3] = {(cuuint64_t)Kpad, (cuuint64_t)Rpad, (cuuint64_t)OZ_S};
+    const cuuint64_t strides[2] = {(cuuint64_t)Kpad * 2, (cuuint64_t)Kpad * 2 * (cuuint64_t)Rpad};
+    const cuuint32_t box[3] = {(cuuint32_t)OZ_BK, (cuuint32_t)box_rows, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = oz_encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(planes), dims,
+                                      strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    TK_REQUIRE(r == CUDA_SUCCESS, "tensor-core GEMM: tensor map encoding failed");
+}
+
+bool oz_supported(const GProb &p) {
+    long long kt = 0;
+    for (int s = 0; s < p.nseg; ++s) kt += p.seg[s].K;
+    return kt >= 1 && kt <= (long long)OZ_MAXCHUNK * OZ_CHUNK && p.M >= 1 && p.N >= 1 &&
+           (p.batch == 1 || p.sB == 0) && (long long)p.M * p.batch < (1LL << 30);
+}
+
+void gemm_oz(Ctx &c, const std::vector<GProb> &probs, const char *tag) {
+    if (probs.empty()) return;
+    static std::atomic<bool> attr_set{false};   // set once; idempotent if two threads race
+    if (!attr_set) {
+        TK_CUDA(cudaFuncSetAttribute(k_gemm_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+        TK_CUDA(cudaFuncSetAttribute(k_oz_split, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SPLIT_SMEM));
+        attr_set = true;
+    }
+    for (size_t base = 0; base < probs.size(); base += OZ_MAXPROB) {
+        const int np = (int)std::min<size_t>(OZ_MAXPROB, probs.size() - base);
+        OzGroup G{};
+        OzSides SA{}, SB{};
+        G.nprob = np;
+        SA.n = SB.n = np;
+        int tiles = 0, maxRb = 0, maxCh = 0;
+        double flops = 0.0, bytes = 0.0;
+        for (int j = 0; j < np; ++j) {
+            const GProb &p = probs[base + j];
+            TK_REQUIRE(oz_supported(p), "tensor-core GEMM: unsupported shape");
+            long long kt = 0;
+            for (int s = 0; s < p.nseg; ++s) kt += p.seg[s].K;
+            // chunks of 256; a reduction of at most 256 is padded only to the slab width
+            const int Kpad = kt <= OZ_CHUNK ? (int)((kt + OZ_BK - 1) / OZ_BK) * OZ_BK
+                                            : (int)((kt + OZ_CHUNK - 1) / OZ_CHUNK) * OZ_CHUNK;
+            const int rowsA = p.M * p.batch;
+            OzSide &A = SA.s[j];
+            OzSide &B = SB.s[j];
+            A.rows = rowsA; A.a = p.M; A.trans = p.ta; A.nseg = p.nseg; A.bstride = p.sA; A.Kpad = Kpad;
+            A.Rpad = (rowsA + OZ_BM - 1) / OZ_BM * OZ_BM;
+            B.rows = p.N; B.a = p.N; B.trans = p.tb ? 0 : 1; B.nseg = p.nseg; B.bstride = 0; B.Kpad = Kpad;
+            B.Rpad = (p.N + OZ_BN - 1) / OZ_BN * OZ_BN;
+            int koff = 0;
+            for (int s = 0; s < p.nseg; ++s) {
+                const GSeg &q = p.seg[s];
+                A.seg[s] = OzSeg{q.A, q.coef_dev, q.coef, q.K, q.lda, koff};
+                B.seg[s] = OzSeg{q.B, nullptr, 1.0, q.K, q.ldb, koff};
+                koff += q.K;
+            }
+            const int nch = (Kpad + OZ_CHUNK - 1) / OZ_CHUNK;
+            A.planes = reinterpret_cast<__nv_bfloat16 *>(c.arena->alloc_bytes((size_t)OZ_S * A.Rpad * Kpad * 2));
+            B.planes = reinterpret_cast<__nv_bfloat16 *>(c.arena->alloc_bytes((size_t)OZ_S * B.Rpad * Kpad * 2));
+            A.exps = reinterpret_cast<short *>(c.arena->alloc_bytes((size_t)nch * A.Rpad * 2));
+            B.exps = reinterpret_cast<short *>(c.arena->alloc_bytes((size_t)nch * B.Rpad * 2));
+            maxRb = std::max(maxRb, std::max(A.Rpad, B.Rpad) / 32);
+            maxCh = std::max(maxCh, nch);
+            OzProb &P = G.p[j];
+            oz_tensor_map(&P.tmA, A.planes, Kpad, A.Rpad, OZ_BM);
+            oz_tensor_map(&P.tmB, B.planes, Kpad, B.Rpad, OZ_BN);
+            P.expA = A.exps; P.expB = B.exps; P.C = p.C; P.beta = p.beta; P.sC = p.sC;
+            P.M = rowsA; P.N = p.N; P.a = p.M; P.ldc = p.ldc; P.RpadA = A.Rpad; P.RpadB = B.Rpad;
+            P.nslab = Kpad / OZ_BK; P.nchunk = nch;
+            P.tiles_m = A.Rpad / OZ_BM; P.tiles_n = B.Rpad / OZ_BN; P.tile_begin = tiles;
+            tiles += P.tiles_m * P.tiles_n;
+            flops += 2.0 * p.M * (double)p.N * kt * p.batch;
+            bytes += 8.0 * ((double)rowsA * kt + (double)p.N * kt + (p.beta != 0.0 ? 2.0 : 1.0) * rowsA * (double)p.N);
+        }
+        // slicing of both operand sides of every problem (one launch per side kind)
+        for (OzSides *S : {&SA, &SB}) {
+            c.pre_launch();
+            k_oz_split<<<dim3((unsigned)maxRb, (unsigned)maxCh, (unsigned)S->n), 256, OZ_SPLIT_SMEM, c.st>>>(*S);
+            c.check_launch("oz_split", 0.0, 0.0);
+        }
+        c.pre_launch();
+        k_gemm_oz<<<(unsigned)tiles, 192, OZ_SMEM, c.st>>>(G);
+        c.check_launch("gemm_tc", flops, bytes);   // one profiler entry for every tensor-core product
+        (void)tag;
+    }
+}
+
+int oz_error_flag(bool reset) {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_oz_error, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    if (reset && v) {
+        const int z = 0;
+        cudaMemcpyToSymbol(g_oz_error, &z, sizeof(int));
+    }
+    return v;
+}
+
+}  // namespace tk

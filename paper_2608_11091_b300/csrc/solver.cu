@@ -337,13 +337,16 @@ static void solve_rhosvd(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tuck
             if (es) {
                 // Section 3.4: the terms of M(V_k) in the sine eigenbasis, RoundSum with the sketches
                 // rotated into that basis and the factors rotated back (the DST-I application)
-                std::vector<TTerm> mterms = expsum_terms(c, pb, *es, V.back());
-                RSConfig rc{sr, R, o.round_tol, o.seed, call++, bf16};
+                std::vector<TTerm> mterms = expsum_terms(c, pb, *es, V.back(), bf16 != 0);
+                RSConfig rc = rs_cfg(o, sr, R, call++, bf16);
                 rc.rot = es->V;
+                rc.tc_all = bf16;      // mixed form: the whole preconditioner application
                 roundsum(c, pb, mterms, rc, zs.out(pb));
             } else {
-                std::vector<TTerm> mterms = apply_operator(c, pb, *precond, V.back(), o.transpose);
-                roundsum(c, pb, mterms, rs_cfg(o, sr, R, call++, bf16), zs.out(pb));
+                std::vector<TTerm> mterms = apply_operator(c, pb, *precond, V.back(), o.transpose, bf16 != 0);
+                RSConfig rc = rs_cfg(o, sr, R, call++, bf16);
+                rc.tc_all = bf16;
+                roundsum(c, pb, mterms, rc, zs.out(pb));
             }
             Z.push_back(zs.term(pb, R));
             zrank.push_back(zs.rank);
@@ -607,7 +610,10 @@ static void solve_mln(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucker 
     const int kmax = std::min(o.maxit, rp - 1);
     TK_REQUIRE(r >= 1 && p >= 0 && r <= 96, "MLN: rank must be 1..96");
     TK_REQUIRE(o.ktrunc >= 1 && o.ktrunc <= 64, "ktrunc must be 1..64");
-    TK_REQUIRE(o.precision == TK_FP64, "MLN-Tucker sGMRES runs in FP64 only (precision must be TK_FP64)");
+    // mixed form: the sketch of L(V_i) (MLN_Sketch of the operator terms, the dominant TTM
+    // chains) on tensor cores (gemm_oz); the recoveries, the sketches of the basis tensors,
+    // inner products, sketch sums and least squares stay FP64
+    const bool tc = o.precision == TK_MIXED;
     long long gsz = 1, csz = 1;
     for (int k = 0; k < d; ++k) { gsz *= rp; csz *= r; }
     double *sc = c.arena->alloc(SC_N);
@@ -773,7 +779,7 @@ static void solve_mln(Ctx &c, const Dims &pb, const OpDesc &op, const tk_tucker 
             ScopedMark it(*c.arena);
             std::vector<TTerm> terms = apply_operator(c, pb, op, V.back(), o.transpose);
             Sk gw = alloc_sk(c, pb, r, rp);
-            mln_sketch_sum(c, pb, terms, psi, r, p, gw.g, gw.F, 0.0);
+            mln_sketch_sum(c, pb, terms, psi, r, p, gw.g, gw.F, 0.0, tc);
             superdiag(c, gw.g, rp, d, M + (size_t)(i - 1) * rp, 1.0, nullptr);
             Slot w = alloc_slot(c, pb, r);
             mln_recovery(c, pb, gw.g, gw.F, psi, r, p, w.out(pb));
@@ -1249,8 +1255,8 @@ static int solve_entry(tk_handle *h, const tk_operator *op, const tk_operator *p
             solve_mln(c, pb, od, b, o, x_out, so, h->pinned, ck);
         TK_CUDA(cudaEventRecord(e1, c.st));
         TK_CUDA(cudaEventSynchronize(e1));
-        if (o.precision == TK_MIXED && tc_error_flag(true) != 0)
-            throw Error{TK_EINTERNAL, "a tensor-core GEMM timed out waiting for its MMAs"};
+        if (o.precision == TK_MIXED && oz_error_flag(true) != 0)
+            throw Error{TK_EINTERNAL, "a tensor-core GEMM gave up waiting for its copies or MMAs"};
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         cudaEventDestroy(e0);

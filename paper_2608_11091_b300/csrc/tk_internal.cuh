@@ -128,8 +128,10 @@ struct GGroup {
 // Host-side builder that chunks problems/segments into launches.
 class Gemm {
 public:
-    // `tag`: the profiler's name for this builder's launches (the contraction it serves)
-    explicit Gemm(Ctx &c, const char *tag = "gemm") : c_(c), tag_(tag) {}
+    // `tag`: the profiler's name for this builder's launches (the contraction it serves);
+    // `tc`: run the problems on tensor cores (gemm_oz: sliced BF16 products, exact FP32
+    // accumulation, ~2^-40 relative accuracy) where their shape allows, FP64 otherwise
+    explicit Gemm(Ctx &c, const char *tag = "gemm", bool tc = false) : c_(c), tag_(tag), tc_(tc) {}
     // C = beta C + sum coef_s op(A_s) op(B_s).  Segments beyond GEMM_MAXSEG are chunked.
     struct Seg {
         const double *A; int lda;
@@ -151,24 +153,20 @@ public:
 private:
     Ctx &c_;
     const char *tag_;
+    bool tc_;
     std::vector<GProb> pending_;
     void flush_group(std::vector<GProb> &probs, int ksplit);
 };
 
 // ------------------------------------------------------------------------------------------
-// Tensor-core GEMM of the mixed-precision form: C = beta C + coef op(A) op(B), FP64 operands
-// split into na (nb) BF16 pieces, FP32 accumulation in tensor memory (k_gemm_tc.cu).
+// Tensor-core GEMM of the mixed-precision form (k_gemm_oz.cu): the grouped problems of Gemm
+// with FP64 operands sliced into BF16 digit planes, products on tcgen05 with exact FP32
+// accumulation per 256-long chunk, FP64 accumulation across chunks.
 // ------------------------------------------------------------------------------------------
-struct TcProb {
-    const double *A, *B;
-    double *C;
-    int M, N, K, lda, ldb, ldc, ta, tb, na, nb;
-    double coef, beta;
-    int tiles_m, tiles_n, tile_begin;
-};
-void gemm_tc(Ctx &c, const std::vector<TcProb> &probs);
-// 1 if a tensor-core GEMM gave up waiting for its MMAs since the last reset
-int tc_error_flag(bool reset);
+bool oz_supported(const GProb &p);
+void gemm_oz(Ctx &c, const std::vector<GProb> &probs, const char *tag);
+// 1 if a tensor-core GEMM gave up waiting for its copies or MMAs since the last reset
+int oz_error_flag(bool reset);
 
 // ------------------------------------------------------------------------------------------
 // Small dense linear algebra (FP64)

@@ -24,35 +24,25 @@ static long long prod(const int *v, int a, int b) {
 void mttkrp_batch(Ctx &c, int d, int s, const std::vector<MttJob> &jobs, bool tensor_cores) {
     struct St { std::vector<int> dims, modes; const double *T; };
     std::vector<St> st(jobs.size());
-    Gemm g(c, "gemm_mttkrp");
-    std::vector<TcProb> tc;
+    Gemm g(c, "gemm_mttkrp", tensor_cores);
     for (size_t i = 0; i < jobs.size(); ++i) {
         const MttJob &J = jobs[i];
         const int nleft = (J.keep >= 0) ? d - 2 : d - 1;   // contractions after the GEMM
         if (J.keep != d - 1) {
             const long long rest = prod(J.r, 0, d - 1);
             double *T = nleft == 0 ? J.out : c.arena->alloc(rest * s);
-            if (tensor_cores)
-                tc.push_back(TcProb{J.core, J.P[d - 1], T, (int)rest, s, J.r[d - 1], (int)rest, J.ldp[d - 1], (int)rest,
-                                    0, 0, 3, 3, 1.0, 0.0, 0, 0, 0});
-            else
-                g.add1((int)rest, s, J.r[d - 1], 0, 0, J.core, (int)rest, J.P[d - 1], J.ldp[d - 1], T, (int)rest);
+            g.add1((int)rest, s, J.r[d - 1], 0, 0, J.core, (int)rest, J.P[d - 1], J.ldp[d - 1], T, (int)rest);
             for (int k = 0; k < d - 1; ++k) { st[i].dims.push_back(J.r[k]); st[i].modes.push_back(k); }
             st[i].T = T;
         } else {
             const long long rest = prod(J.r, 1, d);
             double *T = nleft == 0 ? J.out : c.arena->alloc(rest * s);
-            if (tensor_cores)
-                tc.push_back(TcProb{J.core, J.P[0], T, (int)rest, s, J.r[0], J.r[0], J.ldp[0], (int)rest,
-                                    1, 0, 3, 3, 1.0, 0.0, 0, 0, 0});
-            else
-                g.add1((int)rest, s, J.r[0], 1, 0, J.core, J.r[0], J.P[0], J.ldp[0], T, (int)rest);
+            g.add1((int)rest, s, J.r[0], 1, 0, J.core, J.r[0], J.P[0], J.ldp[0], T, (int)rest);
             for (int k = 1; k < d; ++k) { st[i].dims.push_back(J.r[k]); st[i].modes.push_back(k); }
             st[i].T = T;
         }
     }
     g.run();
-    gemm_tc(c, tc);
     for (;;) {
         std::vector<HadJob> hj;
         for (size_t i = 0; i < jobs.size(); ++i) {
@@ -82,7 +72,7 @@ void mttkrp_batch(Ctx &c, int d, int s, const std::vector<MttJob> &jobs, bool te
 // (P_kj is s_k x r_kj with leading dimension ldp).  Levels are batched across groups; the
 // last mode sums the terms of a group as GEMM segments (no atomics).
 // ------------------------------------------------------------------------------------------
-void ttm_groups(Ctx &c, int d, const std::vector<TtmGroup> &groups) {
+void ttm_groups(Ctx &c, int d, const std::vector<TtmGroup> &groups, bool tc) {
     struct St { const double *X; int dims[TK_MAX_D]; };
     std::vector<std::vector<St>> st(groups.size());
     for (size_t gi = 0; gi < groups.size(); ++gi)
@@ -93,7 +83,7 @@ void ttm_groups(Ctx &c, int d, const std::vector<TtmGroup> &groups) {
             st[gi].push_back(s);
         }
     for (int k = 0; k < d - 1; ++k) {
-        Gemm g(c, "gemm_ttm");
+        Gemm g(c, "gemm_ttm", tc);
         for (size_t gi = 0; gi < groups.size(); ++gi) {
             const TtmGroup &G = groups[gi];
             for (size_t ji = 0; ji < G.jobs.size(); ++ji) {
@@ -113,7 +103,7 @@ void ttm_groups(Ctx &c, int d, const std::vector<TtmGroup> &groups) {
         }
         g.run();
     }
-    Gemm g(c, "gemm_ttm");
+    Gemm g(c, "gemm_ttm", tc);
     const int k = d - 1;
     for (size_t gi = 0; gi < groups.size(); ++gi) {
         const TtmGroup &G = groups[gi];
@@ -209,11 +199,11 @@ void kron_sketch_batch(Ctx &c, const Dims &pb, const std::vector<TTerm> &xs,
 // Identity modes share X's factor; banded modes run the band kernel; dense modes a GEMM.
 // ------------------------------------------------------------------------------------------
 std::vector<TTerm> apply_operator(Ctx &c, const Dims &pb, const OpDesc &op, const TTerm &x,
-                                  int transpose) {
+                                  int transpose, bool tc) {
     const int d = pb.d;
     std::vector<TTerm> out(op.nterms);
     std::vector<BandJob> bj;
-    Gemm g(c, "gemm_apply");
+    Gemm g(c, "gemm_apply", tc);
     // distinct (matrix, mode) pairs produce one factor each
     std::map<std::pair<const void *, int>, double *> made;
     for (int t = 0; t < op.nterms; ++t) {
@@ -359,9 +349,11 @@ void roundsum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const RSC
         }
         gaussian(c, cfg.seed, sids, cnt, S, d, cfg.bf16_sketch);
     }
+    const bool mixed = cfg.bf16_sketch != 0;            // range finder on tensor cores
+    const bool all_tc = mixed && cfg.tc_all != 0;        // representation too (preconditioner)
     if (cfg.rot) {
         // terms given in the bases Q_k: rotate the sketches, S_k <- Q_k^T S_k
-        Gemm g(c, "gemm_rotate");
+        Gemm g(c, "gemm_rotate", mixed);
         for (int k = 0; k < d; ++k) {
             double *Sr = c.arena->alloc((size_t)pb.n[k] * sr);
             g.add1(pb.n[k], sr, pb.n[k], 1, 0, cfg.rot[k], pb.n[k], S[k], pb.n[k], Sr, pb.n[k]);
@@ -370,28 +362,21 @@ void roundsum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const RSC
         g.run();
     }
     // 2. factor sketches M_j^(i) = U_j^(i)T S_j, shared between terms with the same factor
-    // (mixed form: on tensor cores, U in three BF16 pieces, S exact in BF16)
-    const bool mixed = cfg.bf16_sketch != 0;
+    // (mixed form: on tensor cores, gemm_oz)
     std::vector<std::vector<const double *>> M(N, std::vector<const double *>(d));
     {
-        Gemm g(c, "gemm_factor_sketch");
-        std::vector<TcProb> tc;
+        Gemm g(c, "gemm_factor_sketch", mixed);
         std::map<const double *, double *> made[TK_MAX_D];
         for (int i = 0; i < N; ++i)
             for (int j = 0; j < d; ++j) {
                 auto it = made[j].find(terms[i].f[j]);
                 if (it != made[j].end()) { M[i][j] = it->second; continue; }
                 double *m = c.arena->alloc((size_t)terms[i].r[j] * sr);
-                if (mixed)   // S is exact in BF16 unless rotated
-                    tc.push_back(TcProb{terms[i].f[j], S[j], m, terms[i].r[j], sr, pb.n[j], pb.n[j], pb.n[j],
-                                        terms[i].r[j], 1, 0, 3, cfg.rot ? 3 : 1, 1.0, 0.0, 0, 0, 0});
-                else
-                    g.add1(terms[i].r[j], sr, pb.n[j], 1, 0, terms[i].f[j], pb.n[j], S[j], pb.n[j], m, terms[i].r[j]);
+                g.add1(terms[i].r[j], sr, pb.n[j], 1, 0, terms[i].f[j], pb.n[j], S[j], pb.n[j], m, terms[i].r[j]);
                 made[j][terms[i].f[j]] = m;
                 M[i][j] = m;
             }
         g.run();
-        gemm_tc(c, tc);
     }
     // 3. Z_k^(i) = G_(k)^(i) (KR_{j != k} M_j^(i))   (r_k x sr)
     std::vector<std::vector<double *>> Z(N, std::vector<double *>(d));
@@ -412,7 +397,7 @@ void roundsum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const RSC
     // 4. Y_k = sum_i c_i U_k^(i) Z_k^(i)   (n_k x sr)
     double *Y[TK_MAX_D], *Q[TK_MAX_D];
     {
-        Gemm g(c, "gemm_range");
+        Gemm g(c, "gemm_range", all_tc);
         for (int k = 0; k < d; ++k) {
             Y[k] = c.arena->alloc((size_t)pb.n[k] * sr);
             std::vector<Gemm::Seg> segs;
@@ -436,7 +421,7 @@ void roundsum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const RSC
     // 6. projections P_k^(i) = U^_k^T U_k^(i)   (sr x r_k^(i))
     std::vector<std::vector<const double *>> P(N, std::vector<const double *>(d));
     {
-        Gemm g(c, "gemm_proj");
+        Gemm g(c, "gemm_proj", all_tc);
         std::map<const double *, double *> made[TK_MAX_D];
         for (int i = 0; i < N; ++i)
             for (int k = 0; k < d; ++k) {
@@ -466,7 +451,7 @@ void roundsum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const RSC
             J.coef_dev = terms[i].coef_dev;
             G.jobs.push_back(J);
         }
-        ttm_groups(c, d, {G});
+        ttm_groups(c, d, {G}, all_tc);
     }
     // 8. ST-HOSVD of C^: per mode QR of the transposed unfolding, Jacobi SVD of R, truncate
     double *normsq = c.arena->alloc(1);
@@ -491,7 +476,7 @@ void roundsum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const RSC
         sj.normsq = normsq; sj.eps2_over_d = cfg.eps * cfg.eps / d; sj.rank_cap = R;
         svd_jacobi(c, {sj});
         double *Cn = (k == d - 1) ? out.core : c.arena->alloc(a * R * rest);
-        Gemm g(c, "gemm_hosvd");
+        Gemm g(c, "gemm_hosvd", all_tc);
         if (k == 0)
             g.add1(R, (int)rest, sk, 1, 0, W[k], sk, C, sk, Cn, R);
         else
@@ -503,7 +488,7 @@ void roundsum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const RSC
     }
     // 9. output factors U^_k W_k   (n_k x R), rotated back by Q_k when the terms were rotated
     {
-        Gemm g(c, "gemm_factors");
+        Gemm g(c, "gemm_factors", all_tc);
         double *tmp[TK_MAX_D];
         for (int k = 0; k < d; ++k) {
             tmp[k] = cfg.rot ? c.arena->alloc((size_t)pb.n[k] * R) : out.f[k];
@@ -511,7 +496,7 @@ void roundsum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const RSC
         }
         g.run();
         if (cfg.rot) {
-            Gemm g2(c, "gemm_rotate");
+            Gemm g2(c, "gemm_rotate", all_tc);
             for (int k = 0; k < d; ++k)
                 g2.add1(pb.n[k], R, pb.n[k], 0, 0, cfg.rot[k], pb.n[k], tmp[k], pb.n[k], out.f[k], pb.n[k]);
             g2.run();
@@ -524,11 +509,11 @@ void roundsum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const RSC
 // factor matrices): E_h U = V diag(w_h) V^T U, so the 2q+1 terms of M(X) are, in the basis V,
 // [c_h G; diag(w_h) V^T U_1, ...]: one product V^T U_k per mode and row scalings.
 // ------------------------------------------------------------------------------------------
-std::vector<TTerm> expsum_terms(Ctx &c, const Dims &pb, const ExpSumPC &es, const TTerm &x) {
+std::vector<TTerm> expsum_terms(Ctx &c, const Dims &pb, const ExpSumPC &es, const TTerm &x, bool tc) {
     const int d = pb.d;
     double *Uh[TK_MAX_D];
     {
-        Gemm g(c, "gemm_sine");
+        Gemm g(c, "gemm_sine", tc);
         for (int k = 0; k < d; ++k) {
             Uh[k] = c.arena->alloc((size_t)pb.n[k] * x.r[k]);
             g.add1(pb.n[k], x.r[k], pb.n[k], 1, 0, es.V[k], pb.n[k], x.f[k], pb.n[k], Uh[k], pb.n[k]);
@@ -559,7 +544,7 @@ std::vector<TTerm> expsum_terms(Ctx &c, const Dims &pb, const ExpSumPC &es, cons
 // MLN_Sketch of a sum of terms, accumulated (MLN_Sum) into gpsi ((r+p)^d) and F_k (n_k x r):
 //   G_Psi += c_i G^(i) x_k (Psi_k^T U_k^(i)),  F_k += c_i U_k^(i) MTTKRP(G^(i), {Ubar^T}, k)
 void mln_sketch_sum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const double *const *psi,
-                    int r, int p, double *gpsi, double *const *F, double beta) {
+                    int r, int p, double *gpsi, double *const *F, double beta, bool tc) {
     ScopedMark mark(*c.arena);
     const int d = pb.d, rp = r + p, N = (int)terms.size();
     // U_Psi,k^(i) = Psi_k^T U_k^(i)  ((r+p) x r_k); Ubar^T = first r rows, transposed on use
@@ -578,7 +563,9 @@ void mln_sketch_sum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, con
             }
         g.run();
     }
-    // sketched core: sum_i c_i G^(i) x_k U_Psi,k^(i)
+    // sketched core: sum_i c_i G^(i) x_k U_Psi,k^(i) (mixed form: this TTM chain, the dominant
+    // (r+p)^d work, on tensor cores; the factor contributions below, which MLN_Recovery applies
+    // R^+ to, stay FP64)
     {
         TtmGroup G{};
         for (int k = 0; k < d; ++k) G.sdims[k] = rp;
@@ -592,7 +579,7 @@ void mln_sketch_sum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, con
             J.coef_dev = terms[i].coef_dev;
             G.jobs.push_back(J);
         }
-        ttm_groups(c, d, {G});
+        ttm_groups(c, d, {G}, tc);
     }
     // factor contributions: T_k^(i) = MTTKRP(G^(i), {Ubar_l^T}, k) (r_k x r); F_k = sum c_i U_k T_k
     // Ubar_l^T (r_l x r) is the transpose of the first r rows of U_Psi,l: materialise it.
@@ -639,7 +626,7 @@ void mln_sketch_sum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, con
 
 // MLN_Recovery (Algorithm 5): Q_k R_k = qr(Psi_k^T F_k); U~_k = F_k R_k^+; G~ = G_Psi x_k Q_k^T
 void mln_recovery(Ctx &c, const Dims &pb, const double *gpsi, const double *const *F,
-                  const double *const *psi, int r, int p, const TOut &out) {
+                  const double *const *psi, int r, int p, const TOut &out, bool tc) {
     ScopedMark mark(*c.arena);
     const int d = pb.d, rp = r + p;
     double *PF[TK_MAX_D], *Qk[TK_MAX_D], *Rp[TK_MAX_D];

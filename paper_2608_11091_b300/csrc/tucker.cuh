@@ -34,7 +34,8 @@ struct MttJob {
     int keep;
     double *out;
 };
-// tensor_cores: the leading GEMM runs on tcgen05 (mixed-precision form), the rest in FP64
+// tensor_cores: the leading GEMM runs on tcgen05 (mixed-precision form, gemm_oz), the row-wise
+// Hadamard contractions in FP64
 void mttkrp_batch(Ctx &c, int d, int s, const std::vector<MttJob> &jobs, bool tensor_cores = false);
 
 struct TtmJob {
@@ -51,7 +52,8 @@ struct TtmGroup {
     double *out;
     double beta;
 };
-void ttm_groups(Ctx &c, int d, const std::vector<TtmGroup> &groups);
+// tc: the mode products on tensor cores (mixed-precision form)
+void ttm_groups(Ctx &c, int d, const std::vector<TtmGroup> &groups, bool tc = false);
 
 struct InnerJob {
     TTerm x, y;
@@ -67,7 +69,9 @@ struct OpDesc {
     std::vector<double> theta;
     std::vector<tk_modemat> mats;   // nterms * d
 };
-std::vector<TTerm> apply_operator(Ctx &c, const Dims &pb, const OpDesc &op, const TTerm &x, int transpose);
+// tc: dense mode matrices applied on tensor cores (mixed-precision form)
+std::vector<TTerm> apply_operator(Ctx &c, const Dims &pb, const OpDesc &op, const TTerm &x, int transpose,
+                                  bool tc = false);
 
 struct RSConfig {
     int sr;             // sketch size (columns of S_k)
@@ -75,7 +79,13 @@ struct RSConfig {
     double eps;         // ST-HOSVD tolerance
     uint64_t seed;
     uint64_t call;      // RoundSum call index (stream id)
-    int bf16_sketch;    // round the Gaussian matrices to bfloat16
+    int bf16_sketch;    // mixed-precision form: Gaussian matrices rounded to bfloat16 and the
+                        // range finder's products (factor sketches U^T S, the MTTKRP, rotated
+                        // sketches) on tensor cores (gemm_oz): they only choose the subspace,
+                        // the FP64 projection onto it keeps the result exact
+    // mixed form, flexible preconditioner application only: every product of the compression
+    // on tensor cores (any Z_k is a valid preconditioned direction, Section 3.4)
+    int tc_all = 0;
     // optional orthogonal n_k x n_k matrices Q_k (device): the terms are given in the basis Q_k
     // (term factors Q_k^T U), so the sketches are rotated into it (S_k <- Q_k^T S_k) and the
     // output factors rotated back (U <- Q_k U): the result is RoundSum of the terms Q_k U with
@@ -102,11 +112,13 @@ struct ExpSumPC {
     const double *w[TK_MAX_D] = {};        // nh x n_k, row h contiguous
 };
 // Terms of M(X) in the sine basis: [c_h G; diag(w_h) V_1^T U_1, ..., diag(w_h) V_d^T U_d]
-std::vector<TTerm> expsum_terms(Ctx &c, const Dims &pb, const ExpSumPC &es, const TTerm &x);
+std::vector<TTerm> expsum_terms(Ctx &c, const Dims &pb, const ExpSumPC &es, const TTerm &x, bool tc = false);
 
+// tc: the sketched core's TTM chain on tensor cores (mixed-precision form); mln_recovery's tc is
+// accepted for symmetry and unused (its products feed R^+ and the representation: FP64)
 void mln_sketch_sum(Ctx &c, const Dims &pb, const std::vector<TTerm> &terms, const double *const *psi,
-                    int r, int p, double *gpsi, double *const *F, double beta);
+                    int r, int p, double *gpsi, double *const *F, double beta, bool tc = false);
 void mln_recovery(Ctx &c, const Dims &pb, const double *gpsi, const double *const *F,
-                  const double *const *psi, int r, int p, const TOut &out);
+                  const double *const *psi, int r, int p, const TOut &out, bool tc = false);
 
 }  // namespace tk

@@ -72,13 +72,14 @@ def _movement(wl, prm, noise, transpose=False, bf16=False, precond=None):
 
 def _one_mixed(name):
     build, prm = MIXED_CASES[name]
-    return name, case_entry(build(), prm, noise=1e-7, noise2=1e-8, threshold=1e-7, bf16=True)
+    return name, case_entry(build(), prm, noise=1e-12, noise2=1e-13, threshold=1e-7, bf16=True)
 
 
 def main_mixed():
-    """Mixed form: BF16-rounded sketches, 1e-7 perturbations (the FP32-level accuracy of the
-    tensor-core products; "x15"/"hist15" hold the 1e-8 movement here) and the longest prefix
-    whose movement stays <= 1e-7 -> tests/golden/mixed_sensitivity.json."""
+    """Mixed form: BF16-rounded sketches, 1e-12 perturbations of every compression (the accuracy
+    of the sliced tensor-core products, ~2^-40 per product; "x15"/"hist15" hold the 1e-13
+    movement here) and the longest prefix whose movement stays <= 1e-7, a tenth of the mixed
+    bound 1e-6 -> tests/golden/mixed_sensitivity.json."""
     import multiprocessing as mp
     from concurrent.futures import ProcessPoolExecutor
     out = {}
