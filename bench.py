@@ -538,7 +538,7 @@ def secondary(P, W, torch):
         dop = P.DeviceOperator(wl.op)
         b = P.DeviceTucker.from_numpy(wl.b.core, wl.b.factors)
         entry = {"variant": prm.variant}
-        forms = ["fp64", "mixed"] if prm.variant == "rhosvd" else ["fp64"]
+        forms = ["fp64", "mixed"]
         xs = {}
         for form in forms:
             opts = P.Options.from_params(prm, precision=form)
@@ -652,10 +652,26 @@ def secondary(P, W, torch):
     return out
 
 
+def run_profile_target(args):
+    """One gradient step of each form, run serially on the default handle, nothing timed: the
+    command the kernel captures (ncu) profile."""
+    import torch
+    import paper_2608_11091_b300 as P
+    import workloads as W
+    torch.cuda.set_device(0)
+    prob = Problem(P, W, args.workload, seed=0)
+    for form in ("mixed", "fp64"):
+        rep, rep_a, _ = prob.step(P, form, concurrent=False)
+        torch.cuda.synchronize()
+        print(f"{form}: forward {rep.iters} / adjoint {rep_a.iters} iterations, {rep.kernel_launches + rep_a.kernel_launches}"
+              f" launches, {rep.ms_total + rep_a.ms_total:.2f} ms")
+
+
 def main():
     args = parse()
     if args.impl == "native" and args.profile_only:
-        args.no_extras = True
+        run_profile_target(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -15,8 +15,10 @@
 //    is at most (L + 1) 256 2^14 <= 2^24 in magnitude, so the FP32 accumulation in tensor memory
 //    is exact.  Products with p + q > 4 are dropped: the error is about 2^-40 relative to
 //    max|A row| max|B column| per reduction index.
-//  * Accumulation.  Per chunk the epilogue adds 2^(e_m + f_n) sum_L 2^(-8L) S_L into FP64
-//    registers (one output row per thread), then C = beta C + 2^-14 acc.
+//  * Accumulation.  Per chunk the epilogue combines the levels exactly in 64-bit integers,
+//    sum_L S_L 2^(8(4 - L)), and adds 2^(e_m + f_n - 46) times it into FP64 registers (one output
+//    row per thread; the FP64 pipe of this part is slow, so it does one FMA per output and chunk),
+//    then C = beta C + acc.
 //
 // Pipeline (k_gemm_oz, one 128 x 32 output tile per CTA, 6 warps): warp 4 lane 0 issues the TMA
 // loads (five A planes 128 x 64 and five B planes 32 x 64 per K slab of 64, 128-byte swizzle)
@@ -32,7 +34,10 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cstring>
+#include <map>
 #include <mutex>
+#include <string>
 
 #include "tk_internal.cuh"
 
@@ -206,7 +211,7 @@ __global__ void __launch_bounds__(192, 1) k_gemm_oz(const __grid_constant__ OzGr
     __shared__ __align__(8) uint64_t bar_full[OZ_STAGES], bar_empty[OZ_STAGES], bar_accf[2], bar_acce[2];
     __shared__ uint32_t taddr_s;
     __shared__ int stop_s;
-    __shared__ double fsc[OZ_MAXCHUNK][OZ_BN];
+    __shared__ int fex[OZ_MAXCHUNK][OZ_BN];   // column exponents f_n per chunk
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int pi = 0;
@@ -235,7 +240,7 @@ __global__ void __launch_bounds__(192, 1) k_gemm_oz(const __grid_constant__ OzGr
     }
     for (int e = tid; e < P.nchunk * OZ_BN; e += blockDim.x) {
         const int c = e / OZ_BN, j = e % OZ_BN;
-        fsc[c][j] = ldexp(1.0, (int)P.expB[(long long)c * P.RpadB + n0 + j]);
+        fex[c][j] = P.expB[(long long)c * P.RpadB + n0 + j];
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -311,7 +316,9 @@ __global__ void __launch_bounds__(192, 1) k_gemm_oz(const __grid_constant__ OzGr
             }
         }
     } else {
-        // ---------------- epilogue: warps 0-3, one output row per thread
+        // ---------------- epilogue: warps 0-3, one output row per thread.  The levels of a
+        // chunk combine exactly in 64-bit integers (S_L integer, |S_L| < 2^24: sum_L S_L 2^(8(4-L))
+        // < 2^59), so only one conversion and one FMA per output and chunk use the FP64 pipe
         const int row = warp * 32 + lane, m = m0 + row;
         double acc[OZ_BN];
 #pragma unroll
@@ -323,49 +330,49 @@ __global__ void __launch_bounds__(192, 1) k_gemm_oz(const __grid_constant__ OzGr
             const bool arrived = __all_sync(0xffffffffu, oz_wait(oz_smem(&bar_accf[set]), (c / 2) & 1));
             if (!arrived) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const double es = ldexp(1.0, (int)P.expA[(long long)c * P.RpadA + m]);
-            double sl[OZ_BN];
+            const int em = P.expA[(long long)c * P.RpadA + m];
 #pragma unroll
-            for (int j = 0; j < OZ_BN; ++j) sl[j] = 0.0;
+            for (int h = 0; h < OZ_BN / 16; ++h) {           // 16 columns at a time: fewer live registers
+                long long ai[16];
 #pragma unroll
-            for (int L = OZ_L - 1; L >= 0; --L) {
-                uint32_t r[OZ_BN];
-                const uint32_t a = taddr + ((uint32_t)(warp * 32) << 16) + set * OZ_SET_COLS + L * OZ_BN;
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                               "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                               "=r"(r[15])
-                             : "r"(a));
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                             : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
-                               "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
-                               "=r"(r[30]), "=r"(r[31])
-                             : "r"(a + 16));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                // sum_L 2^(-8L) S_L, lowest level first (each S_L an exact integer < 2^24)
-                const double w = ldexp(1.0, -8 * L);
+                for (int j = 0; j < 16; ++j) ai[j] = 0;
 #pragma unroll
-                for (int j = 0; j < OZ_BN; ++j) sl[j] = fma(w, (double)__uint_as_float(r[j]), sl[j]);
+                for (int L = 0; L < OZ_L; ++L) {
+                    uint32_t r[16];
+                    const uint32_t a = taddr + ((uint32_t)(warp * 32) << 16) + set * OZ_SET_COLS + L * OZ_BN + h * 16;
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                                   "=r"(r[14]), "=r"(r[15])
+                                 : "r"(a));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        ai[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << (8 * (OZ_L - 1 - L));
+                }
+                // chunk value: 2^(e_m + f_n) 2^-32 ai, with the final 2^-14: scale 2^(e_m + f_n - 46)
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int ex = em + fex[c][h * 16 + j] - 46;
+                    const double sc = (ex > -1022 && ex < 1024) ? __longlong_as_double((long long)(ex + 1023) << 52)
+                                                                : ldexp(1.0, ex);
+                    acc[h * 16 + j] = fma(sc, (double)ai[j], acc[h * 16 + j]);
+                }
             }
-#pragma unroll
-            for (int j = 0; j < OZ_BN; ++j) acc[j] = fma(es * fsc[c][j], sl[j], acc[j]);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(oz_smem(&bar_acce[set])) : "memory");
         }
         if (!ok) stop_s = 1;
         // folded rows: m = i + a b  ->  C + i + ldc n + sC b
-        if (ok) {
-            if (m < P.M) {
-                const int i = m % P.a, b = m / P.a;
-                double *Cr = P.C + i + (long long)b * P.sC;
+        if (ok && m < P.M) {
+            const int i = m % P.a, b = m / P.a;
+            double *Cr = P.C + i + (long long)b * P.sC;
 #pragma unroll
-                for (int j = 0; j < OZ_BN; ++j) {
-                    const int n = n0 + j;
-                    if (n < P.N) {
-                        double *cp = Cr + (long long)P.ldc * n;
-                        const double v = ldexp(acc[j], -14);
-                        *cp = P.beta == 0.0 ? v : fma(P.beta, *cp, v);
-                    }
+            for (int j = 0; j < OZ_BN; ++j) {
+                const int n = n0 + j;
+                if (n < P.N) {
+                    double *cp = Cr + (long long)P.ldc * n;
+                    *cp = P.beta == 0.0 ? acc[j] : fma(P.beta, *cp, acc[j]);
                 }
             }
         }
@@ -414,7 +421,22 @@ bool oz_supported(const GProb &p) {
            (p.batch == 1 || p.sB == 0) && (long long)p.M * p.batch < (1LL << 30);
 }
 
+// Descriptor of an operand side without its output buffers: two sides with equal keys slice to
+// the same planes (the same sketch matrix or basis used by many problems of a call)
+static std::string oz_key(const OzSide &S) {
+    OzSide k;
+    std::memset(&k, 0, sizeof k);               // padding bytes included: the key is the bytes
+    k.rows = S.rows; k.a = S.a; k.trans = S.trans; k.nseg = S.nseg; k.Kpad = S.Kpad; k.Rpad = S.Rpad;
+    k.bstride = S.bstride;
+    for (int i = 0; i < S.nseg; ++i) {
+        k.seg[i].p = S.seg[i].p; k.seg[i].cd = S.seg[i].cd; k.seg[i].coef = S.seg[i].coef;
+        k.seg[i].K = S.seg[i].K; k.seg[i].ld = S.seg[i].ld; k.seg[i].koff = S.seg[i].koff;
+    }
+    return std::string(reinterpret_cast<const char *>(&k), sizeof(OzSide));
+}
+
 void gemm_oz(Ctx &c, const std::vector<GProb> &probs, const char *tag) {
+    (void)tag;
     if (probs.empty()) return;
     static std::atomic<bool> attr_set{false};   // set once; idempotent if two threads race
     if (!attr_set) {
@@ -422,64 +444,90 @@ void gemm_oz(Ctx &c, const std::vector<GProb> &probs, const char *tag) {
         TK_CUDA(cudaFuncSetAttribute(k_oz_split, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SPLIT_SMEM));
         attr_set = true;
     }
-    for (size_t base = 0; base < probs.size(); base += OZ_MAXPROB) {
-        const int np = (int)std::min<size_t>(OZ_MAXPROB, probs.size() - base);
+    // 1. operand sides of every problem; each distinct side is sliced once
+    const size_t np = probs.size();
+    std::vector<OzSide> A(np), B(np);
+    std::vector<OzSide> uniq;
+    std::map<std::string, size_t> seen;
+    auto place = [&](OzSide &S) {
+        const std::string key = oz_key(S);
+        auto it = seen.find(key);
+        if (it != seen.end()) {
+            S.planes = uniq[it->second].planes;
+            S.exps = uniq[it->second].exps;
+            return;
+        }
+        const int nch = (S.Kpad + OZ_CHUNK - 1) / OZ_CHUNK;
+        S.planes = reinterpret_cast<__nv_bfloat16 *>(c.arena->alloc_bytes((size_t)OZ_S * S.Rpad * S.Kpad * 2));
+        S.exps = reinterpret_cast<short *>(c.arena->alloc_bytes((size_t)nch * S.Rpad * 2));
+        seen[key] = uniq.size();
+        uniq.push_back(S);
+    };
+    for (size_t j = 0; j < np; ++j) {
+        const GProb &p = probs[j];
+        TK_REQUIRE(oz_supported(p), "tensor-core GEMM: unsupported shape");
+        long long kt = 0;
+        for (int s = 0; s < p.nseg; ++s) kt += p.seg[s].K;
+        // chunks of 256; a reduction of at most 256 is padded only to the slab width
+        const int Kpad = kt <= OZ_CHUNK ? (int)((kt + OZ_BK - 1) / OZ_BK) * OZ_BK
+                                        : (int)((kt + OZ_CHUNK - 1) / OZ_CHUNK) * OZ_CHUNK;
+        const int rowsA = p.M * p.batch;
+        OzSide &a = A[j], &b = B[j];
+        a = OzSide{};
+        b = OzSide{};
+        a.rows = rowsA; a.a = p.M; a.trans = p.ta; a.nseg = p.nseg; a.bstride = p.sA; a.Kpad = Kpad;
+        a.Rpad = (rowsA + OZ_BM - 1) / OZ_BM * OZ_BM;
+        b.rows = p.N; b.a = p.N; b.trans = p.tb ? 0 : 1; b.nseg = p.nseg; b.bstride = 0; b.Kpad = Kpad;
+        b.Rpad = (p.N + OZ_BN - 1) / OZ_BN * OZ_BN;
+        int koff = 0;
+        for (int s = 0; s < p.nseg; ++s) {
+            const GSeg &q = p.seg[s];
+            a.seg[s] = OzSeg{q.A, q.coef_dev, q.coef, q.K, q.lda, koff};
+            b.seg[s] = OzSeg{q.B, nullptr, 1.0, q.K, q.ldb, koff};
+            koff += q.K;
+        }
+        place(a);
+        place(b);
+    }
+    // 2. slicing of the distinct sides
+    for (size_t base = 0; base < uniq.size(); base += OZ_MAXSIDES) {
+        OzSides S{};
+        S.n = (int)std::min<size_t>(OZ_MAXSIDES, uniq.size() - base);
+        int maxRb = 0, maxCh = 0;
+        for (int i = 0; i < S.n; ++i) {
+            S.s[i] = uniq[base + i];
+            maxRb = std::max(maxRb, S.s[i].Rpad / 32);
+            maxCh = std::max(maxCh, (S.s[i].Kpad + OZ_CHUNK - 1) / OZ_CHUNK);
+        }
+        c.pre_launch();
+        k_oz_split<<<dim3((unsigned)maxRb, (unsigned)maxCh, (unsigned)S.n), 256, OZ_SPLIT_SMEM, c.st>>>(S);
+        c.check_launch("oz_split", 0.0, 0.0);
+    }
+    // 3. products, OZ_MAXPROB per launch
+    for (size_t base = 0; base < np; base += OZ_MAXPROB) {
         OzGroup G{};
-        OzSides SA{}, SB{};
-        G.nprob = np;
-        SA.n = SB.n = np;
-        int tiles = 0, maxRb = 0, maxCh = 0;
+        G.nprob = (int)std::min<size_t>(OZ_MAXPROB, np - base);
+        int tiles = 0;
         double flops = 0.0, bytes = 0.0;
-        for (int j = 0; j < np; ++j) {
+        for (int j = 0; j < G.nprob; ++j) {
             const GProb &p = probs[base + j];
-            TK_REQUIRE(oz_supported(p), "tensor-core GEMM: unsupported shape");
+            const OzSide &a = A[base + j], &b = B[base + j];
             long long kt = 0;
             for (int s = 0; s < p.nseg; ++s) kt += p.seg[s].K;
-            // chunks of 256; a reduction of at most 256 is padded only to the slab width
-            const int Kpad = kt <= OZ_CHUNK ? (int)((kt + OZ_BK - 1) / OZ_BK) * OZ_BK
-                                            : (int)((kt + OZ_CHUNK - 1) / OZ_CHUNK) * OZ_CHUNK;
-            const int rowsA = p.M * p.batch;
-            OzSide &A = SA.s[j];
-            OzSide &B = SB.s[j];
-            A.rows = rowsA; A.a = p.M; A.trans = p.ta; A.nseg = p.nseg; A.bstride = p.sA; A.Kpad = Kpad;
-            A.Rpad = (rowsA + OZ_BM - 1) / OZ_BM * OZ_BM;
-            B.rows = p.N; B.a = p.N; B.trans = p.tb ? 0 : 1; B.nseg = p.nseg; B.bstride = 0; B.Kpad = Kpad;
-            B.Rpad = (p.N + OZ_BN - 1) / OZ_BN * OZ_BN;
-            int koff = 0;
-            for (int s = 0; s < p.nseg; ++s) {
-                const GSeg &q = p.seg[s];
-                A.seg[s] = OzSeg{q.A, q.coef_dev, q.coef, q.K, q.lda, koff};
-                B.seg[s] = OzSeg{q.B, nullptr, 1.0, q.K, q.ldb, koff};
-                koff += q.K;
-            }
-            const int nch = (Kpad + OZ_CHUNK - 1) / OZ_CHUNK;
-            A.planes = reinterpret_cast<__nv_bfloat16 *>(c.arena->alloc_bytes((size_t)OZ_S * A.Rpad * Kpad * 2));
-            B.planes = reinterpret_cast<__nv_bfloat16 *>(c.arena->alloc_bytes((size_t)OZ_S * B.Rpad * Kpad * 2));
-            A.exps = reinterpret_cast<short *>(c.arena->alloc_bytes((size_t)nch * A.Rpad * 2));
-            B.exps = reinterpret_cast<short *>(c.arena->alloc_bytes((size_t)nch * B.Rpad * 2));
-            maxRb = std::max(maxRb, std::max(A.Rpad, B.Rpad) / 32);
-            maxCh = std::max(maxCh, nch);
             OzProb &P = G.p[j];
-            oz_tensor_map(&P.tmA, A.planes, Kpad, A.Rpad, OZ_BM);
-            oz_tensor_map(&P.tmB, B.planes, Kpad, B.Rpad, OZ_BN);
-            P.expA = A.exps; P.expB = B.exps; P.C = p.C; P.beta = p.beta; P.sC = p.sC;
-            P.M = rowsA; P.N = p.N; P.a = p.M; P.ldc = p.ldc; P.RpadA = A.Rpad; P.RpadB = B.Rpad;
-            P.nslab = Kpad / OZ_BK; P.nchunk = nch;
-            P.tiles_m = A.Rpad / OZ_BM; P.tiles_n = B.Rpad / OZ_BN; P.tile_begin = tiles;
+            oz_tensor_map(&P.tmA, a.planes, a.Kpad, a.Rpad, OZ_BM);
+            oz_tensor_map(&P.tmB, b.planes, b.Kpad, b.Rpad, OZ_BN);
+            P.expA = a.exps; P.expB = b.exps; P.C = p.C; P.beta = p.beta; P.sC = p.sC;
+            P.M = a.rows; P.N = p.N; P.a = p.M; P.ldc = p.ldc; P.RpadA = a.Rpad; P.RpadB = b.Rpad;
+            P.nslab = a.Kpad / OZ_BK; P.nchunk = (a.Kpad + OZ_CHUNK - 1) / OZ_CHUNK;
+            P.tiles_m = a.Rpad / OZ_BM; P.tiles_n = b.Rpad / OZ_BN; P.tile_begin = tiles;
             tiles += P.tiles_m * P.tiles_n;
             flops += 2.0 * p.M * (double)p.N * kt * p.batch;
-            bytes += 8.0 * ((double)rowsA * kt + (double)p.N * kt + (p.beta != 0.0 ? 2.0 : 1.0) * rowsA * (double)p.N);
-        }
-        // slicing of both operand sides of every problem (one launch per side kind)
-        for (OzSides *S : {&SA, &SB}) {
-            c.pre_launch();
-            k_oz_split<<<dim3((unsigned)maxRb, (unsigned)maxCh, (unsigned)S->n), 256, OZ_SPLIT_SMEM, c.st>>>(*S);
-            c.check_launch("oz_split", 0.0, 0.0);
+            bytes += 8.0 * ((double)a.rows * kt + (double)p.N * kt + (p.beta != 0.0 ? 2.0 : 1.0) * a.rows * (double)p.N);
         }
         c.pre_launch();
         k_gemm_oz<<<(unsigned)tiles, 192, OZ_SMEM, c.st>>>(G);
         c.check_launch("gemm_tc", flops, bytes);   // one profiler entry for every tensor-core product
-        (void)tag;
     }
 }
 
