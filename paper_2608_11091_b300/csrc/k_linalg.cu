@@ -85,12 +85,21 @@ struct QRJobs {
 // scaled once by the largest initial column norm and downdated by the new row of R each step
 // (a pivot only has to grade R, it does not enter the result); the argmax is one warp of
 // FP32 shuffles; peer sums use four threads per column.
-// Q (optional) is accumulated backwards, Q = H_0 ... H_{k-1} [I; 0], one exchange per step.
+// The two FP64 passes of a step (partial sums D_c, trailing update) cost one FP64 FMA per element
+// and run at the FP64 pipe's rate only if every warp carries the same number of them with all
+// lanes active: the CTA's (column, row) elements are split into equal contiguous ranges, one per
+// thread, in column-major order (odd range length, so that the lanes of a warp fall on distinct
+// banks), walked as two independent streams (the two halves) with one uniform trip count, so
+// that a column change inside a range costs no partially active FP64 instruction.  A stream's
+// partial sum of a column goes to its half of slot (thread + column) of `pp`; the slots of a
+// column's contributors (the threads whose ranges meet it, a contiguous run) are added in thread
+// order, by one thread when there are at most 8, else by a warp.  The kernel leaves R and the
+// reflectors; qr_form_q builds an explicit Q from them.
 // Rows live in shared memory when they fit (SMEM = true), else in global memory.  The
 // exchange buffers alternate by a running exchange count, so a buffer is rewritten only after
 // every peer has passed the next cluster barrier.
 template <bool SMEM>
-__global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs, int rb_cap) {
+__global__ void __launch_bounds__(256, 1) k_qr(const __grid_constant__ QRJobs jobs, int rb_cap) {
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks();
     const int q = (int)cl.block_rank();
@@ -100,7 +109,6 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
     const int r0 = min(m, q * rb), r1 = min(m, r0 + rb), nr = r1 - r0;
     extern __shared__ double dyn[];
     double *Al = dyn;                              // nr x s, ld rb_cap
-    double *Ql = dyn + (size_t)rb_cap * s;         // nr x s, ld rb_cap
     __shared__ double red[2][2 * QR_MAXS];         // [0, nc1): partial sums, [nc1, 2 nc1): owner's row
     __shared__ double wv[QR_MAXS];
     __shared__ double prow[QR_MAXS];               // owner's row j of the step (local copy)
@@ -108,14 +116,12 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
     __shared__ float nrmf[QR_MAXS];
     __shared__ int permv[QR_MAXS];
     __shared__ double bc[4];
+    __shared__ double pp[4 * QR_MAXS];             // per-thread partial sums (two per slot thread + column)
     __shared__ int pivot;
     const bool piv = J.perm != nullptr;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
     auto A = [&](int i, int c) -> double & {
         return SMEM ? Al[(i - r0) + (size_t)c * rb_cap] : J.A[i + (long long)c * m];
-    };
-    auto Q = [&](int i, int c) -> double & {
-        return SMEM ? Ql[(i - r0) + (size_t)c * rb_cap] : J.Q[i + (long long)c * m];
     };
     if (SMEM)
         for (int e = tid; e < nr * s; e += nt) {
@@ -124,28 +130,99 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
         }
     __syncthreads();
     int xch = 0;   // exchanges so far (selects the buffer)
-    // partial sums over this CTA's rows for columns j0 .. j0 + ncols - 1 into out[]: a group of
-    // eight lanes per column, the rows strided by eight across the group (sum(c, first, 8) is a
-    // plain FMA loop), combined by three xor shuffles: no block barrier and no serial combine.
-    // Every warp runs the same number of passes, so all its lanes reach the shuffles.
-    auto column_sums = [&](int j0, int ncols, auto sum, double *out) {
-        const int grp = tid >> 3, gl = tid & 7, ngrp = nt >> 3;
-        for (int cc0 = 0; cc0 < ncols; cc0 += ngrp) {
-            const int cc = cc0 + grp;
-            double pd = cc < ncols ? sum(j0 + cc, gl) : 0.0;
-            pd += __shfl_xor_sync(0xffffffffu, pd, 1);
-            pd += __shfl_xor_sync(0xffffffffu, pd, 2);
-            pd += __shfl_xor_sync(0xffffffffu, pd, 4);
-            if (cc < ncols && gl == 0) out[cc] = pd;
+    // sum over rows [ib, r1) of x * y for columns cc = 0 .. nc - 1 into out[cc], where
+    // xy(i, cc, x, y) gives the two factors of element (i, cc); ends with out[] complete and
+    // visible to the whole CTA.  Every thread runs the same trip count (all but the last few), so
+    // the FMAs issue with full warps; a column change stores the two partial chains (no FP64
+    // instruction on the divergent path) and the combine adds them.
+    auto flat_sums = [&](int ib, int nc, auto xy, double *out) {
+        const int nrows = r1 - ib;
+        const int T = nrows > 0 ? nrows * nc : 0;
+        const int E = T > 0 ? (((T + nt - 1) / nt) | 1) : 1;
+        const int e0 = min(T, tid * E), cnt = min(T, e0 + E) - e0;
+        if (cnt > 0) {
+            // two streams over the two halves of the range; stream A's partial of a column goes
+            // to pp[2 (tid + cc)], stream B's to pp[2 (tid + cc) + 1] (both zeroed first: a column
+            // may be met by one stream only)
+            const int h = cnt >> 1;
+            const int cf = e0 / nrows, cl_ = (e0 + cnt - 1) / nrows;
+            for (int cc = cf; cc <= cl_; ++cc) {
+                pp[2 * (tid + cc)] = 0.0;
+                pp[2 * (tid + cc) + 1] = 0.0;
+            }
+            int cA = cf, iA = ib + (e0 - cA * nrows);
+            int cB = (e0 + h) / nrows, iB = ib + (e0 + h - cB * nrows);
+            double sA = 0.0, sB = 0.0;
+            for (int k = 0; k < h; ++k) {
+                double xa, ya, xb, yb;
+                xy(iA, cA, xa, ya);
+                xy(iB, cB, xb, yb);
+                sA = fma(xa, ya, sA);
+                sB = fma(xb, yb, sB);
+                if (++iA == r1) { pp[2 * (tid + cA)] = sA; sA = 0.0; iA = ib; ++cA; }
+                if (++iB == r1) { pp[2 * (tid + cB) + 1] = sB; sB = 0.0; iB = ib; ++cB; }
+            }
+            if (cnt & 1) {                                          // the last element: stream B's next
+                double xb, yb;
+                xy(iB, cB, xb, yb);
+                sB = fma(xb, yb, sB);
+                if (++iB == r1) { pp[2 * (tid + cB) + 1] = sB; sB = 0.0; iB = ib; ++cB; }
+            }
+            if (iA != ib) pp[2 * (tid + cA)] = sA;                  // stream A ended inside column cA
+            if (iB != ib) pp[2 * (tid + cB) + 1] = sB;
         }
+        __syncthreads();
+        // the partials of column cc are pp[2 (tlo + cc) .. 2 (thi + cc) + 1]: up to 8 contributors
+        // one thread adds them in order; more (the last steps, few columns) go to a warp each,
+        // 32 lanes strided over them and a shuffle tree
+        const int ncmax = T > 0 ? (nrows + E - 2) / E + 1 : 0;
+        if (ncmax <= 8) {
+            for (int cc = tid; cc < nc; cc += nt) {
+                double acc = 0.0;
+                if (T > 0) {
+                    const int tlo = (cc * nrows) / E, thi = ((cc + 1) * nrows - 1) / E;
+                    for (int t = tlo; t <= thi; ++t) acc += pp[2 * (t + cc)] + pp[2 * (t + cc) + 1];
+                }
+                out[cc] = acc;
+            }
+        } else {
+            for (int cc = warp; cc < nc; cc += nt >> 5) {
+                const int tlo = (cc * nrows) / E, thi = ((cc + 1) * nrows - 1) / E;
+                const int b0 = 2 * (tlo + cc), nv = 2 * (thi - tlo + 1);
+                double acc = 0.0;
+                for (int k = lane; k < nv; k += 32) acc += pp[b0 + k];
+                acc = warp_sum(acc);
+                if (lane == 0) out[cc] = acc;
+            }
+        }
+        __syncthreads();
     };
-    // rows across threads, trailing columns in groups: thread (row lane il, group g) updates
-    // rows ib + il, ib + il + RT, ... in columns cbeg + g, cbeg + g + ng, ... (no division)
-    auto row_layout = [&](int nrows, int &RT, int &ng, int &il, int &g) {
-        RT = nrows <= 64 ? 64 : (nrows <= 128 ? 128 : 256);
-        ng = nt / RT;
-        il = tid % RT;
-        g = tid / RT;
+    // M(i, c0 + cc) -= v(i) * wc[cc] for rows [ib, r1), cc = 0 .. nc - 1 (M = A or Q); one
+    // uniform loop per thread as in flat_sums
+    auto flat_update = [&](int ib, int c0, int nc, auto v, const double *wc, auto M) {
+        const int nrows = r1 - ib;
+        const int T = nrows > 0 ? nrows * nc : 0;
+        if (T == 0) return;
+        const int E = ((T + nt - 1) / nt) | 1;
+        const int e0 = min(T, tid * E), cnt = min(T, e0 + E) - e0;
+        // two independent streams over the two halves of the range, loads issued before the
+        // stores in each iteration (the compiler cannot reorder them across a store itself)
+        const int h = cnt >> 1;
+        int cA = e0 / nrows, iA = ib + (e0 - cA * nrows);
+        int cB = (e0 + h) / nrows, iB = ib + (e0 + h - cB * nrows);
+        double wA = h > 0 ? wc[cA] : 0.0, wB = cnt > h ? wc[cB] : 0.0;
+        for (int k = 0; k < h; ++k) {
+            double &a = M(iA, c0 + cA), &b = M(iB, c0 + cB);
+            const double va = v(iA), vb = v(iB), xa = a, xb = b;
+            a = fma(-va, wA, xa);
+            b = fma(-vb, wB, xb);
+            if (++iA == r1) { iA = ib; ++cA; wA = wc[cA]; }      // cA stays < nc: stream A ends at e0 + h
+            if (++iB == r1) { iB = ib; ++cB; if (k + 1 < h || (cnt & 1)) wB = wc[cB]; }
+        }
+        if (cnt & 1) {                                          // the last element: stream B's next
+            double &b = M(iB, c0 + cB);
+            b = fma(-v(iB), wB, b);
+        }
     };
     // sum over the cluster of rd[lo .. hi) of every peer into dst[lo .. hi): four threads per
     // entry, each over a quarter of the peers (C <= 16: at most four loads, all issued before
@@ -174,11 +251,7 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
     if (piv) {
         for (int c = tid; c < s; c += nt) permv[c] = c;
         double *rd = red[xch & 1];
-        column_sums(0, s, [&](int c, int g) {
-            double pd = 0.0;
-            for (int i = r0 + g; i < r1; i += 8) { const double x = A(i, c); pd = fma(x, x, pd); }
-            return pd;
-        }, rd);
+        flat_sums(r0, s, [&](int i, int c, double &x, double &y) { x = y = A(i, c); }, rd);
         cl.sync();
         ++xch;
         peer_sums(rd, 0, s, 0, nt, wv);
@@ -240,14 +313,9 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
         double *rd = red[xch & 1];
         // rd[0] = sigma2 part (rows > j), rd[cc] = D_{j+cc} part (rows >= j); owner: its row j
         const int ib = max(r0, j);
-        column_sums(j, nc1, [&](int c, int g) {
-            double pd = 0.0;
-            if (c == j) {
-                for (int i = max(ib, j + 1) + g; i < r1; i += 8) { const double x = A(i, j); pd = fma(x, x, pd); }
-            } else {
-                for (int i = ib + g; i < r1; i += 8) pd = fma(A(i, j), A(i, c), pd);
-            }
-            return pd;
+        flat_sums(ib, nc1, [&](int i, int cc, double &x, double &y) {
+            y = A(i, j + cc);
+            x = (cc == 0 && i == j) ? 0.0 : A(i, j);
         }, rd);
         if (owner)
             for (int cc = tid; cc < nc1; cc += nt) rd[nc1 + cc] = A(j, j + cc);
@@ -290,65 +358,26 @@ __global__ void __launch_bounds__(256) k_qr(const __grid_constant__ QRJobs jobs,
         for (int i = max(r0, j + 1) + tid; i < r1; i += nt) A(i, j) *= scal;
         if (owner && tid == 0) A(j, j) = beta;
         __syncthreads();
-        const int nrows = max(0, r1 - ib), nc = nc1 - 1;
         if (piv && warp == 0 && j + 1 < kmax) argmax_pivot(j + 1);   // nrmf is final for step j + 1
-        if (tau != 0.0 && nrows > 0 && nc > 0) {
-            int RT, ng, il, g;
-            row_layout(nrows, RT, ng, il, g);
-            for (int i = ib + il; i < r1; i += RT) {
-                const double v = (i == j) ? 1.0 : A(i, j);
-                for (int cc = 1 + g; cc < nc1; cc += ng) A(i, j + cc) = fma(-v, wv[cc], A(i, j + cc));
-            }
-        }
+        if (tau != 0.0)
+            flat_update(ib, j + 1, nc1 - 1, [&](int i) { return (i == j) ? 1.0 : A(i, j); }, wv + 1,
+                        [&](int i, int c) -> double & { return A(i, c); });
         __syncthreads();
     }
     if (J.tau && q == 0)
         for (int j = tid; j < kmax; j += nt) J.tau[j] = taus[j];
     if (piv && q == 0)
         for (int c = tid; c < s; c += nt) J.perm[c] = permv[c];
-    if (J.Q) {
-        for (int e = tid; e < nr * s; e += nt) {
-            const int i = r0 + e % nr, c = e / nr;
-            Q(i, c) = (i == c) ? 1.0 : 0.0;
-        }
-        __syncthreads();
-        for (int j = kmax - 1; j >= 0; --j) {
-            const double tau = taus[j];
-            if (tau == 0.0) continue;   // uniform across the cluster
-            double *rd = red[xch & 1];
-            const int ib = max(r0, j), ncq = s - j;
-            column_sums(j, ncq, [&](int c, int g) {
-                double pd = 0.0;
-                for (int i = ib + g; i < r1; i += 8) pd = fma(i == j ? 1.0 : A(i, j), Q(i, c), pd);
-                return pd;
-            }, rd);
-            cl.sync();
-            ++xch;
-            peer_sums(rd, 0, ncq, 0, nt, wv);
-            __syncthreads();
-            const int nrows = r1 - ib;
-            if (nrows > 0) {
-                int RT, ng, il, g;
-                row_layout(nrows, RT, ng, il, g);
-                for (int i = ib + il; i < r1; i += RT) {
-                    const double tv = tau * ((i == j) ? 1.0 : A(i, j));   // Q_c -= (tau v) (v^T Q_c)
-                    for (int cc = g; cc < ncq; cc += ng) Q(i, j + cc) = fma(-tv, wv[cc], Q(i, j + cc));
-                }
-            }
-            __syncthreads();
-        }
-    }
     if (SMEM) {
         for (int e = tid; e < nr * s; e += nt) {
             const int i = r0 + e % nr, c = e / nr;
             J.A[i + (long long)c * m] = A(i, c);
-            if (J.Q) J.Q[i + (long long)c * m] = Q(i, c);
         }
     }
     cl.sync();   // keep this CTA's shared memory alive until every peer finished reading it
 }
 
-void qr_householder(Ctx &c, const std::vector<QRJob> &jobs) {
+static void qr_reflectors(Ctx &c, const std::vector<QRJob> &jobs) {
     if (jobs.empty()) return;
     static std::atomic<bool> attr_set{false};   // set once; idempotent if two threads race
     if (!attr_set) {
@@ -361,13 +390,12 @@ void qr_householder(Ctx &c, const std::vector<QRJob> &jobs) {
         QRJobs J{};
         J.n = (int)std::min<size_t>(TK_MAX_D, jobs.size() - base);
         int mmax = 0, smax = 0;
-        bool wantq = false;
         for (int i = 0; i < J.n; ++i) {
             J.j[i] = jobs[base + i];
             TK_REQUIRE(J.j[i].s <= QR_MAXS, "QR: more than 256 columns");
+            TK_REQUIRE(J.j[i].Q == nullptr, "QR kernel: Q is formed by qr_form_q");
             mmax = std::max(mmax, J.j[i].m);
             smax = std::max(smax, J.j[i].s);
-            wantq = wantq || J.j[i].Q != nullptr;
         }
         // cluster of up to 16 CTAs with >= 48 rows each, shrunk until the device can place it
         int C = std::max(1, std::min(16, (mmax + 47) / 48));
@@ -377,7 +405,7 @@ void qr_householder(Ctx &c, const std::vector<QRJob> &jobs) {
         bool use_smem = false;
         for (;;) {
             rb = (mmax + C - 1) / C;
-            const size_t smem = (size_t)rb * smax * sizeof(double) * (wantq ? 2 : 1);
+            const size_t smem = (size_t)rb * smax * sizeof(double);
             use_smem = smem <= 180 * 1024;
             cfg = cudaLaunchConfig_t{};
             cfg.gridDim = dim3((unsigned)C, (unsigned)J.n, 1);
@@ -404,14 +432,154 @@ void qr_householder(Ctx &c, const std::vector<QRJob> &jobs) {
             TK_CUDA(cudaLaunchKernelEx(&cfg, k_qr<true>, J, rb));
         else
             TK_CUDA(cudaLaunchKernelEx(&cfg, k_qr<false>, J, rb));
-        double flops = 0.0;   // Householder: 2 m s^2 - 2 s^3 / 3 for R, the same again for Q
+        double flops = 0.0;   // Householder R: 2 m s^2 - 2 s^3 / 3
         for (int i = 0; i < J.n; ++i) {
             const double m = J.j[i].m, s = std::min(J.j[i].m, J.j[i].s);
-            const double f = 2.0 * m * s * s - 2.0 * s * s * s / 3.0;
-            flops += J.j[i].Q ? 2.0 * f : f;
+            flops += 2.0 * m * s * s - 2.0 * s * s * s / 3.0;
         }
         c.check_launch("qr", flops);
     }
+}
+
+// Explicit Q from the reflectors in compact WY form (Schreiber and Van Loan's representation,
+// with T from the UT transform of Joffrain, Low, Quintana-Orti and van de Geijn): with
+// k = min(m, s), V (m x k) unit lower trapezoidal (v_j(j) = 1, v_j(i) = A(i, j) below, zero above)
+// and tau, H_0 ... H_{k-1} = I - V T V^T where T^{-1} = S = diag(1 / tau) + the strict upper
+// part of V^T V (an algebraic identity for any tau; a reflector with tau = 0 is the identity and
+// its column of V is set to zero, with S_jj = 1).  Q = E - V X with S X = V_1^T, V_1 = V[0:k, :],
+// E = [I_s; 0] (or [I_m, 0] when m < s, columns >= m of Q zero).  The k reflector steps that
+// the backward accumulation would take, each with a cluster exchange, become two FP64 GEMMs over m
+// and a triangular solve of order k whose columns are independent.
+struct QRWY {
+    int n, k[TK_MAX_D], m[TK_MAX_D], s[TK_MAX_D];
+    const double *A[TK_MAX_D], *tau[TK_MAX_D], *W[TK_MAX_D];
+    double *V[TK_MAX_D], *Q[TK_MAX_D], *X[TK_MAX_D];
+};
+
+__global__ void k_qr_wy_init(const __grid_constant__ QRWY J) {
+    const int b = blockIdx.y, m = J.m[b], s = J.s[b], k = J.k[b];
+    const long long n = (long long)m * s;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % m), c = (int)(e / m);
+        if (c < k) {
+            const double v = (i > c) ? J.A[b][e] : (i == c ? 1.0 : 0.0);
+            J.V[b][e] = J.tau[b][c] == 0.0 ? 0.0 : v;
+        }
+        J.Q[b][e] = (i == c && c < k) ? 1.0 : 0.0;
+    }
+}
+
+// S X = V_1^T for columns [c0, c0 + QWY_CPB) of X: S (upper triangle from W = V^T V and tau) in
+// shared memory, right-looking back substitution (row j of X, then the rank-1 update of the rows
+// above it), the block's columns side by side
+constexpr int QWY_CPB = 8;
+__global__ void __launch_bounds__(256) k_qr_wy_solve(const __grid_constant__ QRWY J) {
+    const int b = blockIdx.y, k = J.k[b], m = J.m[b];
+    const int c0 = blockIdx.x * QWY_CPB;
+    if (c0 >= k) return;
+    const int nc = min(QWY_CPB, k - c0);
+    extern __shared__ double wsh[];
+    double *S = wsh;                                  // k x k (upper triangle used)
+    double *Bs = wsh + (size_t)k * k;                 // k x QWY_CPB
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const double *W = J.W[b], *V = J.V[b], *tau = J.tau[b];
+    for (int e = tid; e < k * k; e += nt) S[e] = W[e];
+    for (int e = tid; e < k * nc; e += nt) {
+        const int j = e % k, cc = e / k;
+        Bs[j + cc * k] = V[(c0 + cc) + (long long)j * m];      // V_1^T[j, c] = V[c, j]
+    }
+    __syncthreads();
+    for (int j = k - 1; j >= 0; --j) {
+        const double dj = tau[j] == 0.0 ? 1.0 : tau[j];          // 1 / S_jj
+        if (tid < nc) Bs[j + tid * k] *= dj;
+        __syncthreads();
+        for (int e = tid; e < j * nc; e += nt) {
+            const int i = e % j, cc = e / j;
+            Bs[i + cc * k] = fma(-S[i + j * k], Bs[j + cc * k], Bs[i + cc * k]);
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < k * nc; e += nt) {
+        const int j = e % k, cc = e / k;
+        J.X[b][j + (long long)(c0 + cc) * k] = Bs[j + cc * k];
+    }
+}
+
+static void qr_form_q(Ctx &c, const std::vector<QRJob> &jobs) {
+    for (size_t base = 0; base < jobs.size(); base += TK_MAX_D) {
+        QRWY J{};
+        J.n = (int)std::min<size_t>(TK_MAX_D, jobs.size() - base);
+        int kmax = 0;
+        long long nmax = 0;
+        for (int i = 0; i < J.n; ++i) {
+            const QRJob &q = jobs[base + i];
+            TK_REQUIRE(q.tau != nullptr, "QR: the explicit Q needs tau");
+            J.m[i] = q.m;
+            J.s[i] = q.s;
+            J.k[i] = std::min(q.m, q.s);
+            J.A[i] = q.A;
+            J.tau[i] = q.tau;
+            J.Q[i] = q.Q;
+            J.V[i] = c.arena->alloc((size_t)q.m * J.k[i]);
+            J.W[i] = J.X[i] = nullptr;
+            kmax = std::max(kmax, J.k[i]);
+            nmax = std::max(nmax, (long long)q.m * q.s);
+        }
+        double *Wb[TK_MAX_D];
+        for (int i = 0; i < J.n; ++i) {
+            Wb[i] = c.arena->alloc((size_t)J.k[i] * J.k[i]);
+            J.W[i] = Wb[i];
+            J.X[i] = c.arena->alloc((size_t)J.k[i] * J.k[i]);
+        }
+        c.pre_launch();
+        k_qr_wy_init<<<dim3((unsigned)std::min<long long>((nmax + 255) / 256, 592), (unsigned)J.n), 256, 0, c.st>>>(J);
+        double bytes = 0.0;
+        for (int i = 0; i < J.n; ++i) bytes += 8.0 * ((double)J.m[i] * J.k[i] * 2 + (double)J.m[i] * J.s[i]);
+        c.check_launch("qr_wy", 0.0, bytes);
+        {
+            Gemm g(c, "gemm_qr");
+            for (int i = 0; i < J.n; ++i)
+                g.add1(J.k[i], J.k[i], J.m[i], 1, 0, J.V[i], J.m[i], J.V[i], J.m[i], Wb[i], J.k[i]);
+            g.run();
+        }
+        constexpr int WY_SMEM_MAX = 227 * 1024;
+        static std::atomic<bool> attr_set{false};
+        if (!attr_set) {
+            TK_CUDA(cudaFuncSetAttribute(k_qr_wy_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, WY_SMEM_MAX));
+            attr_set = true;
+        }
+        const size_t smem = sizeof(double) * ((size_t)kmax * kmax + (size_t)kmax * QWY_CPB);
+        TK_REQUIRE(smem <= (size_t)WY_SMEM_MAX, "QR: an explicit Q of more than 165 columns");
+        c.pre_launch();
+        k_qr_wy_solve<<<dim3((unsigned)((kmax + QWY_CPB - 1) / QWY_CPB), (unsigned)J.n), 256, smem, c.st>>>(J);
+        double flops = 0.0;
+        for (int i = 0; i < J.n; ++i) flops += (double)J.k[i] * J.k[i] * J.k[i];
+        c.check_launch("qr_wy", flops);
+        {
+            Gemm g(c, "gemm_qr");
+            for (int i = 0; i < J.n; ++i)
+                g.add1(J.m[i], J.k[i], J.k[i], 0, 0, J.V[i], J.m[i], J.X[i], J.k[i], J.Q[i], J.m[i], 1.0, -1.0);
+            g.run();
+        }
+    }
+}
+
+void qr_householder(Ctx &c, const std::vector<QRJob> &jobs) {
+    if (jobs.empty()) return;
+    // the kernel leaves R and the reflectors; an explicit Q is formed from them afterwards
+    std::vector<QRJob> rj = jobs;
+    bool wantq = false;
+    for (QRJob &j : rj) {
+        wantq = wantq || j.Q != nullptr;
+        j.Q = nullptr;
+    }
+    qr_reflectors(c, rj);
+    if (!wantq) return;
+    std::vector<QRJob> qj;
+    for (const QRJob &j : jobs)
+        if (j.Q) qj.push_back(j);
+    ScopedMark mark(*c.arena);
+    qr_form_q(c, qj);
 }
 
 // ------------------------------------------------------------------------------------------
