@@ -130,6 +130,34 @@ __global__ void __launch_bounds__(256, 1) k_qr(const __grid_constant__ QRJobs jo
         }
     __syncthreads();
     int xch = 0;   // exchanges so far (selects the buffer)
+    // the column sums out[cc] from the partials in pp (slot thread + column, two halves); ends
+    // with out[] visible to the CTA
+    auto combine = [&](int T, int nrows, int E, int nc, double *out) {
+        // the partials of column cc are pp[2 (tlo + cc) .. 2 (thi + cc) + 1]: up to 8 contributors
+        // one thread adds them in order; more (the last steps, few columns) go to a warp each,
+        // 32 lanes strided over them and a shuffle tree
+        const int ncmax = T > 0 ? (nrows + E - 2) / E + 1 : 0;
+        if (ncmax <= 8) {
+            for (int cc = tid; cc < nc; cc += nt) {
+                double acc = 0.0;
+                if (T > 0) {
+                    const int tlo = (cc * nrows) / E, thi = ((cc + 1) * nrows - 1) / E;
+                    for (int t = tlo; t <= thi; ++t) acc += pp[2 * (t + cc)] + pp[2 * (t + cc) + 1];
+                }
+                out[cc] = acc;
+            }
+        } else {
+            for (int cc = warp; cc < nc; cc += nt >> 5) {
+                const int tlo = (cc * nrows) / E, thi = ((cc + 1) * nrows - 1) / E;
+                const int b0 = 2 * (tlo + cc), nv = 2 * (thi - tlo + 1);
+                double acc = 0.0;
+                for (int k = lane; k < nv; k += 32) acc += pp[b0 + k];
+                acc = warp_sum(acc);
+                if (lane == 0) out[cc] = acc;
+            }
+        }
+        __syncthreads();
+    };
     // sum over rows [ib, r1) of x * y for columns cc = 0 .. nc - 1 into out[cc], where
     // xy(i, cc, x, y) gives the two factors of element (i, cc); ends with out[] complete and
     // visible to the whole CTA.  Every thread runs the same trip count (all but the last few), so
@@ -172,30 +200,7 @@ __global__ void __launch_bounds__(256, 1) k_qr(const __grid_constant__ QRJobs jo
             if (iB != ib) pp[2 * (tid + cB) + 1] = sB;
         }
         __syncthreads();
-        // the partials of column cc are pp[2 (tlo + cc) .. 2 (thi + cc) + 1]: up to 8 contributors
-        // one thread adds them in order; more (the last steps, few columns) go to a warp each,
-        // 32 lanes strided over them and a shuffle tree
-        const int ncmax = T > 0 ? (nrows + E - 2) / E + 1 : 0;
-        if (ncmax <= 8) {
-            for (int cc = tid; cc < nc; cc += nt) {
-                double acc = 0.0;
-                if (T > 0) {
-                    const int tlo = (cc * nrows) / E, thi = ((cc + 1) * nrows - 1) / E;
-                    for (int t = tlo; t <= thi; ++t) acc += pp[2 * (t + cc)] + pp[2 * (t + cc) + 1];
-                }
-                out[cc] = acc;
-            }
-        } else {
-            for (int cc = warp; cc < nc; cc += nt >> 5) {
-                const int tlo = (cc * nrows) / E, thi = ((cc + 1) * nrows - 1) / E;
-                const int b0 = 2 * (tlo + cc), nv = 2 * (thi - tlo + 1);
-                double acc = 0.0;
-                for (int k = lane; k < nv; k += 32) acc += pp[b0 + k];
-                acc = warp_sum(acc);
-                if (lane == 0) out[cc] = acc;
-            }
-        }
-        __syncthreads();
+        combine(T, nrows, E, nc, out);
     };
     // M(i, c0 + cc) -= v(i) * wc[cc] for rows [ib, r1), cc = 0 .. nc - 1 (M = A or Q); one
     // uniform loop per thread as in flat_sums
@@ -223,6 +228,57 @@ __global__ void __launch_bounds__(256, 1) k_qr(const __grid_constant__ QRJobs jo
             double &b = M(iB, c0 + cB);
             b = fma(-v(iB), wB, b);
         }
+    };
+    // Step j's trailing update and step j + 1's partial sums in one pass over rows [ib, r1) and
+    // positions c = j + 1 + cc, cc = 0 .. nc - 1: position j + 1 holds the next column x (already
+    // reflected; its element only adds x_i^2 for i > j + 1, the sigma2 part), every other position
+    // takes a' = a - v_i w_c (v_j = 1) and adds x_i a' for i >= j + 1 (D_c part).  Two FP64 FMAs
+    // per element, both streams' loads issued before their stores; partials and combine as in
+    // flat_sums, the combine writing out[cc].
+    auto fused_pass = [&](int j, int ib, int nc, double *out) {
+        const int nrows = r1 - ib;
+        const int T = nrows > 0 ? nrows * nc : 0;
+        const int E = T > 0 ? (((T + nt - 1) / nt) | 1) : 1;
+        const int e0 = min(T, tid * E), cnt = min(T, e0 + E) - e0;
+        const int c0 = j + 1;
+        if (cnt > 0) {
+            const int h = cnt >> 1;
+            const int cf = e0 / nrows, cl_ = (e0 + cnt - 1) / nrows;
+            for (int cc = cf; cc <= cl_; ++cc) {
+                pp[2 * (tid + cc)] = 0.0;
+                pp[2 * (tid + cc) + 1] = 0.0;
+            }
+            int cA = cf, iA = ib + (e0 - cA * nrows);
+            int cB = (e0 + h) / nrows, iB = ib + (e0 + h - cB * nrows);
+            double wA = cA == 0 ? 0.0 : wv[cA + 1], wB = (cB == 0 || cB >= nc) ? 0.0 : wv[cB + 1];
+            double sA = 0.0, sB = 0.0;
+            for (int k = 0; k < h; ++k) {
+                double &a = A(iA, c0 + cA), &b = A(iB, c0 + cB);
+                const double aa = a, bb = b;
+                const double va = (iA == j) ? 1.0 : A(iA, j), vb = (iB == j) ? 1.0 : A(iB, j);
+                const double xa = A(iA, c0), xb = A(iB, c0);
+                const double na = fma(-va, wA, aa), nb = fma(-vb, wB, bb);
+                if (cA != 0) a = na;
+                if (cB != 0) b = nb;
+                sA = fma(iA > (cA == 0 ? j + 1 : j) ? xa : 0.0, na, sA);
+                sB = fma(iB > (cB == 0 ? j + 1 : j) ? xb : 0.0, nb, sB);
+                if (++iA == r1) { pp[2 * (tid + cA)] = sA; sA = 0.0; iA = ib; ++cA; wA = cA < nc ? wv[cA + 1] : 0.0; }
+                if (++iB == r1) { pp[2 * (tid + cB) + 1] = sB; sB = 0.0; iB = ib; ++cB; wB = cB < nc ? wv[cB + 1] : 0.0; }
+            }
+            if (cnt & 1) {                                          // the last element: stream B's next
+                double &b = A(iB, c0 + cB);
+                const double bb = b;
+                const double vb = (iB == j) ? 1.0 : A(iB, j), xb = A(iB, c0);
+                const double nb = fma(-vb, wB, bb);
+                if (cB != 0) b = nb;
+                sB = fma(iB > (cB == 0 ? j + 1 : j) ? xb : 0.0, nb, sB);
+                if (++iB == r1) { pp[2 * (tid + cB) + 1] = sB; sB = 0.0; iB = ib; ++cB; }
+            }
+            if (iA != ib) pp[2 * (tid + cA)] = sA;
+            if (iB != ib) pp[2 * (tid + cB) + 1] = sB;
+        }
+        __syncthreads();
+        combine(T, nrows, E, nc, out);
     };
     // sum over the cluster of rd[lo .. hi) of every peer into dst[lo .. hi): four threads per
     // entry, each over a quarter of the peers (C <= 16: at most four loads, all issued before
@@ -284,41 +340,43 @@ __global__ void __launch_bounds__(256, 1) k_qr(const __grid_constant__ QRJobs jo
             if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
         }
         if (lane == 0) pivot = bi;
+        return bi;                                  // the same in every lane after the butterfly
     };
+    // step j + 1's partial sums are formed in the same pass as step j's trailing update
+    // (fused_pass below); step 0's here: pivot, then the plain sums
+    if (piv) {
+        if (warp == 0) argmax_pivot(0);
+        __syncthreads();
+        const int p0 = pivot;
+        if (p0 != 0) {
+            for (int i = r0 + tid; i < r1; i += nt) {
+                const double t = A(i, 0);
+                A(i, 0) = A(i, p0);
+                A(i, p0) = t;
+            }
+            if (tid == 0) {
+                const float t = nrmf[0]; nrmf[0] = nrmf[p0]; nrmf[p0] = t;
+                const int u = permv[0]; permv[0] = permv[p0]; permv[p0] = u;
+            }
+        }
+        __syncthreads();
+    }
+    if (kmax > 0) {
+        double *rd = red[xch & 1];
+        // rd[0] = sigma2 part (rows > 0), rd[cc] = D_cc part; the owner of row 0 adds its row
+        flat_sums(r0, s, [&](int i, int cc, double &x, double &y) {
+            y = A(i, cc);
+            x = (cc == 0 && i == 0) ? 0.0 : A(i, 0);
+        }, rd);
+        if (q == 0)
+            for (int cc = tid; cc < s; cc += nt) rd[s + cc] = A(0, cc);
+    }
     for (int j = 0; j < kmax; ++j) {
         const int nc1 = s - j;              // columns j .. s-1
         const int own = j / rb;              // CTA holding row j
         const bool owner = (q == own);
-        if (piv) {
-            // pivot for column j: chosen by warp 0 during the previous step's update (step 0:
-            // here), from nrmf, which every CTA holds identically
-            if (j == 0) {
-                if (warp == 0) argmax_pivot(0);
-                __syncthreads();
-            }
-            const int p = pivot;
-            if (p != j) {
-                for (int i = r0 + tid; i < r1; i += nt) {
-                    const double t = A(i, j);
-                    A(i, j) = A(i, p);
-                    A(i, p) = t;
-                }
-                if (tid == 0) {
-                    const float t = nrmf[j]; nrmf[j] = nrmf[p]; nrmf[p] = t;
-                    const int u = permv[j]; permv[j] = permv[p]; permv[p] = u;
-                }
-            }
-            __syncthreads();
-        }
-        double *rd = red[xch & 1];
-        // rd[0] = sigma2 part (rows > j), rd[cc] = D_{j+cc} part (rows >= j); owner: its row j
         const int ib = max(r0, j);
-        flat_sums(ib, nc1, [&](int i, int cc, double &x, double &y) {
-            y = A(i, j + cc);
-            x = (cc == 0 && i == j) ? 0.0 : A(i, j);
-        }, rd);
-        if (owner)
-            for (int cc = tid; cc < nc1; cc += nt) rd[nc1 + cc] = A(j, j + cc);
+        double *rd = red[xch & 1];
         cl.sync();
         ++xch;
         const double *ro = cl.map_shared_rank(rd, own);
@@ -358,11 +416,37 @@ __global__ void __launch_bounds__(256, 1) k_qr(const __grid_constant__ QRJobs jo
         for (int i = max(r0, j + 1) + tid; i < r1; i += nt) A(i, j) *= scal;
         if (owner && tid == 0) A(j, j) = beta;
         __syncthreads();
-        if (piv && warp == 0 && j + 1 < kmax) argmax_pivot(j + 1);   // nrmf is final for step j + 1
-        if (tau != 0.0)
-            flat_update(ib, j + 1, nc1 - 1, [&](int i) { return (i == j) ? 1.0 : A(i, j); }, wv + 1,
-                        [&](int i, int c) -> double & { return A(i, c); });
+        if (j + 1 == kmax) {
+            // last reflector: columns beyond kmax (m < s) still take it
+            if (tau != 0.0)
+                flat_update(ib, j + 1, nc1 - 1, [&](int i) { return (i == j) ? 1.0 : A(i, j); }, wv + 1,
+                            [&](int i, int c) -> double & { return A(i, c); });
+            __syncthreads();
+            break;
+        }
+        // pivot of step j + 1 (every warp finds the same), then that column takes reflector j and
+        // moves to position j + 1 (with its w, FP32 norm and index)
+        int p = j + 1;
+        if (piv) p = argmax_pivot(j + 1);
+        for (int i = r0 + tid; i < r1; i += nt) {
+            const double v = (i == j) ? 1.0 : A(i, j);
+            const double wp = (i >= ib) ? wv[p - j] : 0.0;
+            const double xp = fma(-v, wp, A(i, p));
+            if (p != j + 1) A(i, p) = A(i, j + 1);
+            A(i, j + 1) = xp;
+        }
         __syncthreads();
+        if (tid == 0 && p != j + 1) {
+            const double t = wv[1]; wv[1] = wv[p - j]; wv[p - j] = t;
+            const float f = nrmf[j + 1]; nrmf[j + 1] = nrmf[p]; nrmf[p] = f;
+            const int u = permv[j + 1]; permv[j + 1] = permv[p]; permv[p] = u;
+        }
+        __syncthreads();
+        // reflector j on columns j + 2 .. s - 1 and step j + 1's partial sums in one pass
+        double *rn = red[xch & 1];
+        fused_pass(j, ib, nc1 - 1, rn);
+        if (q == (j + 1) / rb)
+            for (int cc = tid; cc < nc1 - 1; cc += nt) rn[nc1 - 1 + cc] = A(j + 1, j + 1 + cc);
     }
     if (J.tau && q == 0)
         for (int j = tid; j < kmax; j += nt) J.tau[j] = taus[j];
