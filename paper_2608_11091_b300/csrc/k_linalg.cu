@@ -619,7 +619,7 @@ static void qr_form_q(Ctx &c, const std::vector<QRJob> &jobs) {
         k_qr_wy_init<<<dim3((unsigned)std::min<long long>((nmax + 255) / 256, 592), (unsigned)J.n), 256, 0, c.st>>>(J);
         double bytes = 0.0;
         for (int i = 0; i < J.n; ++i) bytes += 8.0 * ((double)J.m[i] * J.k[i] * 2 + (double)J.m[i] * J.s[i]);
-        c.check_launch("qr_wy", 0.0, bytes);
+        c.check_launch("qr_wy_init", 0.0, bytes);
         {
             Gemm g(c, "gemm_qr");
             for (int i = 0; i < J.n; ++i)
@@ -638,7 +638,7 @@ static void qr_form_q(Ctx &c, const std::vector<QRJob> &jobs) {
         k_qr_wy_solve<<<dim3((unsigned)((kmax + QWY_CPB - 1) / QWY_CPB), (unsigned)J.n), 256, smem, c.st>>>(J);
         double flops = 0.0;
         for (int i = 0; i < J.n; ++i) flops += (double)J.k[i] * J.k[i] * J.k[i];
-        c.check_launch("qr_wy", flops);
+        c.check_launch("qr_wy_solve", flops);
         {
             Gemm g(c, "gemm_qr");
             for (int i = 0; i < J.n; ++i)
