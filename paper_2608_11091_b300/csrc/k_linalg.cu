@@ -1428,7 +1428,7 @@ void tikhonov_gcv(Ctx &c, const LSState &st, int ldr, int k, int m, double *lamb
 //      A) and, behind them, an FP32 publish area (s cb floats: columns of E, then of T);
 //   Y: full copies (Y = double(V32), then the gathered A);
 //   Z: [0, s cb) work columns (E, Z, H, T, D) and, behind them, FP32 full gathers (s^2 floats).
-constexpr int SCL = 8;
+constexpr int SCL = 16;
 __global__ void __launch_bounds__(1024) k_svd_cl(const __grid_constant__ SVDJobs jobs) {
     cg::cluster_group cl = cg::this_cluster();
     const int q = (int)cl.block_rank();
@@ -1715,6 +1715,7 @@ static void svd_cl_launch(Ctx &c, SVDJobs &J, int smax) {
     if (!attr_set) {
         TK_CUDA(cudaFuncSetAttribute(k_svd_cl, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      3 * SVD_MAXS * SVD_MAXS * (int)sizeof(double)));
+        TK_CUDA(cudaFuncSetAttribute(k_svd_cl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
         attr_set = true;
     }
     cudaLaunchConfig_t cfg{};
@@ -1739,7 +1740,7 @@ static void svd_cl_launch(Ctx &c, SVDJobs &J, int smax) {
 void svd_jacobi(Ctx &c, const std::vector<SVDJob> &jobs) {
     // graded (ST-HOSVD) jobs of at least 2 SCL columns: the clustered kernel
     bool all_graded = !jobs.empty();
-    for (const SVDJob &j : jobs) all_graded = all_graded && j.perm != nullptr && j.s >= 2 * SCL;
+    for (const SVDJob &j : jobs) all_graded = all_graded && j.perm != nullptr && j.s >= 16;
     if (all_graded) {
         for (size_t base = 0; base < jobs.size(); base += TK_MAX_D) {
             SVDJobs J{};
