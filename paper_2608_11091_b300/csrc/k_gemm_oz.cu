@@ -102,8 +102,20 @@ __global__ void __launch_bounds__(256) k_oz_split(const __grid_constant__ OzSide
     const int W = min(OZ_CHUNK, D.Kpad - k0);        // a multiple of 64
     extern __shared__ long long oz_tile[];
     auto t = [&](int r, int kk) -> long long & { return oz_tile[r * OZ_SPLIT_LD + kk]; };
-    __shared__ int er[32];
+    __shared__ int er[32];                           // row index i within its batch, later the exponents
+    __shared__ long long rowoff[32];                  // per row: bstride b (+ i when not transposed)
+    __shared__ double segscale[GEMM_MAXSEG];         // per segment: coef (* *cd)
     const int tid = threadIdx.x;
+    // the row offsets and the segment scales once per block, not per element (integer division
+    // and FP64 multiplies are slow per element on this part)
+    if (tid < 32) {
+        const int m = r0 + tid;
+        const int i = m % D.a, b = m / D.a;
+        rowoff[tid] = (long long)b * D.bstride + (D.trans ? 0LL : (long long)i);
+        er[tid] = i;
+    }
+    if (tid < D.nseg) segscale[tid] = D.seg[tid].coef * (D.seg[tid].cd ? *D.seg[tid].cd : 1.0);
+    __syncthreads();
     for (int e = tid; e < 32 * W; e += 256) {
         int r, kk;
         if (D.trans) { kk = e % W; r = e / W; } else { r = e % 32; kk = e / 32; }
@@ -113,10 +125,11 @@ __global__ void __launch_bounds__(256) k_oz_split(const __grid_constant__ OzSide
             for (int s = 0; s < D.nseg; ++s) {
                 const OzSeg &g = D.seg[s];
                 if (k >= g.koff && k < g.koff + g.K) {
-                    const int i = m % D.a, b = m / D.a, kl = k - g.koff;
-                    const double *src = g.p + (long long)b * D.bstride;
-                    v = D.trans ? src[kl + (long long)g.ld * i] : src[i + (long long)g.ld * kl];
-                    v *= g.coef * (g.cd ? *g.cd : 1.0);
+                    const int kl = k - g.koff;
+                    const double *src = g.p + rowoff[r];
+                    v = D.trans ? src[kl + (long long)g.ld * er[r]] : src[(long long)g.ld * kl];
+                    const double sc = segscale[s];
+                    if (sc != 1.0) v *= sc;
                     break;
                 }
             }
@@ -126,6 +139,7 @@ __global__ void __launch_bounds__(256) k_oz_split(const __grid_constant__ OzSide
     __syncthreads();
     {
         const int warp = tid >> 5, lane = tid & 31;
+        // er[] now takes the exponents: every read of it as a row index happened before the barrier
         for (int r = warp; r < 32; r += 8) {
             int ef = 0;
             for (int kk = lane; kk < W; kk += 32) ef = max(ef, (int)((t(r, kk) >> 52) & 0x7FF));
@@ -157,11 +171,11 @@ __global__ void __launch_bounds__(256) k_oz_split(const __grid_constant__ OzSide
         __nv_bfloat16 *dst = D.planes + (long long)(r0 + r) * D.Kpad + k0 + kk;
 #pragma unroll
         for (int p = OZ_S - 1; p >= 1; --p) {
-            const long long d = ((X + 128) & 255) - 128;        // balanced digit in [-128, 127]
+            const int d = (int)(((X + 128) & 255) - 128);       // balanced digit in [-128, 127]
             dst[p * plane] = __float2bfloat16_rn((float)d);
             X = (X - d) >> 8;                                    // exact: X - d = 0 mod 256
         }
-        dst[0] = __float2bfloat16_rn((float)X);                 // |d_0| <= 128
+        dst[0] = __float2bfloat16_rn((float)(int)X);            // |d_0| <= 128
     }
 }
 

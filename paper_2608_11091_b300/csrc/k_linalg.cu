@@ -98,8 +98,9 @@ struct QRJobs {
 // Rows live in shared memory when they fit (SMEM = true), else in global memory.  The
 // exchange buffers alternate by a running exchange count, so a buffer is rewritten only after
 // every peer has passed the next cluster barrier.
+constexpr int QR_THREADS = 256;
 template <bool SMEM>
-__global__ void __launch_bounds__(256, 1) k_qr(const __grid_constant__ QRJobs jobs, int rb_cap) {
+__global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QRJobs jobs, int rb_cap) {
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks();
     const int q = (int)cl.block_rank();
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(256, 1) k_qr(const __grid_constant__ QRJobs jo
     __shared__ float nrmf[QR_MAXS];
     __shared__ int permv[QR_MAXS];
     __shared__ double bc[4];
-    __shared__ double pp[4 * QR_MAXS];             // per-thread partial sums (two per slot thread + column)
+    __shared__ double pp[2 * (QR_THREADS + QR_MAXS)];  // per-thread partial sums (two per slot thread + column)
     __shared__ int pivot;
     const bool piv = J.perm != nullptr;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
@@ -493,7 +494,7 @@ static void qr_reflectors(Ctx &c, const std::vector<QRJob> &jobs) {
             use_smem = smem <= 180 * 1024;
             cfg = cudaLaunchConfig_t{};
             cfg.gridDim = dim3((unsigned)C, (unsigned)J.n, 1);
-            cfg.blockDim = dim3(256, 1, 1);
+            cfg.blockDim = dim3(QR_THREADS, 1, 1);
             cfg.dynamicSmemBytes = use_smem ? smem : 0;
             cfg.stream = c.st;
             attr[0].id = cudaLaunchAttributeClusterDimension;
