@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
     // takes a' = a - v_i w_c (v_j = 1) and adds x_i a' for i >= j + 1 (D_c part).  Two FP64 FMAs
     // per element, both streams' loads issued before their stores; partials and combine as in
     // flat_sums, the combine writing out[cc].
-    auto fused_pass = [&](int j, int ib, int nc, double *out) {
+    auto fused_pass = [&](int j, int p, int ib, int nc, double *out) {
         const int nrows = r1 - ib;
         const int T = nrows > 0 ? nrows * nc : 0;
         const int E = T > 0 ? (((T + nt - 1) / nt) | 1) : 1;
@@ -251,7 +251,9 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
             }
             int cA = cf, iA = ib + (e0 - cA * nrows);
             int cB = (e0 + h) / nrows, iB = ib + (e0 + h - cB * nrows);
-            double wA = cA == 0 ? 0.0 : wv[cA + 1], wB = (cB == 0 || cB >= nc) ? 0.0 : wv[cB + 1];
+            // w of position j + 1 + cc (0 for the x column itself)
+            auto wat = [&](int cc) { return (cc == 0 || cc >= nc) ? 0.0 : wv[(j + 1 + cc == p) ? 1 : cc + 1]; };
+            double wA = wat(cA), wB = wat(cB);
             double sA = 0.0, sB = 0.0;
             for (int k = 0; k < h; ++k) {
                 double &a = A(iA, c0 + cA), &b = A(iB, c0 + cB);
@@ -263,8 +265,8 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
                 if (cB != 0) b = nb;
                 sA = fma(iA > (cA == 0 ? j + 1 : j) ? xa : 0.0, na, sA);
                 sB = fma(iB > (cB == 0 ? j + 1 : j) ? xb : 0.0, nb, sB);
-                if (++iA == r1) { pp[2 * (tid + cA)] = sA; sA = 0.0; iA = ib; ++cA; wA = cA < nc ? wv[cA + 1] : 0.0; }
-                if (++iB == r1) { pp[2 * (tid + cB) + 1] = sB; sB = 0.0; iB = ib; ++cB; wB = cB < nc ? wv[cB + 1] : 0.0; }
+                if (++iA == r1) { pp[2 * (tid + cA)] = sA; sA = 0.0; iA = ib; ++cA; wA = wat(cA); }
+                if (++iB == r1) { pp[2 * (tid + cB) + 1] = sB; sB = 0.0; iB = ib; ++cB; wB = wat(cB); }
             }
             if (cnt & 1) {                                          // the last element: stream B's next
                 double &b = A(iB, c0 + cB);
@@ -388,12 +390,15 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
 #pragma unroll
             for (int o = 8; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
             if (lane == 0) {
+                // with nrm = (alpha^2 + sigma2)^(1/2) and a = |alpha|: tau = (beta - alpha) / beta
+                // = 1 + a / nrm and 1 / (alpha - beta) = sign(alpha) / (a + nrm); one reciprocal
+                // square root and one reciprocal in the dependent chain
                 double tau = 0.0, beta = al, scal = 0.0;
                 if (s2 > 0.0) {
-                    const double nrm = sqrt(fma(al, al, s2));
+                    const double x2 = fma(al, al, s2), rn = rsqrt(x2), nrm = x2 * rn, a = fabs(al);
                     beta = al >= 0.0 ? -nrm : nrm;
-                    tau = (beta - al) / beta;
-                    scal = 1.0 / (al - beta);
+                    tau = fma(a, rn, 1.0);
+                    scal = (al >= 0.0 ? 1.0 : -1.0) / (a + nrm);
                 }
                 bc[0] = tau; bc[1] = beta; bc[2] = scal; bc[3] = al;
                 taus[j] = tau;
@@ -426,7 +431,7 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
             break;
         }
         // pivot of step j + 1 (every warp finds the same), then that column takes reflector j and
-        // moves to position j + 1 (with its w, FP32 norm and index)
+        // moves to position j + 1; the old column j + 1 goes to position p
         int p = j + 1;
         if (piv) p = argmax_pivot(j + 1);
         for (int i = r0 + tid; i < r1; i += nt) {
@@ -437,17 +442,16 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
             A(i, j + 1) = xp;
         }
         __syncthreads();
-        if (tid == 0 && p != j + 1) {
-            const double t = wv[1]; wv[1] = wv[p - j]; wv[p - j] = t;
+        // reflector j on columns j + 2 .. s - 1 and step j + 1's partial sums in one pass (the
+        // column now at position p is the old column j + 1: it takes w of position j + 1)
+        double *rn = red[xch & 1];
+        fused_pass(j, p, ib, nc1 - 1, rn);
+        if (q == (j + 1) / rb)
+            for (int cc = tid; cc < nc1 - 1; cc += nt) rn[nc1 - 1 + cc] = A(j + 1, j + 1 + cc);
+        if (tid == 0 && p != j + 1) {                // FP32 norm and index follow the move
             const float f = nrmf[j + 1]; nrmf[j + 1] = nrmf[p]; nrmf[p] = f;
             const int u = permv[j + 1]; permv[j + 1] = permv[p]; permv[p] = u;
         }
-        __syncthreads();
-        // reflector j on columns j + 2 .. s - 1 and step j + 1's partial sums in one pass
-        double *rn = red[xch & 1];
-        fused_pass(j, ib, nc1 - 1, rn);
-        if (q == (j + 1) / rb)
-            for (int cc = tid; cc < nc1 - 1; cc += nt) rn[nc1 - 1 + cc] = A(j + 1, j + 1 + cc);
     }
     if (J.tau && q == 0)
         for (int j = tid; j < kmax; j += nt) J.tau[j] = taus[j];
