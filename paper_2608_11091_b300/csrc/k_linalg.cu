@@ -131,6 +131,10 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
         }
     __syncthreads();
     int xch = 0;   // exchanges so far (selects the buffer)
+    // threads of a pass: a short pass (at most 3200 elements: small unfoldings, the last steps)
+    // is bound by its combine and latency rather than the FP64 pipe, so it takes four warps (one
+    // per sub-partition) and leaves each column half as many partial sums to combine
+    auto pass_threads = [&](int T) { return T > 3200 ? nt : min(nt, 128); };
     // the column sums out[cc] from the partials in pp (slot thread + column, two halves); ends
     // with out[] visible to the CTA
     auto combine = [&](int T, int nrows, int E, int nc, double *out) {
@@ -167,8 +171,9 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
     auto flat_sums = [&](int ib, int nc, auto xy, double *out) {
         const int nrows = r1 - ib;
         const int T = nrows > 0 ? nrows * nc : 0;
-        const int E = T > 0 ? (((T + nt - 1) / nt) | 1) : 1;
-        const int e0 = min(T, tid * E), cnt = min(T, e0 + E) - e0;
+        const int na = pass_threads(T);
+        const int E = T > 0 ? (((T + na - 1) / na) | 1) : 1;
+        const int e0 = tid < na ? min(T, tid * E) : T, cnt = min(T, e0 + E) - e0;
         if (cnt > 0) {
             // two streams over the two halves of the range; stream A's partial of a column goes
             // to pp[2 (tid + cc)], stream B's to pp[2 (tid + cc) + 1] (both zeroed first: a column
@@ -239,8 +244,9 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
     auto fused_pass = [&](int j, int p, int ib, int nc, double *out) {
         const int nrows = r1 - ib;
         const int T = nrows > 0 ? nrows * nc : 0;
-        const int E = T > 0 ? (((T + nt - 1) / nt) | 1) : 1;
-        const int e0 = min(T, tid * E), cnt = min(T, e0 + E) - e0;
+        const int na = pass_threads(T);
+        const int E = T > 0 ? (((T + na - 1) / na) | 1) : 1;
+        const int e0 = tid < na ? min(T, tid * E) : T, cnt = min(T, e0 + E) - e0;
         const int c0 = j + 1;
         if (cnt > 0) {
             const int h = cnt >> 1;
