@@ -185,32 +185,49 @@ def test_adjoint_central_differences_n128(P):
     forward solve reaches a relative residual near 1e-8): the adjoint gradient of l = <w, x> along
     a core direction delta of b, <mu, [delta; U_b]> = <dl/dG_b, delta>, against central
     differences of the GPU forward solve (common random numbers), and the mixed form's gradient
-    against the FP64 one."""
+    against the FP64 one.  l is linear in b, so the exact central difference equals the exact
+    gradient at any step h; the computed ones differ only through the solves' errors, each at most
+    ||A^-1|| times its residual:
+        |grad - fd| <= ||w|| ||A^-1|| (|r+| + |r-|) / (2h) + ||delta_b|| ||A^-T|| |r_mu|,
+    with |r| the true residual norms (A symmetric here: ||A^-T|| = ||A^-1||)."""
     n = 128
-    wl = W.deblur3d(n, 0, None, lam=1.0)
+    lam = 1.0
+    wl = W.deblur3d(n, 0, None, lam=lam)
     prm = W.SolverParams('rhosvd', 48, 128, 5, 30, 1e-13, seed=0)
     dop = P.DeviceOperator(wl.op)
-    wq = to_dev(_unit_weight(n))
+    wq_np = _unit_weight(n)
+    wq = to_dev(wq_np)
     rng = np.random.default_rng(41)
     delta = rng.standard_normal(wl.b.core.shape)
     delta *= np.linalg.norm(wl.b.core) / np.linalg.norm(delta)
+    _, ainv_norm = _blur_eig_inverse(n, lam)
 
     def qoi(core):
-        x, _ = P.tk_solve(dop, to_dev(W.Tucker(core, wl.b.factors)), P.Options.from_params(prm))
-        return P.tk_inner(wq, x)
+        """l(b) and the absolute true residual norm of its forward solve"""
+        bt = W.Tucker(core, wl.b.factors)
+        bd = to_dev(bt)
+        x, _ = P.tk_solve(dop, bd, P.Options.from_params(prm))
+        return P.tk_inner(wq, x), P.tk_residual(dop, x, bd) * np.linalg.norm(OT.full(bt))
 
     grads = {}
+    rmu = {}
     for form in ["fp64", "mixed"]:
         x, _ = P.tk_solve(dop, to_dev(wl.b), P.Options.from_params(prm, precision=form))
         mu, _ = P.tk_solve(dop, wq, P.Options.from_params(prm, precision=form, transpose=True))
+        rmu[form] = P.tk_residual(dop, mu, wq, transpose=True) * np.linalg.norm(OT.full(wq_np))
         _, dG, _ = P.tk_adjoint_grads(dop, mu, x, to_dev(wl.b))
         grads[form] = float(np.sum(dG.cpu().numpy() * delta))
-    # l is linear in b, so a central difference has no truncation error of its own at any step:
-    # a large step keeps the forward solves' ~1e-8 error from being divided by a small one
+    # a large step keeps the forward solves' ~1e-8 errors from being divided by a small one
     h = 0.5
-    fd = (qoi(wl.b.core + h * delta) - qoi(wl.b.core - h * delta)) / (2 * h)
-    # the solves are accurate to ~1e-8 relative; a random direction's derivative is ~1e-3 of
-    # l itself, so both comparisons are made on the scale of l
-    scale = abs(qoi(wl.b.core))
-    assert abs(grads["fp64"] - fd) <= 1e-6 * scale
+    lp, rp = qoi(wl.b.core + h * delta)
+    lm, rm = qoi(wl.b.core - h * delta)
+    fd = (lp - lm) / (2 * h)
+    w_norm = np.linalg.norm(OT.full(wq_np))
+    d_norm = np.linalg.norm(OT.full(W.Tucker(delta, wl.b.factors)))
+    bound = w_norm * ainv_norm * (rp + rm) / (2 * h) + d_norm * ainv_norm * rmu["fp64"]
+    assert abs(grads["fp64"] - fd) <= bound
+    # the bound is not vacuous: it resolves the directional derivative to 0.2% of its size (a wrong
+    # contraction or sign would miss by O(1))
+    assert bound <= 2e-3 * abs(grads["fp64"])
+    scale = abs(qoi(wl.b.core)[0])
     assert abs(grads["mixed"] - grads["fp64"]) <= 1e-6 * scale
