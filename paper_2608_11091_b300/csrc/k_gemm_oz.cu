@@ -28,6 +28,7 @@
 // accumulator full / empty per set.  Every wait has an iteration limit: on expiry the kernel
 // records an error in g_oz_error and all roles stop issuing work; the CTA waits (bounded) for
 // its own copies and MMAs before freeing its tensor memory.
+#include <cooperative_groups.h>
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -196,6 +197,7 @@ constexpr int OZ_MAXPROB = 12;
 struct OzGroup {
     OzProb p[OZ_MAXPROB];
     int nprob;
+    int ks;                                           // K split: CTAs per tile (one cluster)
 };
 
 __device__ __forceinline__ uint32_t oz_smem(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -228,11 +230,17 @@ __global__ void __launch_bounds__(192, 1) k_gemm_oz(const __grid_constant__ OzGr
     __shared__ int fex[OZ_MAXCHUNK][OZ_BN];   // column exponents f_n per chunk
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // a tile's reduction is split over the g.ks CTAs of its cluster: rank r takes the chunks
+    // [r nchunk / ks, (r + 1) nchunk / ks) (possibly none) and the partial tiles are added in rank
+    // order at the end
+    const int ks = g.ks, tile_id = (int)blockIdx.x / ks, rank = (int)blockIdx.x % ks;
     int pi = 0;
-    while (pi + 1 < g.nprob && (int)blockIdx.x >= g.p[pi + 1].tile_begin) ++pi;
+    while (pi + 1 < g.nprob && tile_id >= g.p[pi + 1].tile_begin) ++pi;
     const OzProb &P = g.p[pi];
-    const int t = blockIdx.x - P.tile_begin;
+    const int t = tile_id - P.tile_begin;
     const int m0 = (t % P.tiles_m) * OZ_BM, n0 = (t / P.tiles_m) * OZ_BN;
+    const int c_lo = (rank * P.nchunk) / ks, c_hi = ((rank + 1) * P.nchunk) / ks;
+    const int k_lo = c_lo * OZ_SLABS, nk = max(0, min(c_hi * OZ_SLABS, P.nslab) - k_lo);
     const uint32_t base = (oz_smem(oz_dyn) + 1023u) & ~1023u;   // 1024-aligned stage ring
 
     if (warp == 0) {
@@ -265,9 +273,9 @@ __global__ void __launch_bounds__(192, 1) k_gemm_oz(const __grid_constant__ OzGr
     if (warp == 4) {
         // ---------------- TMA producer
         if (lane == 0) {
-            for (int k = 0; k < P.nslab; ++k) {
-                const int s = k % OZ_STAGES;
-                if (k >= OZ_STAGES && !oz_wait(oz_smem(&bar_empty[s]), ((k / OZ_STAGES) - 1) & 1)) {
+            for (int kl = 0; kl < nk; ++kl) {
+                const int s = kl % OZ_STAGES, k = k_lo + kl;
+                if (kl >= OZ_STAGES && !oz_wait(oz_smem(&bar_empty[s]), ((kl / OZ_STAGES) - 1) & 1)) {
                     stop_s = 1;
                     break;
                 }
@@ -284,7 +292,7 @@ __global__ void __launch_bounds__(192, 1) k_gemm_oz(const __grid_constant__ OzGr
                                    "r"(n0), "r"(p), "r"(fb)
                                  : "memory");
                 }
-                issued_slabs = k + 1;
+                issued_slabs = kl + 1;
             }
             // drain: wait (bounded) until every issued copy has landed before the CTA exits
             for (int k = max(0, issued_slabs - OZ_STAGES); k < issued_slabs; ++k)
@@ -296,20 +304,20 @@ __global__ void __launch_bounds__(192, 1) k_gemm_oz(const __grid_constant__ OzGr
             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
                                    ((uint32_t)(OZ_BM >> 4) << 24);
             bool ok = true;
-            for (int k = 0; k < P.nslab && ok; ++k) {
-                const int s = k % OZ_STAGES, c = k / OZ_SLABS, set = c & 1;
-                if (k % OZ_SLABS == 0 && c >= 2 && !oz_wait(oz_smem(&bar_acce[set]), ((c / 2) - 1) & 1)) ok = false;
-                if (ok && !oz_wait(oz_smem(&bar_full[s]), (k / OZ_STAGES) & 1)) ok = false;
+            for (int kl = 0; kl < nk && ok; ++kl) {
+                const int s = kl % OZ_STAGES, c = kl / OZ_SLABS, set = c & 1;   // c: local chunk
+                if (kl % OZ_SLABS == 0 && c >= 2 && !oz_wait(oz_smem(&bar_acce[set]), ((c / 2) - 1) & 1)) ok = false;
+                if (ok && !oz_wait(oz_smem(&bar_full[s]), (kl / OZ_STAGES) & 1)) ok = false;
                 if (!ok || *(volatile int *)&stop_s) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t st = base + s * OZ_STAGE;
-                for (int ks = 0; ks < OZ_BK / 16; ++ks)
+                for (int kk = 0; kk < OZ_BK / 16; ++kk)
                     for (int L = 0; L < OZ_L; ++L)
                         for (int p = 0; p <= L; ++p) {
                             const int q = L - p;
-                            const uint64_t da = oz_desc(st + p * OZ_A_TILE + ks * 32);
-                            const uint64_t db = oz_desc(st + OZ_S * OZ_A_TILE + q * OZ_B_TILE + ks * 32);
-                            const uint32_t acc = (k % OZ_SLABS == 0 && ks == 0 && p == 0) ? 0u : 1u;
+                            const uint64_t da = oz_desc(st + p * OZ_A_TILE + kk * 32);
+                            const uint64_t db = oz_desc(st + OZ_S * OZ_A_TILE + q * OZ_B_TILE + kk * 32);
+                            const uint32_t acc = (kl % OZ_SLABS == 0 && kk == 0 && p == 0) ? 0u : 1u;
                             const uint32_t d = taddr + set * OZ_SET_COLS + L * OZ_BN;
                             asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
                                          "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
@@ -317,16 +325,16 @@ __global__ void __launch_bounds__(192, 1) k_gemm_oz(const __grid_constant__ OzGr
                         }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                              ::"r"(oz_smem(&bar_empty[s])) : "memory");
-                if (k % OZ_SLABS == OZ_SLABS - 1 || k == P.nslab - 1)
+                if (kl % OZ_SLABS == OZ_SLABS - 1 || kl == nk - 1)
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                                  ::"r"(oz_smem(&bar_accf[set])) : "memory");
-                issued_slabs = k + 1;
+                issued_slabs = kl + 1;
             }
             if (!ok) stop_s = 1;
             // drain: the last commit tracks every MMA issued; wait (bounded) for it
             if (issued_slabs > 0) {
-                const int k = issued_slabs - 1;
-                oz_wait(oz_smem(&bar_empty[k % OZ_STAGES]), (k / OZ_STAGES) & 1);
+                const int kl = issued_slabs - 1;
+                oz_wait(oz_smem(&bar_empty[kl % OZ_STAGES]), (kl / OZ_STAGES) & 1);
             }
         }
     } else {
@@ -338,10 +346,10 @@ __global__ void __launch_bounds__(192, 1) k_gemm_oz(const __grid_constant__ OzGr
 #pragma unroll
         for (int j = 0; j < OZ_BN; ++j) acc[j] = 0.0;
         bool ok = true;
-        for (int c = 0; c < P.nchunk; ++c) {
-            const int set = c & 1;
+        for (int cl = 0; cl < c_hi - c_lo; ++cl) {
+            const int set = cl & 1, c = c_lo + cl;
             // warp-uniform outcome: the tensor-memory loads below are .sync.aligned
-            const bool arrived = __all_sync(0xffffffffu, oz_wait(oz_smem(&bar_accf[set]), (c / 2) & 1));
+            const bool arrived = __all_sync(0xffffffffu, oz_wait(oz_smem(&bar_accf[set]), (cl / 2) & 1));
             if (!arrived) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int em = P.expA[(long long)c * P.RpadA + m];
@@ -377,19 +385,46 @@ __global__ void __launch_bounds__(192, 1) k_gemm_oz(const __grid_constant__ OzGr
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(oz_smem(&bar_acce[set])) : "memory");
         }
         if (!ok) stop_s = 1;
-        // folded rows: m = i + a b  ->  C + i + ldc n + sC b
-        if (ok && m < P.M) {
-            const int i = m % P.a, b = m / P.a;
-            double *Cr = P.C + i + (long long)b * P.sC;
+        if (ks == 1) {
+            // folded rows: m = i + a b  ->  C + i + ldc n + sC b
+            if (ok && m < P.M) {
+                const int i = m % P.a, b = m / P.a;
+                double *Cr = P.C + i + (long long)b * P.sC;
 #pragma unroll
-            for (int j = 0; j < OZ_BN; ++j) {
-                const int n = n0 + j;
-                if (n < P.N) {
-                    double *cp = Cr + (long long)P.ldc * n;
-                    *cp = P.beta == 0.0 ? acc[j] : fma(P.beta, *cp, acc[j]);
+                for (int j = 0; j < OZ_BN; ++j) {
+                    const int n = n0 + j;
+                    if (n < P.N) {
+                        double *cp = Cr + (long long)P.ldc * n;
+                        *cp = P.beta == 0.0 ? acc[j] : fma(P.beta, *cp, acc[j]);
+                    }
                 }
             }
+        } else {
+            // the partial tile into the stage ring (every copy and MMA of this CTA has completed:
+            // the last chunk's accumulator barrier was observed above)
+            double *red = reinterpret_cast<double *>(oz_dyn + (base - oz_smem(oz_dyn)));
+#pragma unroll
+            for (int j = 0; j < OZ_BN; ++j) red[row * OZ_BN + j] = acc[j];
         }
+    }
+    if (ks > 1) {
+        // rank r adds rows [r BM / ks, (r + 1) BM / ks) of the ks partial tiles in rank order
+        namespace cg = cooperative_groups;
+        cg::cluster_group cl = cg::this_cluster();
+        cl.sync();
+        const double *red = reinterpret_cast<const double *>(oz_dyn + (base - oz_smem(oz_dyn)));
+        const int rlo = rank * OZ_BM / ks, rhi = (rank + 1) * OZ_BM / ks;
+        for (int e = tid; e < (rhi - rlo) * OZ_BN; e += blockDim.x) {
+            const int row = rlo + e / OZ_BN, j = e % OZ_BN, m = m0 + row, n = n0 + j;
+            double v = 0.0;
+            for (int r = 0; r < ks; ++r) v += cl.map_shared_rank(red, r)[row * OZ_BN + j];
+            if (!stop_s && m < P.M && n < P.N) {
+                const int i = m % P.a, b = m / P.a;
+                double *cp = P.C + i + (long long)b * P.sC + (long long)P.ldc * n;
+                *cp = P.beta == 0.0 ? v : fma(P.beta, *cp, v);
+            }
+        }
+        cl.sync();   // peers keep their partials until every rank has read them
     }
     __syncthreads();
     if (tid == 0 && stop_s) atomicExch(&g_oz_error, 1);
@@ -539,8 +574,27 @@ void gemm_oz(Ctx &c, const std::vector<GProb> &probs, const char *tag) {
             flops += 2.0 * p.M * (double)p.N * kt * p.batch;
             bytes += 8.0 * ((double)a.rows * kt + (double)p.N * kt + (p.beta != 0.0 ? 2.0 : 1.0) * a.rows * (double)p.N);
         }
+        // split the reduction over a cluster while the grid stays within one wave (one CTA per
+        // SM: the tile takes all of tensor memory) and every split gets at least one chunk
+        int maxch = 1;
+        for (int j = 0; j < G.nprob; ++j) maxch = std::max(maxch, G.p[j].nchunk);
+        int ks = 1;
+        while (ks < 8 && 2 * ks <= maxch && tiles * 2 * ks <= c.num_sms) ks *= 2;
+        G.ks = ks;
+        cudaLaunchConfig_t cfg{};
+        cudaLaunchAttribute attr[1];
+        cfg.gridDim = dim3((unsigned)(tiles * ks), 1, 1);
+        cfg.blockDim = dim3(192, 1, 1);
+        cfg.dynamicSmemBytes = OZ_SMEM;
+        cfg.stream = c.st;
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)ks;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
         c.pre_launch();
-        k_gemm_oz<<<(unsigned)tiles, 192, OZ_SMEM, c.st>>>(G);
+        TK_CUDA(cudaLaunchKernelEx(&cfg, k_gemm_oz, G));
         c.check_launch("gemm_tc", flops, bytes);   // one profiler entry for every tensor-core product
     }
 }
