@@ -155,28 +155,47 @@ __global__ void __launch_bounds__(256) k_oz_split(const __grid_constant__ OzSide
         }
     }
     __syncthreads();
+    // digits, two adjacent reduction indices per thread (one packed BF16 pair per plane).  With
+    // |X| <= 2^39 (a 53-bit significand shifted right by at least 14) the balanced digits of |X|
+    // come from its bytes with a carry: byte u (plus the carry) >= 128 becomes u - 256 and carries
+    // 1; the sign then applies to every digit (|d| <= 128 either way, so products stay <= 2^14)
     const long long plane = (long long)D.Rpad * D.Kpad;
-    for (int e = tid; e < 32 * W; e += 256) {
-        const int r = e / W, kk = e % W;
-        const long long bits = t(r, kk);
-        const int ef = (int)((bits >> 52) & 0x7FF);
-        long long X = 0;
+    auto digits = [&](long long bits, int ew, int (&d)[OZ_S]) {
+        const int ef = (int)((unsigned long long)bits >> 52) & 0x7FF;
+        unsigned lo = 0u, hi = 0u;
         if (ef > 0) {
             // |v| 2^(39 - e) = m 2^(ef - 1075 + 39 - e) with m the significand, e = E - 1022:
             // a right shift by E + 14 - ef >= 14 with rounding to nearest
-            const long long m = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
-            const int sh = er[r] + 14 - ef;
-            if (sh < 63) X = (m + (1LL << (sh - 1))) >> sh;
-            if (bits < 0) X = -X;
+            const unsigned long long m = ((unsigned long long)bits & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+            const int sh = ew + 14 - ef;
+            if (sh < 63) {
+                const unsigned long long X = (m + (1ULL << (sh - 1))) >> sh;
+                lo = (unsigned)X;
+                hi = (unsigned)(X >> 32);
+            }
         }
-        __nv_bfloat16 *dst = D.planes + (long long)(r0 + r) * D.Kpad + k0 + kk;
+        int c = 0;
 #pragma unroll
         for (int p = OZ_S - 1; p >= 1; --p) {
-            const int d = (int)(((X + 128) & 255) - 128);       // balanced digit in [-128, 127]
-            dst[p * plane] = __float2bfloat16_rn((float)d);
-            X = (X - d) >> 8;                                    // exact: X - d = 0 mod 256
+            const int u = (int)((lo >> (8 * (OZ_S - 1 - p))) & 255u) + c;
+            c = u >= 128;
+            d[p] = u - (c << 8);
         }
-        dst[0] = __float2bfloat16_rn((float)(int)X);            // |d_0| <= 128
+        d[0] = (int)hi + c;
+        if (bits < 0)
+#pragma unroll
+            for (int p = 0; p < OZ_S; ++p) d[p] = -d[p];
+    };
+    const int Wh = W >> 1;
+    for (int e = tid; e < 32 * Wh; e += 256) {
+        const int r = e / Wh, kk = 2 * (e % Wh);
+        int da[OZ_S], db[OZ_S];
+        digits(t(r, kk), er[r], da);
+        digits(t(r, kk + 1), er[r], db);
+        __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(D.planes + (long long)(r0 + r) * D.Kpad + k0 + kk);
+#pragma unroll
+        for (int p = 0; p < OZ_S; ++p)
+            dst[(p * plane) >> 1] = __floats2bfloat162_rn((float)da[p], (float)db[p]);
     }
 }
 
