@@ -117,9 +117,8 @@ __global__ void __launch_bounds__(256) k_oz_split(const __grid_constant__ OzSide
     }
     if (tid < D.nseg) segscale[tid] = D.seg[tid].coef * (D.seg[tid].cd ? *D.seg[tid].cd : 1.0);
     __syncthreads();
-    for (int e = tid; e < 32 * W; e += 256) {
-        int r, kk;
-        if (D.trans) { kk = e % W; r = e / W; } else { r = e % 32; kk = e / 32; }
+    const int warp = tid >> 5, lane = tid & 31;
+    auto load = [&](int r, int kk) {
         const int m = r0 + r, k = k0 + kk;
         double v = 0.0;
         if (m < D.rows) {
@@ -136,10 +135,19 @@ __global__ void __launch_bounds__(256) k_oz_split(const __grid_constant__ OzSide
             }
         }
         t(r, kk) = __double_as_longlong(v);
+    };
+    // coalesced: a warp walks a row along the reduction index (transposed storage) or the 32
+    // rows of one reduction index (rows contiguous)
+    if (D.trans) {
+        for (int r = warp; r < 32; r += 8)
+#pragma unroll 4
+            for (int kk = lane; kk < W; kk += 32) load(r, kk);
+    } else {
+#pragma unroll 4
+        for (int kk = warp; kk < W; kk += 8) load(lane, kk);
     }
     __syncthreads();
     {
-        const int warp = tid >> 5, lane = tid & 31;
         // er[] now takes the exponents: every read of it as a row index happened before the barrier
         for (int r = warp; r < 32; r += 8) {
             int ef = 0;
@@ -503,6 +511,33 @@ static std::string oz_key(const OzSide &S) {
     return std::string(reinterpret_cast<const char *>(&k), sizeof(OzSide));
 }
 
+// clusters of `size` CTAs of k_gemm_oz that can be resident at once on this device (queried
+// once per device and size; 0 when the query fails, which keeps the reduction unsplit)
+static int oz_resident_clusters(const Ctx &c, cudaLaunchConfig_t cfg, int size) {
+    constexpr int MAXDEV = 64;
+    static std::atomic<int> cache[MAXDEV][4];        // sizes 1, 2, 4, 8; 0 = not yet queried
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) return 0;
+    const int slot = size == 1 ? 0 : size == 2 ? 1 : size == 4 ? 2 : 3;
+    int v = cache[dev][slot].load();
+    if (v != 0) return v > 0 ? v : 0;
+    cudaLaunchAttribute a[1];
+    a[0].id = cudaLaunchAttributeClusterDimension;
+    a[0].val.clusterDim.x = (unsigned)size;
+    a[0].val.clusterDim.y = 1;
+    a[0].val.clusterDim.z = 1;
+    cfg.attrs = a;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3((unsigned)(size * c.num_sms), 1, 1);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, (const void *)k_gemm_oz, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
+    }
+    cache[dev][slot].store(n > 0 ? n : -1);
+    return n > 0 ? n : 0;
+}
+
 void gemm_oz(Ctx &c, const std::vector<GProb> &probs, const char *tag) {
     (void)tag;
     if (probs.empty()) return;
@@ -593,25 +628,27 @@ void gemm_oz(Ctx &c, const std::vector<GProb> &probs, const char *tag) {
             flops += 2.0 * p.M * (double)p.N * kt * p.batch;
             bytes += 8.0 * ((double)a.rows * kt + (double)p.N * kt + (p.beta != 0.0 ? 2.0 : 1.0) * a.rows * (double)p.N);
         }
-        // split the reduction over a cluster while the grid stays within one wave (one CTA per
-        // SM: the tile takes all of tensor memory) and every split gets at least one chunk
+        // split the reduction over a cluster while the grid stays within one wave and every
+        // split gets at least one chunk.  One CTA per SM (the tile takes all of tensor memory)
+        // and a cluster's CTAs on one GPC: the clusters of a size that fit at once are fewer
+        // than SMs / size (36 clusters of 4 ran as two waves, each SM busy half the launch)
         int maxch = 1;
         for (int j = 0; j < G.nprob; ++j) maxch = std::max(maxch, G.p[j].nchunk);
-        int ks = 1;
-        while (ks < 8 && 2 * ks <= maxch && tiles * 2 * ks <= c.num_sms) ks *= 2;
-        G.ks = ks;
         cudaLaunchConfig_t cfg{};
         cudaLaunchAttribute attr[1];
-        cfg.gridDim = dim3((unsigned)(tiles * ks), 1, 1);
         cfg.blockDim = dim3(192, 1, 1);
         cfg.dynamicSmemBytes = OZ_SMEM;
         cfg.stream = c.st;
         attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = (unsigned)ks;
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
+        int ks = 1;
+        while (ks < 8 && 2 * ks <= maxch && tiles <= oz_resident_clusters(c, cfg, 2 * ks)) ks *= 2;
+        G.ks = ks;
+        cfg.gridDim = dim3((unsigned)(tiles * ks), 1, 1);
+        attr[0].val.clusterDim.x = (unsigned)ks;
         c.pre_launch();
         TK_CUDA(cudaLaunchKernelEx(&cfg, k_gemm_oz, G));
         c.check_launch("gemm_tc", flops, bytes);   // one profiler entry for every tensor-core product
