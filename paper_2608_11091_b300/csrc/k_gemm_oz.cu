@@ -59,6 +59,8 @@ constexpr int OZ_STAGES = 2;
 constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE + 1024;  // + alignment slack
 constexpr int OZ_TMEM_COLS = 512;                     // 2 sets x 5 levels x 32 columns
 constexpr int OZ_SET_COLS = OZ_L * OZ_BN;
+constexpr int OZ_EPI_THREADS = 256;                   // warps 0-7: epilogue (TMEM lane quarter, column half)
+constexpr int OZ_THREADS = OZ_EPI_THREADS + 64;       // warp 8: TMA producer, warp 9: MMA issuer
 constexpr long OZ_SPIN = 1L << 20;                    // bounded waits
 
 // ------------------------------------------------------------------------------------------
@@ -239,6 +241,25 @@ __device__ __forceinline__ bool oz_wait(uint32_t bar, uint32_t parity) {
     return false;
 }
 
+// RN(x) 2^ex for an integer |x| < 2^62, built with integer operations (the FP64 pipe is slow on
+// this part): the same value as RN((double)x) * 2^ex, which is exact, whenever the result is a
+// normal number; outside that range the library path (never inlined, so the common path stays
+// branch-free)
+__device__ __noinline__ double oz_scaled_slow(long long x, int ex) { return ldexp((double)x, ex); }
+__device__ __forceinline__ double oz_scaled(long long x, int ex) {
+    if (x == 0) return 0.0;
+    const unsigned long long sgn = (unsigned long long)x & (1ULL << 63);
+    const unsigned long long u = x < 0 ? 0ULL - (unsigned long long)x : (unsigned long long)x;
+    const int lz = __clzll((long long)u);
+    const int E = 63 - lz + ex + 1023;                  // biased exponent of the leading bit
+    if (E < 1 || E > 2045) return oz_scaled_slow(x, ex);
+    const unsigned long long t = u << lz;                // leading bit at 63
+    const unsigned long long hi = t >> 11, rem = t & 0x7FFULL;
+    // to nearest, ties to even; a carry to 2^53 moves into the exponent field below
+    const unsigned long long mnt = hi + ((rem + 0x3FFULL + (hi & 1ULL)) >> 11);
+    return __longlong_as_double((long long)(sgn | (((unsigned long long)(E - 1) << 52) + mnt)));
+}
+
 // K-major operand tile in shared memory with 128-byte swizzle (8 rows x 128 B atoms)
 __device__ __forceinline__ uint64_t oz_desc(uint32_t saddr) {
     uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
@@ -249,7 +270,7 @@ __device__ __forceinline__ uint64_t oz_desc(uint32_t saddr) {
     return d;
 }
 
-__global__ void __launch_bounds__(192, 1) k_gemm_oz(const __grid_constant__ OzGroup g) {
+__global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const __grid_constant__ OzGroup g) {
     extern __shared__ unsigned char oz_dyn[];
     __shared__ __align__(8) uint64_t bar_full[OZ_STAGES], bar_empty[OZ_STAGES], bar_accf[2], bar_acce[2];
     __shared__ uint32_t taddr_s;
@@ -264,6 +285,13 @@ __global__ void __launch_bounds__(192, 1) k_gemm_oz(const __grid_constant__ OzGr
     int pi = 0;
     while (pi + 1 < g.nprob && tile_id >= g.p[pi + 1].tile_begin) ++pi;
     const OzProb &P = g.p[pi];
+    // the output's parameters in registers: P lives in parameter space behind a dynamic index,
+    // and a load through it could otherwise be repeated after every store to C
+    double *const Cout = P.C;
+    const double beta = P.beta;
+    const long long sC = P.sC;
+    const int Mout = P.M, Nout = P.N, afold = P.a, ldc = P.ldc, RpadA = P.RpadA;
+    const short *const expA = P.expA;
     const int t = tile_id - P.tile_begin;
     const int m0 = (t % P.tiles_m) * OZ_BM, n0 = (t / P.tiles_m) * OZ_BN;
     const int c_lo = (rank * P.nchunk) / ks, c_hi = ((rank + 1) * P.nchunk) / ks;
@@ -282,7 +310,7 @@ __global__ void __launch_bounds__(192, 1) k_gemm_oz(const __grid_constant__ OzGr
         }
         for (int s = 0; s < 2; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(oz_smem(&bar_accf[s])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(oz_smem(&bar_acce[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(oz_smem(&bar_acce[s])), "r"(OZ_EPI_THREADS));
         }
         stop_s = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -297,7 +325,15 @@ __global__ void __launch_bounds__(192, 1) k_gemm_oz(const __grid_constant__ OzGr
     const uint32_t taddr = taddr_s;
     int issued_slabs = 0;       // producer / MMA progress, for the bounded drain at exit
 
-    if (warp == 4) {
+    // epilogue role (warps 0-7): one output row and 16 columns per thread (a warp reads the TMEM
+    // lanes of its quarter, warp & 3, and the column half warp >> 2)
+    constexpr int NH = OZ_BN / 2;
+    const int q4 = warp & 3, h = (warp >> 2) & 1;
+    const int row = q4 * 32 + lane, m = m0 + row;
+    double acc[NH];
+#pragma unroll
+    for (int j = 0; j < NH; ++j) acc[j] = 0.0;
+    if (warp == 8) {
         // ---------------- TMA producer
         if (lane == 0) {
             for (int kl = 0; kl < nk; ++kl) {
@@ -325,11 +361,18 @@ __global__ void __launch_bounds__(192, 1) k_gemm_oz(const __grid_constant__ OzGr
             for (int k = max(0, issued_slabs - OZ_STAGES); k < issued_slabs; ++k)
                 oz_wait(oz_smem(&bar_full[k % OZ_STAGES]), (k / OZ_STAGES) & 1);
         }
-    } else if (warp == 5) {
-        // ---------------- MMA issuer
+    } else if (warp == 9) {
+        // ---------------- MMA issuer.  One MMA per A digit plane p and 16-wide K step: B's planes
+        // q = 0..4-p lie one after another in shared memory (32 rows each, the same 1024-byte
+        // row-group stride), so together they are one operand of N = 32 (5 - p) rows, and with D
+        // starting at level p's columns the product block of plane q lands on level p + q.  Five
+        // wide MMAs instead of fifteen of N = 32 (a small MMA costs its issue, not its math)
         if (lane == 0) {
-            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
-                                   ((uint32_t)(OZ_BM >> 4) << 24);
+            uint32_t idesc[OZ_S];
+#pragma unroll
+            for (int p = 0; p < OZ_S; ++p)
+                idesc[p] = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((OZ_BN * (OZ_S - p)) >> 3) << 17) |
+                           ((uint32_t)(OZ_BM >> 4) << 24);
             bool ok = true;
             for (int kl = 0; kl < nk && ok; ++kl) {
                 const int s = kl % OZ_STAGES, c = kl / OZ_SLABS, set = c & 1;   // c: local chunk
@@ -338,18 +381,24 @@ __global__ void __launch_bounds__(192, 1) k_gemm_oz(const __grid_constant__ OzGr
                 if (!ok || *(volatile int *)&stop_s) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t st = base + s * OZ_STAGE;
+                // descriptors of the stage's first A and B tiles; every other operand is a
+                // constant byte offset from them, added to the start-address field (address >> 4,
+                // 14 bits: shared addresses stay below 256 KB, so the field cannot carry)
+                const uint64_t dA0 = oz_desc(st), dB0 = oz_desc(st + OZ_S * OZ_A_TILE);
+                const uint32_t d0 = taddr + set * OZ_SET_COLS;
+                const uint32_t first = (kl % OZ_SLABS == 0) ? 1u : 0u;   // first slab of a chunk
+#pragma unroll
                 for (int kk = 0; kk < OZ_BK / 16; ++kk)
-                    for (int L = 0; L < OZ_L; ++L)
-                        for (int p = 0; p <= L; ++p) {
-                            const int q = L - p;
-                            const uint64_t da = oz_desc(st + p * OZ_A_TILE + kk * 32);
-                            const uint64_t db = oz_desc(st + OZ_S * OZ_A_TILE + q * OZ_B_TILE + kk * 32);
-                            const uint32_t acc = (kl % OZ_SLABS == 0 && kk == 0 && p == 0) ? 0u : 1u;
-                            const uint32_t d = taddr + set * OZ_SET_COLS + L * OZ_BN;
-                            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
-                                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                                         ::"r"(d), "l"(da), "l"(db), "r"(idesc), "r"(acc));
-                        }
+#pragma unroll
+                    for (int p = 0; p < OZ_S; ++p) {
+                        const uint64_t da = dA0 + (uint64_t)((p * OZ_A_TILE + kk * 32) >> 4);
+                        const uint64_t db = dB0 + (uint64_t)((kk * 32) >> 4);
+                        // the first MMA of a chunk (p = 0 covers every level) overwrites
+                        const uint32_t acc = (kk == 0 && p == 0) ? (first ^ 1u) : 1u;
+                        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                                     ::"r"(d0 + (uint32_t)(p * OZ_BN)), "l"(da), "l"(db), "r"(idesc[p]), "r"(acc));
+                    }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                              ::"r"(oz_smem(&bar_empty[s])) : "memory");
                 if (kl % OZ_SLABS == OZ_SLABS - 1 || kl == nk - 1)
@@ -365,13 +414,9 @@ __global__ void __launch_bounds__(192, 1) k_gemm_oz(const __grid_constant__ OzGr
             }
         }
     } else {
-        // ---------------- epilogue: warps 0-3, one output row per thread.  The levels of a
-        // chunk combine exactly in 64-bit integers (S_L integer, |S_L| < 2^24: sum_L S_L 2^(8(4-L))
-        // < 2^59), so only one conversion and one FMA per output and chunk use the FP64 pipe
-        const int row = warp * 32 + lane, m = m0 + row;
-        double acc[OZ_BN];
-#pragma unroll
-        for (int j = 0; j < OZ_BN; ++j) acc[j] = 0.0;
+        // ---------------- epilogue.  The levels of a chunk combine exactly in 64-bit integers
+        // (S_L integer, |S_L| < 2^24: sum_L S_L 2^(8(4-L)) < 2^59); the chunk value is formed
+        // with integer operations
         bool ok = true;
         for (int cl = 0; cl < c_hi - c_lo; ++cl) {
             const int set = cl & 1, c = c_lo + cl;
@@ -379,79 +424,85 @@ __global__ void __launch_bounds__(192, 1) k_gemm_oz(const __grid_constant__ OzGr
             const bool arrived = __all_sync(0xffffffffu, oz_wait(oz_smem(&bar_accf[set]), (cl / 2) & 1));
             if (!arrived) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int em = P.expA[(long long)c * P.RpadA + m];
+            const int em = expA[(long long)c * RpadA + m];
+            // the five level loads issued together, one wait
+            uint32_t r[OZ_L][NH];
 #pragma unroll
-            for (int h = 0; h < OZ_BN / 16; ++h) {           // 16 columns at a time: fewer live registers
-                long long ai[16];
-#pragma unroll
-                for (int j = 0; j < 16; ++j) ai[j] = 0;
-#pragma unroll
-                for (int L = 0; L < OZ_L; ++L) {
-                    uint32_t r[16];
-                    const uint32_t a = taddr + ((uint32_t)(warp * 32) << 16) + set * OZ_SET_COLS + L * OZ_BN + h * 16;
-                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                                   "=r"(r[14]), "=r"(r[15])
-                                 : "r"(a));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        ai[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << (8 * (OZ_L - 1 - L));
-                }
-                // chunk value: 2^(e_m + f_n) 2^-32 ai, with the final 2^-14: scale 2^(e_m + f_n - 46)
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int ex = em + fex[c][h * 16 + j] - 46;
-                    const double sc = (ex > -1022 && ex < 1024) ? __longlong_as_double((long long)(ex + 1023) << 52)
-                                                                : ldexp(1.0, ex);
-                    acc[h * 16 + j] = fma(sc, (double)ai[j], acc[h * 16 + j]);
-                }
+            for (int L = 0; L < OZ_L; ++L) {
+                const uint32_t a = taddr + ((uint32_t)(q4 * 32) << 16) + set * OZ_SET_COLS + L * OZ_BN + h * NH;
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                             : "=r"(r[L][0]), "=r"(r[L][1]), "=r"(r[L][2]), "=r"(r[L][3]), "=r"(r[L][4]), "=r"(r[L][5]),
+                               "=r"(r[L][6]), "=r"(r[L][7]), "=r"(r[L][8]), "=r"(r[L][9]), "=r"(r[L][10]), "=r"(r[L][11]),
+                               "=r"(r[L][12]), "=r"(r[L][13]), "=r"(r[L][14]), "=r"(r[L][15])
+                             : "r"(a));
             }
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(oz_smem(&bar_acce[set])) : "memory");
+#pragma unroll
+            for (int j = 0; j < NH; ++j) {
+                long long ai = 0;
+#pragma unroll
+                for (int L = 0; L < OZ_L; ++L)
+                    ai += (long long)__float2int_rn(__uint_as_float(r[L][j])) << (8 * (OZ_L - 1 - L));
+                // chunk value 2^(e_m + f_n) 2^-32 ai with the final 2^-14: 2^(e_m + f_n - 46) ai; the
+                // first chunk of the CTA is its value, later ones one FP64 addition
+                const double v = oz_scaled(ai, em + fex[c][h * NH + j] - 46);
+                acc[j] = cl == 0 ? v : acc[j] + v;
+            }
         }
         if (!ok) stop_s = 1;
         if (ks == 1) {
-            // folded rows: m = i + a b  ->  C + i + ldc n + sC b
-            if (ok && m < P.M) {
-                const int i = m % P.a, b = m / P.a;
-                double *Cr = P.C + i + (long long)b * P.sC;
+            // folded rows: m = i + a b  ->  C + i + ldc n + sC b; a warp stores 32 consecutive
+            // rows of a column.  With beta != 0 every old value is loaded before the first store,
+            // so the loads are in flight together
+            if (ok && m < Mout) {
+                const int i = m % afold, b = m / afold;
+                double *Cr = Cout + i + (long long)b * sC + (long long)ldc * (n0 + h * NH);
+                const int nn = min(NH, Nout - n0 - h * NH);
+                if (beta != 0.0) {
 #pragma unroll
-                for (int j = 0; j < OZ_BN; ++j) {
-                    const int n = n0 + j;
-                    if (n < P.N) {
-                        double *cp = Cr + (long long)P.ldc * n;
-                        *cp = P.beta == 0.0 ? acc[j] : fma(P.beta, *cp, acc[j]);
-                    }
+                    for (int j = 0; j < NH; ++j)
+                        if (j < nn) acc[j] = fma(beta, Cr[(long long)ldc * j], acc[j]);
                 }
-            }
-        } else {
-            // the partial tile into the stage ring (every copy and MMA of this CTA has completed:
-            // the last chunk's accumulator barrier was observed above)
-            double *red = reinterpret_cast<double *>(oz_dyn + (base - oz_smem(oz_dyn)));
 #pragma unroll
-            for (int j = 0; j < OZ_BN; ++j) red[row * OZ_BN + j] = acc[j];
+                for (int j = 0; j < NH; ++j)
+                    if (j < nn) Cr[(long long)ldc * j] = acc[j];
+            }
         }
     }
     if (ks > 1) {
-        // rank r adds rows [r BM / ks, (r + 1) BM / ks) of the ks partial tiles in rank order
+        // split reduction: rank o adds rows [o nr, (o + 1) nr), nr = BM / ks.  Each rank pushes
+        // the partial rows into the stage ring of the rank that adds them (remote stores do not
+        // wait), slot `rank` of a [ks][BN][nr] buffer; the owner then adds its ks slots in rank
+        // order from its own shared memory
         namespace cg = cooperative_groups;
         cg::cluster_group cl = cg::this_cluster();
-        cl.sync();
-        const double *red = reinterpret_cast<const double *>(oz_dyn + (base - oz_smem(oz_dyn)));
-        const int rlo = rank * OZ_BM / ks, rhi = (rank + 1) * OZ_BM / ks;
-        for (int e = tid; e < (rhi - rlo) * OZ_BN; e += blockDim.x) {
-            const int row = rlo + e / OZ_BN, j = e % OZ_BN, m = m0 + row, n = n0 + j;
-            double v = 0.0;
-            for (int r = 0; r < ks; ++r) v += cl.map_shared_rank(red, r)[row * OZ_BN + j];
-            if (!stop_s && m < P.M && n < P.N) {
-                const int i = m % P.a, b = m / P.a;
-                double *cp = P.C + i + (long long)b * P.sC + (long long)P.ldc * n;
-                *cp = P.beta == 0.0 ? v : fma(P.beta, *cp, v);
+        const int nr = OZ_BM / ks;
+        cl.sync();                        // every rank is past its main loop: the rings are free
+        if (warp < 8) {
+            const int o = row / nr, lr = row - o * nr;
+#pragma unroll
+            for (int j = 0; j < NH; ++j) {
+                const uint32_t off = (uint32_t)(((rank * OZ_BN + h * NH + j) * nr + lr) * 8);
+                uint32_t ra;
+                asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(base + off), "r"(o));
+                asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(ra), "d"(acc[j]) : "memory");
             }
         }
-        cl.sync();   // peers keep their partials until every rank has read them
+        cl.sync();                        // every partial has arrived
+        const double *buf = reinterpret_cast<const double *>(oz_dyn + (base - oz_smem(oz_dyn)));
+        const bool live = !*(volatile int *)&stop_s;
+        for (int e = tid; e < nr * OZ_BN; e += OZ_THREADS) {
+            const int lr = e % nr, j = e / nr, mm = m0 + rank * nr + lr, n = n0 + j;
+            double v = buf[j * nr + lr];
+            for (int r = 1; r < ks; ++r) v += buf[(r * OZ_BN + j) * nr + lr];
+            if (live && mm < Mout && n < Nout) {
+                const int i = mm % afold, b = mm / afold;
+                double *cp = Cout + i + (long long)b * sC + (long long)ldc * n;
+                *cp = beta == 0.0 ? v : fma(beta, *cp, v);
+            }
+        }
     }
     __syncthreads();
     if (tid == 0 && stop_s) atomicExch(&g_oz_error, 1);
@@ -636,7 +687,7 @@ void gemm_oz(Ctx &c, const std::vector<GProb> &probs, const char *tag) {
         for (int j = 0; j < G.nprob; ++j) maxch = std::max(maxch, G.p[j].nchunk);
         cudaLaunchConfig_t cfg{};
         cudaLaunchAttribute attr[1];
-        cfg.blockDim = dim3(192, 1, 1);
+        cfg.blockDim = dim3(OZ_THREADS, 1, 1);
         cfg.dynamicSmemBytes = OZ_SMEM;
         cfg.stream = c.st;
         attr[0].id = cudaLaunchAttributeClusterDimension;
