@@ -685,7 +685,11 @@ struct SVDJobs {
     SVDJob j[TK_MAX_D];
     double *pinv[TK_MAX_D];   // optional s x s pseudo-inverse outputs
     double rcond;
+    float2 *rlog[TK_MAX_D];   // k_svd_cl: rotation log of the FP32 sweeps (SVD_LOG_SWEEPS sweeps)
+    unsigned long long *prog[TK_MAX_D];   // k_svd_cl: progress word of the FP32 phase
+    unsigned long long tag;               // k_svd_cl: this launch's id << 32
 };
+constexpr int SVD_LOG_SWEEPS = 20;
 
 // Sweep counts of the last k_svd launch (per block: FP32 phase, FP64 phase); diagnostics.
 __device__ int g_svd_sweeps[2 * TK_MAX_D];
@@ -760,6 +764,10 @@ __device__ __forceinline__ void rr_pair(int round, int pr, int sp, int &p, int &
 // checked after every sweep on the full Gram matrix A^T A (one dot product per thread), which
 // replaces a final rotation-free sweep.  Column squared norms are kept in `nrm2` (Rutishauser's
 // updates inside a sweep, exact from the Gram check between sweeps).  Returns the number of sweeps.
+// LOG: V is not touched; the rotation of every live pair of every round is written to `rlog`
+// instead, (cos, sin) as a float2 at [(sweep (s' - 1) + round) np + pair] ((1, 0) when the pair is
+// not rotated), for replay_rotations (the round is bound by moving columns through shared
+// memory, and V's columns are half of that traffic).
 constexpr int J32R = 5;
 __device__ __forceinline__ float dot_rows(const float *x, const float *y, int s) {
     float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
@@ -773,9 +781,18 @@ __device__ __forceinline__ float dot_rows(const float *x, const float *y, int s)
     for (; i < s; ++i) t0 = fmaf(x[i], y[i], t0);
     return (t0 + t1) + (t2 + t3);
 }
-template <int G>
+// Progress word of a logged FP32 phase (global memory): tag (the launch's id << 32) | sweeps
+// logged | SVD_PROG_DONE once the phase has ended; written with release semantics after the
+// block's barrier, so every log entry of the announced sweeps is visible to a reader that
+// acquires it.
+constexpr unsigned long long SVD_PROG_DONE = 1ULL << 16;
+__device__ __forceinline__ void svd_publish(unsigned long long *prog, unsigned long long v) {
+    __threadfence();
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(prog), "l"(v) : "memory");
+}
+template <int G, bool LOG>
 __device__ int jacobi32_g(float *A, float *V, float *nrm2, int s, float tol, float floor2, int max_sweeps,
-                          int *flag) {
+                          int *flag, float2 *rlog, unsigned long long *prog, unsigned long long tag) {
     constexpr int PPW = 32 / G;                      // pairs per warp
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5, nt = blockDim.x;
     const int gl = lane & (G - 1), slot = lane / G;
@@ -822,8 +839,10 @@ __device__ int jacobi32_g(float *A, float *V, float *nrm2, int s, float tol, flo
                         if (live && i < s) {
                             a[k] = A[i + p * s];
                             b[k] = A[i + q * s];
-                            va[k] = V[i + p * s];
-                            vb[k] = V[i + q * s];
+                            if (!LOG) {
+                                va[k] = V[i + p * s];
+                                vb[k] = V[i + q * s];
+                            }
                         }
                     }
                     const float al = live ? nrm2[p] : 0.f, be = live ? nrm2[q] : 0.f;
@@ -832,23 +851,30 @@ __device__ int jacobi32_g(float *A, float *V, float *nrm2, int s, float tol, flo
                     for (int k = 0; k < J32R; ++k) ga = fmaf(a[k], b[k], ga);
 #pragma unroll
                     for (int o = G / 2; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
-                    if (!live || al <= floor2 || be <= floor2) continue;
+                    if (!live) continue;
+                    float2 *lg = LOG ? rlog + ((size_t)(sweeps - 1) * (sp - 1) + round) * np + pr : nullptr;
                     // norms above floor2 = 2^-100 or a positive fraction of ||A||_F^2: normal
                     // numbers, so x * rsqrt(x) is a safe square root
-                    if (!(fabsf(ga) > tol * (al * rsqrtf(al)) * (be * rsqrtf(be)))) continue;
+                    if (al <= floor2 || be <= floor2 || !(fabsf(ga) > tol * (al * rsqrtf(al)) * (be * rsqrtf(be)))) {
+                        if (LOG && gl == 0) *lg = make_float2(1.f, 0.f);
+                        continue;
+                    }
                     const float zeta = __fdividef(be - al, 2.f * ga);
                     const float az = fabsf(zeta), z1 = fmaf(zeta, zeta, 1.f);
                     const float t = az < 1e18f ? __fdividef(copysignf(1.f, zeta), az + z1 * rsqrtf(z1))
                                                : __fdividef(0.5f, zeta);
                     const float cs = rsqrtf(fmaf(t, t, 1.f)), sn = cs * t;
+                    if (LOG && gl == 0) *lg = make_float2(cs, sn);
 #pragma unroll
                     for (int k = 0; k < J32R; ++k) {
                         const int i = gl + G * k;
                         if (i < s) {
                             A[i + p * s] = cs * a[k] - sn * b[k];
                             A[i + q * s] = sn * a[k] + cs * b[k];
-                            V[i + p * s] = cs * va[k] - sn * vb[k];
-                            V[i + q * s] = sn * va[k] + cs * vb[k];
+                            if (!LOG) {
+                                V[i + p * s] = cs * va[k] - sn * vb[k];
+                                V[i + q * s] = sn * va[k] + cs * vb[k];
+                            }
                         }
                     }
                     if (gl == 0) {
@@ -860,16 +886,99 @@ __device__ int jacobi32_g(float *A, float *V, float *nrm2, int s, float tol, flo
             }
         }
         __syncthreads();
+        // this sweep's log is complete (the barrier above): announce it
+        if (LOG && tid == 0) svd_publish(prog, tag | (unsigned long long)sweeps);
     }
+    if (LOG && tid == 0) svd_publish(prog, tag | (unsigned long long)sweeps | SVD_PROG_DONE);
     return sweeps;
 }
 // s <= G J32R rows per group; SVD_MAXS = 96 needs G = 32 at most
+template <bool LOG>
 __device__ int jacobi32(float *A, float *V, float *nrm2, int s, float tol, float floor2, int max_sweeps,
-                        int *flag) {
-    if (s <= 4 * J32R) return jacobi32_g<4>(A, V, nrm2, s, tol, floor2, max_sweeps, flag);
-    if (s <= 8 * J32R) return jacobi32_g<8>(A, V, nrm2, s, tol, floor2, max_sweeps, flag);
-    if (s <= 16 * J32R) return jacobi32_g<16>(A, V, nrm2, s, tol, floor2, max_sweeps, flag);
-    return jacobi32_g<32>(A, V, nrm2, s, tol, floor2, max_sweeps, flag);
+                        int *flag, float2 *rlog = nullptr, unsigned long long *prog = nullptr,
+                        unsigned long long tag = 0) {
+    if (s <= 4 * J32R) return jacobi32_g<4, LOG>(A, V, nrm2, s, tol, floor2, max_sweeps, flag, rlog, prog, tag);
+    if (s <= 8 * J32R) return jacobi32_g<8, LOG>(A, V, nrm2, s, tol, floor2, max_sweeps, flag, rlog, prog, tag);
+    if (s <= 16 * J32R) return jacobi32_g<16, LOG>(A, V, nrm2, s, tol, floor2, max_sweeps, flag, rlog, prog, tag);
+    return jacobi32_g<32, LOG>(A, V, nrm2, s, tol, floor2, max_sweeps, flag, rlog, prog, tag);
+}
+
+// Bounded waits of the replay for the FP32 phase's progress (a sweep takes ~100 us; the limit
+// is ~0.1 s), after which g_svd_error is set and the replay stops.
+__device__ int g_svd_error;
+constexpr long SVD_SPIN = 1L << 17;
+
+// V = the product of the rotations jacobi32<true> logs (V starts as the identity), rows [r0, r1)
+// only, in shared memory row-major with leading dimension s + 1, replayed sweep by sweep while
+// the FP32 phase runs on another CTA: before sweep k the block waits (bounded) until the progress
+// word announces it or the end of the phase.  A row changes only under column rotations, so rows
+// are independent, and the pairs of a round touch disjoint columns: one thread per (row, pair), a
+// barrier over those threads' warps per round; each sweep's log is first staged in shared memory
+// (`stage`, (s' - 1) np float2) by the whole block.  The same products in the same order as
+// rotating V inline.
+__device__ void replay_rotations(const float2 *rlog, const unsigned long long *prog, unsigned long long tag,
+                                 int s, float *Vrows, int r0, int r1, float2 *stage) {
+    __shared__ unsigned long long prog_s;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int sp = s + (s & 1), np = sp / 2, R = sp - 1, ld = s + 1, nrow = r1 - r0;
+    const int ntask = nrow * np, nwt = (ntask + 31) / 32;        // warps holding a task
+    const int row = tid / np, pr = tid % np;
+    for (int e = tid; e < nrow * ld; e += nt) {
+        const int lr = e / ld, c = e % ld;
+        Vrows[e] = (c == r0 + lr) ? 1.f : 0.f;
+    }
+    for (int sw = 0;; ++sw) {
+        if (tid == 0) {
+            unsigned long long v = 0;
+            for (long it = 0;; ++it) {
+                asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(prog) : "memory");
+                if ((v & 0xFFFFFFFF00000000ULL) == tag && ((v & 0xFFFFULL) > (unsigned long long)sw || (v & SVD_PROG_DONE)))
+                    break;
+                if (it >= SVD_SPIN) {                                  // give up: no further sweep
+                    atomicExch(&g_svd_error, 1);
+                    v = tag | SVD_PROG_DONE;
+                    break;
+                }
+                __nanosleep(256);
+            }
+            prog_s = v;
+        }
+        __syncthreads();
+        if ((prog_s & 0xFFFFULL) <= (unsigned long long)sw) break;       // the phase ended before sweep sw
+        const float2 *src = rlog + (size_t)sw * R * np;
+        for (int e = tid; e < R * np; e += nt) stage[e] = __ldcg(src + e);   // written by another SM
+        __syncthreads();
+        if (tid < nwt * 32) {
+            float *v = Vrows + row * ld;
+            for (int round = 0; round < R; ++round) {
+                if (tid < ntask) {
+                    int p, q;
+                    rr_pair(round, pr, sp, p, q);
+                    if (q < s) {
+                        const float2 r = stage[round * np + pr];
+                        const float a = v[p], b = v[q];
+                        v[p] = r.x * a - r.y * b;
+                        v[q] = r.y * a + r.x * b;
+                    }
+                }
+                asm volatile("bar.sync 2, %0;" ::"r"(nwt * 32) : "memory");
+            }
+        }
+        __syncthreads();
+    }
+}
+
+int svd_error_flag(bool reset) {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_svd_error, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    if (reset && v) {
+        const int z = 0;
+        cudaMemcpyToSymbol(g_svd_error, &z, sizeof(int));
+    }
+    return v;
 }
 
 // FP64 phase of the one-sided Jacobi SVD.  Every FP64 warp instruction occupies an SMSP's FP64
@@ -1169,7 +1278,7 @@ __global__ void __launch_bounds__(1024) k_svd(const __grid_constant__ SVDJobs jo
     const float fro = block_sum_f(frop, fscr);
     // phase 1: FP32 sweeps.  On the graded R^T they resolve singular values far below the
     // largest with relative accuracy; columns below 2^-100 (scaled) are left to FP64.
-    const int n32 = jacobi32(A32, V32, nrm32, s, 8.0f * sqrtf((float)s) * 0x1p-24f,
+    const int n32 = jacobi32<false>(A32, V32, nrm32, s, 8.0f * sqrtf((float)s) * 0x1p-24f,
                              graded ? 0x1p-100f : fro * 0x1p-40f, 20, &flag);
     if (tid == 0) g_svd_sweeps[2 * blockIdx.x] = n32;
     // phase 2: V = double(V32), orthonormalised (polar step) into X
@@ -1343,7 +1452,7 @@ __global__ void __launch_bounds__(1024) k_tikhonov(LSState st, int ldr, int k, i
     for (int e = tid; e < ss; e += nt) frop = fmaf(A32[e], A32[e], frop);
     __syncthreads();
     const float fro = block_sum_f(frop, fscr);
-    jacobi32(A32, V32, nrm32, s, 8.0f * sqrtf((float)s) * 0x1p-24f, fro * 0x1p-40f, 20, &flag);
+    jacobi32<false>(A32, V32, nrm32, s, 8.0f * sqrtf((float)s) * 0x1p-24f, fro * 0x1p-40f, 20, &flag);
     polar_step(V32, X, Y, Z, s);
     for (int e = tid; e < ss; e += nt) {
         const int i = e % s, j = e / s;
@@ -1467,41 +1576,58 @@ __global__ void __launch_bounds__(1024) k_svd_cl(const __grid_constant__ SVDJobs
     __shared__ double cpar[SVD_MAXS / 2 + 1], spar[SVD_MAXS / 2 + 1];
     __shared__ int act[SVD_MAXS / 2 + 1];
     __shared__ double scal[2];                                   // CTA 0: mx, fro
+    float2 *const rlog = jobs.rlog[blockIdx.x / SCL];
+    unsigned long long *const prog = jobs.prog[blockIdx.x / SCL];
+    const int rpc = (s + SCL - 2) / (SCL - 1);                   // rows of V per replaying CTA
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
     auto Bat = [&](int i, int c) -> double {                     // B = R^T (lower triangle)
         return (c <= i && c < J.ldr) ? J.R[c + (long long)i * J.ldr] : 0.0;
     };
     auto owner = [&](int col) { return col / cb; };
-    // ---- phase 1 (CTA 0): scaled FP32 sweeps
-    if (q == 0) {
-        float *A32 = reinterpret_cast<float *>(X), *V32 = A32 + ss;
+    // ---- phase 1: CTA 0 runs the scaled FP32 sweeps on A and logs the rotations; CTA q >= 1
+    // replays them on rows [(q - 1) rpc, q rpc) of V (in its Z, row-major, ld s + 1) as each
+    // sweep is announced, staging the sweep's log in its Y.  The progress word is cleared
+    // before any CTA reads it.
+    if (q == 0 && tid == 0) *prog = 0ULL;
+    cl.sync();
+    if (q > 0) {
+        const int r0 = min(s, (q - 1) * rpc), r1 = min(s, r0 + rpc);
+        replay_rotations(rlog, prog, jobs.tag, s, reinterpret_cast<float *>(Z), r0, r1,
+                         reinterpret_cast<float2 *>(Y));
+    } else {
+        float *A32 = reinterpret_cast<float *>(X);
         int emax = 0;
-        for (int e = tid; e < ss; e += nt) emax = max(emax, (__double2hiint(Bat(e % s, e / s)) >> 20) & 0x7ff);
+        // walked in R's storage order (c fastest: coalesced reads of R's rows)
+        for (int e = tid; e < ss; e += nt) emax = max(emax, (__double2hiint(Bat(e / s, e % s)) >> 20) & 0x7ff);
         emax = min(block_max_i(emax, iscr), 2044);
         const double inv = __hiloint2double((2045 - emax) << 20, 0);
+        float frop = 0.f;                                         // ||A32||_F^2 from the values written
         for (int e = tid; e < ss; e += nt) {
-            A32[e] = (float)(Bat(e % s, e / s) * inv);
-            V32[e] = (e % s == e / s) ? 1.f : 0.f;
+            const int i = e / s, c = e % s;
+            const float a = (float)(Bat(i, c) * inv);
+            A32[i + c * s] = a;
+            frop = fmaf(a, a, frop);
         }
-        float frop = 0.f;
-        for (int e = tid; e < ss; e += nt) frop = fmaf(A32[e], A32[e], frop);
         __syncthreads();
         const float fro = block_sum_f(frop, fscr);
-        const int n32 = jacobi32(A32, V32, nrm32, s, 8.0f * sqrtf((float)s) * 0x1p-24f, 0x1p-100f, 20, &flag);
+        const int n32 = jacobi32<true>(A32, nullptr, nrm32, s, 8.0f * sqrtf((float)s) * 0x1p-24f, 0x1p-100f,
+                                       SVD_LOG_SWEEPS, &flag, rlog, prog, jobs.tag);
         if (tid == 0) {
             g_svd_sweeps[2 * (blockIdx.x / SCL)] = n32;
             scal[0] = __hiloint2double((emax + 1) << 20, 0);
             scal[1] = (double)fro;
         }
     }
-    cl.sync();                                                                    // (1)
-    // ---- phase 2: Y = double(V32) everywhere; E columns
+    cl.sync();                                                                    // (1) V's rows ready
+    // ---- phase 2: Y = double(V) everywhere, each row from the CTA that replayed it; E columns
     {
-        const float *V32r = reinterpret_cast<const float *>(cl.map_shared_rank(X, 0)) + ss;
-        for (int e = tid; e < ss; e += nt) Y[e] = (double)V32r[e];
+        for (int e = tid; e < ss; e += nt) {
+            const int r = e % s, c = e / s, o = r / rpc;
+            Y[e] = (double)reinterpret_cast<const float *>(cl.map_shared_rank(Z, 1 + o))[(r - o * rpc) * (s + 1) + c];
+        }
         if (tid < 2) scal[tid] = cl.map_shared_rank(scal, 0)[tid];
     }
-    cl.sync();                                                                    // (2) CTA 0's X free
+    cl.sync();                                                                    // (2) peers' Z free
     const double mx = scal[0], fro = scal[1];
     for (int e = tid; e < s * nc; e += nt) {
         const int i = e % s, jl = e / s, j = c0 + jl;
@@ -1722,6 +1848,18 @@ static void svd_launch(Ctx &c, SVDJobs &J, int smax) {
 
 static void svd_cl_launch(Ctx &c, SVDJobs &J, int smax) {
     const size_t smem = 3 * (size_t)smax * smax * sizeof(double);
+    // rotation logs of the FP32 phase (released with the mark: later work on this stream runs
+    // after the kernel)
+    ScopedMark mark(*c.arena);
+    for (int i = 0; i < J.n; ++i) {
+        const int sp = J.j[i].s + (J.j[i].s & 1);
+        J.rlog[i] = static_cast<float2 *>(
+            c.arena->alloc_bytes((size_t)SVD_LOG_SWEEPS * (sp - 1) * (sp / 2) * sizeof(float2)));
+        J.prog[i] = static_cast<unsigned long long *>(c.arena->alloc_bytes(sizeof(unsigned long long)));
+    }
+    // a progress word left by an earlier launch carries another id (ids repeat after 2^32 launches)
+    static std::atomic<unsigned> launch_id{0};
+    J.tag = (unsigned long long)(launch_id.fetch_add(1) + 1) << 32;
     static std::atomic<bool> attr_set{false};   // set once; idempotent if two threads race
     if (!attr_set) {
         TK_CUDA(cudaFuncSetAttribute(k_svd_cl, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -1257,6 +1257,8 @@ static int solve_entry(tk_handle *h, const tk_operator *op, const tk_operator *p
         TK_CUDA(cudaEventSynchronize(e1));
         if (o.precision == TK_MIXED && oz_error_flag(true) != 0)
             throw Error{TK_EINTERNAL, "a tensor-core GEMM gave up waiting for its copies or MMAs"};
+        if (svd_error_flag(true) != 0)
+            throw Error{TK_EINTERNAL, "a clustered SVD gave up waiting for its FP32 sweeps"};
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         cudaEventDestroy(e0);
@@ -1454,6 +1456,8 @@ int tk_roundsum(tk_handle *h, int32_t nterms, const tk_tucker *xs, const double 
         int hr[TK_MAX_D];
         TK_CUDA(cudaMemcpyAsync(hr, o.rank_dev, sizeof(int) * pb.d, cudaMemcpyDeviceToHost, c.st));
         TK_CUDA(cudaStreamSynchronize(c.st));
+        if (svd_error_flag(true) != 0)
+            throw Error{TK_EINTERNAL, "a clustered SVD gave up waiting for its FP32 sweeps"};
         if (out_rank) for (int k = 0; k < pb.d; ++k) out_rank[k] = hr[k];
         return TK_OK;
     });

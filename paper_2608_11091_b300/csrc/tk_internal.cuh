@@ -167,6 +167,8 @@ bool oz_supported(const GProb &p);
 void gemm_oz(Ctx &c, const std::vector<GProb> &probs, const char *tag);
 // 1 if a tensor-core GEMM gave up waiting for its copies or MMAs since the last reset
 int oz_error_flag(bool reset);
+// Nonzero when a clustered SVD's replay of the FP32 rotations gave up waiting (reset clears it).
+int svd_error_flag(bool reset);
 
 // ------------------------------------------------------------------------------------------
 // Small dense linear algebra (FP64)
