@@ -108,6 +108,7 @@ __global__ void __launch_bounds__(256) k_oz_split(const __grid_constant__ OzSide
     __shared__ int er[32];                           // row index i within its batch, later the exponents
     __shared__ long long rowoff[32];                  // per row: bstride b (+ i when not transposed)
     __shared__ double segscale[GEMM_MAXSEG];         // per segment: coef (* *cd)
+    __shared__ int segunit[GEMM_MAXSEG];             // per segment: the scale is 1 (no FP64 multiply)
     const int tid = threadIdx.x;
     // the row offsets and the segment scales once per block, not per element (integer division
     // and FP64 multiplies are slow per element on this part)
@@ -117,36 +118,62 @@ __global__ void __launch_bounds__(256) k_oz_split(const __grid_constant__ OzSide
         rowoff[tid] = (long long)b * D.bstride + (D.trans ? 0LL : (long long)i);
         er[tid] = i;
     }
-    if (tid < D.nseg) segscale[tid] = D.seg[tid].coef * (D.seg[tid].cd ? *D.seg[tid].cd : 1.0);
+    if (tid < D.nseg) {
+        const double sc = D.seg[tid].coef * (D.seg[tid].cd ? *D.seg[tid].cd : 1.0);
+        segscale[tid] = sc;
+        segunit[tid] = sc == 1.0;
+    }
     __syncthreads();
     const int warp = tid >> 5, lane = tid & 31;
-    auto load = [&](int r, int kk) {
+    // source of element (r, kk) and its segment, or null (padding)
+    auto src_of = [&](int r, int kk, int &sg) -> const double * {
         const int m = r0 + r, k = k0 + kk;
-        double v = 0.0;
-        if (m < D.rows) {
-            for (int s = 0; s < D.nseg; ++s) {
-                const OzSeg &g = D.seg[s];
-                if (k >= g.koff && k < g.koff + g.K) {
-                    const int kl = k - g.koff;
-                    const double *src = g.p + rowoff[r];
-                    v = D.trans ? src[kl + (long long)g.ld * er[r]] : src[(long long)g.ld * kl];
-                    const double sc = segscale[s];
-                    if (sc != 1.0) v *= sc;
-                    break;
-                }
+        sg = 0;
+        if (m >= D.rows || kk >= W) return nullptr;
+        for (int s = 0; s < D.nseg; ++s) {
+            const OzSeg &g = D.seg[s];
+            if (k >= g.koff && k < g.koff + g.K) {
+                const int kl = k - g.koff;
+                const double *src = g.p + rowoff[r];
+                sg = s;
+                return D.trans ? src + kl + (long long)g.ld * er[r] : src + (long long)g.ld * kl;
             }
         }
-        t(r, kk) = __double_as_longlong(v);
+        return nullptr;
+    };
+    // a batch of eight elements per thread: every address first, then the eight loads together
+    // (the segment search would otherwise keep one load in flight), then scale and store
+    auto batch = [&](const int (&rr)[8], const int (&kc)[8]) {
+        const double *src[8];
+        int sg[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) src[u] = src_of(rr[u], kc[u], sg[u]);
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = src[u] ? *src[u] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (kc[u] >= W) continue;
+            if (src[u] && !segunit[sg[u]]) v[u] *= segscale[sg[u]];
+            t(rr[u], kc[u]) = __double_as_longlong(v[u]);
+        }
     };
     // coalesced: a warp walks a row along the reduction index (transposed storage) or the 32
     // rows of one reduction index (rows contiguous)
     if (D.trans) {
-        for (int r = warp; r < 32; r += 8)
-#pragma unroll 4
-            for (int kk = lane; kk < W; kk += 32) load(r, kk);
+        for (int r = warp; r < 32; r += 8) {
+            int rr[8], kc[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) { rr[u] = r; kc[u] = lane + 32 * u; }
+            batch(rr, kc);
+        }
     } else {
-#pragma unroll 4
-        for (int kk = warp; kk < W; kk += 8) load(lane, kk);
+        for (int kk0 = warp; kk0 < W; kk0 += 64) {
+            int rr[8], kc[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) { rr[u] = lane; kc[u] = kk0 + 8 * u; }
+            batch(rr, kc);
+        }
     }
     __syncthreads();
     {
@@ -165,47 +192,41 @@ __global__ void __launch_bounds__(256) k_oz_split(const __grid_constant__ OzSide
         }
     }
     __syncthreads();
-    // digits, two adjacent reduction indices per thread (one packed BF16 pair per plane).  With
-    // |X| <= 2^39 (a 53-bit significand shifted right by at least 14) the balanced digits of |X|
-    // come from its bytes with a carry: byte u (plus the carry) >= 128 becomes u - 256 and carries
-    // 1; the sign then applies to every digit (|d| <= 128 either way, so products stay <= 2^14)
+    // digits, two adjacent reduction indices per thread (one packed BF16 pair per plane).  X is
+    // signed, |X| <= 2^39 (a 53-bit significand shifted right by at least 14).  With
+    // Y = X + 0x80808080 the bytes of Y's low word are d_p + 128 for p = 4, 3, 2, 1 (byte 0 up;
+    // the balanced digits, in [-128, 127]) and Y >> 32 is d_0 (|d_0| <= 128): adding 128 at every
+    // digit position turns the balanced expansion into Y's plain one.  A byte permutation puts
+    // byte u into the float 2^23 + u, and one exact subtraction of 2^23 + 128 gives the digit
     const long long plane = (long long)D.Rpad * D.Kpad;
-    auto digits = [&](long long bits, int ew, int (&d)[OZ_S]) {
+    auto digits = [&](long long bits, int ew, float (&d)[OZ_S]) {
         const int ef = (int)((unsigned long long)bits >> 52) & 0x7FF;
-        unsigned lo = 0u, hi = 0u;
+        long long X = 0;
         if (ef > 0) {
             // |v| 2^(39 - e) = m 2^(ef - 1075 + 39 - e) with m the significand, e = E - 1022:
             // a right shift by E + 14 - ef >= 14 with rounding to nearest
-            const unsigned long long m = ((unsigned long long)bits & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+            const long long m = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
             const int sh = ew + 14 - ef;
-            if (sh < 63) {
-                const unsigned long long X = (m + (1ULL << (sh - 1))) >> sh;
-                lo = (unsigned)X;
-                hi = (unsigned)(X >> 32);
-            }
+            if (sh < 63) X = (m + (1LL << (sh - 1))) >> sh;
+            if (bits < 0) X = -X;
         }
-        int c = 0;
+        const long long Y = X + 0x80808080LL;
+        const unsigned lo = (unsigned)Y;
+        d[0] = (float)(int)(Y >> 32);
 #pragma unroll
-        for (int p = OZ_S - 1; p >= 1; --p) {
-            const int u = (int)((lo >> (8 * (OZ_S - 1 - p))) & 255u) + c;
-            c = u >= 128;
-            d[p] = u - (c << 8);
-        }
-        d[0] = (int)hi + c;
-        if (bits < 0)
-#pragma unroll
-            for (int p = 0; p < OZ_S; ++p) d[p] = -d[p];
+        for (int p = 1; p < OZ_S; ++p)
+            d[p] = __uint_as_float(__byte_perm(lo, 0x4B000000u, 0x7540u + (unsigned)(OZ_S - 1 - p))) - 8388736.f;
     };
     const int Wh = W >> 1;
     for (int e = tid; e < 32 * Wh; e += 256) {
         const int r = e / Wh, kk = 2 * (e % Wh);
-        int da[OZ_S], db[OZ_S];
+        float da[OZ_S], db[OZ_S];
         digits(t(r, kk), er[r], da);
         digits(t(r, kk + 1), er[r], db);
         __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(D.planes + (long long)(r0 + r) * D.Kpad + k0 + kk);
 #pragma unroll
         for (int p = 0; p < OZ_S; ++p)
-            dst[(p * plane) >> 1] = __floats2bfloat162_rn((float)da[p], (float)db[p]);
+            dst[(p * plane) >> 1] = __floats2bfloat162_rn(da[p], db[p]);
     }
 }
 
