@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-extras", action="store_true", help="skip the cpu_baseline and secondary workloads")
     ap.add_argument("--profile-only", action="store_true", help="one step of each form with the kernel profile")
+    ap.add_argument("--maxit", type=int, default=0, help="--profile-only on another workload: iteration cap (0 = its own)")
     return ap.parse_args()
 
 
@@ -310,7 +311,9 @@ def run_native(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     mp = _peaks()
-    peaks = {"fp64_tflops": P.tk_fma_peak(True), "fp32_tflops": P.tk_fma_peak(False),
+    # the FMA-rate probes: best of three (a single run reads a few percent low now and then)
+    peaks = {"fp64_tflops": max(P.tk_fma_peak(True) for _ in range(3)),
+             "fp32_tflops": max(P.tk_fma_peak(False) for _ in range(3)),
              "bf16_tflops": mp.get("bf16_tflops", 1800.0), "hbm_gbs": mp.get("hbm_gbs", 6400.0)}
 
     def barrier():
@@ -409,7 +412,7 @@ def run_native(args):
 
     extras = {}
     if rank == 0 and not args.no_extras:
-        extras = secondary(P, W, torch)
+        extras = secondary(P, W, torch, peaks)
         extras["kernels_fp64_step"] = kernel_table(profs["fp64"], peaks)
 
     if rank == 0:
@@ -473,7 +476,7 @@ def roofline_from_profile(prof, peaks):
            "bound": e.get("bound"), "achieved": e.get("achieved"), "unit": e.get("unit"), "frac": e.get("frac")}
     if e.get("bound") == "alu":
         out.update({"peak": round(peaks["fp64_tflops"], 4), "flops_per_launch": fl / max(n, 1),
-                    "peak_source": "FP64 FMA rate measured in this run (tk_fma_peak, 8 DFMA chains per thread)"})
+                    "peak_source": "FP64 FMA rate measured in this run (tk_fma_peak, 8 DFMA chains per thread, best of three)"})
     elif e.get("bound") == "tensor":
         out.update({"peak": peaks["bf16_tflops"], "flops_per_launch": fl / max(n, 1),
                     "peak_source": "MEASURED_PEAKS bf16_tflops (cuBLAS bf16 GEMM burst)"})
@@ -524,12 +527,14 @@ def regularisation_study(P, W, torch):
     return reg
 
 
-def secondary(P, W, torch):
+def secondary(P, W, torch, peaks):
     """Other workloads of the method, FP64 and mixed form, one solve each after a warm-up
     (reported, not the headline): iterations/s, true residual, and the mixed result's distance
     from the FP64 one (relative Tucker-form difference of the solutions; the two forms draw
     different sketch matrices, so this is the randomized compression's own spread plus the
-    reduced-precision error)."""
+    reduced-precision error).  The convection-diffusion and 4-D MLN workloads also get a
+    per-kernel table (one more solve of each form with the library's event profiler on)."""
+    profiled = ("convdiff3d_n256", "varcoef4d_n128")
     out = {}
     for name in ["convdiff3d_n256", "poisson3d_n32", "deblur3d_n128", "varcoef4d_n128", "poisson3d_n1024_gaussian"]:
         wl = W.workload(name)
@@ -561,6 +566,13 @@ def secondary(P, W, torch):
             entry[form] = {"iters": rep.iters, "status": rep.status, "seconds": round(dt, 4),
                            "iters_per_s": round(rep.iters / dt, 2), "sketched_res": float(f"{rep.sketched_res:.4g}"),
                            "true_rel_residual": float(f"{tr:.4g}")}
+            if name in profiled:
+                P.tk_profile(True)
+                P.tk_profile_report()
+                solve()
+                torch.cuda.synchronize()
+                out[f"kernels_{name}_{form}"] = kernel_table(P.tk_profile_report(), peaks)
+                P.tk_profile(False)
         if len(xs) == 2:
             entry["mixed_vs_fp64_rel_diff_x"] = float(f"{P.tk_sum_norm([xs['mixed'], xs['fp64']], [1.0, -1.0]) / P.tk_sum_norm([xs['fp64']], [1.0]):.3g}")
         out[name] = entry
@@ -662,6 +674,18 @@ def run_profile_target(args):
     import paper_2608_11091_b300 as P
     import workloads as W
     torch.cuda.set_device(0)
+    if args.workload != DEFAULT_WORKLOAD:
+        # another workload: one solve of each form with its own parameters (no preconditioner)
+        wl = W.workload(args.workload)
+        if args.maxit > 0:
+            wl.params.maxit = args.maxit
+        dop = P.DeviceOperator(wl.op)
+        b = P.DeviceTucker.from_numpy(wl.b.core, wl.b.factors)
+        for form in ("mixed", "fp64"):
+            _, rep = P.tk_solve(dop, b, P.Options.from_params(wl.params, precision=form))
+            torch.cuda.synchronize()
+            print(f"{form}: {rep.iters} iterations, {rep.kernel_launches} launches, {rep.ms_total:.2f} ms")
+        return
     prob = Problem(P, W, args.workload, seed=0)
     for form in ("mixed", "fp64"):
         rep, rep_a, _ = prob.step(P, form, concurrent=False)

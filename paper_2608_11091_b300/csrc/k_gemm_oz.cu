@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(256) k_oz_split(const __grid_constant__ OzSide
     __shared__ long long rowoff[32];                  // per row: bstride b (+ i when not transposed)
     __shared__ double segscale[GEMM_MAXSEG];         // per segment: coef (* *cd)
     __shared__ int segunit[GEMM_MAXSEG];             // per segment: the scale is 1 (no FP64 multiply)
+    __shared__ short segk[OZ_CHUNK];                 // per reduction index of the chunk: its segment, -1 past K
     const int tid = threadIdx.x;
     // the row offsets and the segment scales once per block, not per element (integer division
     // and FP64 multiplies are slow per element on this part)
@@ -123,23 +124,26 @@ __global__ void __launch_bounds__(256) k_oz_split(const __grid_constant__ OzSide
         segscale[tid] = sc;
         segunit[tid] = sc == 1.0;
     }
+    for (int kk = tid; kk < OZ_CHUNK; kk += 256) {
+        const int k = k0 + kk;
+        int sg = -1;
+        for (int s = 0; s < D.nseg; ++s)
+            if (k >= D.seg[s].koff && k < D.seg[s].koff + D.seg[s].K) sg = s;
+        segk[kk] = (short)sg;
+    }
     __syncthreads();
     const int warp = tid >> 5, lane = tid & 31;
     // source of element (r, kk) and its segment, or null (padding)
     auto src_of = [&](int r, int kk, int &sg) -> const double * {
-        const int m = r0 + r, k = k0 + kk;
         sg = 0;
-        if (m >= D.rows || kk >= W) return nullptr;
-        for (int s = 0; s < D.nseg; ++s) {
-            const OzSeg &g = D.seg[s];
-            if (k >= g.koff && k < g.koff + g.K) {
-                const int kl = k - g.koff;
-                const double *src = g.p + rowoff[r];
-                sg = s;
-                return D.trans ? src + kl + (long long)g.ld * er[r] : src + (long long)g.ld * kl;
-            }
-        }
-        return nullptr;
+        if (r0 + r >= D.rows || kk >= W) return nullptr;
+        const int s = segk[kk];
+        if (s < 0) return nullptr;
+        sg = s;
+        const OzSeg &g = D.seg[s];
+        const int kl = k0 + kk - g.koff;
+        const double *src = g.p + rowoff[r];
+        return D.trans ? src + kl + (long long)g.ld * er[r] : src + (long long)g.ld * kl;
     };
     // a batch of eight elements per thread: every address first, then the eight loads together
     // (the segment search would otherwise keep one load in flight), then scale and store
