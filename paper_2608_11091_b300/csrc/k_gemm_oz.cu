@@ -59,8 +59,10 @@ constexpr int OZ_STAGES = 2;
 constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE + 1024;  // + alignment slack
 constexpr int OZ_TMEM_COLS = 512;                     // 2 sets x 5 levels x 32 columns
 constexpr int OZ_SET_COLS = OZ_L * OZ_BN;
-constexpr int OZ_EPI_THREADS = 256;                   // warps 0-7: epilogue (TMEM lane quarter, column half)
-constexpr int OZ_THREADS = OZ_EPI_THREADS + 64;       // warp 8: TMA producer, warp 9: MMA issuer
+constexpr int OZ_EPI_WARPS = 16;                      // epilogue: TMEM lane quarter x column quarter
+constexpr int OZ_EPI_THREADS = 32 * OZ_EPI_WARPS;
+constexpr int OZ_THREADS = OZ_EPI_THREADS + 64;       // then the TMA producer warp and the MMA warp
+constexpr int OZ_WARP_TMA = OZ_EPI_WARPS, OZ_WARP_MMA = OZ_EPI_WARPS + 1;
 constexpr long OZ_SPIN = 1L << 20;                    // bounded waits
 
 // ------------------------------------------------------------------------------------------
@@ -350,15 +352,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const __grid_constant
     const uint32_t taddr = taddr_s;
     int issued_slabs = 0;       // producer / MMA progress, for the bounded drain at exit
 
-    // epilogue role (warps 0-7): one output row and 16 columns per thread (a warp reads the TMEM
-    // lanes of its quarter, warp & 3, and the column half warp >> 2)
-    constexpr int NH = OZ_BN / 2;
-    const int q4 = warp & 3, h = (warp >> 2) & 1;
+    // epilogue role (warps 0-15): one output row and 8 columns per thread (a warp reads the TMEM
+    // lanes of its quarter, warp & 3, and the column quarter warp >> 2)
+    constexpr int NH = OZ_BN / (OZ_EPI_WARPS / 4);       // columns per epilogue thread
+    static_assert(NH == 8, "the epilogue's tensor-memory loads are .x8");
+    const int q4 = warp & 3, h = (warp >> 2) % (OZ_EPI_WARPS / 4);
     const int row = q4 * 32 + lane, m = m0 + row;
     double acc[NH];
 #pragma unroll
     for (int j = 0; j < NH; ++j) acc[j] = 0.0;
-    if (warp == 8) {
+    if (warp == OZ_WARP_TMA) {
         // ---------------- TMA producer
         if (lane == 0) {
             for (int kl = 0; kl < nk; ++kl) {
@@ -386,7 +389,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const __grid_constant
             for (int k = max(0, issued_slabs - OZ_STAGES); k < issued_slabs; ++k)
                 oz_wait(oz_smem(&bar_full[k % OZ_STAGES]), (k / OZ_STAGES) & 1);
         }
-    } else if (warp == 9) {
+    } else if (warp == OZ_WARP_MMA) {
         // ---------------- MMA issuer.  One MMA per A digit plane p and 16-wide K step: B's planes
         // q = 0..4-p lie one after another in shared memory (32 rows each, the same 1024-byte
         // row-group stride), so together they are one operand of N = 32 (5 - p) rows, and with D
@@ -455,10 +458,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const __grid_constant
 #pragma unroll
             for (int L = 0; L < OZ_L; ++L) {
                 const uint32_t a = taddr + ((uint32_t)(q4 * 32) << 16) + set * OZ_SET_COLS + L * OZ_BN + h * NH;
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                              : "=r"(r[L][0]), "=r"(r[L][1]), "=r"(r[L][2]), "=r"(r[L][3]), "=r"(r[L][4]), "=r"(r[L][5]),
-                               "=r"(r[L][6]), "=r"(r[L][7]), "=r"(r[L][8]), "=r"(r[L][9]), "=r"(r[L][10]), "=r"(r[L][11]),
-                               "=r"(r[L][12]), "=r"(r[L][13]), "=r"(r[L][14]), "=r"(r[L][15])
+                               "=r"(r[L][6]), "=r"(r[L][7])
                              : "r"(a));
             }
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -505,7 +507,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_gemm_oz(const __grid_constant
         cg::cluster_group cl = cg::this_cluster();
         const int nr = OZ_BM / ks;
         cl.sync();                        // every rank is past its main loop: the rings are free
-        if (warp < 8) {
+        if (warp < OZ_EPI_WARPS) {
             const int o = row / nr, lr = row - o * nr;
 #pragma unroll
             for (int j = 0; j < NH; ++j) {
