@@ -723,7 +723,11 @@ void gemm_oz(Ctx &c, const std::vector<GProb> &probs, const char *tag) {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int ks = 1;
-        while (ks < 8 && 2 * ks <= maxch && tiles <= oz_resident_clusters(c, cfg, 2 * ks)) ks *= 2;
+        // (and leaves the SMs of two 16-CTA clusters free: a concurrent solve's QR or SVD must
+        // not wait behind a split that only shortens this product)
+        while (ks < 8 && 2 * ks <= maxch && tiles <= oz_resident_clusters(c, cfg, 2 * ks) &&
+               tiles * 2 * ks <= c.num_sms - 32)
+            ks *= 2;
         G.ks = ks;
         cfg.gridDim = dim3((unsigned)(tiles * ks), 1, 1);
         attr[0].val.clusterDim.x = (unsigned)ks;
