@@ -14,17 +14,21 @@
 //    integer; grouping the products by level L = p + q (<= 4, 15 products), each level's sum
 //    is at most (L + 1) 256 2^14 <= 2^24 in magnitude, so the FP32 accumulation in tensor memory
 //    is exact.  Products with p + q > 4 are dropped: the error is about 2^-40 relative to
-//    max|A row| max|B column| per reduction index.
+//    max|A row| max|B column| per reduction index.  One MMA per A plane p and 16-wide K step
+//    covers every level at once: B's planes q = 0..4-p are one operand of N = 32 (5 - p) rows,
+//    and the accumulator starts at level p's columns, so plane q's block lands on level p + q.
 //  * Accumulation.  Per chunk the epilogue combines the levels exactly in 64-bit integers,
-//    sum_L S_L 2^(8(4 - L)), and adds 2^(e_m + f_n - 46) times it into FP64 registers (one output
-//    row per thread; the FP64 pipe of this part is slow, so it does one FMA per output and chunk),
-//    then C = beta C + acc.
+//    sum_L S_L 2^(8(4 - L)), and forms 2^(e_m + f_n - 46) times it as an FP64 value with integer
+//    operations (the FP64 pipe of this part is slow), adding it to the output in FP64 registers
+//    when a CTA has more than one chunk; then C = beta C + acc.
 //
-// Pipeline (k_gemm_oz, one 128 x 32 output tile per CTA, 6 warps): warp 4 lane 0 issues the TMA
-// loads (five A planes 128 x 64 and five B planes 32 x 64 per K slab of 64, 128-byte swizzle)
-// into a two-stage ring; warp 5 lane 0 issues the tcgen05.mma (M 128, N 32, K 16) into two
-// alternating sets of five accumulators in tensor memory; warps 0-3 read a finished set back
-// (tcgen05.ld) while the next chunk is multiplied.  mbarriers: full / empty per stage,
+// Pipeline (k_gemm_oz, one 128 x 32 output tile per CTA or a cluster of up to 8 CTAs splitting
+// its reduction, 18 warps): warp 16 lane 0 issues the TMA loads (five A planes 128 x 64 and five
+// B planes 32 x 64 per K slab of 64, 128-byte swizzle) into a two-stage ring; warp 17 lane 0
+// issues the tcgen05.mma (M 128, K 16, five per K step) into two alternating sets of five
+// accumulators in tensor memory; warps 0-15 read a finished set back (tcgen05.ld, a quarter of
+// the columns each) while the next chunk is multiplied; a split reduction pushes each rank's
+// partial rows into the ring of the rank that adds them.  mbarriers: full / empty per stage,
 // accumulator full / empty per set.  Every wait has an iteration limit: on expiry the kernel
 // records an error in g_oz_error and all roles stop issuing work; the CTA waits (bounded) for
 // its own copies and MMAs before freeing its tensor memory.
