@@ -68,7 +68,31 @@ __device__ __forceinline__ void householder(double alpha, double sigma2, double 
 struct QRJobs {
     int n;
     QRJob j[TK_MAX_D];
+    // G = 2 clusters per job: per job every CTA's exchange slot, [2][2 C][QR_XS] doubles (by
+    // exchange parity), and one progress word per CTA; tag = this launch's id << 32
+    int G;
+    double *xbuf[TK_MAX_D];
+    unsigned long long *xflag[TK_MAX_D];
+    unsigned long long tag;
 };
+// a CTA's cross-cluster slot: a copy of its exchange buffer (partial sums, then the pivot row)
+constexpr int QR_XS = 2 * QR_MAXS;
+// bounded waits of the cross-cluster exchange (a step takes ~10 us; the limit is ~0.1 s or more),
+// after which g_qr_error is set and the kernel carries on with its own cluster's sums
+__device__ int g_qr_error;
+constexpr long QR_SPIN = 1L << 18;
+int qr_error_flag(bool reset) {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_qr_error, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    if (reset && v) {
+        const int z = 0;
+        cudaMemcpyToSymbol(g_qr_error, &z, sizeof(int));
+    }
+    return v;
+}
 
 // One reflector per step, one cluster-wide exchange per step.  With x = A[j:, j], alpha = x_0,
 // sigma2 = ||x_1:||^2, nrm = (alpha^2 + sigma2)^(1/2), beta = -sign(alpha) nrm, the reflector
@@ -104,10 +128,11 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks();
     const int q = (int)cl.block_rank();
+    const int G = jobs.G, g = (int)blockIdx.x / C, qg = (int)blockIdx.x;   // cluster, CTA over the job
     const QRJob &J = jobs.j[blockIdx.y];
     const int m = J.m, s = J.s, kmax = min(m, s);
-    const int rb = (m + C - 1) / C;
-    const int r0 = min(m, q * rb), r1 = min(m, r0 + rb), nr = r1 - r0;
+    const int rb = (m + G * C - 1) / (G * C);
+    const int r0 = min(m, qg * rb), r1 = min(m, r0 + rb), nr = r1 - r0;
     extern __shared__ double dyn[];
     double *Al = dyn;                              // nr x s, ld rb_cap
     __shared__ double red[2][2 * QR_MAXS];         // [0, nc1): partial sums, [nc1, 2 nc1): owner's row
@@ -312,14 +337,86 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
             if (e < n4 && g == 0) dst[cc] = d;
         }
     };
+    // G = 2: every CTA copies its exchange buffer to its global slot and raises its progress
+    // word (release) just before the cluster barrier of an exchange; after the barrier a CTA waits
+    // (bounded) for the other cluster's words and reads its CTAs' buffers from global memory beside
+    // the distributed-shared-memory loads of its own cluster.  The two clusters' sums are formed
+    // with the same reduction tree and added in cluster order, so every CTA holds the same doubles.
+    __shared__ int xbad;
+    double *const xb = G > 1 ? jobs.xbuf[blockIdx.y] : nullptr;
+    unsigned long long *const xf = G > 1 ? jobs.xflag[blockIdx.y] : nullptr;
+    auto xslot = [&](int X, int cta) { return xb + (size_t)(((X & 1) * G * C) + cta) * QR_XS; };
+    // the cluster barrier of exchange X with the publication inside it: thread 0's fence and
+    // progress word go between the barrier's arrive and its wait, off the barrier's critical path
+    auto publish_sync = [&](const double *rdb, int n, int X) {
+        __syncthreads();
+        double *dst = xslot(X, qg);
+        for (int e = tid; e < n; e += nt) dst[e] = rdb[e];
+        __syncthreads();
+        asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+        if (tid == 0) {
+            __threadfence();
+            asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(xf + qg), "l"(jobs.tag | (unsigned long long)X)
+                         : "memory");
+        }
+        asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+    };
+    auto await_other = [&](int X) {                           // after the barrier of exchange X
+        if (tid == 0) xbad = 0;
+        __syncthreads();
+        if (tid < C) {
+            const int cta = (1 - g) * C + tid;
+            const unsigned long long want = jobs.tag | (unsigned long long)X;
+            for (long it = 0;; ++it) {
+                unsigned long long w;
+                asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(xf + cta) : "memory");
+                if ((w >> 32) == (want >> 32) && (w & 0xFFFFFFFFULL) >= (want & 0xFFFFFFFFULL)) break;
+                if (it >= QR_SPIN) { xbad = 1; atomicExch(&g_qr_error, 1); break; }
+                __nanosleep(32);
+            }
+        }
+        __syncthreads();
+    };
+    // peer_sums over both clusters (G = 2): the other cluster's buffers are global slot copies
+    // (the pivot row from rowsh in distributed shared memory, or rowgl in a global slot)
+    auto peer_sums2 = [&](const double *rd, int lo, int hi, int t0, int nthr, double *dst, int X,
+                          const double *rowsh, const double *rowgl, double *rowdst) {
+        const int n4 = (hi - lo) * 4;
+        const double *ob = xslot(X, (1 - g) * C);
+        for (int e = tid - t0; e >= 0 && e < ((n4 + 31) & ~31); e += nthr) {
+            const int cc = lo + e / 4, gq = e & 3;
+            double v[4] = {0.0, 0.0, 0.0, 0.0}, w[4] = {0.0, 0.0, 0.0, 0.0};
+            if (e < n4) {
+                if (gq == 0 && rowdst) rowdst[cc] = rowsh ? rowsh[cc] : __ldcg(rowgl + cc);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (gq + 4 * u < C) {
+                        v[u] = cl.map_shared_rank(rd, gq + 4 * u)[cc];
+                        w[u] = xbad ? 0.0 : __ldcg(ob + (size_t)(gq + 4 * u) * QR_XS + cc);
+                    }
+            }
+            double d = (v[0] + v[1]) + (v[2] + v[3]), o = (w[0] + w[1]) + (w[2] + w[3]);
+            d += __shfl_xor_sync(0xffffffffu, d, 1);
+            d += __shfl_xor_sync(0xffffffffu, d, 2);
+            o += __shfl_xor_sync(0xffffffffu, o, 1);
+            o += __shfl_xor_sync(0xffffffffu, o, 2);
+            if (e < n4 && gq == 0) dst[cc] = g == 0 ? d + o : o + d;
+        }
+    };
     double sc2 = 1.0, scr = 1.0;   // pivot-norm scaling (1 / largest initial squared norm)
     if (piv) {
         for (int c = tid; c < s; c += nt) permv[c] = c;
         double *rd = red[xch & 1];
         flat_sums(r0, s, [&](int i, int c, double &x, double &y) { x = y = A(i, c); }, rd);
-        cl.sync();
+        if (G > 1) publish_sync(rd, s, xch + 1);
+        else cl.sync();
         ++xch;
-        peer_sums(rd, 0, s, 0, nt, wv);
+        if (G > 1) {
+            await_other(xch);
+            peer_sums2(rd, 0, s, 0, nt, wv, xch, nullptr, nullptr, nullptr);
+        } else {
+            peer_sums(rd, 0, s, 0, nt, wv);
+        }
         __syncthreads();
         if (warp == 0) {                 // largest squared column norm: one warp of shuffles
             double mxn = 0.0;
@@ -377,24 +474,33 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
             y = A(i, cc);
             x = (cc == 0 && i == 0) ? 0.0 : A(i, 0);
         }, rd);
-        if (q == 0)
+        if (qg == 0)
             for (int cc = tid; cc < s; cc += nt) rd[s + cc] = A(0, cc);
     }
     for (int j = 0; j < kmax; ++j) {
         const int nc1 = s - j;              // columns j .. s-1
-        const int own = j / rb;              // CTA holding row j
-        const bool owner = (q == own);
+        const int own = j / rb;              // CTA holding row j (over the job)
+        const bool owner = (qg == own);
+        const int og = own / C, orank = own % C;   // its cluster and rank there
+        const bool here = (og == g);
         const int ib = max(r0, j);
         double *rd = red[xch & 1];
-        cl.sync();
+        if (G > 1) publish_sync(rd, 2 * nc1, xch + 1);   // partial sums [0, nc1), the owner's row [nc1, 2 nc1)
+        else cl.sync();
         ++xch;
-        const double *ro = cl.map_shared_rank(rd, own);
+        if (G > 1) await_other(xch);
+        const double *ro = cl.map_shared_rank(rd, here ? orank : 0);
         if (warp == 0) {
             // sigma2 over the peers (lane = peer, C <= 16), alpha from the owner, the scalars
             double s2 = lane < C ? cl.map_shared_rank(rd, lane)[0] : 0.0;
-            const double al = ro[nc1];          // issued beside the sigma2 loads
+            double so = (G > 1 && lane < C && !xbad) ? __ldcg(xslot(xch, (1 - g) * C + lane)) : 0.0;
+            const double al = here ? ro[nc1] : __ldcg(xslot(xch, own) + nc1);   // beside the sigma2 loads
 #pragma unroll
-            for (int o = 8; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            for (int o = 8; o > 0; o >>= 1) {
+                s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+                so += __shfl_xor_sync(0xffffffffu, so, o);
+            }
+            if (G > 1) s2 = g == 0 ? s2 + so : so + s2;   // the clusters in order, in every CTA
             if (lane == 0) {
                 // with nrm = (alpha^2 + sigma2)^(1/2) and a = |alpha|: tau = (beta - alpha) / beta
                 // = 1 + a / nrm and 1 / (alpha - beta) = sign(alpha) / (a + nrm); one reciprocal
@@ -409,6 +515,9 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
                 bc[0] = tau; bc[1] = beta; bc[2] = scal; bc[3] = al;
                 taus[j] = tau;
             }
+        } else if (G > 1) {
+            peer_sums2(rd, 1, nc1, 32, nt - 32, wv, xch, here ? ro + nc1 : nullptr,
+                       here ? nullptr : xslot(xch, own) + nc1, prow);   // the owner's row P_c beside them
         } else {
             peer_sums(rd, 1, nc1, 32, nt - 32, wv, ro + nc1, prow);   // owner's row P_c beside them
         }
@@ -452,16 +561,16 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
         // column now at position p is the old column j + 1: it takes w of position j + 1)
         double *rn = red[xch & 1];
         fused_pass(j, p, ib, nc1 - 1, rn);
-        if (q == (j + 1) / rb)
+        if (qg == (j + 1) / rb)
             for (int cc = tid; cc < nc1 - 1; cc += nt) rn[nc1 - 1 + cc] = A(j + 1, j + 1 + cc);
         if (tid == 0 && p != j + 1) {                // FP32 norm and index follow the move
             const float f = nrmf[j + 1]; nrmf[j + 1] = nrmf[p]; nrmf[p] = f;
             const int u = permv[j + 1]; permv[j + 1] = permv[p]; permv[p] = u;
         }
     }
-    if (J.tau && q == 0)
+    if (J.tau && qg == 0)
         for (int j = tid; j < kmax; j += nt) J.tau[j] = taus[j];
-    if (piv && q == 0)
+    if (piv && qg == 0)
         for (int c = tid; c < s; c += nt) J.perm[c] = permv[c];
     if (SMEM) {
         for (int e = tid; e < nr * s; e += nt) {
@@ -492,18 +601,31 @@ static void qr_reflectors(Ctx &c, const std::vector<QRJob> &jobs) {
             mmax = std::max(mmax, J.j[i].m);
             smax = std::max(smax, J.j[i].s);
         }
-        // cluster of up to 16 CTAs with >= 48 rows each, shrunk until the device can place it
+        // cluster of up to 16 CTAs with >= 48 rows each, shrunk until the device can place it;
+        // a single tall unfolding (>= 3000 rows: the FP64 pass dominates its steps) is split over
+        // two clusters that add their per-step sums through global memory
         int C = std::max(1, std::min(16, (mmax + 47) / 48));
+        const int G = (J.n == 1 && mmax >= 3000) ? 2 : 1;
+        J.G = G;
+        ScopedMark mark(*c.arena);
+        if (G > 1) {
+            static std::atomic<unsigned> launch_id{0};
+            J.tag = (unsigned long long)(launch_id.fetch_add(1) + 1) << 32;
+            for (int i = 0; i < J.n; ++i) {      // a slot and a progress word per CTA (C <= 16)
+                J.xbuf[i] = c.arena->alloc((size_t)2 * G * 16 * QR_XS);
+                J.xflag[i] = static_cast<unsigned long long *>(c.arena->alloc_bytes(sizeof(unsigned long long) * G * 16));
+            }
+        }
         cudaLaunchConfig_t cfg{};
         cudaLaunchAttribute attr[1];
         int rb = 0;
         bool use_smem = false;
         for (;;) {
-            rb = (mmax + C - 1) / C;
+            rb = (mmax + G * C - 1) / (G * C);
             const size_t smem = (size_t)rb * smax * sizeof(double);
             use_smem = smem <= 180 * 1024;
             cfg = cudaLaunchConfig_t{};
-            cfg.gridDim = dim3((unsigned)C, (unsigned)J.n, 1);
+            cfg.gridDim = dim3((unsigned)(G * C), (unsigned)J.n, 1);
             cfg.blockDim = dim3(QR_THREADS, 1, 1);
             cfg.dynamicSmemBytes = use_smem ? smem : 0;
             cfg.stream = c.st;
