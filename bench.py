@@ -469,10 +469,9 @@ def roofline_from_profile(prof, peaks):
     name = max(prof.items(), key=lambda kv: kv[1][1])[0]
     e = tab[name]
     n, ms, fl, by = prof[name]
-    # DRAM bytes per launch of the dominant kernel from the ncu capture of this workload
-    # (profiles/qr_svd_gemm_tc_poisson3d_n1024.md: the two ST-HOSVD QRs captured on two
-    # clusters, 2.80 and 2.56 MB)
-    traffic = {"qr": 2.68e6}.get(name)
+    # DRAM bytes per launch of the dominant kernel from an ncu capture of this workload; None
+    # until the current kernel has been captured
+    traffic = {}.get(name)
     out = {"kernel": name, "launches": n, "avg_us": e["avg_us"], "share": e["share"], "traffic": traffic,
            "bound": e.get("bound"), "achieved": e.get("achieved"), "unit": e.get("unit"), "frac": e.get("frac")}
     if e.get("bound") == "alu":

@@ -12,6 +12,7 @@
 #include <algorithm>
 
 #include <atomic>
+#include <type_traits>
 
 #include "tk_internal.cuh"
 
@@ -68,19 +69,34 @@ __device__ __forceinline__ void householder(double alpha, double sigma2, double 
 struct QRJobs {
     int n;
     QRJob j[TK_MAX_D];
-    // G = 2 clusters per job: per job every CTA's exchange slot, [2][2 C][QR_XS] doubles (by
-    // exchange parity), and one progress word per CTA; tag = this launch's id << 32
-    int G;
-    double *xbuf[TK_MAX_D];
-    unsigned long long *xflag[TK_MAX_D];
-    unsigned long long tag;
+    // with G > 1 clusters per job (n = 1): every CTA's exchange slot in global memory, two per CTA
+    // (by exchange parity), each xs values of two tagged words (zeroed before the launch)
+    int xs;
+    unsigned long long *xw[TK_MAX_D];
 };
-// a CTA's cross-cluster slot: a copy of its exchange buffer (partial sums, then the pivot row)
-constexpr int QR_XS = 2 * QR_MAXS;
+constexpr int QR_GMAX = 3;
 // bounded waits of the cross-cluster exchange (a step takes ~10 us; the limit is ~0.1 s or more),
-// after which g_qr_error is set and the kernel carries on with its own cluster's sums
+// after which g_qr_error is set and the kernel carries on with zeros for the missing sums
 __device__ int g_qr_error;
 constexpr long QR_SPIN = 1L << 18;
+// A value crosses clusters as two 64-bit words, each a 32-bit half of the double under the
+// 32-bit exchange number X: an aligned 64-bit access is single-copy atomic, so a reader that
+// sees X in both words holds the value of exchange X, with no flag, fence or second round trip
+// (slots start zeroed and X >= 1).
+__device__ __forceinline__ void xw_put(unsigned long long *w, double v, unsigned X) {
+    const unsigned long long t = (unsigned long long)X << 32;
+    const unsigned long long a = t | (unsigned)__double2loint(v), b = t | (unsigned)__double2hiint(v);
+    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(w), "l"(a), "l"(b) : "memory");
+}
+__device__ __forceinline__ void xw_load(const unsigned long long *w, unsigned long long &a, unsigned long long &b) {
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(w) : "memory");
+}
+__device__ __forceinline__ bool xw_ok(unsigned long long a, unsigned long long b, unsigned X) {
+    return (unsigned)(a >> 32) == X && (unsigned)(b >> 32) == X;
+}
+__device__ __forceinline__ double xw_val(unsigned long long a, unsigned long long b) {
+    return __hiloint2double((int)(unsigned)b, (int)(unsigned)a);
+}
 int qr_error_flag(bool reset) {
     int v = 0;
     if (cudaMemcpyFromSymbol(&v, g_qr_error, sizeof(int)) != cudaSuccess) {
@@ -121,14 +137,18 @@ int qr_error_flag(bool reset) {
 // reflectors; qr_form_q builds an explicit Q from them.
 // Rows live in shared memory when they fit (SMEM = true), else in global memory.  The
 // exchange buffers alternate by a running exchange count, so a buffer is rewritten only after
-// every peer has passed the next cluster barrier.
+// every peer has passed the next cluster barrier.  A tall single unfolding runs on G <= 3
+// clusters: each CTA also writes its exchange buffer to a global slot as tagged words (xw_put)
+// inside its cluster barrier, and reads the other clusters' slots beside its own cluster's
+// distributed-shared-memory loads; a slot of exchange X is rewritten at X + 2, which no CTA
+// reaches before every CTA has read X.
 constexpr int QR_THREADS = 256;
-template <bool SMEM>
+template <bool SMEM, int G>
 __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QRJobs jobs, int rb_cap) {
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks();
     const int q = (int)cl.block_rank();
-    const int G = jobs.G, g = (int)blockIdx.x / C, qg = (int)blockIdx.x;   // cluster, CTA over the job
+    const int g = (int)blockIdx.x / C, qg = (int)blockIdx.x;   // cluster, CTA over the job
     const QRJob &J = jobs.j[blockIdx.y];
     const int m = J.m, s = J.s, kmax = min(m, s);
     const int rb = (m + G * C - 1) / (G * C);
@@ -314,109 +334,125 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
         __syncthreads();
         combine(T, nrows, E, nc, out);
     };
-    // sum over the cluster of rd[lo .. hi) of every peer into dst[lo .. hi): four threads per
-    // entry, each over a quarter of the peers (C <= 16: at most four loads, all issued before
-    // the first add), combined by two shuffles within the group
-    // (optional: the group's first thread also copies rowsrc[cc] into rowdst[cc], a load issued
-    // with the others)
-    auto peer_sums = [&](const double *rd, int lo, int hi, int t0, int nthr, double *dst,
-                         const double *rowsrc = nullptr, double *rowdst = nullptr) {
-        const int n4 = (hi - lo) * 4;
-        for (int e = tid - t0; e >= 0 && e < ((n4 + 31) & ~31); e += nthr) {
-            const int cc = lo + e / 4, g = e & 3;
-            double v[4] = {0.0, 0.0, 0.0, 0.0};
-            if (e < n4) {
-                if (rowsrc && g == 0) rowdst[cc] = rowsrc[cc];
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (g + 4 * u < C) v[u] = cl.map_shared_rank(rd, g + 4 * u)[cc];
-            }
-            double d = (v[0] + v[1]) + (v[2] + v[3]);
-            d += __shfl_xor_sync(0xffffffffu, d, 1);
-            d += __shfl_xor_sync(0xffffffffu, d, 2);
-            if (e < n4 && g == 0) dst[cc] = d;
+    // G > 1: after its cluster barrier's arrive every CTA writes its exchange buffer to its global
+    // slot as tagged words; after the barrier's wait it reads its own cluster's buffers through
+    // distributed shared memory and the other clusters' slots from global memory (bounded waits on
+    // the tags).  A cluster's sum is formed with the same reduction tree wherever it is read and
+    // the clusters' sums are added in cluster order, so every CTA holds the same doubles.
+    unsigned long long *const xw = G > 1 ? jobs.xw[blockIdx.y] : nullptr;
+    auto xslot = [&](int X, int cta) { return xw + (size_t)((X & 1) * G * C + cta) * jobs.xs * 2; };
+    // the cluster barrier of exchange X (rdb[0 .. n) published inside it when G > 1)
+    auto xsync = [&](const double *rdb, int n, int X) {
+        if (G == 1) {
+            cl.sync();
+            return;
         }
-    };
-    // G = 2: every CTA copies its exchange buffer to its global slot and raises its progress
-    // word (release) just before the cluster barrier of an exchange; after the barrier a CTA waits
-    // (bounded) for the other cluster's words and reads its CTAs' buffers from global memory beside
-    // the distributed-shared-memory loads of its own cluster.  The two clusters' sums are formed
-    // with the same reduction tree and added in cluster order, so every CTA holds the same doubles.
-    __shared__ int xbad;
-    double *const xb = G > 1 ? jobs.xbuf[blockIdx.y] : nullptr;
-    unsigned long long *const xf = G > 1 ? jobs.xflag[blockIdx.y] : nullptr;
-    auto xslot = [&](int X, int cta) { return xb + (size_t)(((X & 1) * G * C) + cta) * QR_XS; };
-    // the cluster barrier of exchange X with the publication inside it: thread 0's fence and
-    // progress word go between the barrier's arrive and its wait, off the barrier's critical path
-    auto publish_sync = [&](const double *rdb, int n, int X) {
-        __syncthreads();
-        double *dst = xslot(X, qg);
-        for (int e = tid; e < n; e += nt) dst[e] = rdb[e];
         __syncthreads();
         asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-        if (tid == 0) {
-            __threadfence();
-            asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(xf + qg), "l"(jobs.tag | (unsigned long long)X)
-                         : "memory");
-        }
+        unsigned long long *dst = xslot(X, qg);
+        for (int e = tid; e < n; e += nt) xw_put(dst + 2 * e, rdb[e], (unsigned)X);
         asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
     };
-    auto await_other = [&](int X) {                           // after the barrier of exchange X
-        if (tid == 0) xbad = 0;
-        __syncthreads();
-        if (tid < C) {
-            const int cta = (1 - g) * C + tid;
-            const unsigned long long want = jobs.tag | (unsigned long long)X;
-            for (long it = 0;; ++it) {
-                unsigned long long w;
-                asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(xf + cta) : "memory");
-                if ((w >> 32) == (want >> 32) && (w & 0xFFFFFFFFULL) >= (want & 0xFFFFFFFFULL)) break;
-                if (it >= QR_SPIN) { xbad = 1; atomicExch(&g_qr_error, 1); break; }
-                __nanosleep(32);
-            }
-        }
-        __syncthreads();
-    };
-    // peer_sums over both clusters (G = 2): the other cluster's buffers are global slot copies
-    // (the pivot row from rowsh in distributed shared memory, or rowgl in a global slot)
-    auto peer_sums2 = [&](const double *rd, int lo, int hi, int t0, int nthr, double *dst, int X,
-                          const double *rowsh, const double *rowgl, double *rowdst) {
-        const int n4 = (hi - lo) * 4;
-        const double *ob = xslot(X, (1 - g) * C);
-        for (int e = tid - t0; e >= 0 && e < ((n4 + 31) & ~31); e += nthr) {
-            const int cc = lo + e / 4, gq = e & 3;
-            double v[4] = {0.0, 0.0, 0.0, 0.0}, w[4] = {0.0, 0.0, 0.0, 0.0};
-            if (e < n4) {
-                if (gq == 0 && rowdst) rowdst[cc] = rowsh ? rowsh[cc] : __ldcg(rowgl + cc);
+    // sum over every cluster's peers of rd[lo .. hi) into dst[lo .. hi): TPC threads per entry
+    // (4, or 2 when four would take the threads a second round: every load of a thread is then in
+    // flight at once, one round trip), each over the peers q = gq + TPC u of every cluster (C <=
+    // 16), combined by shuffles within the group.  Per peer slot u the clusters' values are added
+    // in cluster order, then one tree over u: the same doubles in every CTA.  Optionally the
+    // group's first thread also copies the owner's row entry into rowdst[cc], from rowsh
+    // (distributed shared memory) or from value rowoff + cc of CTA rowcta's slot.
+    auto peer_sums_t = [&](auto tpc, const double *rd, int lo, int hi, int t0, int nthr, double *dst, int X,
+                           const double *rowsh, int rowcta, int rowoff, double *rowdst) {
+        constexpr int TPC = decltype(tpc)::value, PPT = 16 / TPC, NO = G > 1 ? G - 1 : 1;
+        const int nT = (hi - lo) * TPC;
+        for (int e = tid - t0; e >= 0 && e < ((nT + 31) & ~31); e += nthr) {
+            const int cc = lo + e / TPC, gq = e % TPC;
+            const bool act = e < nT;
+            double v[PPT], o[NO][PPT];          // own cluster; the others (k: cluster k + (k >= g))
+            unsigned long long wa[NO][PPT], wb[NO][PPT], ra = 0, rb2 = 0;
+            unsigned long long need = 0;
+            double rowv = 0.0;
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (gq + 4 * u < C) {
-                        v[u] = cl.map_shared_rank(rd, gq + 4 * u)[cc];
-                        w[u] = xbad ? 0.0 : __ldcg(ob + (size_t)(gq + 4 * u) * QR_XS + cc);
-                    }
+            for (int u = 0; u < PPT; ++u) {
+                v[u] = 0.0;
+#pragma unroll
+                for (int k = 0; k < NO; ++k) {
+                    o[k][u] = 0.0;
+                    if (act && k < G - 1 && gq + TPC * u < C) need |= 1ull << (PPT * k + u);
+                }
             }
-            double d = (v[0] + v[1]) + (v[2] + v[3]), o = (w[0] + w[1]) + (w[2] + w[3]);
-            d += __shfl_xor_sync(0xffffffffu, d, 1);
-            d += __shfl_xor_sync(0xffffffffu, d, 2);
-            o += __shfl_xor_sync(0xffffffffu, o, 1);
-            o += __shfl_xor_sync(0xffffffffu, o, 2);
-            if (e < n4 && gq == 0) dst[cc] = g == 0 ? d + o : o + d;
+            if (act) {
+                if (rowdst && gq == 0) {
+                    if (rowsh) rowv = rowsh[cc];
+                    else need |= 1ull << 40;
+                }
+#pragma unroll
+                for (int u = 0; u < PPT; ++u)
+                    if (gq + TPC * u < C) v[u] = cl.map_shared_rank(rd, gq + TPC * u)[cc];
+            }
+            for (long it = 0; need; ++it) {
+#pragma unroll
+                for (int k = 0; k < NO; ++k)
+#pragma unroll
+                    for (int u = 0; u < PPT; ++u)
+                        if (need >> (PPT * k + u) & 1ull)
+                            xw_load(xslot(X, (k + (k >= g)) * C + gq + TPC * u) + 2 * cc, wa[k][u], wb[k][u]);
+                if (need >> 40 & 1ull) xw_load(xslot(X, rowcta) + 2 * (rowoff + cc), ra, rb2);
+#pragma unroll
+                for (int k = 0; k < NO; ++k)
+#pragma unroll
+                    for (int u = 0; u < PPT; ++u)
+                        if ((need >> (PPT * k + u) & 1ull) && xw_ok(wa[k][u], wb[k][u], (unsigned)X)) {
+                            o[k][u] = xw_val(wa[k][u], wb[k][u]);
+                            need &= ~(1ull << (PPT * k + u));
+                        }
+                if ((need >> 40 & 1ull) && xw_ok(ra, rb2, (unsigned)X)) {
+                    rowv = xw_val(ra, rb2);
+                    need &= ~(1ull << 40);
+                }
+                if (need) {
+                    if (it >= QR_SPIN) { atomicExch(&g_qr_error, 1); break; }
+                    __nanosleep(32);
+                }
+            }
+            if (act && rowdst && gq == 0) rowdst[cc] = rowv;
+            double x[PPT];
+#pragma unroll
+            for (int u = 0; u < PPT; ++u) {
+                x[u] = v[u];
+                if (G > 1) {
+                    // cluster c's value: own (c == g), else o[c - (c > g)]
+                    x[u] = g == 0 ? v[u] : o[0][u];
+#pragma unroll
+                    for (int c2 = 1; c2 < G; ++c2)
+                        x[u] += c2 == g ? v[u] : (c2 > g ? o[c2 - 1][u] : o[c2 < NO ? c2 : 0][u]);
+                }
+            }
+            double tot;
+            if (PPT == 4) {
+                tot = (x[0] + x[1]) + (x[2] + x[3]);
+            } else {
+                tot = ((x[0] + x[1]) + (x[2] + x[3])) + ((x[4 % PPT] + x[5 % PPT]) + (x[6 % PPT] + x[7 % PPT]));
+            }
+#pragma unroll
+            for (int sh = 1; sh < TPC; sh <<= 1) tot += __shfl_xor_sync(0xffffffffu, tot, sh);
+            if (act && gq == 0) dst[cc] = tot;
         }
+    };
+    auto peer_sums = [&](const double *rd, int lo, int hi, int t0, int nthr, double *dst, int X,
+                         const double *rowsh, int rowcta, int rowoff, double *rowdst) {
+        if ((hi - lo) * 4 <= nthr)
+            peer_sums_t(std::integral_constant<int, 4>{}, rd, lo, hi, t0, nthr, dst, X, rowsh, rowcta, rowoff, rowdst);
+        else
+            peer_sums_t(std::integral_constant<int, 2>{}, rd, lo, hi, t0, nthr, dst, X, rowsh, rowcta, rowoff, rowdst);
     };
     double sc2 = 1.0, scr = 1.0;   // pivot-norm scaling (1 / largest initial squared norm)
     if (piv) {
         for (int c = tid; c < s; c += nt) permv[c] = c;
         double *rd = red[xch & 1];
         flat_sums(r0, s, [&](int i, int c, double &x, double &y) { x = y = A(i, c); }, rd);
-        if (G > 1) publish_sync(rd, s, xch + 1);
-        else cl.sync();
+        xsync(rd, s, xch + 1);
         ++xch;
-        if (G > 1) {
-            await_other(xch);
-            peer_sums2(rd, 0, s, 0, nt, wv, xch, nullptr, nullptr, nullptr);
-        } else {
-            peer_sums(rd, 0, s, 0, nt, wv);
-        }
+        peer_sums(rd, 0, s, 0, nt, wv, xch, nullptr, 0, 0, nullptr);
         __syncthreads();
         if (warp == 0) {                 // largest squared column norm: one warp of shuffles
             double mxn = 0.0;
@@ -485,22 +521,52 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
         const bool here = (og == g);
         const int ib = max(r0, j);
         double *rd = red[xch & 1];
-        if (G > 1) publish_sync(rd, 2 * nc1, xch + 1);   // partial sums [0, nc1), the owner's row [nc1, 2 nc1)
-        else cl.sync();
+        xsync(rd, owner ? 2 * nc1 : nc1, xch + 1);   // partial sums [0, nc1), the owner's row [nc1, 2 nc1)
         ++xch;
-        if (G > 1) await_other(xch);
         const double *ro = cl.map_shared_rank(rd, here ? orank : 0);
         if (warp == 0) {
-            // sigma2 over the peers (lane = peer, C <= 16), alpha from the owner, the scalars
+            // sigma2 over the peers (lane = peer, C <= 16) of every cluster, alpha from the owner,
+            // the scalars
             double s2 = lane < C ? cl.map_shared_rank(rd, lane)[0] : 0.0;
-            double so = (G > 1 && lane < C && !xbad) ? __ldcg(xslot(xch, (1 - g) * C + lane)) : 0.0;
-            const double al = here ? ro[nc1] : __ldcg(xslot(xch, own) + nc1);   // beside the sigma2 loads
+            double so[G];
+            unsigned long long wa[G], wb[G], aa = 0, ab = 0;
+            unsigned need = 0;
+            double al = 0.0;
 #pragma unroll
-            for (int o = 8; o > 0; o >>= 1) {
-                s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-                so += __shfl_xor_sync(0xffffffffu, so, o);
+            for (int c2 = 0; c2 < G; ++c2) {
+                so[c2] = 0.0;
+                if (c2 != g && lane < C) need |= 1u << c2;
             }
-            if (G > 1) s2 = g == 0 ? s2 + so : so + s2;   // the clusters in order, in every CTA
+            if (here) al = ro[nc1];                   // beside the sigma2 loads
+            else if (lane == 0) need |= 1u << 8;
+            for (long it = 0; need; ++it) {
+#pragma unroll
+                for (int c2 = 0; c2 < G; ++c2)
+                    if (need >> c2 & 1u) xw_load(xslot(xch, c2 * C + lane), wa[c2], wb[c2]);
+                if (need >> 8 & 1u) xw_load(xslot(xch, own) + 2 * nc1, aa, ab);
+#pragma unroll
+                for (int c2 = 0; c2 < G; ++c2)
+                    if ((need >> c2 & 1u) && xw_ok(wa[c2], wb[c2], (unsigned)xch)) {
+                        so[c2] = xw_val(wa[c2], wb[c2]);
+                        need &= ~(1u << c2);
+                    }
+                if ((need >> 8 & 1u) && xw_ok(aa, ab, (unsigned)xch)) {
+                    al = xw_val(aa, ab);
+                    need &= ~(1u << 8);
+                }
+                if (need) {
+                    if (it >= QR_SPIN) { atomicExch(&g_qr_error, 1); break; }
+                    __nanosleep(32);
+                }
+            }
+            // per peer (lane) the clusters in order, then one tree over the peers: the same
+            // doubles in every CTA
+            double x = g == 0 ? s2 : so[0];
+#pragma unroll
+            for (int c2 = 1; c2 < G; ++c2) x += c2 == g ? s2 : so[c2];
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            s2 = x;
             if (lane == 0) {
                 // with nrm = (alpha^2 + sigma2)^(1/2) and a = |alpha|: tau = (beta - alpha) / beta
                 // = 1 + a / nrm and 1 / (alpha - beta) = sign(alpha) / (a + nrm); one reciprocal
@@ -515,11 +581,8 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
                 bc[0] = tau; bc[1] = beta; bc[2] = scal; bc[3] = al;
                 taus[j] = tau;
             }
-        } else if (G > 1) {
-            peer_sums2(rd, 1, nc1, 32, nt - 32, wv, xch, here ? ro + nc1 : nullptr,
-                       here ? nullptr : xslot(xch, own) + nc1, prow);   // the owner's row P_c beside them
         } else {
-            peer_sums(rd, 1, nc1, 32, nt - 32, wv, ro + nc1, prow);   // owner's row P_c beside them
+            peer_sums(rd, 1, nc1, 32, nt - 32, wv, xch, here ? ro + nc1 : nullptr, own, nc1, prow);
         }
         __syncthreads();
         const double tau = bc[0], beta = bc[1], scal = bc[2], al = bc[3];
@@ -581,13 +644,22 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
     cl.sync();   // keep this CTA's shared memory alive until every peer finished reading it
 }
 
+using QRKernel = void (*)(QRJobs, int);
+static QRKernel qr_kernel(bool smem, int G) {
+    static const QRKernel k[2][QR_GMAX] = {{k_qr<false, 1>, k_qr<false, 2>, k_qr<false, 3>},
+                                           {k_qr<true, 1>, k_qr<true, 2>, k_qr<true, 3>}};
+    return k[smem ? 1 : 0][G - 1];
+}
+
 static void qr_reflectors(Ctx &c, const std::vector<QRJob> &jobs) {
     if (jobs.empty()) return;
     static std::atomic<bool> attr_set{false};   // set once; idempotent if two threads race
     if (!attr_set) {
-        TK_CUDA(cudaFuncSetAttribute(k_qr<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-        TK_CUDA(cudaFuncSetAttribute(k_qr<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-        TK_CUDA(cudaFuncSetAttribute(k_qr<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 180 * 1024));
+        for (int G = 1; G <= QR_GMAX; ++G) {
+            TK_CUDA(cudaFuncSetAttribute(qr_kernel(true, G), cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+            TK_CUDA(cudaFuncSetAttribute(qr_kernel(false, G), cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+            TK_CUDA(cudaFuncSetAttribute(qr_kernel(true, G), cudaFuncAttributeMaxDynamicSharedMemorySize, 180 * 1024));
+        }
         attr_set = true;
     }
     for (size_t base = 0; base < jobs.size(); base += TK_MAX_D) {
@@ -602,20 +674,13 @@ static void qr_reflectors(Ctx &c, const std::vector<QRJob> &jobs) {
             smax = std::max(smax, J.j[i].s);
         }
         // cluster of up to 16 CTAs with >= 48 rows each, shrunk until the device can place it;
-        // a single tall unfolding (>= 3000 rows: the FP64 pass dominates its steps) is split over
-        // two clusters that add their per-step sums through global memory
+        // a single tall unfolding (the FP64 pass dominates its steps) is split over G <= 3 clusters
+        // of >= 64 rows per CTA that add their per-step sums through global memory.  Clusters wait
+        // only for their own job's clusters, so a job can stall only if it cannot have all G
+        // resident: with one other such job running concurrently, 2 G - 1 co-resident clusters
+        // guarantee that one of the two has all of its clusters
         int C = std::max(1, std::min(16, (mmax + 47) / 48));
-        const int G = (J.n == 1 && mmax >= 3000) ? 2 : 1;
-        J.G = G;
-        ScopedMark mark(*c.arena);
-        if (G > 1) {
-            static std::atomic<unsigned> launch_id{0};
-            J.tag = (unsigned long long)(launch_id.fetch_add(1) + 1) << 32;
-            for (int i = 0; i < J.n; ++i) {      // a slot and a progress word per CTA (C <= 16)
-                J.xbuf[i] = c.arena->alloc((size_t)2 * G * 16 * QR_XS);
-                J.xflag[i] = static_cast<unsigned long long *>(c.arena->alloc_bytes(sizeof(unsigned long long) * G * 16));
-            }
-        }
+        int G = J.n == 1 ? std::max(1, std::min(QR_GMAX, mmax / (16 * 64))) : 1;
         cudaLaunchConfig_t cfg{};
         cudaLaunchAttribute attr[1];
         int rb = 0;
@@ -635,20 +700,23 @@ static void qr_reflectors(Ctx &c, const std::vector<QRJob> &jobs) {
             attr[0].val.clusterDim.z = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            if (C == 1) break;
+            if (C == 1 && G == 1) break;
             int nclusters = 0;
-            const cudaError_t e = use_smem
-                ? cudaOccupancyMaxActiveClusters(&nclusters, k_qr<true>, &cfg)
-                : cudaOccupancyMaxActiveClusters(&nclusters, k_qr<false>, &cfg);
-            if (e == cudaSuccess && nclusters > 0) break;
-            cudaGetLastError();
-            C = C > 8 ? 8 : C / 2;
+            const cudaError_t e = cudaOccupancyMaxActiveClusters(&nclusters, qr_kernel(use_smem, G), &cfg);
+            if (e != cudaSuccess) cudaGetLastError();
+            if (e == cudaSuccess && nclusters >= 2 * G - 1) break;
+            if (G > 1) --G;
+            else C = C > 8 ? 8 : C / 2;
+        }
+        ScopedMark mark(*c.arena);
+        if (G > 1) {                  // two slots per CTA of xs values, two words each, zeroed
+            J.xs = 2 * smax;
+            const size_t words = (size_t)2 * G * C * J.xs * 2;
+            J.xw[0] = static_cast<unsigned long long *>(c.arena->alloc_bytes(sizeof(unsigned long long) * words));
+            TK_CUDA(cudaMemsetAsync(J.xw[0], 0, sizeof(unsigned long long) * words, c.st));
         }
         c.pre_launch();
-        if (use_smem)
-            TK_CUDA(cudaLaunchKernelEx(&cfg, k_qr<true>, J, rb));
-        else
-            TK_CUDA(cudaLaunchKernelEx(&cfg, k_qr<false>, J, rb));
+        TK_CUDA(cudaLaunchKernelEx(&cfg, qr_kernel(use_smem, G), J, rb));
         double flops = 0.0;   // Householder R: 2 m s^2 - 2 s^3 / 3
         for (int i = 0; i < J.n; ++i) {
             const double m = J.j[i].m, s = std::min(J.j[i].m, J.j[i].s);

@@ -1260,7 +1260,7 @@ static int solve_entry(tk_handle *h, const tk_operator *op, const tk_operator *p
         if (svd_error_flag(true) != 0)
             throw Error{TK_EINTERNAL, "a clustered SVD gave up waiting for its FP32 sweeps"};
         if (qr_error_flag(true) != 0)
-            throw Error{TK_EINTERNAL, "a two-cluster QR gave up waiting for the other cluster"};
+            throw Error{TK_EINTERNAL, "a multi-cluster QR gave up waiting for another cluster's sums"};
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         cudaEventDestroy(e0);
@@ -1461,7 +1461,7 @@ int tk_roundsum(tk_handle *h, int32_t nterms, const tk_tucker *xs, const double 
         if (svd_error_flag(true) != 0)
             throw Error{TK_EINTERNAL, "a clustered SVD gave up waiting for its FP32 sweeps"};
         if (qr_error_flag(true) != 0)
-            throw Error{TK_EINTERNAL, "a two-cluster QR gave up waiting for the other cluster"};
+            throw Error{TK_EINTERNAL, "a multi-cluster QR gave up waiting for another cluster's sums"};
         if (out_rank) for (int k = 0; k < pb.d; ++k) out_rank[k] = hr[k];
         return TK_OK;
     });

@@ -169,7 +169,7 @@ void gemm_oz(Ctx &c, const std::vector<GProb> &probs, const char *tag);
 int oz_error_flag(bool reset);
 // Nonzero when a clustered SVD's replay of the FP32 rotations gave up waiting (reset clears it).
 int svd_error_flag(bool reset);
-// Nonzero when a two-cluster QR gave up waiting for the other cluster's sums (reset clears it).
+// Nonzero when a multi-cluster QR gave up waiting for another cluster's sums (reset clears it).
 int qr_error_flag(bool reset);
 
 // ------------------------------------------------------------------------------------------
