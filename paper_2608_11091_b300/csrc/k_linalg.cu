@@ -72,9 +72,12 @@ struct QRJobs {
     // with G > 1 clusters per job (n = 1): every CTA's exchange slot in global memory, two per CTA
     // (by exchange parity), each xs values of two tagged words (zeroed before the launch)
     int xs;
+    // receive area in dynamic shared memory: [2 parities][C senders][rxs] doubles from rx_off
+    int rx_off, rxs;
     unsigned long long *xw[TK_MAX_D];
 };
 constexpr int QR_GMAX = 3;
+constexpr int QR_DSMEM = 200 * 1024;   // dynamic shared memory of a QR CTA at most (rows + receive area)
 // bounded waits of the cross-cluster exchange (a step takes ~10 us; the limit is ~0.1 s or more),
 // after which g_qr_error is set and the kernel carries on with zeros for the missing sums
 __device__ int g_qr_error;
@@ -97,6 +100,35 @@ __device__ __forceinline__ bool xw_ok(unsigned long long a, unsigned long long b
 __device__ __forceinline__ double xw_val(unsigned long long a, unsigned long long b) {
     return __hiloint2double((int)(unsigned)b, (int)(unsigned)a);
 }
+// Inside a cluster a CTA pushes its exchange buffer into every peer's shared memory with
+// st.async, each store counted (in bytes) on the peer's mbarrier of that exchange's parity; the
+// receiver posts the bytes it expects and waits for the phase, so no cluster barrier or remote
+// load is on a step's path.  An mbarrier's transaction count may run below zero while stores
+// land before the expectation is posted; the phase cannot complete before the receiver's arrive.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned cluster_addr(unsigned a, int rank) {
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void push2(unsigned dst, double a, double b, unsigned mb) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];"
+                 ::"r"(dst), "d"(a), "d"(b), "r"(mb) : "memory");
+}
+__device__ __forceinline__ void push1(unsigned dst, double a, unsigned mb) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f64 [%0], %1, [%2];"
+                 ::"r"(dst), "d"(a), "r"(mb) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(unsigned mb, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
+}
+// waits for the phase of the given parity, suspended at most ~1 us per call
+__device__ __forceinline__ bool mbar_try(unsigned mb, unsigned parity) {
+    unsigned ok;
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(ok) : "r"(mb), "r"(parity), "r"(1000) : "memory");
+    return ok != 0;
+}
 int qr_error_flag(bool reset) {
     int v = 0;
     if (cudaMemcpyFromSymbol(&v, g_qr_error, sizeof(int)) != cudaSuccess) {
@@ -118,8 +150,8 @@ int qr_error_flag(bool reset) {
 // low-rank block are rounding noise and each step shrinks them further.)  For every trailing
 // column c, v^T A[j:, c] = P_c + (D_c - alpha P_c) / (alpha - beta) with D_c = x^T A[j:, c] and
 // P_c = A[j, c], so a step needs, from every CTA over its own rows, the partial sigma2 and
-// D_c, and from the CTA owning row j its row (alpha, P_c): exchanged through distributed
-// shared memory after one cluster barrier.  On this part an FP64 warp instruction holds an
+// D_c, and from the CTA owning row j its row (alpha, P_c): pushed into every peer's shared
+// memory, one exchange per step.  On this part an FP64 warp instruction holds an
 // SMSP's FP64 pipe for ~64 cycles whatever the active lanes, so the scalar work is kept off
 // the FP64 pipe where it can be: pivoting (largest remaining norm first) uses FP32 norms,
 // scaled once by the largest initial column norm and downdated by the new row of R each step
@@ -135,13 +167,15 @@ int qr_error_flag(bool reset) {
 // column's contributors (the threads whose ranges meet it, a contiguous run) are added in thread
 // order, by one thread when there are at most 8, else by a warp.  The kernel leaves R and the
 // reflectors; qr_form_q builds an explicit Q from them.
-// Rows live in shared memory when they fit (SMEM = true), else in global memory.  The
-// exchange buffers alternate by a running exchange count, so a buffer is rewritten only after
-// every peer has passed the next cluster barrier.  A tall single unfolding runs on G <= 3
-// clusters: each CTA also writes its exchange buffer to a global slot as tagged words (xw_put)
-// inside its cluster barrier, and reads the other clusters' slots beside its own cluster's
-// distributed-shared-memory loads; a slot of exchange X is rewritten at X + 2, which no CTA
-// reaches before every CTA has read X.
+// Rows live in shared memory when they fit (SMEM = true), else in global memory.  Each CTA
+// pushes its exchange buffer into its cluster peers' receive areas (st.async counted on an
+// mbarrier per exchange parity) and reads their sums locally: no cluster barrier and no remote
+// load on a step's path (against a barrier and distributed-shared-memory loads: 532 vs 549 us
+// per launch on average).  A tall single unfolding runs on G <= 3 clusters: each CTA also writes
+// its exchange buffer to a global slot as tagged words (xw_put) and reads the other clusters'
+// slots beside its local values.  A receive area or slot of exchange X is rewritten at X + 2,
+// which no CTA reaches before every CTA has read X (it needs every CTA's sums of X + 1, formed
+// after reading X).
 constexpr int QR_THREADS = 256;
 template <bool SMEM, int G>
 __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QRJobs jobs, int rb_cap) {
@@ -153,8 +187,10 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
     const int m = J.m, s = J.s, kmax = min(m, s);
     const int rb = (m + G * C - 1) / (G * C);
     const int r0 = min(m, qg * rb), r1 = min(m, r0 + rb), nr = r1 - r0;
-    extern __shared__ double dyn[];
+    extern __shared__ __align__(16) double dyn[];
     double *Al = dyn;                              // nr x s, ld rb_cap
+    double *const rx = dyn + jobs.rx_off;          // [2][C][rxs]: the peers' exchange buffers
+    __shared__ __align__(8) unsigned long long mbar[2];   // one per exchange parity
     __shared__ double red[2][2 * QR_MAXS];         // [0, nc1): partial sums, [nc1, 2 nc1): owner's row
     __shared__ double wv[QR_MAXS];
     __shared__ double prow[QR_MAXS];               // owner's row j of the step (local copy)
@@ -174,8 +210,20 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
             const int i = r0 + e % nr, c = e / nr;
             A(i, c) = J.A[i + (long long)c * m];
         }
-    __syncthreads();
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    cl.sync();     // every peer's mbarriers initialised before the first push
     int xch = 0;   // exchanges so far (selects the buffer)
+    bool xgive = false;   // this thread gave up a wait (the error flag is set; results are void)
+    // the exchange buffer that CTA `from` (cluster rank) pushed here for exchange parity P
+    auto rxb = [&](int P, int from) { return rx + (size_t)(P * C + from) * jobs.rxs; };
+    // entry e of cluster peer `peer`'s exchange buffer of exchange X (own: rd)
+    auto peer_val = [&](const double *rd, int X, int peer, int e) -> double {
+        return peer == q ? rd[e] : rxb(X & 1, peer)[e];
+    };
     // threads of a pass: a short pass (at most 3200 elements: small unfoldings, the last steps)
     // is bound by its combine and latency rather than the FP64 pipe, so it takes four warps (one
     // per sub-partition) and leaves each column half as many partial sums to combine
@@ -341,17 +389,29 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
     // the clusters' sums are added in cluster order, so every CTA holds the same doubles.
     unsigned long long *const xw = G > 1 ? jobs.xw[blockIdx.y] : nullptr;
     auto xslot = [&](int X, int cta) { return xw + (size_t)((X & 1) * G * C + cta) * jobs.xs * 2; };
-    // the cluster barrier of exchange X (rdb[0 .. n) published inside it when G > 1)
-    auto xsync = [&](const double *rdb, int n, int X) {
-        if (G == 1) {
-            cl.sync();
-            return;
+    // exchange X: push rdb[0 .. n) into every peer's receive area (and, when G > 1, into this
+    // CTA's global slot as tagged words), then wait until the bytes_in expected from the peers
+    // have landed here (bounded)
+    auto xsync = [&](const double *rdb, int n, int X, unsigned bytes_in) {
+        const int P = X & 1;
+        const unsigned mb = smem_u32(&mbar[P]);
+        __syncthreads();                              // rdb complete
+        if (tid == 0) mbar_expect(mb, bytes_in);
+        const int npair = (n + 1) >> 1;
+        const unsigned src = smem_u32(rxb(P, q));     // this CTA's slot, at the same offset in every peer
+        for (int k = tid; k < (C - 1) * npair; k += nt) {
+            const int pi = k / npair, e2 = k - pi * npair, peer = pi + (pi >= q);
+            const unsigned dst = cluster_addr(src + 16u * e2, peer), rmb = cluster_addr(mb, peer);
+            if (2 * e2 + 1 < n) push2(dst, rdb[2 * e2], rdb[2 * e2 + 1], rmb);
+            else push1(dst, rdb[2 * e2], rmb);
         }
-        __syncthreads();
-        asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-        unsigned long long *dst = xslot(X, qg);
-        for (int e = tid; e < n; e += nt) xw_put(dst + 2 * e, rdb[e], (unsigned)X);
-        asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+        if (G > 1) {
+            unsigned long long *dst = xslot(X, qg);
+            for (int e = tid; e < n; e += nt) xw_put(dst + 2 * e, rdb[e], (unsigned)X);
+        }
+        const unsigned par = ((X - 1) >> 1) & 1;       // completions of this mbarrier so far, mod 2
+        for (long it = 0; !xgive && !mbar_try(mb, par); ++it)
+            if (it >= QR_SPIN) { atomicExch(&g_qr_error, 1); xgive = true; }   // no further waits
     };
     // sum over every cluster's peers of rd[lo .. hi) into dst[lo .. hi): TPC threads per entry
     // (4, or 2 when four would take the threads a second round: every load of a thread is then in
@@ -387,9 +447,9 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
                 }
 #pragma unroll
                 for (int u = 0; u < PPT; ++u)
-                    if (gq + TPC * u < C) v[u] = cl.map_shared_rank(rd, gq + TPC * u)[cc];
+                    if (gq + TPC * u < C) v[u] = peer_val(rd, X, gq + TPC * u, cc);
             }
-            for (long it = 0; need; ++it) {
+            for (long it = 0; need && !xgive; ++it) {
 #pragma unroll
                 for (int k = 0; k < NO; ++k)
 #pragma unroll
@@ -410,7 +470,7 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
                     need &= ~(1ull << 40);
                 }
                 if (need) {
-                    if (it >= QR_SPIN) { atomicExch(&g_qr_error, 1); break; }
+                    if (it >= QR_SPIN) { atomicExch(&g_qr_error, 1); xgive = true; break; }
                     __nanosleep(32);
                 }
             }
@@ -450,7 +510,7 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
         for (int c = tid; c < s; c += nt) permv[c] = c;
         double *rd = red[xch & 1];
         flat_sums(r0, s, [&](int i, int c, double &x, double &y) { x = y = A(i, c); }, rd);
-        xsync(rd, s, xch + 1);
+        xsync(rd, s, xch + 1, 8u * (C - 1) * s);
         ++xch;
         peer_sums(rd, 0, s, 0, nt, wv, xch, nullptr, 0, 0, nullptr);
         __syncthreads();
@@ -521,13 +581,14 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
         const bool here = (og == g);
         const int ib = max(r0, j);
         double *rd = red[xch & 1];
-        xsync(rd, owner ? 2 * nc1 : nc1, xch + 1);   // partial sums [0, nc1), the owner's row [nc1, 2 nc1)
+        // partial sums [0, nc1), the owner's row [nc1, 2 nc1)
+        xsync(rd, owner ? 2 * nc1 : nc1, xch + 1, 8u * ((C - 1) * nc1 + (here && !owner ? nc1 : 0)));
         ++xch;
-        const double *ro = cl.map_shared_rank(rd, here ? orank : 0);
+        const double *ro = !here ? nullptr : orank == q ? rd : rxb(xch & 1, orank);   // the owner's buffer
         if (warp == 0) {
             // sigma2 over the peers (lane = peer, C <= 16) of every cluster, alpha from the owner,
             // the scalars
-            double s2 = lane < C ? cl.map_shared_rank(rd, lane)[0] : 0.0;
+            double s2 = lane >= C ? 0.0 : peer_val(rd, xch, lane, 0);
             double so[G];
             unsigned long long wa[G], wb[G], aa = 0, ab = 0;
             unsigned need = 0;
@@ -539,7 +600,7 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
             }
             if (here) al = ro[nc1];                   // beside the sigma2 loads
             else if (lane == 0) need |= 1u << 8;
-            for (long it = 0; need; ++it) {
+            for (long it = 0; need && !xgive; ++it) {
 #pragma unroll
                 for (int c2 = 0; c2 < G; ++c2)
                     if (need >> c2 & 1u) xw_load(xslot(xch, c2 * C + lane), wa[c2], wb[c2]);
@@ -555,7 +616,7 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
                     need &= ~(1u << 8);
                 }
                 if (need) {
-                    if (it >= QR_SPIN) { atomicExch(&g_qr_error, 1); break; }
+                    if (it >= QR_SPIN) { atomicExch(&g_qr_error, 1); xgive = true; break; }
                     __nanosleep(32);
                 }
             }
@@ -658,7 +719,8 @@ static void qr_reflectors(Ctx &c, const std::vector<QRJob> &jobs) {
         for (int G = 1; G <= QR_GMAX; ++G) {
             TK_CUDA(cudaFuncSetAttribute(qr_kernel(true, G), cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
             TK_CUDA(cudaFuncSetAttribute(qr_kernel(false, G), cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-            TK_CUDA(cudaFuncSetAttribute(qr_kernel(true, G), cudaFuncAttributeMaxDynamicSharedMemorySize, 180 * 1024));
+            TK_CUDA(cudaFuncSetAttribute(qr_kernel(true, G), cudaFuncAttributeMaxDynamicSharedMemorySize, QR_DSMEM));
+            TK_CUDA(cudaFuncSetAttribute(qr_kernel(false, G), cudaFuncAttributeMaxDynamicSharedMemorySize, QR_DSMEM));
         }
         attr_set = true;
     }
@@ -686,13 +748,17 @@ static void qr_reflectors(Ctx &c, const std::vector<QRJob> &jobs) {
         int rb = 0;
         bool use_smem = false;
         for (;;) {
+            // dynamic shared memory: the rows (when they fit) and the receive area
             rb = (mmax + G * C - 1) / (G * C);
-            const size_t smem = (size_t)rb * smax * sizeof(double);
-            use_smem = smem <= 180 * 1024;
+            const size_t rows = (size_t)rb * smax * sizeof(double);
+            const size_t rxbytes = (size_t)2 * C * 2 * smax * sizeof(double);
+            use_smem = rows + rxbytes <= QR_DSMEM;
+            J.rxs = 2 * smax;
+            J.rx_off = use_smem ? (rb * smax + 1) & ~1 : 0;   // 16-byte aligned
             cfg = cudaLaunchConfig_t{};
             cfg.gridDim = dim3((unsigned)(G * C), (unsigned)J.n, 1);
             cfg.blockDim = dim3(QR_THREADS, 1, 1);
-            cfg.dynamicSmemBytes = use_smem ? smem : 0;
+            cfg.dynamicSmemBytes = (size_t)J.rx_off * sizeof(double) + rxbytes;
             cfg.stream = c.st;
             attr[0].id = cudaLaunchAttributeClusterDimension;
             attr[0].val.clusterDim.x = C;
