@@ -167,15 +167,15 @@ int qr_error_flag(bool reset) {
 // column's contributors (the threads whose ranges meet it, a contiguous run) are added in thread
 // order, by one thread when there are at most 8, else by a warp.  The kernel leaves R and the
 // reflectors; qr_form_q builds an explicit Q from them.
-// Rows live in shared memory when they fit (SMEM = true), else in global memory.  Each CTA
-// pushes its exchange buffer into its cluster peers' receive areas (st.async counted on an
-// mbarrier per exchange parity) and reads their sums locally: no cluster barrier and no remote
-// load on a step's path (against a barrier and distributed-shared-memory loads: 532 vs 549 us
-// per launch on average).  A tall single unfolding runs on G <= 3 clusters: each CTA also writes
-// its exchange buffer to a global slot as tagged words (xw_put) and reads the other clusters'
-// slots beside its local values.  A receive area or slot of exchange X is rewritten at X + 2,
-// which no CTA reaches before every CTA has read X (it needs every CTA's sums of X + 1, formed
-// after reading X).
+// Rows live in shared memory when they fit (SMEM = true), else in global memory.  On one
+// cluster the peers' exchange buffers are read through distributed shared memory after a cluster
+// barrier; the buffers alternate by a running exchange count, so a buffer is rewritten only after
+// every peer has passed the next barrier.  A tall single unfolding runs on G <= 3 clusters: each
+// CTA pushes its exchange buffer into its cluster peers' receive areas (st.async counted on an
+// mbarrier per exchange parity), writes it to a global slot as tagged words (xw_put) for the
+// other clusters, and reads all of them locally or from the slots.  A receive area or slot of
+// exchange X is rewritten at X + 2, which no CTA reaches before every CTA has read X (it needs
+// every CTA's sums of X + 1, formed after reading X).
 constexpr int QR_THREADS = 256;
 template <bool SMEM, int G>
 __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QRJobs jobs, int rb_cap) {
@@ -189,6 +189,12 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
     const int r0 = min(m, qg * rb), r1 = min(m, r0 + rb), nr = r1 - r0;
     extern __shared__ __align__(16) double dyn[];
     double *Al = dyn;                              // nr x s, ld rb_cap
+    // the exchange inside the cluster: pushes into the peers' receive areas (several clusters:
+    // the barrier's latency would add to the other clusters' round trip), or one cluster barrier
+    // and distributed-shared-memory loads of the peers' buffers (one cluster: ncu 400 vs 420 us
+    // for the range finder's 1024 x 69 QRs, pushes 616 vs 630 us for the 4761 x 69 unfolding on
+    // three clusters)
+    constexpr bool PUSH = G > 1;
     double *const rx = dyn + jobs.rx_off;          // [2][C][rxs]: the peers' exchange buffers
     __shared__ __align__(8) unsigned long long mbar[2];   // one per exchange parity
     __shared__ double red[2][2 * QR_MAXS];         // [0, nc1): partial sums, [nc1, 2 nc1): owner's row
@@ -220,9 +226,11 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
     bool xgive = false;   // this thread gave up a wait (the error flag is set; results are void)
     // the exchange buffer that CTA `from` (cluster rank) pushed here for exchange parity P
     auto rxb = [&](int P, int from) { return rx + (size_t)(P * C + from) * jobs.rxs; };
-    // entry e of cluster peer `peer`'s exchange buffer of exchange X (own: rd)
+    // entry e of cluster peer `peer`'s exchange buffer of exchange X (own: rd): pushed here
+    // (PUSH), else read through distributed shared memory after the cluster barrier
     auto peer_val = [&](const double *rd, int X, int peer, int e) -> double {
-        return peer == q ? rd[e] : rxb(X & 1, peer)[e];
+        if (PUSH) return peer == q ? rd[e] : rxb(X & 1, peer)[e];
+        return cl.map_shared_rank(rd, peer)[e];
     };
     // threads of a pass: a short pass (at most 3200 elements: small unfoldings, the last steps)
     // is bound by its combine and latency rather than the FP64 pipe, so it takes four warps (one
@@ -393,6 +401,10 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
     // CTA's global slot as tagged words), then wait until the bytes_in expected from the peers
     // have landed here (bounded)
     auto xsync = [&](const double *rdb, int n, int X, unsigned bytes_in) {
+        if (!PUSH) {
+            cl.sync();
+            return;
+        }
         const int P = X & 1;
         const unsigned mb = smem_u32(&mbar[P]);
         __syncthreads();                              // rdb complete
@@ -584,7 +596,8 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
         // partial sums [0, nc1), the owner's row [nc1, 2 nc1)
         xsync(rd, owner ? 2 * nc1 : nc1, xch + 1, 8u * ((C - 1) * nc1 + (here && !owner ? nc1 : 0)));
         ++xch;
-        const double *ro = !here ? nullptr : orank == q ? rd : rxb(xch & 1, orank);   // the owner's buffer
+        const double *ro = !here ? nullptr                       // the owner's buffer
+                           : PUSH ? (orank == q ? rd : rxb(xch & 1, orank)) : cl.map_shared_rank(rd, orank);
         if (warp == 0) {
             // sigma2 over the peers (lane = peer, C <= 16) of every cluster, alpha from the owner,
             // the scalars
@@ -751,7 +764,7 @@ static void qr_reflectors(Ctx &c, const std::vector<QRJob> &jobs) {
             // dynamic shared memory: the rows (when they fit) and the receive area
             rb = (mmax + G * C - 1) / (G * C);
             const size_t rows = (size_t)rb * smax * sizeof(double);
-            const size_t rxbytes = (size_t)2 * C * 2 * smax * sizeof(double);
+            const size_t rxbytes = G > 1 ? (size_t)2 * C * 2 * smax * sizeof(double) : 0;
             use_smem = rows + rxbytes <= QR_DSMEM;
             J.rxs = 2 * smax;
             J.rx_off = use_smem ? (rb * smax + 1) & ~1 : 0;   // 16-byte aligned
