@@ -122,10 +122,20 @@ def _rs_case(name):
         n = 64
         wl = W.poisson3d_point(n, None, 8, "p")
         return [(1.0, t) for t in OO.apply_op(wl.op, wl.b)], 32, 5
+    if name in ("tall_g2", "tall_g3"):
+        # exact rank below the cap with a sketch of 50 (69) columns: the ST-HOSVD unfoldings of
+        # the 50^3 (69^3) core have 2500 and 2100 (4761, 4140, 3600) rows, so the QR runs on two
+        # (three) clusters that exchange their sums through global memory
+        n = [90, 80, 100]
+        r, R = (14, 45) if name == "tall_g2" else (20, 64)
+        ts = [(1.0, rand_tucker(n, [r] * 3, 17)), (-0.5, rand_tucker(n, [r] * 3, 18)),
+              (0.25, rand_tucker(n, [r] * 3, 19))]
+        return ts, R, 5
     raise KeyError(name)
 
 
-@pytest.mark.parametrize("case", ["exact_lowrank", "truncating", "small_n", "matvec_terms", "order4", "point_source"])
+@pytest.mark.parametrize("case", ["exact_lowrank", "truncating", "small_n", "matvec_terms", "order4", "point_source",
+                                  "tall_g2", "tall_g3"])
 def test_roundsum(P, case):
     terms, R, p = _rs_case(case)
     n = terms[0][1].n
