@@ -246,6 +246,16 @@ int tk_checkpoint_load(tk_handle *h, const void *buf, int64_t size);
  * through which callers (and the tests) bound the library's device memory. */
 int tk_set_workspace_limit(tk_handle *h, int64_t bytes);
 
+/* tk_selftest_qr_wait: failure detection of the multi-cluster QR without a fault.  Runs one
+ * R-only QR of a 2560 x 50 matrix on two 16-CTA clusters (the path the ST-HOSVD of tall
+ * unfoldings takes) with one exchange made to go missing: mode 1, the CTAs of cluster 0 expect 8
+ * bytes more than their peers push at the first step; mode 2, CTA 0 does not publish its first
+ * step's sums to the other cluster.  The waiting CTAs give up after their bound (~0.3 s), set the
+ * library's QR error flag and run to the end, so the context stays usable.  The paper has no
+ * counterpart.  Returns TK_OK when the lost exchange was detected (the flag is then cleared),
+ * TK_EINTERNAL when it was not, TK_EINVAL for another mode.  Synchronizes `stream`. */
+int tk_selftest_qr_wait(tk_handle *h, int32_t mode, void *stream);
+
 /* tk_expsum_laplacian: the exponential-sum approximation of the inverse Laplacian
  * (Section 3.4): Delta_d^{-1} ~ sum_{h=-q}^{q} c_h E_h x ... x E_h with E_h = exp(-t_h T_n),
  * T_n = tridiag(-1, 2, -1), t_h = exp(h eta), c_h = eta t_h, eta = pi / sqrt(q) (the printed

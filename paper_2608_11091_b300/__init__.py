@@ -11,6 +11,6 @@ from .api import (DeviceOperator, DeviceTucker, Handle, Options, Report, TuckerE
                   tk_sketched_ls, tk_sketched_ls_static, tk_solve, tk_sum_norm, tk_adjoint_grads,
                   tk_solve_precond, tk_expsum_laplacian, tk_checkpoint_save, tk_checkpoint_load,
                   tk_set_workspace_limit, tk_fma_peak, tk_solve_expsum,
-                  tk_solve_concurrent)
+                  tk_solve_concurrent, tk_selftest_qr_wait)
 
 from . import autograd  # noqa: E402,F401

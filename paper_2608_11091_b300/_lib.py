@@ -22,7 +22,7 @@ EXPORTS = ["tk_create", "tk_destroy", "tk_last_error", "tk_solve", "tk_apply", "
            "tk_sketched_ls", "tk_mln_roundsum", "tk_profile", "tk_profile_report",
            "tk_sketched_ls_static", "tk_sum_norm", "tk_adjoint_grads", "tk_solve_precond",
            "tk_expsum_laplacian", "tk_checkpoint_save", "tk_checkpoint_load", "tk_set_workspace_limit",
-           "tk_fma_peak", "tk_solve_expsum", "tk_solve_concurrent"]
+           "tk_fma_peak", "tk_solve_expsum", "tk_solve_concurrent", "tk_selftest_qr_wait"]
 
 
 class tk_tucker(ctypes.Structure):
@@ -117,6 +117,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tk_checkpoint_load": (ctypes.c_int, [vp, vp, i64]),
         "tk_set_workspace_limit": (ctypes.c_int, [vp, i64]),
         "tk_fma_peak": (ctypes.c_int, [vp, i32, dp, vp]),
+        "tk_selftest_qr_wait": (ctypes.c_int, [vp, i32, vp]),
         "tk_solve_expsum": (ctypes.c_int, [vp, P(tk_operator), i32, P(tk_tucker), P(tk_opts), P(tk_tucker),
                                            P(tk_report), vp]),
         "tk_solve_concurrent": (ctypes.c_int, [i32, P(tk_solve_job)]),

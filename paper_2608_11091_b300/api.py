@@ -410,6 +410,14 @@ def tk_fma_peak(fp64: bool = True, device: Optional[int] = None, stream=None) ->
     return out.value
 
 
+def tk_selftest_qr_wait(mode: int, device: Optional[int] = None, stream=None):
+    """Failure detection of the multi-cluster QR (tk_selftest_qr_wait): one exchange made to go
+    missing (mode 1: a byte count inside a cluster, 2: a publication to the other cluster); raises
+    TuckerError unless the kernel gave up waiting, reported it and finished."""
+    h = handle(device)
+    h.check(h.lib.tk_selftest_qr_wait(h.h, int(mode), _stream(stream)), "tk_selftest_qr_wait")
+
+
 def tk_set_workspace_limit(nbytes: int, device: Optional[int] = None):
     """Cap the device workspace of this device's handle (0: no cap); beyond it calls fail with TK_ENOMEM."""
     h = handle(device)

@@ -74,6 +74,10 @@ struct QRJobs {
     int xs;
     // receive area in dynamic shared memory: [2 parities][C senders][rxs] doubles from rx_off
     int rx_off, rxs;
+    // self-test of the bounded waits (0 in every solve): 1 = cluster 0 expects 8 bytes more than
+    // its peers push at the first exchange, 2 = CTA 0 does not publish the first exchange to the
+    // other clusters; the waiting CTAs run out their limit, set g_qr_error and finish
+    int inject;
     unsigned long long *xw[TK_MAX_D];
 };
 constexpr int QR_GMAX = 3;
@@ -408,7 +412,8 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
         const int P = X & 1;
         const unsigned mb = smem_u32(&mbar[P]);
         __syncthreads();                              // rdb complete
-        if (tid == 0) mbar_expect(mb, bytes_in);
+        // (after a wait gave up no more arrivals: a phase that did not complete takes no second one)
+        if (tid == 0 && !xgive) mbar_expect(mb, bytes_in + (jobs.inject == 1 && X == 1 && g == 0 ? 8u : 0u));
         const int npair = (n + 1) >> 1;
         const unsigned src = smem_u32(rxb(P, q));     // this CTA's slot, at the same offset in every peer
         for (int k = tid; k < (C - 1) * npair; k += nt) {
@@ -417,7 +422,7 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
             if (2 * e2 + 1 < n) push2(dst, rdb[2 * e2], rdb[2 * e2 + 1], rmb);
             else push1(dst, rdb[2 * e2], rmb);
         }
-        if (G > 1) {
+        if (G > 1 && !(jobs.inject == 2 && X == 1 && qg == 0)) {
             unsigned long long *dst = xslot(X, qg);
             for (int e = tid; e < n; e += nt) xw_put(dst + 2 * e, rdb[e], (unsigned)X);
         }
@@ -725,7 +730,7 @@ static QRKernel qr_kernel(bool smem, int G) {
     return k[smem ? 1 : 0][G - 1];
 }
 
-static void qr_reflectors(Ctx &c, const std::vector<QRJob> &jobs) {
+static void qr_reflectors(Ctx &c, const std::vector<QRJob> &jobs, int inject = 0) {
     if (jobs.empty()) return;
     static std::atomic<bool> attr_set{false};   // set once; idempotent if two threads race
     if (!attr_set) {
@@ -739,6 +744,7 @@ static void qr_reflectors(Ctx &c, const std::vector<QRJob> &jobs) {
     }
     for (size_t base = 0; base < jobs.size(); base += TK_MAX_D) {
         QRJobs J{};
+        J.inject = inject;
         J.n = (int)std::min<size_t>(TK_MAX_D, jobs.size() - base);
         int mmax = 0, smax = 0;
         for (int i = 0; i < J.n; ++i) {
@@ -926,6 +932,22 @@ static void qr_form_q(Ctx &c, const std::vector<QRJob> &jobs) {
             g.run();
         }
     }
+}
+
+// Self-test of the multi-cluster QR's bounded waits: one R-only QR of a 2560 x 50 matrix (zeros:
+// the values do not matter) on two clusters with an exchange made to go missing (inject 1 or 2,
+// see QRJobs::inject).  Returns 1 when the kernel gave up waiting, set the error flag and
+// finished (the flag is cleared), 0 otherwise.
+int qr_wait_selftest(Ctx &c, int inject) {
+    TK_REQUIRE(inject == 1 || inject == 2, "QR self-test: mode 1 or 2");
+    const int m = 2560, s = 50;
+    double *A = c.arena->alloc((size_t)m * s);
+    double *tau = c.arena->alloc(s);
+    TK_CUDA(cudaMemsetAsync(A, 0, sizeof(double) * m * s, c.st));
+    qr_error_flag(true);
+    qr_reflectors(c, {QRJob{A, tau, nullptr, m, s, nullptr}}, inject);
+    TK_CUDA(cudaStreamSynchronize(c.st));
+    return qr_error_flag(true) != 0 ? 1 : 0;
 }
 
 void qr_householder(Ctx &c, const std::vector<QRJob> &jobs) {

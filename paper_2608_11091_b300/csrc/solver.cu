@@ -1371,6 +1371,17 @@ int tk_fma_peak(tk_handle *h, int32_t fp64, double *tflops_host, void *stream) {
     });
 }
 
+int tk_selftest_qr_wait(tk_handle *h, int32_t mode, void *stream) {
+    return guarded(h, [&]() -> int {
+        TK_REQUIRE(mode == 1 || mode == 2, "selftest_qr_wait: mode 1 or 2");
+        Ctx c = make_ctx(h, stream);
+        ScopedMark mark(h->arena);
+        if (!qr_wait_selftest(c, mode))
+            throw Error{TK_EINTERNAL, "selftest_qr_wait: the lost exchange was not detected"};
+        return TK_OK;
+    });
+}
+
 int tk_set_workspace_limit(tk_handle *h, int64_t bytes) {
     return guarded(h, [&]() -> int {
         TK_REQUIRE(bytes >= 0, "workspace limit must be >= 0");

@@ -171,6 +171,9 @@ int oz_error_flag(bool reset);
 int svd_error_flag(bool reset);
 // Nonzero when a multi-cluster QR gave up waiting for another cluster's sums (reset clears it).
 int qr_error_flag(bool reset);
+// Self-test of the multi-cluster QR's bounded waits (inject 1 or 2): 1 when the lost exchange was
+// detected (kernel finished, flag set and cleared), 0 otherwise.
+int qr_wait_selftest(Ctx &c, int inject);
 
 // ------------------------------------------------------------------------------------------
 // Small dense linear algebra (FP64)

@@ -2,6 +2,8 @@
 
 Sizes span several 32 x 32 GEMM tiles with ragged tails (n = 37, 70, 131), d = 3 and 4,
 n smaller than the sketch size, rank-one and rank-deficient inputs."""
+import time
+
 import numpy as np
 import pytest
 
@@ -208,6 +210,19 @@ def test_true_residual(P, transpose):
     b = rand_tucker([n] * 3, [3, 3, 3], 20)
     v = P.tk_residual(P.DeviceOperator(wl.op), to_dev(x), to_dev(b), transpose)
     assert np.isclose(v, ORS.true_residual(wl.op, x, b, transpose), rtol=1e-11)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_qr_bounded_wait_reports_and_context_stays_usable(P, mode):
+    """Failure detection without a fault: a two-cluster QR with one exchange made to go missing
+    (mode 1 inside a cluster, mode 2 between the clusters) gives up after its bounded wait, sets
+    the error flag and finishes; the same context then runs a multi-cluster RoundSum to parity."""
+    t0 = time.time()
+    P.tk_selftest_qr_wait(mode)
+    assert time.time() - t0 < 30.0
+    with pytest.raises(P.TuckerError):
+        P.tk_selftest_qr_wait(3)
+    test_roundsum(P, "tall_g2")
 
 
 def test_invalid_arguments_fail_loudly(P):
