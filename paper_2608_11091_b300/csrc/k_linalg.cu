@@ -154,13 +154,12 @@ int qr_error_flag(bool reset) {
 // low-rank block are rounding noise and each step shrinks them further.)  For every trailing
 // column c, v^T A[j:, c] = P_c + (D_c - alpha P_c) / (alpha - beta) with D_c = x^T A[j:, c] and
 // P_c = A[j, c], so a step needs, from every CTA over its own rows, the partial sigma2 and
-// D_c, and from the CTA owning row j its row (alpha, P_c): pushed into every peer's shared
-// memory, one exchange per step.  On this part an FP64 warp instruction holds an
+// D_c, and from the CTA owning row j its row (alpha, P_c): one exchange per step (below).  On this part an FP64 warp instruction holds an
 // SMSP's FP64 pipe for ~64 cycles whatever the active lanes, so the scalar work is kept off
 // the FP64 pipe where it can be: pivoting (largest remaining norm first) uses FP32 norms,
 // scaled once by the largest initial column norm and downdated by the new row of R each step
 // (a pivot only has to grade R, it does not enter the result); the argmax is one warp of
-// FP32 shuffles; peer sums use four threads per column.
+// FP32 shuffles; peer sums use two or four threads per column.
 // The two FP64 passes of a step (partial sums D_c, trailing update) cost one FP64 FMA per element
 // and run at the FP64 pipe's rate only if every warp carries the same number of them with all
 // lanes active: the CTA's (column, row) elements are split into equal contiguous ranges, one per
