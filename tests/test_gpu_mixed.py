@@ -47,7 +47,8 @@ def P():
     return P
 
 
-@pytest.mark.parametrize("case", ["exact_lowrank", "truncating", "small_n", "matvec_terms", "order4"])
+@pytest.mark.parametrize("case", ["exact_lowrank", "truncating", "small_n", "matvec_terms", "order4",
+                                  "tall_g2", "tall_g3"])
 def test_mixed_roundsum(P, case):
     terms, R, p = _rs_case(case)
     n = terms[0][1].n
