@@ -243,8 +243,9 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
     // with out[] visible to the CTA
     auto combine = [&](int T, int nrows, int E, int nc, double *out) {
         // the partials of column cc are pp[2 (tlo + cc) .. 2 (thi + cc) + 1]: up to 8 contributors
-        // one thread adds them in order; more (the last steps, few columns) go to a warp each,
-        // 32 lanes strided over them and a shuffle tree
+        // one thread adds them in order; more (the last steps, few columns) go to a group of L
+        // lanes each, strided over them and a shuffle tree, with L chosen so that every warp takes
+        // its columns in one round (one column per warp at a time cost up to ~3k cycles a step)
         const int ncmax = T > 0 ? (nrows + E - 2) / E + 1 : 0;
         if (ncmax <= 8) {
             for (int cc = tid; cc < nc; cc += nt) {
@@ -256,13 +257,19 @@ __global__ void __launch_bounds__(QR_THREADS, 1) k_qr(const __grid_constant__ QR
                 out[cc] = acc;
             }
         } else {
-            for (int cc = warp; cc < nc; cc += nt >> 5) {
-                const int tlo = (cc * nrows) / E, thi = ((cc + 1) * nrows - 1) / E;
-                const int b0 = 2 * (tlo + cc), nv = 2 * (thi - tlo + 1);
+            const int nw = nt >> 5, cpw = (nc + nw - 1) / nw;   // columns per warp
+            const int L = cpw <= 1 ? 32 : cpw <= 2 ? 16 : cpw <= 4 ? 8 : cpw <= 8 ? 4 : 2;
+            const int gpw = 32 / L, grp = lane / L, gl = lane & (L - 1);
+            for (int base = warp * gpw; base < nc; base += nw * gpw) {   // warp-uniform trip count
+                const int cc = base + grp;
                 double acc = 0.0;
-                for (int k = lane; k < nv; k += 32) acc += pp[b0 + k];
-                acc = warp_sum(acc);
-                if (lane == 0) out[cc] = acc;
+                if (cc < nc) {
+                    const int tlo = (cc * nrows) / E, thi = ((cc + 1) * nrows - 1) / E;
+                    const int b0 = 2 * (tlo + cc), nv = 2 * (thi - tlo + 1);
+                    for (int k = gl; k < nv; k += L) acc += pp[b0 + k];
+                }
+                for (int o = L >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (cc < nc && gl == 0) out[cc] = acc;
             }
         }
         __syncthreads();
