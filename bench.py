@@ -471,8 +471,8 @@ def roofline_from_profile(prof, peaks):
     n, ms, fl, by = prof[name]
     # DRAM bytes per launch of the dominant kernel from the ncu capture of this workload
     # (profiles/qr_svd_gemm_tc_poisson3d_n1024.md: the two ST-HOSVD QRs captured on three
-    # clusters, 2.79 and 2.62 MB)
-    traffic = {"qr": 2.70e6}.get(name)
+    # clusters, 2.79 and 2.63 MB)
+    traffic = {"qr": 2.71e6}.get(name)
     out = {"kernel": name, "launches": n, "avg_us": e["avg_us"], "share": e["share"], "traffic": traffic,
            "bound": e.get("bound"), "achieved": e.get("achieved"), "unit": e.get("unit"), "frac": e.get("frac")}
     if e.get("bound") == "alu":
