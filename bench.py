@@ -285,7 +285,7 @@ def kernel_table(prof, peaks):
             a = fl / (ms * 1e-3) / 1e12
             e.update({"bound": "tensor", "achieved": round(a, 4), "unit": "TFLOP/s",
                       "frac": round(a / peaks["bf16_tflops"], 5)})
-        elif fl > 0 and (name.startswith("gemm") or name in ("qr", "svd", "tikhonov", "hadamard")):
+        elif fl > 0 and (name.startswith("gemm") or name in ("qr", "svd", "tikhonov", "hadamard", "qr_wy_solve", "ls")):
             a = fl / (ms * 1e-3) / 1e12
             e.update({"bound": "alu", "achieved": round(a, 4), "unit": "TFLOP/s",
                       "frac": round(a / peaks["fp64_tflops"], 5)})

@@ -679,14 +679,20 @@ void gemm_oz(Ctx &c, const std::vector<GProb> &probs, const char *tag) {
         OzSides S{};
         S.n = (int)std::min<size_t>(OZ_MAXSIDES, uniq.size() - base);
         int maxRb = 0, maxCh = 0;
+        double bytes = 0.0;   // the operand read once, the digit planes and exponents written once
         for (int i = 0; i < S.n; ++i) {
             S.s[i] = uniq[base + i];
             maxRb = std::max(maxRb, S.s[i].Rpad / 32);
-            maxCh = std::max(maxCh, (S.s[i].Kpad + OZ_CHUNK - 1) / OZ_CHUNK);
+            const int nch = (S.s[i].Kpad + OZ_CHUNK - 1) / OZ_CHUNK;
+            maxCh = std::max(maxCh, nch);
+            long long kt = 0;
+            for (int g = 0; g < S.s[i].nseg; ++g) kt += S.s[i].seg[g].K;
+            bytes += 8.0 * S.s[i].rows * (double)kt + 2.0 * OZ_S * S.s[i].Rpad * (double)S.s[i].Kpad +
+                     2.0 * nch * S.s[i].Rpad;
         }
         c.pre_launch();
         k_oz_split<<<dim3((unsigned)maxRb, (unsigned)maxCh, (unsigned)S.n), 256, OZ_SPLIT_SMEM, c.st>>>(S);
-        c.check_launch("oz_split", 0.0, 0.0);
+        c.check_launch("oz_split", 0.0, bytes);
     }
     // 3. products, OZ_MAXPROB per launch
     for (size_t base = 0; base < np; base += OZ_MAXPROB) {

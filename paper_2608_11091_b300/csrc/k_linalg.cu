@@ -2452,7 +2452,8 @@ void ls_update(Ctx &c, const double *M, const double *b, int s, int c0, int k, c
         k_ls_wy<<<1, 512, 0, c.st>>>(M, b, s, c0, k, st, init_qtb);
     else
         k_ls<<<1, 512, 0, c.st>>>(M, b, s, c0, k, st, init_qtb);
-    c.check_launch("ls");
+    // new columns c0 .. k-1: each takes the earlier reflectors (4 s j flops) and its own
+    c.check_launch("ls", 2.0 * s * ((double)k * k - (double)c0 * c0) + 4.0 * s * (k - c0));
 }
 
 }  // namespace tk

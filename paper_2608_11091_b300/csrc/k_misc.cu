@@ -176,18 +176,19 @@ void gaussian(Ctx &c, uint64_t seed, const uint64_t *sids, const long long *coun
     for (int base = 0; base < nmat; base += TK_MAX_D * 2) {
         GaussJobs J{};
         J.n = std::min(TK_MAX_D * 2, nmat - base);
-        long long mx = 1;
+        long long mx = 1, total = 0;
         for (int i = 0; i < J.n; ++i) {
             J.sid[i] = sids[base + i];
             J.count[i] = counts[base + i];
             J.out[i] = outs[base + i];
             mx = std::max(mx, (counts[base + i] + 1) / 2);
+            total += counts[base + i];
         }
         const int threads = 256;
         const long long blocks = std::min<long long>((mx + threads - 1) / threads, 4096);
         c.pre_launch();
         k_gaussian<<<dim3((unsigned)blocks, J.n), threads, 0, c.st>>>(seed, J, bf16);
-        c.check_launch("gaussian");
+        c.check_launch("gaussian", 0.0, 8.0 * (double)total);   // every value written once
     }
 }
 
@@ -422,7 +423,7 @@ void scale_by(Ctx &c, double *y, const double *x, long long n, const double *s, 
     const long long blocks = std::min<long long>((n + 255) / 256, 4096);
     c.pre_launch();
     k_scale_by<<<(unsigned)blocks, 256, 0, c.st>>>(y, x, n, s, inv);
-    c.check_launch("scale");
+    c.check_launch("scale", 0.0, 16.0 * (double)n);
 }
 
 void copy(Ctx &c, double *dst, const double *src, long long n) {
@@ -551,7 +552,7 @@ void sine_basis(Ctx &c, double *V, int n, double t) {
     const long long blocks = std::min<long long>((total + 255) / 256, 4096);
     c.pre_launch();
     k_sine_basis<<<(unsigned)blocks, 256, 0, c.st>>>(V, n, t);
-    c.check_launch("sine_basis");
+    c.check_launch("sine_basis", 0.0, 8.0 * (double)total);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -636,7 +637,7 @@ void expsum_weights(Ctx &c, double *w, int n, int q, double eta) {
     const long long blocks = std::min<long long>((total + 255) / 256, 1024);
     c.pre_launch();
     k_expsum_weights<<<(unsigned)blocks, 256, 0, c.st>>>(w, n, q, eta);
-    c.check_launch("expsum_weights");
+    c.check_launch("expsum_weights", 0.0, 8.0 * (double)total);
 }
 
 __global__ void k_set_identity(double *p, int n) {
@@ -652,7 +653,7 @@ void set_identity(Ctx &c, double *p, int n) {
     const long long blocks = std::min<long long>((total + 255) / 256, 1024);
     c.pre_launch();
     k_set_identity<<<(unsigned)blocks, 256, 0, c.st>>>(p, n);
-    c.check_launch("identity");
+    c.check_launch("identity", 0.0, 8.0 * (double)total);
 }
 
 __global__ void k_sqrt_scalar(const double *in, double *out) { *out = sqrt(fmax(*in, 0.0)); }
