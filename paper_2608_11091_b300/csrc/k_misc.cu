@@ -207,7 +207,7 @@ void philox_raw(Ctx &c, uint64_t seed, uint64_t sid, uint64_t first, long long n
     const long long blocks = std::min<long long>((nb + 255) / 256, 4096);
     c.pre_launch();
     k_philox_raw<<<(unsigned)std::max<long long>(blocks, 1), 256, 0, c.st>>>(seed, sid, first, nb, out);
-    c.check_launch("philox");
+    c.check_launch("philox", 0.0, 16.0 * (double)nb);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -408,7 +408,7 @@ void fill(Ctx &c, double *p, long long n, double v) {
     const long long blocks = std::min<long long>((n + 255) / 256, 4096);
     c.pre_launch();
     k_fill<<<(unsigned)blocks, 256, 0, c.st>>>(p, n, v);
-    c.check_launch("fill");
+    c.check_launch("fill", 0.0, 8.0 * (double)n);
 }
 
 __global__ void k_scale_by(double *y, const double *x, long long n, const double *s, int inv) {
@@ -448,7 +448,7 @@ void copy_pad(Ctx &c, double *dst, int ld_dst, int rows_dst, int cols_dst, const
     c.pre_launch();
     k_copy_pad<<<(unsigned)blocks, 256, 0, c.st>>>(dst, ld_dst, rows_dst, cols_dst, src, ld_src,
                                                    rows_src, cols_src);
-    c.check_launch("copy_pad");
+    c.check_launch("copy_pad", 0.0, 8.0 * ((double)total + (double)std::min(rows_src, rows_dst) * std::min(cols_src, cols_dst)));
 }
 
 struct CoreDims { int d; int rd[TK_MAX_D]; int rs[TK_MAX_D]; };
@@ -477,7 +477,7 @@ void copy_core_pad(Ctx &c, double *dst, const int *rdst, const double *src, cons
     const long long blocks = std::min<long long>((total + 255) / 256, 4096);
     c.pre_launch();
     k_copy_core_pad<<<(unsigned)blocks, 256, 0, c.st>>>(dst, src, D, total);
-    c.check_launch("copy_core_pad");
+    c.check_launch("copy_core_pad", 0.0, 16.0 * (double)total);
 }
 
 __global__ void k_superdiag(const double *G, int m, int d, double *out, double sh, const double *sd) {
@@ -492,7 +492,7 @@ void superdiag(Ctx &c, const double *G, int m, int d, double *out, double scale_
                const double *scale_dev) {
     c.pre_launch();
     k_superdiag<<<(m + 255) / 256, 256, 0, c.st>>>(G, m, d, out, scale_host, scale_dev);
-    c.check_launch("superdiag");
+    c.check_launch("superdiag", 0.0, 16.0 * (double)m);
 }
 
 __global__ void k_transpose(double *dst, int ldd, const double *src, int lds, int rows, int cols) {
@@ -510,7 +510,7 @@ void transpose_block(Ctx &c, double *dst, int ldd, const double *src, int lds, i
     const long long blocks = std::min<long long>((total + 255) / 256, 4096);
     c.pre_launch();
     k_transpose<<<(unsigned)blocks, 256, 0, c.st>>>(dst, ldd, src, lds, rows, cols);
-    c.check_launch("transpose");
+    c.check_launch("transpose", 0.0, 16.0 * (double)total);
 }
 
 __global__ void k_triu(double *dst, int ldd, const double *src, int lds, int rows, int cols) {
@@ -528,7 +528,7 @@ void triu_copy(Ctx &c, double *dst, int ldd, const double *src, int lds, int row
     const long long blocks = std::min<long long>((total + 255) / 256, 4096);
     c.pre_launch();
     k_triu<<<(unsigned)blocks, 256, 0, c.st>>>(dst, ldd, src, lds, rows, cols);
-    c.check_launch("triu");
+    c.check_launch("triu", 0.0, 16.0 * (double)total);
 }
 
 // Sine eigenvectors of tridiag(-1, 2, -1) (the DST-I basis, Section 3.4), column-major:
@@ -611,14 +611,16 @@ void weighted_copy(Ctx &c, const std::vector<WeightedCopyJob> &jobs) {
         WeightedCopyJobs J{};
         J.n = (int)std::min<size_t>(WC_MAXJ, jobs.size() - base);
         long long mx = 1;
+        double bytes = 0.0;
         for (int i = 0; i < J.n; ++i) {
             J.j[i] = jobs[base + i];
             mx = std::max(mx, (long long)J.j[i].n * J.j[i].r);
+            bytes += 16.0 * J.j[i].n * (double)J.j[i].r;   // each factor entry read and written once
         }
         const long long blocks = std::min<long long>((mx + 255) / 256, 256);
         c.pre_launch();
         k_weighted_copy<<<dim3((unsigned)blocks, J.n), 256, 0, c.st>>>(J);
-        c.check_launch("weighted_copy");
+        c.check_launch("weighted_copy", 0.0, bytes);
     }
 }
 
