@@ -663,7 +663,7 @@ __global__ void k_sqrt_scalar(const double *in, double *out) { *out = sqrt(fmax(
 void sqrt_scalar(Ctx &c, const double *in, double *out) {
     c.pre_launch();
     k_sqrt_scalar<<<1, 1, 0, c.st>>>(in, out);
-    c.check_launch("sqrt");
+    c.check_launch("sqrt", 0.0, 16.0);
 }
 
 }  // namespace tk
